@@ -1,0 +1,307 @@
+"""ctypes front end of the FP64 CPU oracle (``mg_oracle.c``).
+
+Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it; the solver package never imports it.
+
+The oracle follows J. T. Wallis, "Methods toward better Multigrid Solver
+Convergence" (2008): the preconditioned-Richardson smoothers of section
+"Smoothers" / "The choice of C" and the recursive algorithm MG(l, u, g) of
+section "The Multigrid Technique", run as the F-cycle named in the abstract.
+See ``mg_oracle.c`` for the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mg_oracle.c")
+_HDR = os.path.join(_HERE, "mg_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_LOCK = threading.Lock()
+
+CONST, SEPARABLE, CELL = 0, 1, 2
+JACOBI, RBGS, LINE_X, LINE_Y, ZEBRA_X, ZEBRA_Y = range(6)
+RED_FIRST, BLACK_FIRST = 0, 1
+CYCLE_F, CYCLE_V = 0, 1
+COARSE_EXACT, COARSE_SMOOTH = 0, 1
+OK, EINVAL, ENOMEM, ENOCONV, EDIVERGED = 0, 1, 2, 4, 5
+
+SMOOTHERS = {"jacobi": JACOBI, "rbgs": RBGS, "line_x": LINE_X, "line_y": LINE_Y,
+             "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FP contraction)."""
+    with _LOCK:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+            return _SO
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+        return _SO
+
+
+class _Config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("periodic_y", C.c_int), ("kind", C.c_int),
+                ("h", C.c_double * 3), ("c", C.c_double * 3),
+                ("sx", C.c_void_p), ("sy", C.c_void_p), ("sz", C.c_void_p), ("k", C.c_void_p),
+                ("levels", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
+                ("nu1", C.c_int), ("nu2", C.c_int), ("omega_corr", C.c_double),
+                ("coarse_mode", C.c_int), ("coarse_sweeps", C.c_int), ("dense_max", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        L.or_create.argtypes = [C.POINTER(_Config), C.POINTER(P)]
+        L.or_create.restype = C.c_int
+        L.or_destroy.argtypes = [P]
+        L.or_levels.argtypes = [P]
+        L.or_levels.restype = C.c_int
+        L.or_level_dims.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
+        L.or_level_nodes.argtypes = [P, C.c_int]
+        L.or_level_nodes.restype = C.c_size_t
+        L.or_level_unknowns.argtypes = [P, C.c_int]
+        L.or_level_unknowns.restype = C.c_int
+        L.or_level_coeffs.argtypes = [P, C.c_int, P]
+        L.or_apply.argtypes = [P, C.c_int, P, P]
+        L.or_diag.argtypes = [P, C.c_int, P]
+        L.or_defect.argtypes = [P, C.c_int, P, P, P]
+        L.or_norm2.argtypes = [P, C.c_int, P]
+        L.or_norm2.restype = C.c_double
+        L.or_smooth.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
+        L.or_restrict.argtypes = [P, C.c_int, P, P]
+        L.or_prolong_add.argtypes = [P, C.c_int, P, P, C.c_double]
+        L.or_coarse_solve.argtypes = [P, P, P]
+        L.or_cycle.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
+        L.or_solve.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, C.c_int,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.or_solve.restype = C.c_int
+        L.or_grad_k.argtypes = [P, P, P, P]
+        L.or_thomas.argtypes = [C.c_int, P, P, P, P, P]
+        L.or_counts.argtypes = [P, P, C.POINTER(C.c_long)]
+        L.or_reset_counts.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Problem:
+    """Operator description on the finest grid (see ``mg_oracle.h``)."""
+
+    def __init__(self, dim=2, n=(129, 129, 1), periodic_y=False, kind=CONST, h=(1.0, 1.0, 1.0),
+                 c=(1.0, 1.0, 1.0), sx=None, sy=None, sz=None, k=None):
+        self.dim = dim
+        self.n = tuple(int(v) for v in n) + (1,) * (3 - len(n))
+        if dim == 2:
+            self.n = (self.n[0], self.n[1], 1)
+        self.periodic_y = bool(periodic_y)
+        self.kind = kind
+        self.h = tuple(float(v) for v in h)
+        self.c = tuple(float(v) for v in c)
+        self.sx = None if sx is None else np.ascontiguousarray(sx, dtype=np.float64)
+        self.sy = None if sy is None else np.ascontiguousarray(sy, dtype=np.float64)
+        self.sz = None if sz is None else np.ascontiguousarray(sz, dtype=np.float64)
+        self.k = None if k is None else np.ascontiguousarray(k, dtype=np.float64)
+
+    @property
+    def shape(self):
+        """numpy shape of a node array: (n1, n0) in 2D, (n2, n1, n0) in 3D."""
+        return (self.n[1], self.n[0]) if self.dim == 2 else (self.n[2], self.n[1], self.n[0])
+
+
+class Oracle:
+    """One multigrid hierarchy of the oracle."""
+
+    def __init__(self, prob: Problem, levels=2, smoother="rbgs", omega=1.0, nu1=2, nu2=2,
+                 omega_corr=1.0, coarse_mode=COARSE_EXACT, coarse_sweeps=2, dense_max=1024):
+        self.prob = prob
+        cfg = _Config()
+        cfg.dim = prob.dim
+        cfg.n = (C.c_int * 3)(*prob.n)
+        cfg.periodic_y = int(prob.periodic_y)
+        cfg.kind = prob.kind
+        cfg.h = (C.c_double * 3)(*prob.h)
+        cfg.c = (C.c_double * 3)(*prob.c)
+        self._keep = []
+        for name in ("sx", "sy", "sz", "k"):
+            arr = getattr(prob, name)
+            if arr is not None:
+                self._keep.append(arr)
+                setattr(cfg, name, arr.ctypes.data)
+        cfg.levels = levels
+        cfg.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else int(smoother)
+        cfg.omega = omega
+        cfg.nu1, cfg.nu2 = nu1, nu2
+        cfg.omega_corr = omega_corr
+        cfg.coarse_mode = coarse_mode
+        cfg.coarse_sweeps = coarse_sweeps
+        cfg.dense_max = dense_max
+        h = C.c_void_p()
+        st = lib().or_create(C.byref(cfg), C.byref(h))
+        if st != OK:
+            raise ValueError(f"oracle setup failed with status {st}")
+        self._h = h
+        self.levels = levels
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.or_destroy(h)
+            self._h = None
+
+    # -- level geometry ----------------------------------------------------------
+    def dims(self, l):
+        n = (C.c_int * 3)()
+        lib().or_level_dims(self._h, l, n)
+        return tuple(n)
+
+    def shape(self, l=None):
+        n = self.dims(self.levels if l is None else l)
+        return (n[1], n[0]) if self.prob.dim == 2 else (n[2], n[1], n[0])
+
+    def zeros(self, l=None):
+        return np.zeros(self.shape(l), dtype=np.float64)
+
+    def unknown_mask(self, l=None):
+        n = self.dims(self.levels if l is None else l)
+        m = np.zeros(self.shape(l), dtype=bool)
+        if self.prob.dim == 2:
+            ys = slice(None) if self.prob.periodic_y else slice(1, n[1] - 1)
+            m[ys, 1:n[0] - 1] = True
+        else:
+            ys = slice(None) if self.prob.periodic_y else slice(1, n[1] - 1)
+            m[1:n[2] - 1, ys, 1:n[0] - 1] = True
+        return m
+
+    def unknowns(self, l=None):
+        return lib().or_level_unknowns(self._h, self.levels if l is None else l)
+
+    # -- steps of the method -----------------------------------------------------
+    def apply(self, u, l=None):
+        l = self.levels if l is None else l
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = self.zeros(l)
+        lib().or_apply(self._h, l, _ptr(u), _ptr(out))
+        return out
+
+    def diag(self, l=None):
+        l = self.levels if l is None else l
+        out = self.zeros(l)
+        lib().or_diag(self._h, l, _ptr(out))
+        return out
+
+    def defect(self, u, g, l=None):
+        l = self.levels if l is None else l
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        out = self.zeros(l)
+        lib().or_defect(self._h, l, _ptr(u), _ptr(g), _ptr(out))
+        return out
+
+    def norm(self, v, l=None):
+        l = self.levels if l is None else l
+        return lib().or_norm2(self._h, l, _ptr(np.ascontiguousarray(v, dtype=np.float64)))
+
+    def smooth(self, u, g, sweeps=1, order=RED_FIRST, l=None):
+        l = self.levels if l is None else l
+        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        lib().or_smooth(self._h, l, _ptr(u), _ptr(g), sweeps, order)
+        return u
+
+    def restrict(self, rf, lf=None):
+        lf = self.levels if lf is None else lf
+        rf = np.ascontiguousarray(rf, dtype=np.float64)
+        out = self.zeros(lf - 1)
+        lib().or_restrict(self._h, lf, _ptr(rf), _ptr(out))
+        return out
+
+    def prolong_add(self, ec, uf, w=1.0, lf=None):
+        lf = self.levels if lf is None else lf
+        ec = np.ascontiguousarray(ec, dtype=np.float64)
+        uf = np.array(uf, dtype=np.float64, copy=True, order="C")
+        lib().or_prolong_add(self._h, lf, _ptr(ec), _ptr(uf), w)
+        return uf
+
+    def coarse_solve(self, g):
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        out = self.zeros(1)
+        lib().or_coarse_solve(self._h, _ptr(g), _ptr(out))
+        return out
+
+    def cycle(self, u, g, l=None, cycle=CYCLE_F, transposed=False):
+        l = self.levels if l is None else l
+        u = np.array(u, dtype=np.float64, copy=True, order="C")
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        lib().or_cycle(self._h, l, _ptr(u), _ptr(g), cycle, int(transposed))
+        return u
+
+    def solve(self, b, x0=None, tol=1e-10, maxit=100, transposed=False):
+        """F-cycles until ||b - A x|| / ||b|| <= tol.  Returns (x, status, cycles, relres, history)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = self.zeros() if x0 is None else np.array(x0, dtype=np.float64, copy=True, order="C")
+        hist = np.zeros(maxit + 1, dtype=np.float64)
+        cyc = C.c_int()
+        rr = C.c_double()
+        st = lib().or_solve(self._h, _ptr(b), _ptr(x), tol, maxit, int(transposed), _ptr(hist), maxit + 1,
+                            C.byref(cyc), C.byref(rr))
+        return x, st, cyc.value, rr.value, hist[:cyc.value + 1].copy()
+
+    def grad_k(self, u, lam):
+        p = self.prob
+        cx = p.n[0] - 1
+        cy = p.n[1] if p.periodic_y else p.n[1] - 1
+        shape = (cy, cx) if p.dim == 2 else (p.n[2] - 1, cy, cx)
+        out = np.zeros(shape, dtype=np.float64)
+        lib().or_grad_k(self._h, _ptr(np.ascontiguousarray(u, dtype=np.float64)),
+                        _ptr(np.ascontiguousarray(lam, dtype=np.float64)), _ptr(out))
+        return out
+
+    def level_coeffs(self, l):
+        n = self.dims(l)
+        p = self.prob
+        if p.kind == CONST:
+            out = np.zeros(3)
+        elif p.kind == SEPARABLE:
+            out = np.zeros(3 * n[0])
+        else:
+            cy = n[1] if p.periodic_y else n[1] - 1
+            out = np.zeros((n[0] - 1) * cy * (n[2] - 1 if p.dim == 3 else 1))
+        lib().or_level_coeffs(self._h, l, _ptr(out))
+        return out
+
+    def counts(self):
+        sm = np.zeros(self.levels, dtype=np.int64)
+        nc = C.c_long()
+        lib().or_counts(self._h, sm.ctypes.data_as(C.c_void_p), C.byref(nc))
+        return sm, nc.value
+
+    def reset_counts(self):
+        lib().or_reset_counts(self._h)
+
+
+def thomas(lo, di, up, d):
+    m = len(di)
+    x = np.zeros(m)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (lo, di, up, d)]
+    lib().or_thomas(m, *[_ptr(a) for a in arrs], _ptr(x))
+    return x

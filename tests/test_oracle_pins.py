@@ -1,0 +1,534 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: closed-form
+eigenpairs of the discrete operators, exact invariants of Gauss-Seidel-type
+sweeps, the adjointness of restriction and prolongation, dense direct solves on
+tiny grids (numpy), textbook two-grid rates, finite differences of the loss.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_0805_3041_gb300 import inputs
+
+
+def const_problem(n, eps=1.0, dim=2, periodic_y=False):
+    if dim == 2:
+        n0, n1 = n if isinstance(n, tuple) else (n, n)
+        hx = 1.0 / (n0 - 1)
+        hy = 1.0 / n1 if periodic_y else 1.0 / (n1 - 1)
+        return orc.Problem(dim=2, n=(n0, n1, 1), periodic_y=periodic_y, kind=orc.CONST, h=(hx, hy, 1.0),
+                           c=(eps / hx ** 2, 1.0 / hy ** 2, 0.0))
+    h = 1.0 / (n - 1)
+    hy = 1.0 / (n - 1) if not periodic_y else 1.0 / (n - 1)
+    return orc.Problem(dim=3, n=(n, n - 1 if periodic_y else n, n), periodic_y=periodic_y, kind=orc.CONST,
+                       h=(h, hy, h), c=(eps / h ** 2, 1.0 / hy ** 2, 2.0 / h ** 2))
+
+
+def rand_field(o, rng, l=None):
+    return rng.standard_normal(o.shape(l)) * o.unknown_mask(l)
+
+
+# --------------------------------------------------------------------------------------
+# operator
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,eps", [(17, 1.0), (33, 0.01), (9, 1e-4)])
+def test_eigenpairs_2d(n, eps):
+    """A sin(p pi x) sin(q pi y) = (4/h^2)(eps sin^2(p pi h/2) + sin^2(q pi h/2)) sin sin."""
+    o = orc.Oracle(const_problem(n, eps), levels=1)
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    for p, q in [(1, 1), (2, 5), (n - 2, 1), (3, n - 2)]:
+        v = np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+        lam = 4.0 / h ** 2 * (eps * math.sin(p * math.pi * h / 2) ** 2 + math.sin(q * math.pi * h / 2) ** 2)
+        Av = o.apply(v)
+        assert np.max(np.abs(Av - lam * v * o.unknown_mask())) <= 1e-12 * lam
+
+
+def test_eigenpairs_3d():
+    n = 9
+    o = orc.Oracle(const_problem(n, 0.5, dim=3), levels=1)
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    cx, cy, cz = 0.5 / h ** 2, 1.0 / h ** 2, 2.0 / h ** 2
+    for p, q, r in [(1, 1, 1), (2, 3, 7), (7, 1, 4)]:
+        v = np.einsum("k,j,i->kji", np.sin(r * math.pi * x), np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+        lam = 4 * (cx * math.sin(p * math.pi * h / 2) ** 2 + cy * math.sin(q * math.pi * h / 2) ** 2
+                   + cz * math.sin(r * math.pi * h / 2) ** 2)
+        assert np.max(np.abs(o.apply(v) - lam * v * o.unknown_mask())) <= 1e-12 * lam
+
+
+def test_eigenpairs_periodic_y():
+    """Periodic y with n1 distinct nodes: mode sin(p pi x) cos(2 pi m j / n1)."""
+    n0, n1 = 17, 16
+    o = orc.Oracle(const_problem((n0, n1), 0.3, periodic_y=True), levels=1)
+    hx = 1.0 / (n0 - 1)
+    cx, cy = 0.3 / hx ** 2, float(n1) ** 2
+    i = np.arange(n0)
+    j = np.arange(n1)
+    for p, m in [(1, 0), (3, 1), (15, 8), (2, 5)]:
+        v = np.outer(np.cos(2 * math.pi * m * j / n1), np.sin(p * math.pi * i * hx))
+        lam = 4 * cx * math.sin(p * math.pi * hx / 2) ** 2 + 4 * cy * math.sin(math.pi * m / n1) ** 2
+        assert np.max(np.abs(o.apply(v) - lam * v * o.unknown_mask())) <= 1e-12 * max(lam, 1.0)
+
+
+def _kinds(dim, periodic_y, rng):
+    n = (17, 16 if periodic_y else 17, 9 if dim == 3 else 1)
+    h = (1 / 16, 1 / 16, 1 / 8)
+    out = [orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.CONST, h=h, c=(3.0, 1.5, 0.7))]
+    out.append(orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.SEPARABLE, h=h,
+                           sx=rng.uniform(0.5, 2, n[0] - 1), sy=rng.uniform(0.5, 2, n[0]),
+                           sz=rng.uniform(0.5, 2, n[0])))
+    cy = n[1] if periodic_y else n[1] - 1
+    kshape = (cy, n[0] - 1) if dim == 2 else (n[2] - 1, cy, n[0] - 1)
+    out.append(orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.CELL, h=h,
+                           k=np.exp(rng.standard_normal(kshape))))
+    return out
+
+
+@pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False), (3, True)])
+def test_symmetry_all_kinds(dim, periodic_y):
+    """<A u, v> = <u, A v> and <A u, u> > 0 for every coefficient kind on every level."""
+    rng = np.random.default_rng(0)
+    for prob in _kinds(dim, periodic_y, rng):
+        o = orc.Oracle(prob, levels=3)
+        for l in (1, 2, 3):
+            u, v = rand_field(o, rng, l), rand_field(o, rng, l)
+            a, b = np.vdot(o.apply(u, l), v), np.vdot(u, o.apply(v, l))
+            assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
+            assert np.vdot(o.apply(u, l), u) > 0
+
+
+def test_energy_edge_sum_cell_kind():
+    """u^T A u equals the edge sum sum_e w_e (u_p - u_q)^2 with w_e the mean of the
+    cells touching the edge over h^2 (finite-volume weights), written out here by hand."""
+    rng = np.random.default_rng(3)
+    n = 9
+    h = 1.0 / (n - 1)
+    k = np.exp(rng.standard_normal((n - 1, n - 1)))
+    o = orc.Oracle(orc.Problem(dim=2, n=(n, n, 1), kind=orc.CELL, h=(h, h, 1), k=k), levels=1)
+    u = rand_field(o, rng)
+    e = 0.0
+    for j in range(n):
+        for i in range(n):
+            if i + 1 < n and 0 < j < n - 1:
+                e += (k[j - 1, i] + k[j, i]) / (2 * h * h) * (u[j, i] - u[j, i + 1]) ** 2
+            if j + 1 < n and 0 < i < n - 1:
+                e += (k[j, i - 1] + k[j, i]) / (2 * h * h) * (u[j, i] - u[j + 1, i]) ** 2
+    assert abs(np.vdot(u, o.apply(u)) - e) <= 1e-12 * e
+
+
+def test_cell_kind_with_constant_k_is_laplacian():
+    n = 17
+    h = 1.0 / (n - 1)
+    oc = orc.Oracle(orc.Problem(dim=2, n=(n, n, 1), kind=orc.CELL, h=(h, h, 1),
+                                k=np.full((n - 1, n - 1), 2.5)), levels=3)
+    ol = orc.Oracle(const_problem(n, 1.0), levels=3)
+    u = rand_field(oc, np.random.default_rng(1))
+    assert np.allclose(oc.apply(u), 2.5 * ol.apply(u), rtol=1e-13, atol=0)
+    # the coarse cell fields average children: a constant stays constant, and h doubles
+    assert np.allclose(oc.level_coeffs(2), 2.5)
+
+
+def test_separable_coarsening_rule():
+    """Coarse x-edge weight = 1/4 harmonic mean of the two fine edges; y-weights injected x 1/4;
+    constant weights just scale by 1/4."""
+    rng = np.random.default_rng(2)
+    n = 17
+    sx, sy = rng.uniform(1, 3, n - 1), rng.uniform(1, 3, n)
+    o = orc.Oracle(orc.Problem(dim=2, n=(n, n, 1), kind=orc.SEPARABLE, sx=sx, sy=sy, sz=np.zeros(n)), levels=2)
+    cc = o.level_coeffs(1)
+    nc = 9
+    a, b = sx[0::2], sx[1::2]
+    assert np.allclose(cc[:nc - 1], 0.25 / (0.5 / a + 0.5 / b), rtol=1e-14)
+    assert np.allclose(cc[nc:2 * nc], 0.25 * sy[0::2], rtol=1e-14)
+    oc = orc.Oracle(const_problem(17, 0.3), levels=3)
+    assert np.allclose(oc.level_coeffs(1)[:2], np.array([0.3, 1.0]) * 16 ** 2 / 16, rtol=1e-14)
+
+
+def test_polar_weights_are_second_order():
+    """The annulus weights discretise r * (-Laplace u) in polar coordinates: the
+    truncation error on a smooth u falls 4x per halving of h."""
+    errs = []
+    for nr, nt in [(33, 32), (65, 64), (129, 128)]:
+        sp = inputs.annulus_2d(nr=nr, nt=nt)
+        o = orc.Oracle(orc.Problem(dim=2, n=sp.n, periodic_y=True, kind=orc.SEPARABLE, h=sp.h,
+                                   sx=sp.sx, sy=sp.sy, sz=sp.sz), levels=1)
+        r = 0.1 + sp.h[0] * np.arange(nr)
+        t = sp.h[1] * np.arange(nt)
+        R, T = np.meshgrid(r, t)
+        s = (R - 0.1) / 0.9
+        u = np.sin(math.pi * s) * (1 + 0.5 * np.cos(2 * T))     # zero at r = 0.1 and r = 1
+        # -(1/r) d/dr(r u_r) - (1/r^2) u_tt, times r
+        a = math.pi / 0.9
+        ur = a * np.cos(math.pi * s) * (1 + 0.5 * np.cos(2 * T))
+        urr = -a * a * np.sin(math.pi * s) * (1 + 0.5 * np.cos(2 * T))
+        utt = np.sin(math.pi * s) * (-2.0 * np.cos(2 * T))
+        exact = -(R * urr + ur) - utt / R
+        m = o.unknown_mask()
+        errs.append(np.max(np.abs((o.apply(u) - exact)[m])))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.7
+
+
+def test_diag_is_operator_diagonal():
+    rng = np.random.default_rng(5)
+    for prob in _kinds(2, True, rng) + _kinds(3, False, rng):
+        o = orc.Oracle(prob, levels=1)
+        D = o.diag()
+        m = o.unknown_mask()
+        idx = np.argwhere(m)[:: max(1, int(m.sum()) // 25)]
+        for t in idx:
+            e = np.zeros(o.shape())
+            e[tuple(t)] = 1.0
+            assert abs(o.apply(e)[tuple(t)] - D[tuple(t)]) <= 1e-13 * D[tuple(t)]
+
+
+# --------------------------------------------------------------------------------------
+# smoothers
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("omega", [0.8, 0.5])
+def test_jacobi_mode_multiplier(omega):
+    """One damped-Jacobi sweep multiplies a Dirichlet sine mode by 1 - omega lambda / D."""
+    n, eps = 17, 0.25
+    o = orc.Oracle(const_problem(n, eps), levels=1, smoother="jacobi", omega=omega)
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    D = 2 * eps / h ** 2 + 2 / h ** 2
+    for p, q in [(1, 2), (9, 3), (15, 15)]:
+        v = np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+        lam = 4.0 / h ** 2 * (eps * math.sin(p * math.pi * h / 2) ** 2 + math.sin(q * math.pi * h / 2) ** 2)
+        out = o.smooth(v, np.zeros_like(v), 1)
+        assert np.max(np.abs(out - (1 - omega * lam / D) * v * o.unknown_mask())) <= 1e-13
+
+
+def test_jacobi_smoothing_factor():
+    """Over the high modes (max(p,q) >= n/2) damped Jacobi with omega = 0.8 reduces
+    every mode by at most mu = max(|1-2w|, |1-w/2|) = 0.6 (2-D Poisson)."""
+    n = 33
+    o = orc.Oracle(const_problem(n), levels=1, smoother="jacobi", omega=0.8)
+    x = np.arange(n) / (n - 1)
+    worst = 0.0
+    for p in range(1, n - 1):
+        for q in range(1, n - 1):
+            if max(p, q) < (n - 1) // 2:
+                continue
+            v = np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+            out = o.smooth(v, np.zeros_like(v), 1)
+            worst = max(worst, np.linalg.norm(out) / np.linalg.norm(v))
+    assert 0.58 < worst <= 0.6 + 1e-12
+
+
+@pytest.mark.parametrize("smoother,order,colour_of", [
+    ("rbgs", orc.RED_FIRST, lambda i, j, k: (i + j + k) % 2 == 1),
+    ("rbgs", orc.BLACK_FIRST, lambda i, j, k: (i + j + k) % 2 == 0),
+    ("zebra_x", orc.RED_FIRST, lambda i, j, k: (j + k) % 2 == 1),
+    ("zebra_y", orc.BLACK_FIRST, lambda i, j, k: (i + k) % 2 == 0),
+])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gauss_seidel_invariant(smoother, order, colour_of, dim):
+    """With omega = 1 the colour updated last has exactly zero residual afterwards."""
+    rng = np.random.default_rng(7)
+    prob = _kinds(dim, False, rng)[2]
+    o = orc.Oracle(prob, levels=1, smoother=smoother, omega=1.0)
+    u, g = rand_field(o, rng), rand_field(o, rng)
+    r = o.defect(o.smooth(u, g, 1, order), g)
+    m = o.unknown_mask()
+    last = np.zeros_like(m)
+    for idx in np.argwhere(m):
+        if dim == 2:
+            j, i = idx
+            k = 0
+        else:
+            k, j, i = idx
+        last[tuple(idx)] = colour_of(i, j, k)
+    scale = np.max(np.abs(o.defect(u, g)))
+    assert np.max(np.abs(r[last])) <= 1e-12 * scale
+    assert np.max(np.abs(r[m & ~last])) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("direction", ["x", "y"])
+def test_line_jacobi_mode_multiplier(direction):
+    """Line Jacobi (C = tridiagonal part of A along the line) multiplies a sine mode by
+    1 - omega lambda / c with c = 2 w_perp + 4 w_line sin^2(theta_line / 2)."""
+    n, eps, omega = 17, 1e-3, 0.7
+    o = orc.Oracle(const_problem(n, eps), levels=1, smoother="line_" + direction, omega=omega)
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    wx, wy = eps / h ** 2, 1 / h ** 2
+    for p, q in [(1, 1), (4, 13), (15, 2)]:
+        v = np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+        sx, sy = math.sin(p * math.pi * h / 2) ** 2, math.sin(q * math.pi * h / 2) ** 2
+        lam = 4 * wx * sx + 4 * wy * sy
+        c = 2 * wy + 4 * wx * sx if direction == "x" else 2 * wx + 4 * wy * sy
+        out = o.smooth(v, np.zeros_like(v), 1)
+        assert np.max(np.abs(out - (1 - omega * lam / c) * v * o.unknown_mask())) <= 1e-12
+
+
+def test_thomas_matches_dense():
+    rng = np.random.default_rng(9)
+    m = 37
+    lo, up = -rng.uniform(0, 1, m), -rng.uniform(0, 1, m)
+    di = 2.5 + rng.uniform(0, 1, m)
+    d = rng.standard_normal(m)
+    T = np.diag(di) + np.diag(lo[1:], -1) + np.diag(up[:-1], 1)
+    assert np.allclose(orc.thomas(lo, di, up, d), np.linalg.solve(T, d), rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------------------
+# grid transfers
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False), (3, True)])
+def test_restriction_is_scaled_transpose_of_prolongation(dim, periodic_y):
+    """<R r, e>_coarse = 2^-d <r, P e>_fine for all r, e (full weighting vs. (bi/tri)linear)."""
+    rng = np.random.default_rng(4)
+    o = orc.Oracle(_kinds(dim, periodic_y, rng)[0], levels=3)
+    for lf in (2, 3):
+        r, e = rand_field(o, rng, lf), rand_field(o, rng, lf - 1)
+        lhs = np.vdot(o.restrict(r, lf), e)
+        Pe = o.prolong_add(e, np.zeros(o.shape(lf)), 1.0, lf)
+        assert abs(lhs - 2.0 ** -dim * np.vdot(r, Pe)) <= 1e-13 * np.abs(r).sum()
+
+
+def test_prolongation_reproduces_bilinear():
+    n = 33
+    o = orc.Oracle(const_problem(n), levels=2)
+    xc = np.arange(17) / 16
+    X, Y = np.meshgrid(xc, xc)
+    e = 0.3 + 1.7 * X - 0.9 * Y + 2.3 * X * Y
+    u = o.prolong_add(e, np.zeros(o.shape()), 1.0)
+    xf = np.arange(n) / (n - 1)
+    Xf, Yf = np.meshgrid(xf, xf)
+    ef = 0.3 + 1.7 * Xf - 0.9 * Yf + 2.3 * Xf * Yf
+    # fine nodes whose interpolation stencil uses only coarse unknowns
+    assert np.max(np.abs(u[2:-2, 2:-2] - ef[2:-2, 2:-2])) <= 1e-13
+    # 3-D trilinear
+    o3 = orc.Oracle(const_problem(17, dim=3), levels=2)
+    xc = np.arange(9) / 8
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    e = 1 + X - 2 * Y + 3 * Z + X * Y * Z
+    u = o3.prolong_add(e, np.zeros(o3.shape()), 1.0)
+    xf = np.arange(17) / 16
+    Z, Y, X = np.meshgrid(xf, xf, xf, indexing="ij")
+    ef = 1 + X - 2 * Y + 3 * Z + X * Y * Z
+    assert np.max(np.abs(u[2:-2, 2:-2, 2:-2] - ef[2:-2, 2:-2, 2:-2])) <= 1e-13
+
+
+def test_restriction_of_constant():
+    o = orc.Oracle(const_problem(33), levels=2)
+    g = o.restrict(np.full(o.shape(), 1.0) * o.unknown_mask())
+    assert np.allclose(g[1:-1, 1:-1][1:-1, 1:-1], 1.0, rtol=0, atol=1e-15)
+    # periodic y: the constant is kept on every coarse row
+    o = orc.Oracle(const_problem((17, 16), periodic_y=True), levels=2)
+    g = o.restrict(np.full(o.shape(), 2.0) * o.unknown_mask())
+    assert np.allclose(g[:, 2:-2], 2.0, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------------------
+# coarsest solve, F-cycle
+# --------------------------------------------------------------------------------------
+
+def dense_matrix(o, l=None):
+    m = o.unknown_mask(l)
+    idx = np.argwhere(m)
+    A = np.zeros((len(idx), len(idx)))
+    for c, t in enumerate(idx):
+        e = np.zeros(o.shape(l))
+        e[tuple(t)] = 1.0
+        A[:, c] = o.apply(e, l)[m]
+    return A, m
+
+
+@pytest.mark.parametrize("kind_idx", [0, 1, 2])
+def test_coarse_solve_matches_dense(kind_idx):
+    rng = np.random.default_rng(6)
+    o = orc.Oracle(_kinds(2, True, rng)[kind_idx], levels=3)
+    A, m = dense_matrix(o, 1)
+    g = rand_field(o, rng, 1)
+    u = o.coarse_solve(g)
+    assert np.allclose(u[m], np.linalg.solve(A, g[m]), rtol=0, atol=1e-13 * np.abs(np.linalg.solve(A, g[m])).max())
+
+
+def test_coarse_cg_matches_dense():
+    rng = np.random.default_rng(6)
+    o = orc.Oracle(_kinds(2, False, rng)[2], levels=2, dense_max=10)
+    A, m = dense_matrix(o, 1)
+    g = rand_field(o, rng, 1)
+    ref = np.linalg.solve(A, g[m])
+    assert np.max(np.abs(o.coarse_solve(g)[m] - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+CASES = [
+    (2, False, 0, "rbgs", 5, 2), (2, False, 2, "jacobi", 9, 3), (2, True, 1, "zebra_x", 17, 4),
+    (2, False, 2, "zebra_y", 17, 4), (2, False, 0, "line_y", 17, 3), (3, False, 0, "rbgs", 5, 2),
+    (3, True, 1, "zebra_x", 9, 3), (3, False, 2, "jacobi", 9, 2),
+]
+
+
+def _small(dim, periodic_y, kind_idx, n, rng):
+    probs = _kinds(dim, periodic_y, rng)
+    p = probs[kind_idx]
+    ny = n - 1 if periodic_y else n
+    nn = (n, ny, n if dim == 3 else 1)
+    h = p.h
+    if p.kind == orc.CONST:
+        return orc.Problem(dim=dim, n=nn, periodic_y=periodic_y, kind=orc.CONST, h=h, c=p.c)
+    if p.kind == orc.SEPARABLE:
+        return orc.Problem(dim=dim, n=nn, periodic_y=periodic_y, kind=orc.SEPARABLE, h=h,
+                           sx=rng.uniform(0.5, 2, n - 1), sy=rng.uniform(0.5, 2, n), sz=rng.uniform(0.5, 2, n))
+    cy = ny if periodic_y else ny - 1
+    ks = (cy, n - 1) if dim == 2 else (n - 1, cy, n - 1)
+    return orc.Problem(dim=dim, n=nn, periodic_y=periodic_y, kind=orc.CELL, h=h, k=np.exp(rng.standard_normal(ks)))
+
+
+@pytest.mark.parametrize("dim,per,kind_idx,smoother,n,levels", CASES)
+def test_fcycle_converges_to_dense_solution(dim, per, kind_idx, smoother, n, levels):
+    rng = np.random.default_rng(10)
+    prob = _small(dim, per, kind_idx, n, rng)
+    omega = 0.8 if smoother in ("jacobi", "line_y") else 1.0
+    o = orc.Oracle(prob, levels=levels, smoother=smoother, omega=omega)
+    A, m = dense_matrix(o)
+    b = rand_field(o, rng)
+    x, st, cyc, rr, hist = o.solve(b, tol=1e-13, maxit=200)
+    assert st == orc.OK
+    ref = np.linalg.solve(A, b[m])
+    assert np.max(np.abs(x[m] - ref)) <= 1e-11 * np.abs(ref).max()
+    assert np.all(x[~m] == 0.0)
+
+
+@pytest.mark.parametrize("L", [2, 3, 5])
+def test_fcycle_level_visits(L):
+    """F(l) visits level l once and runs F(l-1) then V(l-1) (V skipped when l-1 is the
+    coarsest grid): level k >= 2 is smoothed on 1 + (L - k) visits, the coarsest grid is
+    solved L - 1 times per cycle."""
+    n = 2 ** L + 1
+    o = orc.Oracle(const_problem(n), levels=L, nu1=1, nu2=2)
+    b = rand_field(o, np.random.default_rng(0))
+    o.reset_counts()
+    o.cycle(np.zeros_like(b), b)
+    sweeps, coarse = o.counts()
+    for k in range(2, L + 1):
+        assert sweeps[k - 1] == (1 + L - k) * 3
+    assert coarse == L - 1
+
+
+def _rate(o, b, ncyc):
+    """Asymptotic residual reduction per cycle, measured before the rounding floor."""
+    x, st, cyc, rr, hist = o.solve(b, tol=0.0, maxit=ncyc)
+    m = max(i for i in range(len(hist)) if hist[i] > 1e-11 * hist[0])
+    s = max(1, m - 3) if m > 1 else 0
+    return (hist[m] / hist[s]) ** (1.0 / max(1, m - s))
+
+
+def test_two_grid_rate_rbgs_matches_lfa():
+    """Two-grid method, red-black Gauss-Seidel nu1 = nu2 = 1, full weighting, bilinear
+    interpolation, 2-D Poisson: local Fourier analysis gives rho = 0.074 (textbook value)."""
+    o = orc.Oracle(const_problem(65), levels=2, smoother="rbgs", nu1=1, nu2=1)
+    b = rand_field(o, np.random.default_rng(1))
+    assert 0.055 <= _rate(o, b, 12) <= 0.085
+
+
+def test_fcycle_rate_is_mesh_independent():
+    rates = []
+    for n, L in [(33, 5), (65, 6), (129, 7)]:
+        o = orc.Oracle(const_problem(n), levels=L, smoother="rbgs", nu1=2, nu2=2)
+        rates.append(_rate(o, rand_field(o, np.random.default_rng(2)), 10))
+    assert max(rates) < 0.06
+    assert max(rates) - min(rates) < 0.02
+
+
+def test_line_smoother_is_robust_for_anisotropy_point_smoother_is_not():
+    """Section "Anisotropies": point smoothers degrade for -eps u_xx - u_yy with eps << 1;
+    y-line smoothing (lines along the strong coupling) does not."""
+    eps = 1e-3
+    o_pt = orc.Oracle(const_problem(65, eps), levels=6, smoother="rbgs")
+    o_ln = orc.Oracle(const_problem(65, eps), levels=6, smoother="zebra_y")
+    b = rand_field(o_pt, np.random.default_rng(3))
+    assert _rate(o_pt, b, 10) > 0.5
+    assert _rate(o_ln, b, 10) < 0.1
+
+
+def test_manufactured_closed_form_solution():
+    """f = 2 pi^2 sin(pi x) sin(pi y) is an eigenvector of the 5-point operator, so the
+    discrete solution is u = [2 pi^2 h^2 / (8 sin^2(pi h / 2))] sin(pi x) sin(pi y)."""
+    sp = inputs.poisson_sin(129)
+    o = orc.Oracle(orc.Problem(dim=2, n=sp.n, kind=orc.CONST, h=sp.h, c=sp.c), levels=6,
+                   smoother="jacobi", omega=0.8)
+    x, st, cyc, rr, hist = o.solve(sp.b, tol=1e-10, maxit=50)
+    h = 1.0 / 128
+    xs = np.arange(129) * h
+    exact = 2 * math.pi ** 2 * h ** 2 / (8 * math.sin(math.pi * h / 2) ** 2) * np.outer(
+        np.sin(math.pi * xs), np.sin(math.pi * xs))
+    exact[0, :] = exact[-1, :] = exact[:, 0] = exact[:, -1] = 0.0
+    assert st == orc.OK and rr <= 1e-10
+    assert np.linalg.norm(x - exact) <= 2e-10 * np.linalg.norm(exact)
+
+
+def test_solve_reports_no_convergence():
+    o = orc.Oracle(const_problem(33, 1e-4), levels=5, smoother="jacobi", omega=0.8)
+    b = rand_field(o, np.random.default_rng(0))
+    x, st, cyc, rr, hist = o.solve(b, tol=1e-10, maxit=5)
+    assert st == orc.ENOCONV and cyc == 5 and rr > 1e-10 and len(hist) == 6
+
+
+# --------------------------------------------------------------------------------------
+# adjoint and gradient
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,per,kind_idx,smoother,n,levels", CASES)
+@pytest.mark.parametrize("ncyc", [1, 2, 3])
+def test_transposed_cycle_dot_product(dim, per, kind_idx, smoother, n, levels, ncyc):
+    """<M b, c> = <b, M^T c>, M = ncyc F-cycles from zero, M^T = ncyc transposed cycles."""
+    rng = np.random.default_rng(20)
+    prob = _small(dim, per, kind_idx, n, rng)
+    o = orc.Oracle(prob, levels=levels, smoother=smoother, omega=0.8, nu1=1, nu2=2)
+    b, c = rand_field(o, rng), rand_field(o, rng)
+    xb, xc = np.zeros_like(b), np.zeros_like(c)
+    for _ in range(ncyc):
+        xb = o.cycle(xb, b)
+        xc = o.cycle(xc, c, transposed=True)
+    lhs, rhs = np.vdot(xb, c), np.vdot(b, xc)
+    assert abs(lhs - rhs) <= 1e-12 * (np.linalg.norm(xb) * np.linalg.norm(c))
+
+
+def _loss_and_grad(n, k, f, uobs, levels):
+    h = 1.0 / (n - 1)
+    o = orc.Oracle(orc.Problem(dim=2, n=(n, n, 1), kind=orc.CELL, h=(h, h, 1), k=k), levels=levels,
+                   smoother="rbgs")
+    u, st, *_ = o.solve(f, tol=1e-14, maxit=100)
+    m = o.unknown_mask()
+    L = float(np.sum(((u - uobs) * m) ** 2))
+    lam, st2, *_ = o.solve(2 * (u - uobs) * m, tol=1e-14, maxit=100, transposed=True)
+    return L, o.grad_k(u, lam), lam
+
+
+def test_gradient_matches_central_differences():
+    n = 17
+    rng = np.random.default_rng(30)
+    k = np.exp(0.5 * rng.standard_normal((n - 1, n - 1)))
+    f = rng.uniform(-1, 1, (n, n))
+    uobs = 0.01 * rng.standard_normal((n, n))
+    L0, g, lam = _loss_and_grad(n, k, f, uobs, 3)
+    for t in range(12):
+        c = (int(rng.integers(0, n - 1)), int(rng.integers(0, n - 1)))
+        d = 1e-6 * k[c]
+        kp, km = k.copy(), k.copy()
+        kp[c] += d
+        km[c] -= d
+        fd = (_loss_and_grad(n, kp, f, uobs, 3)[0] - _loss_and_grad(n, km, f, uobs, 3)[0]) / (2 * d)
+        assert abs(fd - g[c]) <= 1e-5 * abs(g).max()
+
+
+def test_adjoint_solution_matches_dense():
+    rng = np.random.default_rng(31)
+    prob = _small(2, False, 2, 17, rng)
+    o = orc.Oracle(prob, levels=3, smoother="rbgs", nu1=1, nu2=2)
+    A, m = dense_matrix(o)
+    g = rand_field(o, rng)
+    lam, st, *_ = o.solve(g, tol=1e-13, maxit=100, transposed=True)
+    ref = np.linalg.solve(A.T, g[m])
+    assert st == orc.OK and np.max(np.abs(lam[m] - ref)) <= 1e-11 * np.abs(ref).max()
