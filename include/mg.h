@@ -1,0 +1,172 @@
+/*
+ * mg.h -- C ABI of the GB300 geometric multigrid solver.
+ *
+ * The solver computes the method of J. T. Wallis, "Methods toward better
+ * Multigrid Solver Convergence" (2008): the F-cycle (abstract; section "The
+ * Multigrid Technique", algorithm MG(l, u, g)) with preconditioned-Richardson
+ * smoothers x <- x - omega C^{-1}(A x - b) (section "Smoothers", choices of C
+ * in "The choice of C") for the Poisson-type problems of sections
+ * "Introduction / Motivation" and "Anisotropies": 5-point (2-D) / 7-point
+ * (3-D) operators with constant, separable (mapped polar / cylindrical) or
+ * per-cell coefficients, zero Dirichlet data, optionally periodic in y.
+ *
+ * Conventions
+ *   - Every array argument is a DEVICE pointer to a full node array (Dirichlet
+ *     nodes included), contiguous, x fastest: (n1, n0) in 2-D, (n2, n1, n0) in
+ *     3-D.  Entries at Dirichlet nodes of right-hand sides are ignored; those of
+ *     solutions are written as 0.  Cell arrays are (ncy, n0-1) / (n2-1, ncy, n0-1)
+ *     with ncy = n1 if y is periodic else n1-1.
+ *   - Level 1 is the coarsest grid and level L the finest, as in the paper.
+ *   - Every call is stream-ordered on mg_params.stream (a cudaStream_t).  Calls
+ *     that report convergence (mg_solve, mg_solve_adjoint) synchronise that
+ *     stream once per cycle to read the residual norm.
+ *   - Memory: the caller allocates the workspace (mg_workspace_bytes) and all
+ *     argument arrays; the library allocates only the opaque context on the
+ *     host and its CUDA graph.  The library never calls cudaMalloc.
+ *   - Errors: every call returns an mg_status; no exception crosses the ABI.
+ *     MG_EINVAL is returned before any launch for bad arguments; CUDA failures
+ *     give MG_ECUDA with the text in mg_last_error().
+ */
+#ifndef MG_H
+#define MG_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,     /* bad argument (sizes, levels, null pointer, workspace too small) */
+  MG_ENOMEM = 2,     /* host allocation of the context failed */
+  MG_ECUDA = 3,      /* a CUDA call failed; see mg_last_error */
+  MG_ENOCONV = 4,    /* max_cycles reached before the tolerance; x holds the last iterate */
+  MG_EDIVERGED = 5,  /* the residual norm became non-finite */
+  MG_ETIMEOUT = 6,   /* a bounded device wait gave up (reserved) */
+  MG_EBOUNDS = 7     /* a device-side check found an out-of-range index (reserved) */
+} mg_status;
+
+/* Choice of C in x <- x + omega C^{-1} (b - A x) (section "The choice of C"). */
+typedef enum {
+  MG_JACOBI = 0,   /* C = D, damped by omega                                              */
+  MG_RBGS = 1,     /* Gauss-Seidel / SOR in red-black order (red: i+j+k even, first)       */
+  MG_LINE_X = 2,   /* TRIx: C = tridiagonal part of A along x lines, all lines at once       */
+  MG_LINE_Y = 3,   /* TRIy: the same along y lines (the paper's "virtually transposed" TRI) */
+  MG_ZEBRA_X = 4,  /* GSTRIx: x lines in two colours by parity of (j + k), even first       */
+  MG_ZEBRA_Y = 5   /* GSTRIy: y lines in two colours by parity of (i + k), even first       */
+} mg_smoother;
+
+typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2 } mg_coef_kind;
+
+/* MG_FP64: every step in double precision.
+ * MG_MIXED: iterative refinement -- the FP64 defect r = b - A x drives one or
+ * more single-precision F-cycles (smoothing, restriction, prolongation in
+ * FP32; the coarsest-grid solve in FP64) whose correction is added to x in FP64. */
+typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
+
+#define MG_FLAG_NO_GRAPH 1u   /* launch the cycle kernel by kernel instead of as a CUDA graph */
+#define MG_FLAG_TIMING   2u   /* record CUDA events around every finest-level smoothing launch */
+
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int n[3];               /* finest-grid nodes per direction: 2^m + 1, or 2^m in periodic y */
+  int periodic_y;         /* 1: y is periodic (n[1] distinct nodes) */
+  int levels;             /* number of grids L, 1 <= L <= max for n */
+  mg_smoother smoother;
+  double omega;           /* smoother damping / SOR parameter */
+  int nu1, nu2;           /* pre- and post-smoothing steps */
+  double omega_corr;      /* omega_l of the correction u + omega_l P e (fixed) */
+  mg_precision precision;
+  int max_cycles;         /* F-cycles (FP64) or refinement steps (MG_MIXED) */
+  int inner_cycles;       /* MG_MIXED: single-precision F-cycles per refinement step (>= 1) */
+  void *stream;           /* cudaStream_t; NULL = legacy default stream */
+  unsigned flags;         /* MG_FLAG_* */
+} mg_params;
+
+typedef struct {
+  mg_coef_kind kind;
+  double h[3];            /* mesh widths; MG_COEF_CELL forms weights from them */
+  double c[3];            /* MG_COEF_CONST: edge weight per direction (e.g. eps/h^2, 1/h^2) */
+  const double *sx;       /* MG_COEF_SEPARABLE (device): weight of x-edge (i, i+1), length n0-1 */
+  const double *sy;       /* MG_COEF_SEPARABLE (device): weight of the y-edges at x-index i, length n0 */
+  const double *sz;       /* MG_COEF_SEPARABLE (device): weight of the z-edges at x-index i (3-D) */
+  const double *k;        /* MG_COEF_CELL (device): coefficient per cell of -div(k grad u) */
+} mg_coeffs;
+
+typedef struct {
+  int cycles;             /* F-cycles (or refinement steps) performed */
+  double relres;          /* ||b - A x||_2 / ||b||_2 over the unknowns, in FP64, at return */
+  double rate;            /* (relres / relres_0)^(1/cycles) */
+  mg_status status;
+  double *history;        /* HOST array, relres before each cycle and at return; may be NULL */
+  int history_cap;
+  double seconds;         /* wall time of the call (host clock, after the final sync) */
+} mg_report;
+
+/* Workspace size in bytes for these parameters and coefficient kind.  Returns 0
+ * for invalid parameters. */
+size_t mg_workspace_bytes(const mg_params *p, const mg_coeffs *k);
+
+/* a1: build the level hierarchy (coarsened coefficients, diagonal inverses, the
+ * dense inverse of the coarsest operator, the CUDA graph of one cycle) inside
+ * the caller's workspace (device memory, >= mg_workspace_bytes, 256-byte
+ * aligned).  The coefficient arrays are copied; the caller may free them after
+ * the call returns.  On success *out owns a host context; free it with
+ * mg_destroy.  Sections "The Multigrid Technique" (A_l, S_l, P, R, A_1^{-1})
+ * and "The choice of C" (preconditioner memory set up before iterating). */
+mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size_t ws_bytes, mg_ctx **out);
+
+/* Solve A x = b by F-cycles until ||b - A x|| / ||b|| <= tol or max_cycles.
+ * b: device, read-only.  x: device, in = start vector, out = solution (start
+ * vector choice: section "Start-Vector Choice").  rep may be NULL.
+ * Returns MG_OK, MG_ENOCONV (x = last iterate) or MG_EDIVERGED. */
+mg_status mg_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep);
+
+/* Adjoint solve A^T lambda = g with the transposed F-cycle M^T (steps of the
+ * cycle in reverse order, each transposed).  Same conventions as mg_solve. */
+mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep);
+
+/* MG_COEF_CELL only: dk[c] = -sum over the edges e of cell c of
+ * (d w_e / d k_c) (u_p - u_q)(lambda_p - lambda_q), i.e. dL/dk for a loss L
+ * whose gradient in u is A^T lambda.  dk: device cell array, overwritten. */
+mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double *dk);
+
+/* Au = A_l u on level l (1..L).  u, Au: device node arrays of level l. */
+mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au);
+
+/* Level geometry: nodes per direction of level l. */
+mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]);
+
+/* Single steps of the cycle, for testing; FP64 node arrays of the given level,
+ * device pointers, out-of-place outputs.
+ *   mg_step_smooth:   out = S^sweeps(u, g) with colour order 0 = red first, 1 = black first
+ *   mg_step_defect:   r = g - A_l u
+ *   mg_step_restrict: gc = R r            (level = fine level, >= 2)
+ *   mg_step_prolong:  u_out = u + w P ec  (level = fine level, >= 2)
+ *   mg_step_coarse:   u = A_1^{-1} g
+ *   mg_step_cycle:    x_out = one F-cycle (transposed = 1: one transposed cycle) from x */
+mg_status mg_step_smooth(mg_ctx *c, int level, const double *u, const double *g, double *out, int sweeps, int order);
+mg_status mg_step_defect(mg_ctx *c, int level, const double *u, const double *g, double *r);
+mg_status mg_step_restrict(mg_ctx *c, int level, const double *r, double *gc);
+mg_status mg_step_prolong(mg_ctx *c, int level, const double *ec, const double *u, double *u_out, double w);
+mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u);
+mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed);
+
+/* Mean duration (ms) of the finest-level smoothing launches recorded since the
+ * last call (MG_FLAG_TIMING), their count, and the algorithmic bytes one such
+ * launch moves.  Resets the record. */
+mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *bytes_per_launch);
+
+/* Number of kernels the library launched since the context was created. */
+long long mg_launch_count(const mg_ctx *c);
+
+void mg_destroy(mg_ctx *c);
+const char *mg_status_str(mg_status s);
+const char *mg_last_error(const mg_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,435 @@
+// kernels_point.cu -- point-wise stencil kernels: damped Jacobi, red-black
+// Gauss-Seidel half-sweeps, defect, defect norms, the mixed-precision defect and
+// refinement update, and the cell-coefficient gradient.
+//
+// Smoothers are preconditioned Richardson steps x <- x + omega C^{-1}(b - A x)
+// (Wallis 2008, section "Smoothers"); C = D for Jacobi and C = D + L in
+// red-black order for Gauss-Seidel (section "The choice of C").
+//
+// Launch shape: blocks of 32 x 8 threads.  threadIdx.x runs along x (coalesced
+// rows), each thread handles R consecutive unknown rows (j, k).  Every thread
+// writes only unknown nodes of its own rows.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+static constexpr int BX = 32, BY = 8;
+
+static inline int rows_per_thread(long long rows) { return rows >= 2048 ? 4 : 1; }
+
+static inline dim3 grid_for(long long xthreads, long long rows, int R) {
+  long long gy = (rows + (long long)BY * R - 1) / ((long long)BY * R);
+  return dim3((unsigned)((xthreads + BX - 1) / BX), (unsigned)gy, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// damped Jacobi, out of place: out = u + omega D^{-1} (g - A u)
+// ---------------------------------------------------------------------------------------
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_jacobi(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
+                                                   T *__restrict__ out, T omega, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(L, r, j, k);
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    T s = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+    out[p] = fma(omega * w.dinv, s, u[p]);
+  }
+}
+
+// first sweep from a zero iterate: out = omega D^{-1} g
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_jacobi_zero(Lev<T> L, const T *__restrict__ g, T *__restrict__ out,
+                                                        T omega, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(L, r, j, k);
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    out[p] = omega * w.dinv * g[p];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// red-black Gauss-Seidel half-sweep, in place on the nodes with (i+j+k) % 2 == colour.
+// Only nodes of the other colour are read as neighbours, so the update is race free.
+// Thread t of a row handles node i = 1 + 2t + ((colour + j + k + 1) & 1).
+// ---------------------------------------------------------------------------------------
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_rb_half(Lev<T> L, T *u, const T *__restrict__ g, T omega, int colour,
+                                                    int R) {
+  int t = blockIdx.x * BX + threadIdx.x;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(L, r, j, k);
+    int i = 1 + 2 * t + ((colour + j + k + 1) & 1);
+    if (i > L.n0 - 2) continue;
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    T s = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+    u[p] = fma(omega * w.dinv, s, u[p]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// defect r = g - A u
+// ---------------------------------------------------------------------------------------
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_defect(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
+                                                   T *__restrict__ r_out, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(L, r, j, k);
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    r_out[p] = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+  }
+}
+
+// deterministic block sum of a double (fixed shuffle pattern, fixed smem tree)
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31, wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  double s = 0.0;
+  if (wid == 0) {
+    s = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// sum of squares of the defect over the unknowns, one partial per block
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_defect_norm(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
+                                                        double *__restrict__ partials, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  double acc = 0.0;
+  if (i <= L.n0 - 2) {
+    for (int q = 0; q < R; ++q) {
+      long long r = r0 + q;
+      if (r >= nr) break;
+      int j, k;
+      row_jk(L, r, j, k);
+      long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+      yoffs(L, j, dm, dp);
+      Weights<T, DIM, KIND> w;
+      w.load(L, i, p, dm);
+      double s = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+      acc = fma(s, s, acc);
+    }
+  }
+  double bs = block_sum(acc);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX *BY) k_norm_parts(Lev<T> L, const T *__restrict__ v, double *__restrict__ partials,
+                                                       int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  double acc = 0.0;
+  if (i <= L.n0 - 2) {
+    for (int q = 0; q < R; ++q) {
+      long long r = r0 + q;
+      if (r >= nr) break;
+      int j, k;
+      row_jk(L, r, j, k);
+      double s = (double)v[(long long)k * L.plane + (long long)j * L.pitch + i];
+      acc = fma(s, s, acc);
+    }
+  }
+  double bs = block_sum(acc);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+}
+
+// single block: out[0] = sum of partials in a fixed order
+__global__ void __launch_bounds__(1024) k_norm_finish(const double *__restrict__ partials, int n, double *out) {
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) acc += partials[t];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[0] = s;
+  }
+}
+
+// relres = sqrt(sq) / sqrt(bsq), recorded in the device history
+__global__ void k_relres(const double *sq, const double *bsq, double *hist, int it, double *out) {
+  double rel = sqrt(sq[0]) / sqrt(bsq[0]);
+  out[0] = rel;
+  if (hist) hist[it] = rel;
+}
+
+// ---------------------------------------------------------------------------------------
+// mixed precision: r32 = (float)(b - A x) with the defect in FP64, plus norm partials;
+// refinement update x += (double)c
+// ---------------------------------------------------------------------------------------
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_defect64_to32(Lev<double> L, const double *__restrict__ x,
+                                                          const double *__restrict__ b, float *__restrict__ r32,
+                                                          long long pitch32, long long plane32,
+                                                          double *__restrict__ partials, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  double acc = 0.0;
+  if (i <= L.n0 - 2) {
+    for (int q = 0; q < R; ++q) {
+      long long r = r0 + q;
+      if (r >= nr) break;
+      int j, k;
+      row_jk(L, r, j, k);
+      long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+      yoffs(L, j, dm, dp);
+      Weights<double, DIM, KIND> w;
+      w.load(L, i, p, dm);
+      double s = residual_at<double, DIM, KIND>(L, w, x, p, dm, dp, b[p]);
+      r32[(long long)k * plane32 + (long long)j * pitch32 + i] = (float)s;
+      acc = fma(s, s, acc);
+    }
+  }
+  double bs = block_sum(acc);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+}
+
+__global__ void __launch_bounds__(BX *BY) k_ir_update(Lev<double> L, double *__restrict__ x, const float *__restrict__ c,
+                                                      long long pitch32, long long plane32, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(L, r, j, k);
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
+    x[p] += (double)c[(long long)k * plane32 + (long long)j * pitch32 + i];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// dL/dk for the cell field: dk_c = -sum_{edges e of cell c} (dw_e/dk_c)(u_p-u_q)(l_p-l_q)
+// (2-D: 4 edges with dw/dk = 1/(2h^2); 3-D: 12 edges with dw/dk = 1/(4h^2))
+// ---------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(BX *BY) k_grad_k(Lev<double> L, const double *__restrict__ u,
+                                                   const double *__restrict__ lam, double *__restrict__ dk, int R) {
+  int i = blockIdx.x * BX + threadIdx.x;   // cell x index 0 .. n0-2
+  if (i > L.n0 - 2) return;
+  int ncy = L.per ? L.n1 : L.n1 - 1, ncz = DIM == 3 ? L.n2 - 1 : 1;
+  long long nrows = (long long)ncy * ncz;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nrows) return;
+    int j = (int)(r % ncy), k = (int)(r / ncy);
+    long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
+    long long up = (L.per && j == L.n1 - 1) ? -(long long)(L.n1 - 1) * L.pitch : L.pitch;
+    if (DIM == 2) {
+      double u00 = u[p], u10 = u[p + 1], u01 = u[p + up], u11 = u[p + up + 1];
+      double l00 = lam[p], l10 = lam[p + 1], l01 = lam[p + up], l11 = lam[p + up + 1];
+      double sx = (u00 - u10) * (l00 - l10) + (u01 - u11) * (l01 - l11);
+      double sy = (u00 - u01) * (l00 - l01) + (u10 - u11) * (l10 - l11);
+      dk[p] = -(L.ax * sx + L.ay * sy);
+    } else {
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b) {
+          long long q0 = p + c * L.plane + b * up;   // x-edges at (j+b, k+c)
+          sx += (u[q0] - u[q0 + 1]) * (lam[q0] - lam[q0 + 1]);
+          long long q1 = p + c * L.plane + b;        // y-edges at (i+b, k+c)
+          sy += (u[q1] - u[q1 + up]) * (lam[q1] - lam[q1 + up]);
+          long long q2 = p + c * up + b;             // z-edges at (i+b, j+c)
+          sz += (u[q2] - u[q2 + L.plane]) * (lam[q2] - lam[q2 + L.plane]);
+        }
+      dk[p] = -(L.ax * sx + L.ay * sy + L.az * sz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+#define DISPATCH_DK(DIMV, KINDV, KERNEL, ...)                                  \
+  do {                                                                         \
+    if ((DIMV) == 2) {                                                         \
+      if ((KINDV) == K_CONST) KERNEL<T, 2, K_CONST> __VA_ARGS__;               \
+      else if ((KINDV) == K_SEP) KERNEL<T, 2, K_SEP> __VA_ARGS__;              \
+      else KERNEL<T, 2, K_CELL> __VA_ARGS__;                                   \
+    } else {                                                                   \
+      if ((KINDV) == K_CONST) KERNEL<T, 3, K_CONST> __VA_ARGS__;               \
+      else if ((KINDV) == K_SEP) KERNEL<T, 3, K_SEP> __VA_ARGS__;              \
+      else KERNEL<T, 3, K_CELL> __VA_ARGS__;                                   \
+    }                                                                          \
+  } while (0)
+
+template <typename T>
+void launch_jacobi(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega) {
+  long long rows = L.unk_rows();
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_jacobi, <<<gr, bl, 0, lc.s>>>(L, u, g, out, omega, R));
+  ++*lc.counter;
+}
+
+template <typename T>
+void launch_jacobi_zero(const Lev<T> &L, int kind, const Launch &lc, const T *g, T *out, T omega) {
+  long long rows = L.unk_rows();
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_jacobi_zero, <<<gr, bl, 0, lc.s>>>(L, g, out, omega, R));
+  ++*lc.counter;
+}
+
+template <typename T>
+void launch_rb_half(const Launch &lc, const Lev<T> &L, int kind, T *u, const T *g, T omega, int colour) {
+  long long rows = L.unk_rows();
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for((L.xunk() + 1) / 2, rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_rb_half, <<<gr, bl, 0, lc.s>>>(L, u, g, omega, colour, R));
+  ++*lc.counter;
+}
+
+template <typename T>
+void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *r) {
+  long long rows = L.unk_rows();
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_defect, <<<gr, bl, 0, lc.s>>>(L, u, g, r, R));
+  ++*lc.counter;
+}
+
+static inline int norm_R(long long rows, long long xthreads, int nparts) {
+  int R = rows_per_thread(rows);
+  while (true) {
+    dim3 gr = grid_for(xthreads, rows, R);
+    if ((long long)gr.x * gr.y <= nparts) return R;
+    R *= 2;
+  }
+}
+
+int norm_parts_count() { return 65536; }
+
+template <typename T>
+void launch_defect_norm(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, double *partials,
+                        int nparts, double *out_sq) {
+  long long rows = L.unk_rows();
+  int R = norm_R(rows, L.xunk(), nparts);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_defect_norm, <<<gr, bl, 0, lc.s>>>(L, u, g, partials, R));
+  ++*lc.counter;
+  launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
+}
+
+template <typename T>
+void launch_norm_parts(const Launch &lc, const Lev<T> &L, const T *v, double *partials, int nparts, double *out_sq) {
+  long long rows = L.unk_rows();
+  int R = norm_R(rows, L.xunk(), nparts);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  k_norm_parts<T><<<gr, bl, 0, lc.s>>>(L, v, partials, R);
+  ++*lc.counter;
+  launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
+}
+
+void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq) {
+  k_norm_finish<<<1, 1024, 0, lc.s>>>(partials, nparts, out_sq);
+  ++*lc.counter;
+}
+
+void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out) {
+  k_relres<<<1, 1, 0, lc.s>>>(sq, bsq, hist, it, relres_out);
+  ++*lc.counter;
+}
+
+void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
+                          float *r32, double *partials, int nparts, double *out_sq) {
+  long long rows = L.unk_rows();
+  int R = norm_R(rows, L.xunk(), nparts);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  long long p32 = L.pitch, pl32 = L.plane;   // the FP32 finest level uses the same element pitch
+  if (L.dim == 2) {
+    if (kind == K_CONST) k_defect64_to32<2, K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    else if (kind == K_SEP) k_defect64_to32<2, K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    else k_defect64_to32<2, K_CELL><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+  } else {
+    if (kind == K_CONST) k_defect64_to32<3, K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    else if (kind == K_SEP) k_defect64_to32<3, K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    else k_defect64_to32<3, K_CELL><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+  }
+  ++*lc.counter;
+  launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
+}
+
+void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c) {
+  long long rows = L.unk_rows();
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  k_ir_update<<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
+  ++*lc.counter;
+}
+
+void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, const double *lam, double *dk) {
+  int ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
+  long long rows = (long long)ncy * ncz;
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(L.n0 - 1, rows, R), bl(BX, BY);
+  if (L.dim == 2) k_grad_k<2><<<gr, bl, 0, lc.s>>>(L, u, lam, dk, R);
+  else k_grad_k<3><<<gr, bl, 0, lc.s>>>(L, u, lam, dk, R);
+  ++*lc.counter;
+}
+
+#define INST(T)                                                                                              \
+  template void launch_jacobi<T>(const Launch &, const Lev<T> &, int, const T *, const T *, T *, T);         \
+  template void launch_jacobi_zero<T>(const Lev<T> &, int, const Launch &, const T *, T *, T);              \
+  template void launch_rb_half<T>(const Launch &, const Lev<T> &, int, T *, const T *, T, int);             \
+  template void launch_defect<T>(const Launch &, const Lev<T> &, int, const T *, const T *, T *);           \
+  template void launch_defect_norm<T>(const Launch &, const Lev<T> &, int, const T *, const T *, double *, int, \
+                                      double *);                                                              \
+  template void launch_norm_parts<T>(const Launch &, const Lev<T> &, const T *, double *, int, double *);
+INST(double)
+INST(float)
+
+}  // namespace mg

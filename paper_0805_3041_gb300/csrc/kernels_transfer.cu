@@ -1,0 +1,384 @@
+// kernels_transfer.cu -- grid transfers (full-weighting restriction, bilinear /
+// trilinear prolongation with correction), the coarsest-grid solve
+// u = A_1^{-1} g with a dense inverse built on the device by Gauss-Jordan
+// elimination, set-up kernels (coefficient coarsening, diagonal inverses), and
+// layout conversions between the caller's compact arrays and the padded levels.
+//
+// Wallis (2008), section "The Multigrid Technique": g_{l-1} = R d_l,
+// u + omega_l P u_{l-1}, and A_1^{-1} g on the coarsest grid.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+static constexpr int BX = 32, BY = 8;
+
+static inline dim3 grid2(long long xthreads, long long rows, int R) {
+  long long gy = (rows + (long long)BY * R - 1) / ((long long)BY * R);
+  return dim3((unsigned)((xthreads + BX - 1) / BX), (unsigned)gy, 1);
+}
+static inline int rpt(long long rows) { return rows >= 2048 ? 4 : 1; }
+
+// ---------------------------------------------------------------------------------------
+// full weighting: g_c(I) = sum_a prod_d w(a_d) r_f(2I + a), w = [1/4, 1/2, 1/4]
+// ---------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(BX *BY) k_restrict(Lev<T> F, Lev<T> C, const T *__restrict__ rf, T *__restrict__ gc,
+                                                     int R) {
+  int I = 1 + blockIdx.x * BX + threadIdx.x;
+  if (I > C.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = C.unk_rows();
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int J, K;
+    row_jk(C, r, J, K);
+    long long dm, dp;
+    yoffs(F, 2 * J, dm, dp);
+    long long pf = (long long)(2 * K) * F.plane + (long long)(2 * J) * F.pitch + 2 * I;
+    auto row3 = [&](long long c) -> T { return (rf[c - 1] + rf[c + 1]) + T(2) * rf[c]; };
+    auto plane3 = [&](long long c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
+    T s;
+    if (DIM == 2) {
+      s = plane3(pf) * T(0.0625);
+    } else {
+      s = ((plane3(pf - F.plane) + plane3(pf + F.plane)) + T(2) * plane3(pf)) * T(0.015625);
+    }
+    gc[(long long)K * C.plane + (long long)J * C.pitch + I] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// u_f += w * P e_c (bilinear / trilinear; coarse Dirichlet nodes hold 0)
+// ---------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, const T *__restrict__ ec,
+                                                        T *__restrict__ uf, T w, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  if (i > F.n0 - 2) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = F.unk_rows();
+  int I0 = i >> 1, I1 = (i + 1) >> 1;
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nr) return;
+    int j, k;
+    row_jk(F, r, j, k);
+    int J0 = j >> 1, J1 = (j + 1) >> 1;
+    if (J1 >= C.n1) J1 -= C.n1;   // periodic wrap (only reachable when y is periodic)
+    long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+    T s;
+    if (DIM == 2) {
+      s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
+    } else {
+      long long z0 = (long long)(k >> 1) * C.plane, z1 = (long long)((k + 1) >> 1) * C.plane;
+      T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
+      T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
+      s = (s0 + s1) * T(0.125);
+    }
+    long long p = (long long)k * F.plane + (long long)j * F.pitch + i;
+    uf[p] = fma(w, s, uf[p]);
+  }
+}
+
+template <typename T>
+void launch_restrict(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *rf, T *gc) {
+  long long rows = C.unk_rows();
+  int R = rpt(rows);
+  dim3 gr = grid2(C.xunk(), rows, R), bl(BX, BY);
+  if (F.dim == 2) k_restrict<T, 2><<<gr, bl, 0, lc.s>>>(F, C, rf, gc, R);
+  else k_restrict<T, 3><<<gr, bl, 0, lc.s>>>(F, C, rf, gc, R);
+  ++*lc.counter;
+}
+
+template <typename T>
+void launch_prolong_add(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *ec, T *uf, T w) {
+  long long rows = F.unk_rows();
+  int R = rpt(rows);
+  dim3 gr = grid2(F.xunk(), rows, R), bl(BX, BY);
+  if (F.dim == 2) k_prolong_add<T, 2><<<gr, bl, 0, lc.s>>>(F, C, ec, uf, w, R);
+  else k_prolong_add<T, 3><<<gr, bl, 0, lc.s>>>(F, C, ec, uf, w, R);
+  ++*lc.counter;
+}
+
+// ---------------------------------------------------------------------------------------
+// coarsest grid
+// ---------------------------------------------------------------------------------------
+
+// u[cidx[r]] = sum_c Ainv[r][c] g[cidx[c]], FP64 arithmetic, one warp per row
+template <typename T>
+__global__ void k_coarse_apply(const double *__restrict__ Ainv, const long long *__restrict__ cidx, int nc,
+                               const T *__restrict__ g, T *__restrict__ u) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  const double *row = Ainv + (long long)warp * nc;
+  double s = 0.0;
+  for (int c = lane; c < nc; c += 32) s = fma(row[c], (double)g[cidx[c]], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) u[cidx[warp]] = (T)s;
+}
+
+template <typename T>
+void launch_coarse_apply(const Launch &lc, const double *Ainv, const long long *cidx, int nc, const T *g, T *u) {
+  int threads = 256, blocks = (nc * 32 + threads - 1) / threads;
+  k_coarse_apply<T><<<blocks, threads, 0, lc.s>>>(Ainv, cidx, nc, g, u);
+  ++*lc.counter;
+}
+
+// Dense matrix of the coarsest operator: row r of unknown p = cidx[r] holds D_p on the
+// diagonal and -w_e for every edge to another unknown (Dirichlet neighbours drop out).
+template <typename T, int DIM, int KIND>
+__global__ void k_assemble_dense(Lev<T> L, const long long *__restrict__ cidx, const int *__restrict__ cmap, int nc,
+                                 double *__restrict__ A) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nc) return;
+  long long p = cidx[r];
+  int k = (int)(p / L.plane);
+  int j = (int)((p - (long long)k * L.plane) / L.pitch);
+  int i = (int)(p - (long long)k * L.plane - (long long)j * L.pitch);
+  long long dm, dp;
+  yoffs(L, j, dm, dp);
+  Weights<T, DIM, KIND> w;
+  w.load(L, i, p, dm);
+  double *row = A + (long long)r * nc;
+  double D = (double)w.wW + (double)w.wE + (double)w.wS + (double)w.wN;
+  if (DIM == 3) D += (double)w.wB + (double)w.wF;
+  row[r] += D;
+  long long nb[6] = {p - 1, p + 1, p + dm, p + dp, p - L.plane, p + L.plane};
+  double ww[6] = {(double)w.wW, (double)w.wE, (double)w.wS, (double)w.wN, (double)w.wB, (double)w.wF};
+  for (int e = 0; e < 2 * DIM; ++e) {
+    int c = cmap[nb[e]];
+    if (c >= 0) row[c] -= ww[e];
+  }
+}
+
+template <typename T>
+void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const long long *cidx, const int *cmap,
+                           int nc, double *A) {
+  int th = 128, bl = (nc + th - 1) / th;
+  if (L.dim == 2) {
+    if (kind == K_CONST) k_assemble_dense<T, 2, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else if (kind == K_SEP) k_assemble_dense<T, 2, K_SEP><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else k_assemble_dense<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+  } else {
+    if (kind == K_CONST) k_assemble_dense<T, 3, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else if (kind == K_SEP) k_assemble_dense<T, 3, K_SEP><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else k_assemble_dense<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+  }
+  ++*lc.counter;
+}
+
+// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed), step k:
+//   (a) save column k, divide row k by the pivot, set A[k][k] = 1/pivot;
+//   (b) A[i][j] -= col[i] * A[k][j] for i != k, with A[i][k] := -col[i] / pivot.
+__global__ void k_gj_a(double *A, double *col, int n, int k) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(long long)i * n + k];
+  __syncthreads();
+  double piv = col[k];
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    A[(long long)k * n + j] = (j == k ? 1.0 : A[(long long)k * n + j]) / piv;
+}
+__global__ void k_gj_b(double *A, const double *__restrict__ col, int n, int k) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int i = (int)(t / n), j = (int)(t % n);
+  if (i == k) return;
+  double a = (j == k) ? 0.0 : A[t];
+  A[t] = a - col[i] * A[(long long)k * n + j];
+}
+void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep) {
+  k_gj_a<<<1, 256, 0, lc.s>>>(A, col, n, kstep);
+  long long tot = (long long)n * n;
+  k_gj_b<<<(unsigned)((tot + 255) / 256), 256, 0, lc.s>>>(A, col, n, kstep);
+  *lc.counter += 2;
+}
+
+// ---------------------------------------------------------------------------------------
+// set-up: coefficient coarsening and diagonal inverses (FP64)
+// ---------------------------------------------------------------------------------------
+
+// separable weights: W_x(I) = 1/4 H(w_x(2I), w_x(2I+1)), W_y(I) = 1/4 w_y(2I), W_z(I) = 1/4 w_z(2I)
+__global__ void k_coarsen_sep(const double *fsx, const double *fsy, const double *fsz, int nf0, double *csx,
+                              double *csy, double *csz, int nc0) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc0) return;
+  if (I < nc0 - 1) {
+    double a = fsx[2 * I], b = fsx[2 * I + 1];
+    csx[I] = 0.25 * (2.0 * a * b / (a + b));
+  } else {
+    csx[I] = 0.0;
+  }
+  csy[I] = 0.25 * fsy[2 * I];
+  csz[I] = 0.25 * fsz[2 * I];
+}
+void launch_coarsen_sep(const Launch &lc, const double *fsx, const double *fsy, const double *fsz, int nf0,
+                        double *csx, double *csy, double *csz, int nc0) {
+  k_coarsen_sep<<<(nc0 + 127) / 128, 128, 0, lc.s>>>(fsx, fsy, fsz, nf0, csx, csy, csz, nc0);
+  ++*lc.counter;
+}
+
+__global__ void k_sep_dinv(const double *sx, const double *sy, const double *sz, int n0, int dim, double *dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  if (i < 1 || i > n0 - 2) { dinv[i] = 0.0; return; }
+  double D = sx[i - 1] + sx[i] + sy[i] + sy[i];
+  if (dim == 3) D += sz[i] + sz[i];
+  dinv[i] = 1.0 / D;
+}
+void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const double *sz, int n0, int dim,
+                     double *dinv) {
+  k_sep_dinv<<<(n0 + 127) / 128, 128, 0, lc.s>>>(sx, sy, sz, n0, dim, dinv);
+  ++*lc.counter;
+}
+
+// coarse cell coefficient = mean of the 2^d child cells
+__global__ void k_coarsen_cell(Lev<double> F, Lev<double> C, const double *__restrict__ kf, double *__restrict__ kc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y, K = blockIdx.z;
+  int ncx = C.n0 - 1, ncy = C.per ? C.n1 : C.n1 - 1;
+  if (I >= ncx || J >= ncy) return;
+  int nz = C.dim == 3 ? 2 : 1;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a)
+        s += kf[(long long)(2 * K + (C.dim == 3 ? z : 0)) * F.plane + (long long)(2 * J + b) * F.pitch + 2 * I + a];
+  kc[(long long)K * C.plane + (long long)J * C.pitch + I] = s * (C.dim == 3 ? 0.125 : 0.25);
+}
+void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *kf, double *kc) {
+  int ncx = C.n0 - 1, ncy = C.per ? C.n1 : C.n1 - 1, ncz = C.dim == 3 ? C.n2 - 1 : 1;
+  dim3 gr((ncx + 127) / 128, ncy, ncz);
+  k_coarsen_cell<<<gr, 128, 0, lc.s>>>(F, C, kf, kc);
+  ++*lc.counter;
+}
+
+template <int DIM>
+__global__ void k_cell_dinv(Lev<double> L, double *__restrict__ dinv) {
+  int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r = blockIdx.y + (long long)blockIdx.z * gridDim.y;
+  if (r >= L.unk_rows()) return;
+  int j, k;
+  row_jk(L, r, j, k);
+  long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+  yoffs(L, j, dm, dp);
+  const double *kk = L.k;
+  double D;
+  if (DIM == 2) {
+    double sw = kk[p + dm - 1], se = kk[p + dm], nw = kk[p - 1], ne = kk[p];
+    D = L.ax * (sw + nw) + L.ax * (se + ne) + L.ay * (sw + se) + L.ay * (nw + ne);
+  } else {
+    long long pl = L.plane;
+    double sw0 = kk[p - pl + dm - 1], se0 = kk[p - pl + dm], nw0 = kk[p - pl - 1], ne0 = kk[p - pl];
+    double sw1 = kk[p + dm - 1], se1 = kk[p + dm], nw1 = kk[p - 1], ne1 = kk[p];
+    D = L.ax * ((sw0 + nw0) + (sw1 + nw1)) + L.ax * ((se0 + ne0) + (se1 + ne1)) +
+        L.ay * ((sw0 + se0) + (sw1 + se1)) + L.ay * ((nw0 + ne0) + (nw1 + ne1)) +
+        L.az * ((sw0 + se0) + (nw0 + ne0)) + L.az * ((sw1 + se1) + (nw1 + ne1));
+  }
+  dinv[p] = 1.0 / D;
+}
+void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
+  long long rows = L.unk_rows();
+  unsigned gy = (unsigned)(rows < 65535 ? rows : 65535), gz = (unsigned)((rows + gy - 1) / gy);
+  dim3 gr((L.xunk() + 127) / 128, gy, gz);
+  if (L.dim == 2) k_cell_dinv<2><<<gr, 128, 0, lc.s>>>(L, dinv);
+  else k_cell_dinv<3><<<gr, 128, 0, lc.s>>>(L, dinv);
+  ++*lc.counter;
+}
+
+__global__ void k_to_float(const double *__restrict__ s, float *__restrict__ d, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long st = (long long)gridDim.x * blockDim.x;
+  for (; t < n; t += st) d[t] = (float)s[t];
+}
+void launch_to_float(const Launch &lc, const double *src, float *dst, long long n) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_to_float<<<(unsigned)blocks, 256, 0, lc.s>>>(src, dst, n);
+  ++*lc.counter;
+}
+
+// ---------------------------------------------------------------------------------------
+// layout conversions (compact caller arrays <-> padded level arrays)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_pack(Lev<T> L, const double *__restrict__ src, T *__restrict__ dst, int zero_boundary) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y, k = blockIdx.z;
+  if (i >= L.n0) return;
+  long long s = ((long long)k * L.n1 + j) * L.n0 + i;
+  long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  bool bnd = (i == 0 || i == L.n0 - 1) || (!L.per && (j == 0 || j == L.n1 - 1)) ||
+             (L.dim == 3 && (k == 0 || k == L.n2 - 1));
+  dst[d] = (zero_boundary && bnd) ? T(0) : (T)src[s];
+}
+template <typename T>
+__global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict__ dst, double scale) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y, k = blockIdx.z;
+  if (i >= L.n0) return;
+  dst[((long long)k * L.n1 + j) * L.n0 + i] = scale * (double)src[(long long)k * L.plane + (long long)j * L.pitch + i];
+}
+template <typename T>
+__global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.pitch) return;
+  dst[(long long)blockIdx.z * L.plane + (long long)blockIdx.y * L.pitch + i] = T(0);
+}
+
+template <typename T>
+void launch_pack(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary) {
+  dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
+  k_pack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, zero_boundary);
+  ++*lc.counter;
+}
+template <typename T>
+void launch_unpack(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale) {
+  dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
+  k_unpack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, scale);
+  ++*lc.counter;
+}
+template <typename T>
+void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst) {
+  dim3 gr((unsigned)((L.pitch + 127) / 128), L.n1, L.dim == 3 ? L.n2 : 1);
+  k_zero_level<T><<<gr, 128, 0, lc.s>>>(L, dst);
+  ++*lc.counter;
+}
+
+// cell arrays: compact (ncz, ncy, n0-1) <-> node layout of the level
+__global__ void k_cell_pack(Lev<double> L, const double *__restrict__ src, double *__restrict__ dst, int dir) {
+  int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1;
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= ncx || j >= ncy) return;
+  long long c = ((long long)k * ncy + j) * ncx + i;
+  long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  if (dir == 0) dst[d] = src[c];
+  else dst[c] = src[d];
+}
+void launch_cell_pack(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst) {
+  int ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
+  dim3 gr((L.n0 - 1 + 127) / 128, ncy, ncz);
+  k_cell_pack<<<gr, 128, 0, lc.s>>>(L, src_compact, dst, 0);
+  ++*lc.counter;
+}
+void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact) {
+  int ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
+  dim3 gr((L.n0 - 1 + 127) / 128, ncy, ncz);
+  k_cell_pack<<<gr, 128, 0, lc.s>>>(L, src, dst_compact, 1);
+  ++*lc.counter;
+}
+
+#define INST(T)                                                                                              \
+  template void launch_restrict<T>(const Launch &, const Lev<T> &, const Lev<T> &, const T *, T *);          \
+  template void launch_prolong_add<T>(const Launch &, const Lev<T> &, const Lev<T> &, const T *, T *, T);    \
+  template void launch_coarse_apply<T>(const Launch &, const double *, const long long *, int, const T *, T *); \
+  template void launch_pack<T>(const Launch &, const Lev<T> &, const double *, T *, int);                    \
+  template void launch_unpack<T>(const Launch &, const Lev<T> &, const T *, double *, double);                       \
+  template void launch_zero_level<T>(const Launch &, const Lev<T> &, T *);
+INST(double)
+INST(float)
+template void launch_assemble_dense<double>(const Launch &, const Lev<double> &, int, const long long *, const int *,
+                                            int, double *);
+
+}  // namespace mg

@@ -1,0 +1,891 @@
+// mg_capi.cu -- host side of the solver: parameter checks, workspace layout,
+// set-up of the level hierarchy, the F-cycle schedule (captured as a CUDA graph)
+// and the C ABI declared in include/mg.h.
+//
+// The cycle follows Wallis (2008), section "The Multigrid Technique",
+// algorithm MG(l, u, g), run as the F-cycle of the abstract: F(l) = pre-smooth,
+// restrict the defect, F(l-1) from zero then V(l-1), correct with omega_l P e,
+// post-smooth; V(l) recurses once; level 1 is solved directly.  The transposed
+// cycle (adjoint solves) runs the same steps in reverse order, each transposed.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.cuh"
+
+using namespace mg;
+
+static const int MAXLEV = 16;
+
+// ---------------------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------------------
+struct Bump {
+  char *base;
+  size_t off;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? (T *)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+template <typename T>
+struct LevData {
+  T *u[2] = {nullptr, nullptr};
+  T *g = nullptr, *r = nullptr;
+  T *sx = nullptr, *sy = nullptr, *sz = nullptr, *sdinv = nullptr;
+  T *k = nullptr, *ndinv = nullptr;
+};
+
+struct LevGeom {
+  int n[3];
+  long long pitch, plane, count;   // elements per row / plane / array
+  double c[3], d, dinv;            // CONST
+  double ax, ay, az, h[3];         // CELL
+};
+
+struct mg_ctx {
+  mg_params P;
+  mg_coeffs K;
+  int L;
+  int kind;
+  LevGeom geo[MAXLEV + 1];
+  LevData<double> d64[MAXLEV + 1];
+  LevData<float> d32[MAXLEV + 1];
+  bool mixed;
+  // finest FP64 vectors of the mixed form
+  double *x64 = nullptr, *b64 = nullptr;
+  // scratch for reductions and scalars
+  double *partials = nullptr;
+  double *scal = nullptr;       // [0] bsq, [1] sq, [2] relres, [3..] spare
+  double *hist = nullptr;       // device history, max_cycles + 2
+  double *grad_tmp = nullptr;   // CELL gradient: padded dk
+  // coarsest grid
+  int nc = 0;
+  long long *cidx = nullptr;
+  int *cmap = nullptr;
+  double *Ainv = nullptr, *gjcol = nullptr;
+  // bookkeeping
+  int cur[MAXLEV + 1];          // current u buffer per level (schedule state)
+  long long launches = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // forward / transposed cycle + check
+  long long graph_kernels[2] = {0, 0};
+  double *h_relres = nullptr;   // pinned
+  // timing of finest-level smoothing launches
+  std::vector<cudaEvent_t> ev;  // pool: [0, 2048) direct launches, [2048, 4096) forward graph,
+                                // [4096, 6144) transposed graph
+  int ev_used = 0;
+  int ev_graph_n[2] = {0, 0};
+  double t_sum_ms = 0.0;
+  long long t_count = 0;
+  std::string err;
+};
+
+static size_t padded_pitch(int n0) { return (size_t)((n0 + 31) / 32) * 32; }
+
+static int coarsen_dims(const int nf[3], int dim, int per, int nc[3]) {
+  if ((nf[0] - 1) % 2 || nf[0] < 5) return 0;
+  nc[0] = (nf[0] - 1) / 2 + 1;
+  if (per) {
+    if (nf[1] % 2 || nf[1] < 4) return 0;
+    nc[1] = nf[1] / 2;
+  } else {
+    if ((nf[1] - 1) % 2 || nf[1] < 5) return 0;
+    nc[1] = (nf[1] - 1) / 2 + 1;
+  }
+  if (dim == 3) {
+    if ((nf[2] - 1) % 2 || nf[2] < 5) return 0;
+    nc[2] = (nf[2] - 1) / 2 + 1;
+  } else {
+    nc[2] = 1;
+  }
+  return 1;
+}
+
+static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
+  if (!p || !k) return MG_EINVAL;
+  if (p->dim != 2 && p->dim != 3) return MG_EINVAL;
+  if (p->levels < 1 || p->levels > MAXLEV) return MG_EINVAL;
+  if (p->smoother < MG_JACOBI || p->smoother > MG_ZEBRA_Y) return MG_EINVAL;
+  if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y)) return MG_EINVAL;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
+  if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
+  if (p->max_cycles < 0) return MG_EINVAL;
+  if (k->kind < MG_COEF_CONST || k->kind > MG_COEF_CELL) return MG_EINVAL;
+  if (k->kind == MG_COEF_SEPARABLE && (!k->sx || !k->sy || (p->dim == 3 && !k->sz))) return MG_EINVAL;
+  if (k->kind == MG_COEF_CELL && !k->k) return MG_EINVAL;
+  int n[3] = {p->n[0], p->n[1], p->dim == 3 ? p->n[2] : 1};
+  if (n[0] < 3 || n[1] < (p->periodic_y ? 2 : 3) || (p->dim == 3 && n[2] < 3)) return MG_EINVAL;
+  if (p->periodic_y && (n[1] % 2)) return MG_EINVAL;
+  if ((long long)n[0] * n[1] * n[2] > (1LL << 34)) return MG_EINVAL;
+  for (int l = 1; l < p->levels; ++l) {
+    int c[3];
+    if (!coarsen_dims(n, p->dim, p->periodic_y, c)) return MG_EINVAL;
+    memcpy(n, c, sizeof(n));
+  }
+  // coarsest grid solved with a dense inverse
+  long long nc = (long long)(n[0] - 2) * (p->periodic_y ? n[1] : n[1] - 2) * (p->dim == 3 ? n[2] - 2 : 1);
+  if (nc > 4096) return MG_EINVAL;
+  return MG_OK;
+}
+
+// Fill geometry; with ws == nullptr only sizes are computed.  Returns total bytes.
+static size_t layout(mg_ctx *c, char *ws) {
+  const mg_params &P = c->P;
+  Bump b{ws, 0};
+  int n[3] = {P.n[0], P.n[1], P.dim == 3 ? P.n[2] : 1};
+  double h[3] = {c->K.h[0], c->K.h[1], c->K.h[2]};
+  for (int l = c->L; l >= 1; --l) {
+    LevGeom &g = c->geo[l];
+    memcpy(g.n, n, sizeof(n));
+    g.pitch = (long long)padded_pitch(n[0]);
+    g.plane = g.pitch * n[1];
+    g.count = g.plane * n[2];
+    memcpy(g.h, h, sizeof(h));
+    if (l > 1) {
+      int cn[3];
+      coarsen_dims(n, P.dim, P.periodic_y, cn);
+      memcpy(n, cn, sizeof(n));
+      for (int d = 0; d < 3; ++d) h[d] *= 2.0;
+    }
+  }
+  for (int l = c->L; l >= 1; --l) {
+    LevGeom &g = c->geo[l];
+    size_t cnt = (size_t)g.count, n0 = (size_t)g.n[0];
+    LevData<double> &D = c->d64[l];
+    // FP64 coefficient data on every level (set-up and the FP64 coarsest solve use it)
+    if (c->kind == K_SEP) {
+      D.sx = b.take<double>(n0);
+      D.sy = b.take<double>(n0);
+      D.sz = b.take<double>(n0);
+      D.sdinv = b.take<double>(n0);
+    } else if (c->kind == K_CELL) {
+      D.k = b.take<double>(cnt);
+      D.ndinv = b.take<double>(cnt);
+    }
+    if (!c->mixed) {
+      D.u[0] = b.take<double>(cnt);
+      D.u[1] = b.take<double>(cnt);
+      D.g = b.take<double>(cnt);
+      D.r = b.take<double>(cnt);
+    } else {
+      LevData<float> &F = c->d32[l];
+      F.u[0] = b.take<float>(cnt);
+      F.u[1] = b.take<float>(cnt);
+      F.g = b.take<float>(cnt);
+      F.r = b.take<float>(cnt);
+      if (c->kind == K_SEP) {
+        F.sx = b.take<float>(n0);
+        F.sy = b.take<float>(n0);
+        F.sz = b.take<float>(n0);
+        F.sdinv = b.take<float>(n0);
+      } else if (c->kind == K_CELL) {
+        F.k = b.take<float>(cnt);
+        F.ndinv = b.take<float>(cnt);
+      }
+    }
+  }
+  size_t fine = (size_t)c->geo[c->L].count;
+  if (c->mixed) {
+    c->x64 = b.take<double>(fine);
+    c->b64 = b.take<double>(fine);
+    // FP64 scratch of the finest level for mg_apply and the gradient
+    c->d64[c->L].u[0] = b.take<double>(fine);
+    c->d64[c->L].g = b.take<double>(fine);
+    c->d64[c->L].r = b.take<double>(fine);
+  }
+  if (c->kind == K_CELL) c->grad_tmp = b.take<double>(fine);
+  c->partials = b.take<double>((size_t)norm_parts_count());
+  c->scal = b.take<double>(16);
+  c->hist = b.take<double>((size_t)P.max_cycles + 2);
+  // coarsest grid
+  const LevGeom &g1 = c->geo[1];
+  long long nc = (long long)(g1.n[0] - 2) * (P.periodic_y ? g1.n[1] : g1.n[1] - 2) * (P.dim == 3 ? g1.n[2] - 2 : 1);
+  c->nc = (int)nc;
+  c->cidx = b.take<long long>((size_t)nc);
+  c->cmap = b.take<int>((size_t)g1.count);
+  c->Ainv = b.take<double>((size_t)nc * nc);
+  c->gjcol = b.take<double>((size_t)nc);
+  return b.off + 256;
+}
+
+template <typename T>
+static Lev<T> make_lev(const mg_ctx *c, int l) {
+  const LevGeom &g = c->geo[l];
+  Lev<T> L;
+  memset(&L, 0, sizeof(L));
+  L.dim = c->P.dim;
+  L.n0 = g.n[0];
+  L.n1 = g.n[1];
+  L.n2 = g.n[2];
+  L.per = c->P.periodic_y ? 1 : 0;
+  L.pitch = g.pitch;
+  L.plane = g.plane;
+  L.cx = (T)g.c[0];
+  L.cy = (T)g.c[1];
+  L.cz = (T)g.c[2];
+  L.d = (T)g.d;
+  L.dinv = (T)g.dinv;
+  L.ax = (T)g.ax;
+  L.ay = (T)g.ay;
+  L.az = (T)g.az;
+  return L;
+}
+static Lev<double> lev64(const mg_ctx *c, int l) {
+  Lev<double> L = make_lev<double>(c, l);
+  const LevData<double> &D = c->d64[l];
+  L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
+  L.k = D.k; L.ndinv = D.ndinv;
+  return L;
+}
+static Lev<float> lev32(const mg_ctx *c, int l) {
+  Lev<float> L = make_lev<float>(c, l);
+  const LevData<float> &D = c->d32[l];
+  L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
+  L.k = D.k; L.ndinv = D.ndinv;
+  return L;
+}
+template <typename T> struct LevOf;
+template <> struct LevOf<double> {
+  static Lev<double> get(const mg_ctx *c, int l) { return lev64(c, l); }
+  static LevData<double> &data(mg_ctx *c, int l) { return c->d64[l]; }
+};
+template <> struct LevOf<float> {
+  static Lev<float> get(const mg_ctx *c, int l) { return lev32(c, l); }
+  static LevData<float> &data(mg_ctx *c, int l) { return c->d32[l]; }
+};
+
+#define CK(call)                                                         \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                             \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+      return MG_ECUDA;                                                   \
+    }                                                                    \
+  } while (0)
+
+static mg_status last_launch(mg_ctx *c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->err = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// the cycle schedule
+// ---------------------------------------------------------------------------------------
+struct Sched {
+  mg_ctx *c;
+  Launch lc;
+  bool timing;
+  int ev_base = 0;      // first event of this schedule's range in the pool
+  int *ev_next = nullptr;
+};
+
+static void record_event(Sched &S) {
+  mg_ctx *c = S.c;
+  if (!S.timing || !S.ev_next) return;
+  int idx = S.ev_base + *S.ev_next;
+  if (*S.ev_next >= 2046 || idx >= (int)c->ev.size()) return;
+  cudaEventRecord(c->ev[idx], S.lc.s);
+  ++*S.ev_next;
+}
+
+template <typename T>
+static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero_start) {
+  mg_ctx *c = S.c;
+  LevData<T> &D = LevOf<T>::data(c, l);
+  Lev<T> L = LevOf<T>::get(c, l);
+  T om = (T)c->P.omega;
+  int &cur = c->cur[l];
+  if (sweeps <= 0) {
+    if (zero_start) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+    return;
+  }
+  bool fine = (l == c->L) && S.timing;
+  int odd_guard = 0;
+  bool jac = c->P.smoother == MG_JACOBI;
+  bool line = c->P.smoother >= MG_LINE_X;
+  if (zero_start && !jac) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+  for (int s = 0; s < sweeps; ++s) {
+    if (fine && S.ev_next && *S.ev_next < 2046) {
+      record_event(S);
+      odd_guard = 1;
+    }
+    if (jac) {
+      if (zero_start && s == 0) launch_jacobi_zero<T>(L, c->kind, S.lc, g, D.u[1 - cur], om);
+      else launch_jacobi<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om);
+      cur = 1 - cur;
+    } else if (!line) {
+      int first = order;
+      launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, first);
+      launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, 1 - first);
+    } else {
+      int dir = (c->P.smoother == MG_LINE_X || c->P.smoother == MG_ZEBRA_X) ? 0 : 1;
+      int zebra = c->P.smoother >= MG_ZEBRA_X;
+      if (zebra) {
+        launch_line<T>(S.lc, L, c->kind, dir, 1, order, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+        launch_line<T>(S.lc, L, c->kind, dir, 1, 1 - order, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+      } else {
+        launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
+        cur = 1 - cur;
+      }
+    }
+    if (fine && odd_guard) {
+      record_event(S);
+      odd_guard = 0;
+    }
+  }
+}
+
+template <typename T>
+static void coarse_solve(Sched &S, const T *g) {
+  mg_ctx *c = S.c;
+  LevData<T> &D = LevOf<T>::data(c, 1);
+  launch_coarse_apply<T>(S.lc, c->Ainv, c->cidx, c->nc, g, D.u[c->cur[1]]);
+}
+
+// One cycle at level l on (u = current buffer of level l, g).  type 0 = F, 1 = V.
+template <typename T>
+static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool zero_start) {
+  mg_ctx *c = S.c;
+  if (l == 1) {
+    coarse_solve<T>(S, g);
+    return;
+  }
+  LevData<T> &D = LevOf<T>::data(c, l);
+  LevData<T> &Dc = LevOf<T>::data(c, l - 1);
+  Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
+  int npre = transposed ? c->P.nu2 : c->P.nu1, npost = transposed ? c->P.nu1 : c->P.nu2;
+  int order = transposed ? 1 : 0;
+  smooth<T>(S, l, g, npre, order, zero_start);
+  launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
+  launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
+  c->cur[l - 1] = 0;
+  if (type == 0) {
+    int first = transposed ? 1 : 0, second = transposed ? 0 : 1;
+    cycle<T>(S, l - 1, Dc.g, first, transposed, true);
+    if (l - 1 > 1) cycle<T>(S, l - 1, Dc.g, second, transposed, false);
+  } else {
+    cycle<T>(S, l - 1, Dc.g, 1, transposed, true);
+  }
+  launch_prolong_add<T>(S.lc, L, Lc, Dc.u[c->cur[l - 1]], D.u[c->cur[l]], (T)c->P.omega_corr);
+  smooth<T>(S, l, g, npost, order, false);
+}
+
+// Ensure the finest level's current buffer is buffer 0 at the end of a cycle.
+template <typename T>
+static void finest_to_zero(Sched &S) {
+  mg_ctx *c = S.c;
+  int L = c->L;
+  if (c->cur[L] != 0) {
+    LevData<T> &D = LevOf<T>::data(c, L);
+    cudaMemcpyAsync(D.u[0], D.u[1], sizeof(T) * (size_t)c->geo[L].count, cudaMemcpyDeviceToDevice, S.lc.s);
+    c->cur[L] = 0;
+  }
+}
+
+// FP64 form: one F-cycle on the finest level followed by the residual check.
+static void emit_fp64_cycle(Sched &S, int transposed) {
+  mg_ctx *c = S.c;
+  int L = c->L;
+  c->cur[L] = 0;
+  cycle<double>(S, L, c->d64[L].g, 0, transposed, false);
+  finest_to_zero<double>(S);
+  launch_defect_norm<double>(S.lc, lev64(c, L), c->kind, c->d64[L].u[0], c->d64[L].g, c->partials,
+                             norm_parts_count(), c->scal + 1);
+  launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+}
+
+// Mixed form: FP32 inner F-cycles on r32 from zero, FP64 update, FP64 defect and check.
+static void emit_mixed_step(Sched &S, int transposed) {
+  mg_ctx *c = S.c;
+  int L = c->L;
+  for (int q = 0; q < c->P.inner_cycles; ++q) {
+    c->cur[L] = 0;
+    cycle<float>(S, L, c->d32[L].g, 0, transposed, q == 0);
+    finest_to_zero<float>(S);
+  }
+  launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
+  launch_defect64_to32(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                       c->scal + 1);
+  launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+}
+
+static mg_status build_graph(mg_ctx *c, int transposed) {
+  if (c->gexec[transposed]) return MG_OK;
+  bool timing = (c->P.flags & MG_FLAG_TIMING) != 0;
+  c->ev_graph_n[transposed] = 0;
+  Sched S{c, Launch{c->cap, &c->launches}, timing, 2048 * (1 + transposed), &c->ev_graph_n[transposed]};
+  long long before = c->launches;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  if (c->mixed) emit_mixed_step(S, transposed);
+  else emit_fp64_cycle(S, transposed);
+  cudaGraph_t graph;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+  if (e != cudaSuccess) {
+    c->err = std::string("graph capture: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return MG_ECUDA;
+  }
+  c->graph_kernels[transposed] = c->launches - before;
+  c->launches = before;
+  e = cudaGraphInstantiate(&c->gexec[transposed], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    c->gexec[transposed] = nullptr;
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// set-up
+// ---------------------------------------------------------------------------------------
+static mg_status setup_levels(mg_ctx *c) {
+  Launch lc{c->stream, &c->launches};
+  const mg_params &P = c->P;
+  int L = c->L;
+  // geometry constants per level
+  for (int l = L; l >= 1; --l) {
+    LevGeom &g = c->geo[l];
+    double scale = std::ldexp(1.0, -2 * (L - l));   // CONST weights: 1/4 per coarsening
+    for (int d = 0; d < 3; ++d) g.c[d] = c->K.c[d] * scale;
+    if (P.dim == 2) g.c[2] = 0.0;
+    g.d = 2.0 * (g.c[0] + g.c[1] + g.c[2]);
+    g.dinv = 1.0 / g.d;
+    double f = (P.dim == 2) ? 0.5 : 0.25;
+    g.ax = f / (g.h[0] * g.h[0]);
+    g.ay = f / (g.h[1] * g.h[1]);
+    g.az = (P.dim == 3) ? f / (g.h[2] * g.h[2]) : 0.0;
+  }
+  // coefficient arrays
+  if (c->kind == K_SEP) {
+    LevData<double> &F = c->d64[L];
+    int n0 = c->geo[L].n[0];
+    CK(cudaMemsetAsync(F.sx, 0, sizeof(double) * n0, c->stream));
+    CK(cudaMemsetAsync(F.sz, 0, sizeof(double) * n0, c->stream));
+    CK(cudaMemcpyAsync(F.sx, c->K.sx, sizeof(double) * (n0 - 1), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(F.sy, c->K.sy, sizeof(double) * n0, cudaMemcpyDeviceToDevice, c->stream));
+    if (P.dim == 3) CK(cudaMemcpyAsync(F.sz, c->K.sz, sizeof(double) * n0, cudaMemcpyDeviceToDevice, c->stream));
+    for (int l = L; l > 1; --l) {
+      LevData<double> &A = c->d64[l], &B = c->d64[l - 1];
+      launch_coarsen_sep(lc, A.sx, A.sy, A.sz, c->geo[l].n[0], B.sx, B.sy, B.sz, c->geo[l - 1].n[0]);
+    }
+    for (int l = L; l >= 1; --l) {
+      LevData<double> &A = c->d64[l];
+      launch_sep_dinv(lc, A.sx, A.sy, A.sz, c->geo[l].n[0], P.dim, A.sdinv);
+    }
+  } else if (c->kind == K_CELL) {
+    for (int l = L; l >= 1; --l) CK(cudaMemsetAsync(c->d64[l].k, 0, sizeof(double) * c->geo[l].count, c->stream));
+    launch_cell_pack(lc, lev64(c, L), c->K.k, c->d64[L].k);
+    for (int l = L; l > 1; --l) launch_coarsen_cell(lc, lev64(c, l), lev64(c, l - 1), c->d64[l].k, c->d64[l - 1].k);
+    for (int l = L; l >= 1; --l) {
+      CK(cudaMemsetAsync(c->d64[l].ndinv, 0, sizeof(double) * c->geo[l].count, c->stream));
+      launch_cell_dinv(lc, lev64(c, l), c->d64[l].ndinv);
+    }
+  }
+  // work vectors start at zero (Dirichlet nodes stay zero for good)
+  for (int l = L; l >= 1; --l) {
+    size_t cnt = (size_t)c->geo[l].count;
+    if (!c->mixed) {
+      LevData<double> &D = c->d64[l];
+      for (double *p : {D.u[0], D.u[1], D.g, D.r}) CK(cudaMemsetAsync(p, 0, sizeof(double) * cnt, c->stream));
+    } else {
+      LevData<float> &D = c->d32[l];
+      for (float *p : {D.u[0], D.u[1], D.g, D.r}) CK(cudaMemsetAsync(p, 0, sizeof(float) * cnt, c->stream));
+      if (c->kind == K_SEP) {
+        size_t n0 = (size_t)c->geo[l].n[0];
+        launch_to_float(lc, c->d64[l].sx, D.sx, (long long)n0);
+        launch_to_float(lc, c->d64[l].sy, D.sy, (long long)n0);
+        launch_to_float(lc, c->d64[l].sz, D.sz, (long long)n0);
+        launch_to_float(lc, c->d64[l].sdinv, D.sdinv, (long long)n0);
+      } else if (c->kind == K_CELL) {
+        launch_to_float(lc, c->d64[l].k, D.k, (long long)cnt);
+        launch_to_float(lc, c->d64[l].ndinv, D.ndinv, (long long)cnt);
+      }
+    }
+  }
+  if (c->mixed) {
+    size_t fine = (size_t)c->geo[L].count;
+    for (double *p : {c->x64, c->b64, c->d64[L].u[0], c->d64[L].g, c->d64[L].r})
+      CK(cudaMemsetAsync(p, 0, sizeof(double) * fine, c->stream));
+  }
+  // coarsest grid: unknown index maps (built on the host: O(nodes of the coarsest grid))
+  {
+    const LevGeom &g = c->geo[1];
+    std::vector<long long> cidx;
+    std::vector<int> cmap((size_t)g.count, -1);
+    int kz0 = P.dim == 3 ? 1 : 0, kz1 = P.dim == 3 ? g.n[2] - 2 : 0;
+    int j0 = P.periodic_y ? 0 : 1, j1 = P.periodic_y ? g.n[1] - 1 : g.n[1] - 2;
+    for (int k = kz0; k <= kz1; ++k)
+      for (int j = j0; j <= j1; ++j)
+        for (int i = 1; i <= g.n[0] - 2; ++i) {
+          long long p = (long long)k * g.plane + (long long)j * g.pitch + i;
+          cmap[(size_t)p] = (int)cidx.size();
+          cidx.push_back(p);
+        }
+    c->nc = (int)cidx.size();
+    if (c->nc > 0) {
+      CK(cudaMemcpyAsync(c->cidx, cidx.data(), sizeof(long long) * cidx.size(), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->cmap, cmap.data(), sizeof(int) * cmap.size(), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemsetAsync(c->Ainv, 0, sizeof(double) * (size_t)c->nc * c->nc, c->stream));
+      launch_assemble_dense<double>(lc, lev64(c, 1), c->kind, c->cidx, c->cmap, c->nc, c->Ainv);
+      for (int k = 0; k < c->nc; ++k) launch_gj_step(lc, c->Ainv, c->gjcol, c->nc, k);
+    }
+    CK(cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
+  }
+  CK(cudaMemsetAsync(c->scal, 0, sizeof(double) * 16, c->stream));
+  mg_status st = last_launch(c);
+  if (st) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+size_t mg_workspace_bytes(const mg_params *p, const mg_coeffs *k) {
+  if (check_params(p, k) != MG_OK) return 0;
+  mg_ctx *c = new (std::nothrow) mg_ctx();
+  if (!c) return 0;
+  c->P = *p;
+  c->K = *k;
+  c->L = p->levels;
+  c->kind = k->kind;
+  c->mixed = p->precision == MG_MIXED;
+  size_t s = layout(c, nullptr);
+  delete c;
+  return s;
+}
+
+mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size_t ws_bytes, mg_ctx **out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  mg_status st = check_params(p, k);
+  if (st) return st;
+  if (!workspace || ((uintptr_t)workspace & 255)) return MG_EINVAL;
+  mg_ctx *c = new (std::nothrow) mg_ctx();
+  if (!c) return MG_ENOMEM;
+  c->P = *p;
+  if (c->P.inner_cycles < 1) c->P.inner_cycles = 1;
+  c->K = *k;
+  c->L = p->levels;
+  c->kind = k->kind;
+  c->mixed = p->precision == MG_MIXED;
+  c->stream = (cudaStream_t)p->stream;
+  size_t need = layout(c, nullptr);
+  if (ws_bytes < need) {
+    delete c;
+    return MG_EINVAL;
+  }
+  layout(c, (char *)workspace);
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&c->h_relres, sizeof(double) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MG_ECUDA;
+  }
+  if (p->flags & MG_FLAG_TIMING) {
+    c->ev.resize(6144);
+    for (auto &e : c->ev) cudaEventCreate(&e);
+  }
+  st = setup_levels(c);
+  if (st) {
+    *out = c;   // keep the error text available through mg_last_error
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx *c) {
+  if (!c) return;
+  for (int t = 0; t < 2; ++t)
+    if (c->gexec[t]) cudaGraphExecDestroy(c->gexec[t]);
+  for (auto &e : c->ev) cudaEventDestroy(e);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->h_relres) cudaFreeHost(c->h_relres);
+  delete c;
+}
+
+const char *mg_status_str(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "out of host memory";
+    case MG_ECUDA: return "CUDA error";
+    case MG_ENOCONV: return "maximum number of cycles reached";
+    case MG_EDIVERGED: return "residual norm not finite";
+    case MG_ETIMEOUT: return "device wait timed out";
+    case MG_EBOUNDS: return "index out of bounds";
+  }
+  return "unknown status";
+}
+
+const char *mg_last_error(const mg_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+long long mg_launch_count(const mg_ctx *c) { return c ? c->launches : 0; }
+
+mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]) {
+  if (!c || level < 1 || level > c->L || !n) return MG_EINVAL;
+  for (int d = 0; d < 3; ++d) n[d] = c->geo[level].n[d];
+  return MG_OK;
+}
+
+// read back the timing events recorded during the last cycle
+static void harvest_events(mg_ctx *c, int base, int n) {
+  for (int t = base; t + 1 < base + n; t += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[t], c->ev[t + 1]) == cudaSuccess) {
+      c->t_sum_ms += ms;
+      c->t_count++;
+    }
+  }
+  cudaGetLastError();
+}
+
+// Shared driver of mg_solve / mg_solve_adjoint.
+static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep, int transposed) {
+  auto t0 = std::chrono::steady_clock::now();
+  int L = c->L;
+  Launch lc{c->stream, &c->launches};
+  bool use_graph = !(c->P.flags & MG_FLAG_NO_GRAPH);
+  bool timing = (c->P.flags & MG_FLAG_TIMING) != 0;
+  bool launched = false;
+  Lev<double> F64 = lev64(c, L);
+  if (c->mixed) {
+    launch_pack<double>(lc, F64, b, c->b64, 1);
+    launch_pack<double>(lc, F64, x, c->x64, 1);
+    launch_norm_parts<double>(lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
+    launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
+  } else {
+    launch_pack<double>(lc, F64, b, c->d64[L].g, 1);
+    launch_pack<double>(lc, F64, x, c->d64[L].u[0], 1);
+    launch_norm_parts<double>(lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
+    launch_defect_norm<double>(lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
+                               c->scal + 1);
+  }
+  launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+  if (use_graph) {
+    mg_status st = build_graph(c, transposed);
+    if (st) return st;
+  }
+  std::vector<double> hist;
+  mg_status result = MG_OK;
+  double bsq = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (timing && launched) {
+      if (use_graph) harvest_events(c, 2048 * (1 + transposed), c->ev_graph_n[transposed]);
+      else harvest_events(c, 0, c->ev_used);
+      c->ev_used = 0;
+    }
+    mg_status st = last_launch(c);
+    if (st) return st;
+    bsq = c->h_relres[0];
+    double rr = c->h_relres[2];
+    if (bsq == 0.0) {
+      rr = 0.0;
+      hist.push_back(rr);
+      result = MG_OK;
+      break;
+    }
+    hist.push_back(rr);
+    if (!std::isfinite(rr)) { result = MG_EDIVERGED; break; }
+    if (rr <= tol) { result = MG_OK; break; }
+    if (it >= c->P.max_cycles) { result = MG_ENOCONV; break; }
+    if (use_graph) {
+      CK(cudaGraphLaunch(c->gexec[transposed], c->stream));
+      c->launches += c->graph_kernels[transposed];
+    } else {
+      c->ev_used = 0;
+      Sched S{c, lc, timing, 0, &c->ev_used};
+      if (c->mixed) emit_mixed_step(S, transposed);
+      else emit_fp64_cycle(S, transposed);
+    }
+    launched = true;
+  }
+  // write back the solution
+  if (bsq == 0.0) {
+    if (c->mixed) CK(cudaMemsetAsync(c->x64, 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
+    else CK(cudaMemsetAsync(c->d64[L].u[0], 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
+  }
+  launch_unpack<double>(lc, F64, c->mixed ? c->x64 : c->d64[L].u[0], x, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  mg_status st = last_launch(c);
+  if (st) return st;
+  if (rep) {
+    rep->cycles = it;
+    rep->relres = hist.back();
+    rep->rate = (it > 0 && hist[0] > 0.0) ? std::pow(hist.back() / hist[0], 1.0 / it) : 0.0;
+    rep->status = result;
+    if (rep->history)
+      for (int t = 0; t < (int)hist.size() && t < rep->history_cap; ++t) rep->history[t] = hist[t];
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+mg_status mg_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep) {
+  if (!c || !b || !x || !(tol >= 0.0)) return MG_EINVAL;
+  return run_solve(c, b, x, tol, rep, 0);
+}
+
+mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep) {
+  if (!c || !g || !lambda || !(tol >= 0.0)) return MG_EINVAL;
+  return run_solve(c, g, lambda, tol, rep, 1);
+}
+
+mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double *dk) {
+  if (!c || !u || !lambda || !dk) return MG_EINVAL;
+  if (c->kind != K_CELL) return MG_EINVAL;
+  int L = c->L;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> F = lev64(c, L);
+  double *ub = c->mixed ? c->d64[L].u[0] : c->d64[L].u[1];
+  double *lb = c->d64[L].r;
+  launch_pack<double>(lc, F, u, ub, 1);
+  launch_pack<double>(lc, F, lambda, lb, 1);
+  launch_grad_k(lc, F, ub, lb, c->grad_tmp);
+  launch_cell_unpack(lc, F, c->grad_tmp, dk);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au) {
+  if (!c || !u || !Au || level < 1 || level > c->L) return MG_EINVAL;
+  if (c->mixed && level != c->L) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> Lv = lev64(c, level);
+  LevData<double> &D = c->d64[level];
+  double *ub = c->mixed ? D.u[0] : D.u[1];
+  launch_pack<double>(lc, Lv, u, ub, 1);
+  CK(cudaMemsetAsync(D.g, 0, sizeof(double) * (size_t)c->geo[level].count, c->stream));
+  launch_defect<double>(lc, Lv, c->kind, ub, D.g, D.r);   // r = 0 - A u
+  launch_unpack<double>(lc, Lv, D.r, Au, -1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+static mg_status need_fp64(mg_ctx *c) {
+  if (!c) return MG_EINVAL;
+  if (c->mixed) return MG_EINVAL;
+  return MG_OK;
+}
+
+mg_status mg_step_smooth(mg_ctx *c, int level, const double *u, const double *g, double *out, int sweeps, int order) {
+  if (need_fp64(c) || level < 1 || level > c->L || !u || !g || !out || sweeps < 0) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> Lv = lev64(c, level);
+  LevData<double> &D = c->d64[level];
+  launch_pack<double>(lc, Lv, u, D.u[0], 1);
+  launch_pack<double>(lc, Lv, g, D.g, 1);
+  c->cur[level] = 0;
+  Sched S{c, lc, false};
+  smooth<double>(S, level, D.g, sweeps, order ? 1 : 0, false);
+  launch_unpack<double>(lc, Lv, D.u[c->cur[level]], out, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_step_defect(mg_ctx *c, int level, const double *u, const double *g, double *r) {
+  if (need_fp64(c) || level < 1 || level > c->L || !u || !g || !r) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> Lv = lev64(c, level);
+  LevData<double> &D = c->d64[level];
+  launch_pack<double>(lc, Lv, u, D.u[0], 1);
+  launch_pack<double>(lc, Lv, g, D.g, 1);
+  launch_defect<double>(lc, Lv, c->kind, D.u[0], D.g, D.r);
+  launch_unpack<double>(lc, Lv, D.r, r, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_step_restrict(mg_ctx *c, int level, const double *r, double *gc) {
+  if (need_fp64(c) || level < 2 || level > c->L || !r || !gc) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
+  launch_pack<double>(lc, F, r, c->d64[level].r, 1);
+  launch_restrict<double>(lc, F, C, c->d64[level].r, c->d64[level - 1].g);
+  launch_unpack<double>(lc, C, c->d64[level - 1].g, gc, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_step_prolong(mg_ctx *c, int level, const double *ec, const double *u, double *u_out, double w) {
+  if (need_fp64(c) || level < 2 || level > c->L || !ec || !u || !u_out) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
+  launch_pack<double>(lc, C, ec, c->d64[level - 1].u[0], 1);
+  launch_pack<double>(lc, F, u, c->d64[level].u[0], 1);
+  launch_prolong_add<double>(lc, F, C, c->d64[level - 1].u[0], c->d64[level].u[0], w);
+  launch_unpack<double>(lc, F, c->d64[level].u[0], u_out, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u) {
+  if (need_fp64(c) || !g || !u) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> C = lev64(c, 1);
+  launch_pack<double>(lc, C, g, c->d64[1].g, 1);
+  CK(cudaMemsetAsync(c->d64[1].u[0], 0, sizeof(double) * (size_t)c->geo[1].count, c->stream));
+  launch_coarse_apply<double>(lc, c->Ainv, c->cidx, c->nc, c->d64[1].g, c->d64[1].u[0]);
+  launch_unpack<double>(lc, C, c->d64[1].u[0], u, 1.0);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed) {
+  if (need_fp64(c) || !x || !b || !x_out) return MG_EINVAL;
+  int L = c->L;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> F = lev64(c, L);
+  launch_pack<double>(lc, F, b, c->d64[L].g, 1);
+  launch_pack<double>(lc, F, x, c->d64[L].u[0], 1);
+  Sched S{c, lc, false};
+  c->cur[L] = 0;
+  if (transposed) cycle<double>(S, L, c->d64[L].g, 0, 1, false);
+  else cycle<double>(S, L, c->d64[L].g, 0, 0, false);
+  launch_unpack<double>(lc, F, c->d64[L].u[c->cur[L]], x_out, 1.0);
+  c->cur[L] = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
+mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *bytes_per_launch) {
+  if (!c) return MG_EINVAL;
+  if (mean_ms) *mean_ms = c->t_count ? c->t_sum_ms / c->t_count : 0.0;
+  if (launches) *launches = (int)c->t_count;
+  if (bytes_per_launch) {
+    // algorithmic bytes of one finest-level smoothing sweep: read u, g, write u
+    const LevGeom &g = c->geo[c->L];
+    double unk = (double)(g.n[0] - 2) * (c->P.periodic_y ? g.n[1] : g.n[1] - 2) * (c->P.dim == 3 ? g.n[2] - 2 : 1);
+    double es = c->mixed ? 4.0 : 8.0;
+    *bytes_per_launch = 3.0 * es * unk;
+  }
+  c->t_sum_ms = 0.0;
+  c->t_count = 0;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// mg_internal.cuh -- device-side level view, stencil helpers and kernel launchers.
+//
+// Data layout in HBM (every level, both precisions): node (i, j, k) of level l
+// lives at  base + k * plane + j * pitch + i,  pitch = round_up(n0, 32)
+// elements, plane = pitch * n1, each array 256-byte aligned.  Dirichlet nodes
+// are stored and hold 0; kernels only ever write unknowns.  A periodic y
+// direction has n1 distinct rows and wraps.  Cell coefficients (per-cell k of
+// -div(k grad u)) use the node layout of their level, cell (i, j, k) spanning
+// nodes [i, i+1] x [j, j+1] x [k, k+1].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+enum Kind { K_CONST = 0, K_SEP = 1, K_CELL = 2 };
+
+// Everything a kernel needs to know about one level.  Passed by value.
+template <typename T>
+struct Lev {
+  int dim, n0, n1, n2, per;
+  long long pitch, plane;
+  // constant coefficients: edge weights, diagonal, its inverse
+  T cx, cy, cz, d, dinv;
+  // separable coefficients: per x-index arrays of length n0 (sx has n0-1 used entries)
+  const T *sx, *sy, *sz, *sdinv;
+  // cell coefficients: k per cell, 1/D per node, weight factors 1/(2h^2) (2-D) or 1/(4h^2) (3-D)
+  const T *k, *ndinv;
+  T ax, ay, az;
+
+  __host__ __device__ int ylo() const { return per ? 0 : 1; }
+  __host__ __device__ int yrows() const { return per ? n1 : n1 - 2; }
+  __host__ __device__ int zrows() const { return dim == 3 ? n2 - 2 : 1; }
+  __host__ __device__ long long unk_rows() const { return (long long)yrows() * zrows(); }
+  __host__ __device__ int xunk() const { return n0 - 2; }
+};
+
+// Offsets of the y neighbours of row j (periodic wrap).
+template <typename T>
+__device__ __forceinline__ void yoffs(const Lev<T> &L, int j, long long &dm, long long &dp) {
+  dm = -L.pitch;
+  dp = L.pitch;
+  if (L.per) {
+    if (j == 0) dm = (long long)(L.n1 - 1) * L.pitch;
+    if (j == L.n1 - 1) dp = -(long long)(L.n1 - 1) * L.pitch;
+  }
+}
+
+// Row index r in [0, unk_rows) -> (j, k) of an unknown row.
+template <typename T>
+__device__ __forceinline__ void row_jk(const Lev<T> &L, long long r, int &j, int &k) {
+  int yr = L.yrows();
+  j = L.ylo() + (int)(r % yr);
+  k = (L.dim == 3 ? 1 : 0) + (int)(r / yr);
+}
+
+// Edge weights around node p = (i, j, k): W, E (x), S, N (y), B, F (z), and 1/D.
+template <typename T, int DIM, int KIND>
+struct Weights {
+  T wW, wE, wS, wN, wB, wF, dinv;
+  __device__ __forceinline__ void load(const Lev<T> &L, int i, long long p, long long dm) {
+    if (KIND == K_CONST) {
+      wW = wE = L.cx;
+      wS = wN = L.cy;
+      wB = wF = L.cz;
+      dinv = L.dinv;
+    } else if (KIND == K_SEP) {
+      wW = L.sx[i - 1];
+      wE = L.sx[i];
+      wS = wN = L.sy[i];
+      wB = wF = L.sz[i];
+      dinv = L.sdinv[i];
+    } else {
+      // cells around node p: SW = (i-1, j-1), SE = (i, j-1), NW = (i-1, j), NE = (i, j)
+      const T *k = L.k;
+      if (DIM == 2) {
+        T sw = k[p + dm - 1], se = k[p + dm], nw = k[p - 1], ne = k[p];
+        wW = L.ax * (sw + nw);
+        wE = L.ax * (se + ne);
+        wS = L.ay * (sw + se);
+        wN = L.ay * (nw + ne);
+        wB = wF = T(0);
+      } else {
+        long long pl = L.plane;
+        T sw0 = k[p - pl + dm - 1], se0 = k[p - pl + dm], nw0 = k[p - pl - 1], ne0 = k[p - pl];
+        T sw1 = k[p + dm - 1], se1 = k[p + dm], nw1 = k[p - 1], ne1 = k[p];
+        wW = L.ax * ((sw0 + nw0) + (sw1 + nw1));
+        wE = L.ax * ((se0 + ne0) + (se1 + ne1));
+        wS = L.ay * ((sw0 + se0) + (sw1 + se1));
+        wN = L.ay * ((nw0 + ne0) + (nw1 + ne1));
+        wB = L.az * ((sw0 + se0) + (nw0 + ne0));
+        wF = L.az * ((sw1 + se1) + (nw1 + ne1));
+      }
+      dinv = L.ndinv[p];
+    }
+  }
+};
+
+// r_p = g_p - (A u)_p  =  g_p - D u_p + sum_q w_pq u_q, written as an FMA chain.
+template <typename T, int DIM, int KIND>
+__device__ __forceinline__ T residual_at(const Lev<T> &L, const Weights<T, DIM, KIND> &w, const T *__restrict__ u,
+                                         long long p, long long dm, long long dp, T gp) {
+  T up = u[p];
+  T s;
+  if (KIND == K_CONST) {
+    s = fma(-L.d, up, gp);
+  } else {
+    T D = (w.wW + w.wE) + (w.wS + w.wN);
+    if (DIM == 3) D += w.wB + w.wF;
+    s = fma(-D, up, gp);
+  }
+  s = fma(w.wW, u[p - 1], s);
+  s = fma(w.wE, u[p + 1], s);
+  s = fma(w.wS, u[p + dm], s);
+  s = fma(w.wN, u[p + dp], s);
+  if (DIM == 3) {
+    s = fma(w.wB, u[p - L.plane], s);
+    s = fma(w.wF, u[p + L.plane], s);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------------------
+
+struct Launch {
+  cudaStream_t s;
+  long long *counter;   // incremented once per kernel launch
+};
+
+template <typename T>
+void launch_jacobi(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega);
+template <typename T>
+void launch_jacobi_zero(const Lev<T> &L, int kind, const Launch &lc, const T *g, T *out, T omega);
+template <typename T>
+void launch_rb_half(const Launch &lc, const Lev<T> &L, int kind, T *u, const T *g, T omega, int colour);
+template <typename T>
+void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *r);
+// sum of squares over the unknowns -> *out_sq (deterministic: per-block partials, fixed-order finish)
+template <typename T>
+void launch_defect_norm(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, double *partials,
+                        int nparts, double *out_sq);
+template <typename T>
+void launch_norm_parts(const Launch &lc, const Lev<T> &L, const T *v, double *partials, int nparts, double *out_sq);
+template <typename T>
+void launch_restrict(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *rf, T *gc);
+template <typename T>
+void launch_prolong_add(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *ec, T *uf, T w);
+// line smoother (dir 0: x lines, 1: y lines); zebra = 1 updates the lines of one colour in
+// place (out == u), zebra = 0 is line Jacobi (out != u).  s1, s2: scratch arrays of the level.
+template <typename T>
+void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra, int colour, const T *u,
+                 const T *g, T *out, T omega, T *s1, T *s2);
+
+int norm_parts_count();
+void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq);
+
+// coarsest grid: u = A^{-1} g with a dense inverse (FP64), I/O in T
+template <typename T>
+void launch_coarse_apply(const Launch &lc, const double *Ainv, const long long *cidx, int nc, const T *g, T *u);
+template <typename T>
+void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const long long *cidx, const int *cmap,
+                           int nc, double *A);
+void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep);
+
+// setup
+void launch_coarsen_sep(const Launch &lc, const double *fsx, const double *fsy, const double *fsz, int nf0,
+                        double *csx, double *csy, double *csz, int nc0);
+void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const double *sz, int n0, int dim,
+                     double *dinv);
+void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *kf, double *kc);
+void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv);
+void launch_to_float(const Launch &lc, const double *src, float *dst, long long n);
+void launch_cell_pack(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst);
+void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact);
+
+// copies between compact user arrays and the padded layout
+template <typename T>
+void launch_pack(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary);
+template <typename T>
+void launch_unpack(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale);
+template <typename T>
+void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst);
+
+// mixed precision
+void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
+                          float *r32, double *partials, int nparts, double *out_sq);
+void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c);
+
+// gradient with respect to the cell field
+void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, const double *lam, double *dk);
+
+// finish kernel: relres = sqrt(sq) / bnorm, history, status word
+void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out);
+
+}  // namespace mg
