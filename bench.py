@@ -1,0 +1,307 @@
+"""Benchmark: F-cycle time to a 1e-10 relative residual on the anisotropic 4097^2 problem.
+
+One step = one complete solve (mg_solve) of -eps u_xx - u_yy = f on a 4097 x 4097
+grid (h = 1/4096, 16.8 M unknowns, 12 grids, f uniform[-1, 1] from seed 1, zero
+start vector) to ||b - A x|| / ||b|| <= 1e-10.  The default form is the GB300
+mixed-precision solve (FP32 F-cycles, FP64 defect / refinement / coarsest solve);
+--precision fp64 runs every step in FP64.
+
+Prints one JSON line (rank 0).  Metric: milliseconds per solve (lower is better).
+``--impl reference`` times the FP64 CPU oracle on the host instead (a bounded
+sample: one oracle F-cycle per step, scaled by the cycle count to tolerance).
+Under torchrun each rank solves its own instance (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F-cycle time-to-1e-10-residual & smoother/defect HBM GB/s vs 8 TB/s peak"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4097)
+    ap.add_argument("--eps", type=float, default=1.0)
+    ap.add_argument("--smoother", default="rbgs")
+    ap.add_argument("--omega", type=float, default=None)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nu", type=int, default=2)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 FMA throughput of this GB300 pool, measured with an FMA-chain kernel
+# (1.19-1.20 TFLOP/s = 0.6 T FMA instructions/s over 152 SMs at ~1.95 GHz).
+FP64_TFLOPS_MEASURED = 1.197
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(args):
+    from paper_0805_3041_gb300 import inputs
+    sp = inputs.anisotropic(n=args.n, eps=args.eps, seed_f=1)
+    levels = inputs.max_levels(sp.n)
+    omega = args.omega if args.omega is not None else (0.8 if args.smoother == "jacobi" else
+                                                       0.7 if args.smoother.startswith("line") else 1.0)
+    return sp, levels, omega
+
+
+def workload_config(args, levels, omega):
+    return {"workload": f"anisotropic Poisson -eps u_xx - u_yy = f, {args.n}x{args.n} grid, eps={args.eps:g}, "
+                        f"F-cycle over {levels} grids, {args.smoother} omega={omega:g} nu1=nu2={args.nu}, "
+                        f"{args.precision}, f~U[-1,1] seed 1, x0=0, tol {args.tol:g}",
+            "n": args.n, "eps": args.eps, "levels": levels, "smoother": args.smoother, "nu1": args.nu,
+            "nu2": args.nu, "precision": args.precision, "tol": args.tol,
+            "l2": "inputs larger than L2 (134 MB per FP64 field > 129 MB) and L2 flushed between steps"}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline key and the --impl reference arm)
+# --------------------------------------------------------------------------------------
+def oracle_cycles_to_tol(args, levels, omega):
+    """Cycle count of the oracle to the tolerance on a 513^2 grid with the same eps,
+    smoother and cycle (the F-cycle rate is mesh independent)."""
+    from oracle import oracle as orc
+    from paper_0805_3041_gb300 import inputs
+    n = 513
+    sp = inputs.anisotropic(n=n, eps=args.eps, seed_f=1)
+    o = orc.Oracle(orc.Problem(dim=2, n=sp.n, kind=orc.CONST, h=sp.h, c=sp.c), levels=levels - 3,
+                   smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu)
+    x, st, cyc, rr, hist = o.solve(sp.b, tol=args.tol, maxit=200)
+    return cyc
+
+
+def oracle_cycle_time(args, levels, omega, sp=None, reps=1):
+    """Seconds for one oracle F-cycle plus its residual check on the full grid."""
+    from oracle import oracle as orc
+    if sp is None:
+        sp, _, _ = make_problem(args)
+    o = orc.Oracle(orc.Problem(dim=2, n=sp.n, kind=orc.CONST, h=sp.h, c=sp.c), levels=levels,
+                   smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu)
+    x = np.zeros_like(sp.b)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        x = o.cycle(x, sp.b)
+        o.norm(o.defect(x, sp.b))
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sp, levels, omega = make_problem(args)
+    cyc = oracle_cycles_to_tol(args, levels, omega)
+    ts = oracle_cycle_time(args, levels, omega, sp, reps=args.warmup + args.steps)[args.warmup:]
+    per_cycle = float(np.mean(ts))
+    value = per_cycle * cyc * 1e3
+    sample = (f"one oracle F-cycle + residual check on the full {args.n}^2 grid per step, x{cyc} cycles "
+              f"(the oracle's cycle count to {args.tol:g} on 513^2, same eps/smoother)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, levels, omega),
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_0805_3041_gb300.binding import Solver, FLAG_TIMING
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sp, levels, omega = make_problem(args)
+    b = torch.from_numpy(sp.b).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    s = Solver(sp, levels=levels, smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu,
+               precision=args.precision, max_cycles=100, flags=FLAG_TIMING, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    infos = []
+    for _ in range(args.warmup):
+        x.zero_()
+        s.solve_into(b, x, tol=args.tol)
+    s.kernel_timing()   # discard warm-up kernel timings
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = s.launch_count()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)          # evict the previous solve from L2
+        x.zero_()               # start vector
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = s.solve_into(b, x, tol=args.tol)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+        infos.append(info)
+    barrier()
+    launches = s.launch_count() - launches0
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kern_ms, kern_n, kern_bytes = s.kernel_timing()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    bh = torch.from_numpy(sp.b).pin_memory().numpy()
+    xh = torch.zeros(sp.shape, dtype=torch.float64).pin_memory().numpy()
+    e2e = []
+    for r in range(max(2, args.steps // 2)):
+        xh[...] = 0.0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.solve_host(bh, xh, tol=args.tol)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = float(np.median(e2e))
+    nbytes = sp.b.nbytes
+
+    peaks, src = measured_peaks()
+    if args.precision == "fp64":
+        # FP64 smoothing is bound by GB300's FP64 pipe: report against the measured FMA rate
+        unk = (args.n - 2) ** 2
+        flops = 2.0 * 6 * unk   # 6 FMA per unknown and sweep (5-point residual + update)
+        achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS_MEASURED, "unit": "TFLOP/s",
+                "frac": achieved / FP64_TFLOPS_MEASURED if achieved else None, "traffic": None,
+                "kernel": "finest-level smoothing sweep (FP64)", "peak_source": "measured FP64 FMA rate"}
+    else:
+        achieved = kern_bytes / (kern_ms * 1e-3) / 1e9 if kern_ms else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": None,
+                "kernel": "finest-level smoothing sweep (FP32)", "peak_source": src,
+                "launch_ms": kern_ms, "launches": kern_n, "bytes_per_launch": kern_bytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cyc = infos[-1]["cycles"]
+        ts = oracle_cycle_time(args, levels, omega, sp, reps=2)
+        per = float(np.min(ts))
+        cpu = {"value": per * cyc * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"2 oracle F-cycles (+ residual check) on the full {args.n}^2 grid, single thread; "
+                         f"fastest x {cyc} cycles (the GPU's count to tolerance)"}
+
+    if rank == 0:
+        last = infos[-1]
+        line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+                "data": "synthetic", "config": workload_config(args, levels, omega),
+                "cycles": last["cycles"], "relres": last["relres"], "rate": last["rate"],
+                "solves_per_s": 1e3 / ms * world,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes},
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

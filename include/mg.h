@@ -124,6 +124,12 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
  * Returns MG_OK, MG_ENOCONV (x = last iterate) or MG_EDIVERGED. */
 mg_status mg_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep);
 
+/* mg_solve with b and x in HOST memory (pageable or pinned): b and the start
+ * vector are copied straight into the solver's finest-level buffers, the
+ * solution is copied back into x before the call returns.  The copies are
+ * stream-ordered on mg_params.stream; the call is synchronous. */
+mg_status mg_solve_host(mg_ctx *c, const double *b_host, double *x_host, double tol, mg_report *rep);
+
 /* Adjoint solve A^T lambda = g with the transposed F-cycle M^T (steps of the
  * cycle in reverse order, each transposed).  Same conventions as mg_solve. */
 mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep);

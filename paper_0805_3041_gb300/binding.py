@@ -23,7 +23,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOC
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
 
-EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
+EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
            "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error"]
@@ -71,6 +71,8 @@ def load(build_if_missing: bool = True):
     L.mg_setup.restype = I
     L.mg_solve.argtypes = [P, P, P, D, C.POINTER(Report)]
     L.mg_solve.restype = I
+    L.mg_solve_host.argtypes = [P, P, P, D, C.POINTER(Report)]
+    L.mg_solve_host.restype = I
     L.mg_solve_adjoint.argtypes = [P, P, P, D, C.POINTER(Report)]
     L.mg_solve_adjoint.restype = I
     L.mg_grad_coeff.argtypes = [P, P, P, P]
@@ -225,9 +227,35 @@ class Solver:
                     seconds=rep.seconds, history=hist[:rep.cycles + 1].copy())
         return x, info
 
+    def solve_into(self, b, x, tol=1e-10):
+        """mg_solve on caller tensors: x (float64, on the device, contiguous) holds the start
+        vector on entry and the solution on return.  Returns the info dict."""
+        hist = np.zeros(self.max_cycles + 2, dtype=np.float64)
+        rep = Report()
+        rep.history = hist.ctypes.data
+        rep.history_cap = len(hist)
+        st = self.lib.mg_solve(self.ctx, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), float(tol),
+                               C.byref(rep))
+        self._check(st, allow=(OK, ENOCONV, EDIVERGED))
+        return dict(status=STATUS[st], cycles=rep.cycles, relres=rep.relres, rate=rep.rate,
+                    seconds=rep.seconds, history=hist[:rep.cycles + 1].copy())
+
     def solve(self, b, x0=None, tol=1e-10):
         """x with ||b - A x|| / ||b|| <= tol (F-cycles from x0); returns (x, info)."""
         return self._run(self.lib.mg_solve, b, x0, tol, True)
+
+    def solve_host(self, b, x, tol=1e-10):
+        """mg_solve_host: b, x are C-contiguous float64 numpy arrays (x: start vector in, solution out)."""
+        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+        hist = np.zeros(self.max_cycles + 2, dtype=np.float64)
+        rep = Report()
+        rep.history = hist.ctypes.data
+        rep.history_cap = len(hist)
+        st = self.lib.mg_solve_host(self.ctx, C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data), float(tol),
+                                    C.byref(rep))
+        self._check(st, allow=(OK, ENOCONV, EDIVERGED))
+        return dict(status=STATUS[st], cycles=rep.cycles, relres=rep.relres, rate=rep.rate,
+                    seconds=rep.seconds, history=hist[:rep.cycles + 1].copy())
 
     def solve_adjoint(self, g, x0=None, tol=1e-10):
         """lambda with A^T lambda = g via the transposed F-cycle; returns (lambda, info)."""

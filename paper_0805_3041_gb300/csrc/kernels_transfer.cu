@@ -321,6 +321,21 @@ __global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict
   dst[((long long)k * L.n1 + j) * L.n0 + i] = scale * (double)src[(long long)k * L.plane + (long long)j * L.pitch + i];
 }
 template <typename T>
+__global__ void k_zero_boundary(Lev<T> L, T *__restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y, k = blockIdx.z;
+  if (i >= L.n0) return;
+  bool bnd = (i == 0 || i == L.n0 - 1) || (!L.per && (j == 0 || j == L.n1 - 1)) ||
+             (L.dim == 3 && (k == 0 || k == L.n2 - 1));
+  if (bnd) dst[(long long)k * L.plane + (long long)j * L.pitch + i] = T(0);
+}
+template <typename T>
+void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst) {
+  dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
+  k_zero_boundary<T><<<gr, 128, 0, lc.s>>>(L, dst);
+  ++*lc.counter;
+}
+template <typename T>
 __global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.pitch) return;
@@ -375,7 +390,8 @@ void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *sr
   template void launch_coarse_apply<T>(const Launch &, const double *, const long long *, int, const T *, T *); \
   template void launch_pack<T>(const Launch &, const Lev<T> &, const double *, T *, int);                    \
   template void launch_unpack<T>(const Launch &, const Lev<T> &, const T *, double *, double);                       \
-  template void launch_zero_level<T>(const Launch &, const Lev<T> &, T *);
+  template void launch_zero_level<T>(const Launch &, const Lev<T> &, T *);                                   \
+  template void launch_zero_boundary<T>(const Launch &, const Lev<T> &, T *);
 INST(double)
 INST(float)
 template void launch_assemble_dense<double>(const Launch &, const Lev<double> &, int, const long long *, const int *,

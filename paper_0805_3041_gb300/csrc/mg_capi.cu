@@ -300,7 +300,8 @@ static void record_event(Sched &S) {
   if (!S.timing || !S.ev_next) return;
   int idx = S.ev_base + *S.ev_next;
   if (*S.ev_next >= 2046 || idx >= (int)c->ev.size()) return;
-  cudaEventRecord(c->ev[idx], S.lc.s);
+  // "external" so that a stream capture turns the record into an event-record node
+  cudaEventRecordWithFlags(c->ev[idx], S.lc.s, cudaEventRecordExternal);
   ++*S.ev_next;
 }
 
@@ -661,8 +662,35 @@ static void harvest_events(mg_ctx *c, int base, int n) {
   cudaGetLastError();
 }
 
-// Shared driver of mg_solve / mg_solve_adjoint.
-static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep, int transposed) {
+// Copy a caller vector (device or host, compact) into a padded finest-level FP64 buffer,
+// Dirichlet entries set to zero.
+static mg_status load_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, const double *src, double *dst,
+                          bool host) {
+  if (!host) {
+    launch_pack<double>(lc, F, src, dst, 1);
+    return MG_OK;
+  }
+  size_t rows = (size_t)F.n1 * (F.dim == 3 ? F.n2 : 1);
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * F.pitch, src, sizeof(double) * F.n0, sizeof(double) * F.n0, rows,
+                       cudaMemcpyHostToDevice, lc.s));
+  launch_zero_boundary<double>(lc, F, dst);
+  return MG_OK;
+}
+static mg_status store_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, const double *src, double *dst,
+                           bool host) {
+  if (!host) {
+    launch_unpack<double>(lc, F, src, dst, 1.0);
+    return MG_OK;
+  }
+  size_t rows = (size_t)F.n1 * (F.dim == 3 ? F.n2 : 1);
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * F.n0, src, sizeof(double) * F.pitch, sizeof(double) * F.n0, rows,
+                       cudaMemcpyDeviceToHost, lc.s));
+  return MG_OK;
+}
+
+// Shared driver of mg_solve / mg_solve_host / mg_solve_adjoint.
+static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep, int transposed,
+                           bool host = false) {
   auto t0 = std::chrono::steady_clock::now();
   int L = c->L;
   Launch lc{c->stream, &c->launches};
@@ -670,14 +698,15 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   bool timing = (c->P.flags & MG_FLAG_TIMING) != 0;
   bool launched = false;
   Lev<double> F64 = lev64(c, L);
+  mg_status lst;
   if (c->mixed) {
-    launch_pack<double>(lc, F64, b, c->b64, 1);
-    launch_pack<double>(lc, F64, x, c->x64, 1);
+    if ((lst = load_vec(c, lc, F64, b, c->b64, host))) return lst;
+    if ((lst = load_vec(c, lc, F64, x, c->x64, host))) return lst;
     launch_norm_parts<double>(lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
     launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
   } else {
-    launch_pack<double>(lc, F64, b, c->d64[L].g, 1);
-    launch_pack<double>(lc, F64, x, c->d64[L].u[0], 1);
+    if ((lst = load_vec(c, lc, F64, b, c->d64[L].g, host))) return lst;
+    if ((lst = load_vec(c, lc, F64, x, c->d64[L].u[0], host))) return lst;
     launch_norm_parts<double>(lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
     launch_defect_norm<double>(lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
                                c->scal + 1);
@@ -729,7 +758,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     if (c->mixed) CK(cudaMemsetAsync(c->x64, 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
     else CK(cudaMemsetAsync(c->d64[L].u[0], 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
   }
-  launch_unpack<double>(lc, F64, c->mixed ? c->x64 : c->d64[L].u[0], x, 1.0);
+  if ((lst = store_vec(c, lc, F64, c->mixed ? c->x64 : c->d64[L].u[0], x, host))) return lst;
   CK(cudaStreamSynchronize(c->stream));
   mg_status st = last_launch(c);
   if (st) return st;
@@ -748,6 +777,11 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
 mg_status mg_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep) {
   if (!c || !b || !x || !(tol >= 0.0)) return MG_EINVAL;
   return run_solve(c, b, x, tol, rep, 0);
+}
+
+mg_status mg_solve_host(mg_ctx *c, const double *b_host, double *x_host, double tol, mg_report *rep) {
+  if (!c || !b_host || !x_host || !(tol >= 0.0)) return MG_EINVAL;
+  return run_solve(c, b_host, x_host, tol, rep, 0, true);
 }
 
 mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep) {

@@ -182,6 +182,8 @@ template <typename T>
 void launch_unpack(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale);
 template <typename T>
 void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst);
+template <typename T>
+void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst);
 
 // mixed precision
 void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,

@@ -139,7 +139,11 @@ def test_fixed_cycles_and_cycle_count(pair):
     xg4, info4 = s4.solve(sp.b, tol=0.0)
     assert info4["status"] == "MG_ENOCONV" and info4["cycles"] == 4
     assert rel(xg4, xo) <= 1e-11
-    assert np.allclose(info4["history"], ho, rtol=1e-9, atol=0)
+    # the computed residual carries a cancellation error ~ eps * || |A| |x| ||; relres differences
+    # between two correct FP64 implementations are bounded by a small multiple of that over ||b||
+    absAx = 2.0 * o.diag() * np.abs(xo)
+    bound = 64 * 2.2e-16 * np.linalg.norm(absAx) / o.norm(sp.b)
+    assert np.all(np.abs(info4["history"] - ho) <= 1e-12 * ho + bound)
     # same number of cycles to 1e-10 (unless a residual sits within 1e-3 of the tolerance)
     xo, sto, co, rro, ho = o.solve(sp.b, tol=1e-10, maxit=60)
     xg, info = s.solve(sp.b, tol=1e-10)
