@@ -68,6 +68,8 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 
 #define MG_FLAG_NO_GRAPH 1u   /* launch the cycle kernel by kernel instead of as a CUDA graph */
 #define MG_FLAG_TIMING   2u   /* record CUDA events around every finest-level smoothing launch */
+#define MG_FLAG_NO_FUSED_COARSE 4u  /* run every grid with per-step kernels (no single-CTA coarse cycle) */
+#define MG_FLAG_NO_FUSED_SWEEP  8u  /* 2-D: red-black half-sweep kernels and a separate defect / restriction */
 
 typedef struct {
   int dim;                /* 2 or 3 */

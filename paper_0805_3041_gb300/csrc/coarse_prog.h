@@ -1,0 +1,22 @@
+// coarse_prog.h -- step codes of the single-CTA coarse-cycle program (kernels_coarse.cu).
+// A program is an array of int4 {code, level, a, b}; the CTA runs the steps in order
+// with a barrier after each.
+#pragma once
+
+namespace mg {
+
+enum CoarseOp {
+  CP_LOAD_G = 1,    // g_y <- global g (padded layout of level y)
+  CP_LOAD_U = 2,    // u_y[a] <- global u
+  CP_STORE_U = 3,   // global u <- u_y[a] (unknowns)
+  CP_ZERO_U = 4,    // u_y[a] = 0
+  CP_JACOBI = 5,    // u_y[b] = u_y[a] + omega D^-1 (g - A u_y[a]);  a < 0: from a zero iterate
+  CP_RB_HALF = 6,   // red-black half sweep of colour a on u_y[b], in place
+  CP_LINE = 7,      // a = dir | zebra << 1 | colour << 2,  b = src | dst << 4 | scratch << 8
+  CP_DEFECT = 8,    // r_y = g_y - A u_y[a]
+  CP_RESTRICT = 9,  // g_{y-1} = R r_y
+  CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b]
+  CP_COARSE = 11    // u_1[a] = A_1^{-1} g_1
+};
+
+}  // namespace mg

@@ -1,0 +1,330 @@
+// kernels_coarse.cu -- the coarse end of the cycle in one CTA.
+//
+// Every grid at or below a cut-off level lc lives in shared memory (compact
+// layout, pitch = n0).  One CTA executes the whole recursive part of the cycle
+// below the finer grid that calls it -- pre-smoothing, defect, full-weighting
+// restriction, the coarsest solve A_1^{-1} g, bilinear/trilinear correction,
+// post-smoothing (Wallis 2008, section "The Multigrid Technique") -- as a
+// program of steps built on the host, with one __syncthreads() between steps.
+// This turns the ~L^2/2 coarse level visits of an F-cycle, each a handful of
+// latency-bound kernels, into a single launch per visit of level lc + 1.
+#include "mg_internal.cuh"
+#include "coarse_prog.h"
+
+namespace mg {
+
+template <typename T>
+struct SLev {
+  Lev<T> L;              // smem view: pitch = n0, k / ndinv point into shared memory
+  int off_u0, off_u1, off_g, off_r, off_k, off_dinv;   // element offsets into the smem pool
+  long long gpitch, gplane;                            // padded global layout of this level
+  const T *gk, *gdinv;                                 // global cell data (loaded at start)
+};
+
+template <typename T>
+__device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + off : nullptr; }
+
+// loop over the unknowns of a level (node index p, coordinates i, j, k)
+#define FOR_UNK(Lv, ...)                                                    \
+  {                                                                         \
+    int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows(), nz_ = (Lv).zrows();          \
+    int tot_ = nx_ * ny_ * nz_;                                             \
+    for (int t_ = threadIdx.x; t_ < tot_; t_ += blockDim.x) {               \
+      int i = 1 + t_ % nx_;                                                 \
+      int r_ = t_ / nx_;                                                    \
+      int j = (Lv).ylo() + r_ % ny_;                                        \
+      int k = ((Lv).dim == 3 ? 1 : 0) + r_ / ny_;                           \
+      long long p = (long long)k * (Lv).plane + (long long)j * (Lv).pitch + i; \
+      __VA_ARGS__                                                           \
+    }                                                                       \
+  }
+
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
+                                                       int nops, int lc, const T *__restrict__ g_in,
+                                                       const T *__restrict__ u_in, T *__restrict__ u_out,
+                                                       const double *__restrict__ Ainv,
+                                                       const long long *__restrict__ cidx_smem, int nc, T omega,
+                                                       T omega_corr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *pool = reinterpret_cast<T *>(smem_raw);
+  // zero all level arrays, load cell data
+  for (int l = 1; l <= lc; ++l) {
+    const SLev<T> &S = levs[l];
+    int cnt = (int)(S.L.plane * S.L.n2);
+    T *u0 = pool + S.off_u0, *u1 = pool + S.off_u1, *g = pool + S.off_g, *r = pool + S.off_r;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      u0[t] = T(0);
+      u1[t] = T(0);
+      g[t] = T(0);
+      r[t] = T(0);
+    }
+    if (KIND == K_CELL) {
+      T *kk = pool + S.off_k, *dv = pool + S.off_dinv;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        int i = t % S.L.n0, rr = t / S.L.n0, j = rr % S.L.n1, k = rr / S.L.n1;
+        long long gp = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+        kk[t] = S.gk[gp];
+        dv[t] = S.gdinv[gp];
+      }
+    }
+  }
+  __syncthreads();
+  for (int op = 0; op < nops; ++op) {
+    int4 o = prog[op];
+    const SLev<T> &S = levs[o.y];
+    Lev<T> L = S.L;
+    if (KIND == K_CELL) {
+      L.k = pool + S.off_k;
+      L.ndinv = pool + S.off_dinv;
+    }
+    T *ub[2] = {pool + S.off_u0, pool + S.off_u1};
+    T *g = pool + S.off_g, *r = pool + S.off_r;
+    switch (o.x) {
+      case CP_LOAD_G:
+        FOR_UNK(L, { g[p] = g_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
+        break;
+      case CP_LOAD_U:
+        FOR_UNK(L, { ub[o.z][p] = u_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
+        break;
+      case CP_STORE_U:
+        FOR_UNK(L, { u_out[(long long)k * S.gplane + (long long)j * S.gpitch + i] = ub[o.z][p]; });
+        break;
+      case CP_ZERO_U:
+        FOR_UNK(L, { ub[o.z][p] = T(0); });
+        break;
+      case CP_JACOBI: {   // z = src, w = dst; src < 0: zero iterate
+        const T *src = o.z >= 0 ? ub[o.z] : nullptr;
+        T *dst = ub[o.w];
+        FOR_UNK(L, {
+          long long dm, dp;
+          yoffs(L, j, dm, dp);
+          Weights<T, DIM, KIND> w;
+          w.load(L, i, p, dm);
+          if (src) dst[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, src, p, dm, dp, g[p]), src[p]);
+          else dst[p] = omega * w.dinv * g[p];
+        });
+        break;
+      }
+      case CP_RB_HALF: {   // z = colour, w = buffer
+        T *u = ub[o.w];
+        int colour = o.z;
+        FOR_UNK(L, {
+          if (((i + j + k) & 1) == colour) {
+            long long dm, dp;
+            yoffs(L, j, dm, dp);
+            Weights<T, DIM, KIND> w;
+            w.load(L, i, p, dm);
+            u[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]), u[p]);
+          }
+        });
+        break;
+      }
+      case CP_LINE: {   // z = dir | zebra << 1 | colour << 2, w = src | dst << 4 | scratch << 8
+        int dir = o.z & 1, zebra = (o.z >> 1) & 1, colour = (o.z >> 2) & 1;
+        T *src = ub[o.w & 15], *dst = ub[(o.w >> 4) & 15];
+        T *cps = r, *dps = ub[(o.w >> 8) & 15];
+        int nlines = dir == 0 ? (int)L.unk_rows() : (L.n0 - 2) * L.zrows();
+        for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
+          int m, a_fixed, kk;
+          long long base, stride;
+          if (dir == 0) {
+            int jj, k2;
+            row_jk(L, t, jj, k2);
+            if (zebra && ((jj + k2) & 1) != colour) continue;
+            m = L.n0 - 2;
+            base = (long long)k2 * L.plane + (long long)jj * L.pitch + 1;
+            stride = 1;
+            a_fixed = jj;
+            kk = k2;
+          } else {
+            int nx = L.n0 - 2;
+            int ii = 1 + t % nx, k2 = (DIM == 3 ? 1 : 0) + t / nx;
+            if (zebra && ((ii + k2) & 1) != colour) continue;
+            m = L.n1 - 2;
+            base = (long long)k2 * L.plane + L.pitch + ii;
+            stride = L.pitch;
+            a_fixed = ii;
+            kk = k2;
+          }
+          (void)kk;
+          T cprev = T(0), dprev = T(0);
+          for (int s = 0; s < m; ++s) {
+            long long p = base + s * stride;
+            int i = dir == 0 ? 1 + s : a_fixed;
+            int j = dir == 0 ? a_fixed : 1 + s;
+            long long dm, dp;
+            yoffs(L, j, dm, dp);
+            Weights<T, DIM, KIND> w;
+            w.load(L, i, p, dm);
+            T res = residual_at<T, DIM, KIND>(L, w, src, p, dm, dp, g[p]);
+            T D = (w.wW + w.wE) + (w.wS + w.wN);
+            if (DIM == 3) D += w.wB + w.wF;
+            if (KIND == K_CONST) D = L.d;
+            T lo = (s > 0) ? -(dir == 0 ? w.wW : w.wS) : T(0);
+            T up = (s < m - 1) ? -(dir == 0 ? w.wE : w.wN) : T(0);
+            T den = D - lo * cprev;
+            T cp = up / den;
+            T dpv = (res - lo * dprev) / den;
+            cps[p] = cp;
+            dps[p] = dpv;
+            cprev = cp;
+            dprev = dpv;
+          }
+          T x = T(0);
+          for (int s = m - 1; s >= 0; --s) {
+            long long p = base + s * stride;
+            x = dps[p] - cps[p] * x;
+            dst[p] = fma(omega, x, src[p]);
+          }
+        }
+        break;
+      }
+      case CP_DEFECT: {   // z = buffer
+        const T *u = ub[o.z];
+        FOR_UNK(L, {
+          long long dm, dp;
+          yoffs(L, j, dm, dp);
+          Weights<T, DIM, KIND> w;
+          w.load(L, i, p, dm);
+          r[p] = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+        });
+        break;
+      }
+      case CP_RESTRICT: {   // level y -> y-1 (r of level y into g of level y-1)
+        const SLev<T> &Cs = levs[o.y - 1];
+        Lev<T> C = Cs.L;
+        T *gc = pool + Cs.off_g;
+        FOR_UNK(C, {
+          int I = i, J = j, K = k;
+          long long dm, dp;
+          yoffs(L, 2 * J, dm, dp);
+          long long pf = (long long)(2 * K) * L.plane + (long long)(2 * J) * L.pitch + 2 * I;
+          auto row3 = [&](long long c) -> T { return (r[c - 1] + r[c + 1]) + T(2) * r[c]; };
+          auto plane3 = [&](long long c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
+          T s;
+          if (DIM == 2) s = plane3(pf) * T(0.0625);
+          else s = ((plane3(pf - L.plane) + plane3(pf + L.plane)) + T(2) * plane3(pf)) * T(0.015625);
+          gc[p] = s;
+        });
+        break;
+      }
+      case CP_PROLONG: {   // level y (fine), z = fine buffer, w = coarse buffer
+        const SLev<T> &Cs = levs[o.y - 1];
+        Lev<T> C = Cs.L;
+        const T *ec = (o.w ? pool + Cs.off_u1 : pool + Cs.off_u0);
+        T *uf = ub[o.z];
+        FOR_UNK(L, {
+          int I0 = i >> 1, I1 = (i + 1) >> 1;
+          int J0 = j >> 1, J1 = (j + 1) >> 1;
+          if (J1 >= C.n1) J1 -= C.n1;
+          long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+          T s;
+          if (DIM == 2) {
+            s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
+          } else {
+            long long z0 = (long long)(k >> 1) * C.plane, z1 = (long long)((k + 1) >> 1) * C.plane;
+            T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
+            T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
+            s = (s0 + s1) * T(0.125);
+          }
+          uf[p] = fma(omega_corr, s, uf[p]);
+        });
+        break;
+      }
+      case CP_COARSE: {   // level 1: u[z] = A^{-1} g, one warp per row of the dense inverse
+        T *u = ub[o.z];
+        int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int row = warp; row < nc; row += nw) {
+          const double *arow = Ainv + (long long)row * nc;
+          double s = 0.0;
+          for (int c = lane; c < nc; c += 32) s = fma(arow[c], (double)g[cidx_smem[c]], s);
+          for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, o2);
+          if (lane == 0) u[cidx_smem[row]] = (T)s;
+        }
+        break;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, const int4 *prog, int nops, int lcut,
+                         const T *g_in, const T *u_in, T *u_out, const double *Ainv, const long long *cidx_smem,
+                         int nc, T omega, T omega_corr, size_t smem_bytes) {
+#define CC_LAUNCH(D, K)                                                                                      \
+  do {                                                                                                       \
+    auto fn = k_coarse_cycle<T, D, K>;                                                                       \
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);                  \
+    fn<<<1, 1024, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,      \
+                                      cidx_smem, nc, omega, omega_corr);                                     \
+  } while (0)
+  if (dim == 2) {
+    if (kind == K_CONST) CC_LAUNCH(2, K_CONST);
+    else if (kind == K_SEP) CC_LAUNCH(2, K_SEP);
+    else CC_LAUNCH(2, K_CELL);
+  } else {
+    if (kind == K_CONST) CC_LAUNCH(3, K_CONST);
+    else if (kind == K_SEP) CC_LAUNCH(3, K_SEP);
+    else CC_LAUNCH(3, K_CELL);
+  }
+#undef CC_LAUNCH
+  ++*lc.counter;
+}
+
+template <typename T>
+size_t coarse_slev_size() {
+  return sizeof(SLev<T>);
+}
+
+// Fill the level descriptors (host): smem offsets in elements of T, returns the pool size in bytes.
+template <typename T>
+size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long long *gpitch, const long long *gplane,
+                          int kind) {
+  static_assert(sizeof(SLev<T>) <= 512, "level table slot");
+  SLev<T> *S = (SLev<T> *)out;
+  int off = 0;
+  auto take = [&](long long cnt) {
+    int o = off;
+    off += (int)((cnt + 3) / 4 * 4);
+    return o;
+  };
+  for (int l = 1; l <= lcut; ++l) {
+    SLev<T> &s = S[l];
+    s.L = glev[l];
+    s.L.pitch = s.L.n0;
+    s.L.plane = (long long)s.L.n0 * s.L.n1;
+    long long cnt = s.L.plane * s.L.n2;
+    s.gpitch = gpitch[l];
+    s.gplane = gplane[l];
+    s.gk = glev[l].k;
+    s.gdinv = glev[l].ndinv;
+    s.off_u0 = take(cnt);
+    s.off_u1 = take(cnt);
+    s.off_g = take(cnt);
+    s.off_r = take(cnt);
+    if (kind == K_CELL) {
+      s.off_k = take(cnt);
+      s.off_dinv = take(cnt);
+    } else {
+      s.off_k = s.off_dinv = -1;
+    }
+    s.L.k = nullptr;
+    s.L.ndinv = nullptr;
+  }
+  return (size_t)off * sizeof(T);
+}
+
+template void launch_coarse_cycle<double>(const Launch &, int, int, const void *, const int4 *, int, int, const double *,
+                                          const double *, double *, const double *, const long long *, int, double,
+                                          double, size_t);
+template void launch_coarse_cycle<float>(const Launch &, int, int, const void *, const int4 *, int, int, const float *,
+                                         const float *, float *, const double *, const long long *, int, float, float,
+                                         size_t);
+template size_t coarse_slev_size<double>();
+template size_t coarse_slev_size<float>();
+template size_t coarse_fill_levels<double>(void *, int, const Lev<double> *, const long long *, const long long *, int);
+template size_t coarse_fill_levels<float>(void *, int, const Lev<float> *, const long long *, const long long *, int);
+
+}  // namespace mg

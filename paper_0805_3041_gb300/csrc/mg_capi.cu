@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "coarse_prog.h"
 #include "mg_internal.cuh"
 
 using namespace mg;
@@ -74,6 +75,13 @@ struct mg_ctx {
   long long *cidx = nullptr;
   int *cmap = nullptr;
   double *Ainv = nullptr, *gjcol = nullptr;
+  // single-CTA coarse kernel: every grid <= lcut in shared memory (lcut = 0: not used)
+  int lcut = 0;
+  void *slev = nullptr;            // device table of shared-memory level views
+  int4 *prog = nullptr;            // device programs
+  int prog_off[8] = {0}, prog_len[8] = {0};
+  long long *cidx_s = nullptr;     // coarsest unknowns in the compact shared-memory layout
+  size_t csk_smem = 0;
   // bookkeeping
   int cur[MAXLEV + 1];          // current u buffer per level (schedule state)
   long long launches = 0;
@@ -217,6 +225,22 @@ static size_t layout(mg_ctx *c, char *ws) {
   c->cmap = b.take<int>((size_t)g1.count);
   c->Ainv = b.take<double>((size_t)nc * nc);
   c->gjcol = b.take<double>((size_t)nc);
+  // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
+  c->lcut = 0;
+  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE)) {
+    size_t es = c->mixed ? 4 : 8, arrays = 4 + (c->kind == K_CELL ? 2 : 0), total = 0;
+    long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
+    for (int l = 1; l <= c->L; ++l) {
+      long long nodes = (long long)c->geo[l].n[0] * c->geo[l].n[1] * c->geo[l].n[2];
+      total += arrays * (size_t)((nodes + 3) / 4 * 4) * es;
+      if (total > 200 * 1024 || nodes > cap) break;
+      c->lcut = l;
+    }
+    if (c->lcut < 2) c->lcut = 0;
+  }
+  c->slev = b.take<char>((size_t)(MAXLEV + 1) * 512);
+  c->prog = b.take<int4>(32768);
+  c->cidx_s = b.take<long long>((size_t)nc);
   return b.off + 256;
 }
 
@@ -305,22 +329,31 @@ static void record_event(Sched &S) {
   ++*S.ev_next;
 }
 
+// `sweeps` smoothing steps on level l.  With ec != nullptr the coarse-grid correction
+// u += omega_l P ec is applied first -- folded into the first fused red-black sweep when
+// there is one, as its own kernel otherwise.
 template <typename T>
-static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero_start) {
+static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero_start, const Lev<T> *Cp = nullptr,
+                   const T *ec = nullptr) {
   mg_ctx *c = S.c;
   LevData<T> &D = LevOf<T>::data(c, l);
   Lev<T> L = LevOf<T>::get(c, l);
-  T om = (T)c->P.omega;
+  T om = (T)c->P.omega, oc = (T)c->P.omega_corr;
   int &cur = c->cur[l];
+  bool jac = c->P.smoother == MG_JACOBI;
+  bool line = c->P.smoother >= MG_LINE_X;
+  bool rb2d = c->P.smoother == MG_RBGS && c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP);
+  if (ec && !(rb2d && sweeps > 0)) {
+    launch_prolong_add<T>(S.lc, L, *Cp, ec, D.u[cur], oc);
+    ec = nullptr;
+  }
   if (sweeps <= 0) {
     if (zero_start) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
     return;
   }
   bool fine = (l == c->L) && S.timing;
   int odd_guard = 0;
-  bool jac = c->P.smoother == MG_JACOBI;
-  bool line = c->P.smoother >= MG_LINE_X;
-  if (zero_start && !jac) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+  if (zero_start && !jac && !rb2d) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
   for (int s = 0; s < sweeps; ++s) {
     if (fine && S.ev_next && *S.ev_next < 2046) {
       record_event(S);
@@ -329,6 +362,10 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
     if (jac) {
       if (zero_start && s == 0) launch_jacobi_zero<T>(L, c->kind, S.lc, g, D.u[1 - cur], om);
       else launch_jacobi<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om);
+      cur = 1 - cur;
+    } else if (rb2d) {
+      int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
+      launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
       cur = 1 - cur;
     } else if (!line) {
       int first = order;
@@ -359,6 +396,102 @@ static void coarse_solve(Sched &S, const T *g) {
   launch_coarse_apply<T>(S.lc, c->Ainv, c->cidx, c->nc, g, D.u[c->cur[1]]);
 }
 
+// Programs of the single-CTA coarse kernel: 0..3 run the whole cycle on the finest grid
+// (when every grid fits in shared memory), 4..7 the coarse correction below lcut + 1.
+static int prog_id_fine(int zero, int tr) { return zero * 2 + tr; }
+static int prog_id_sub(int type, int tr) { return 4 + type * 2 + tr; }
+
+template <typename T>
+static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out) {
+  mg_ctx *c = S.c;
+  launch_coarse_cycle<T>(S.lc, c->P.dim, c->kind, c->slev, c->prog + c->prog_off[pid], c->prog_len[pid], c->lcut,
+                         g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)c->P.omega_corr,
+                         c->csk_smem);
+}
+
+// Host-side builder of the coarse programs: mirrors smooth() and cycle() step by step,
+// tracking which of the two u buffers of each level is current.
+struct ProgBuilder {
+  const mg_ctx *c;
+  std::vector<int4> ops;
+  int cur[MAXLEV + 1] = {0};
+  void op(int code, int lev, int a, int b) { ops.push_back(make_int4(code, lev, a, b)); }
+  void smooth(int l, int sweeps, int order, bool zero) {
+    int &cu = cur[l];
+    int sm = c->P.smoother;
+    if (sweeps <= 0) {
+      if (zero) op(CP_ZERO_U, l, cu, 0);
+      return;
+    }
+    if (sm == MG_JACOBI) {
+      for (int s = 0; s < sweeps; ++s) {
+        op(CP_JACOBI, l, (zero && s == 0) ? -1 : cu, 1 - cu);
+        cu = 1 - cu;
+      }
+      return;
+    }
+    if (zero) op(CP_ZERO_U, l, cu, 0);
+    if (sm == MG_RBGS) {
+      for (int s = 0; s < sweeps; ++s) {
+        op(CP_RB_HALF, l, order, cu);
+        op(CP_RB_HALF, l, 1 - order, cu);
+      }
+      return;
+    }
+    int dir = (sm == MG_LINE_X || sm == MG_ZEBRA_X) ? 0 : 1;
+    bool zebra = sm >= MG_ZEBRA_X;
+    for (int s = 0; s < sweeps; ++s) {
+      if (zebra) {
+        int bufs = cu | (cu << 4) | ((1 - cu) << 8);
+        op(CP_LINE, l, dir | 2 | (order << 2), bufs);
+        op(CP_LINE, l, dir | 2 | ((1 - order) << 2), bufs);
+      } else {
+        op(CP_LINE, l, dir, cu | ((1 - cu) << 4) | ((1 - cu) << 8));
+        cu = 1 - cu;
+      }
+    }
+  }
+  void cycle(int l, int type, int tr, bool zero) {
+    if (l == 1) {
+      op(CP_COARSE, 1, cur[1], 0);
+      return;
+    }
+    int npre = tr ? c->P.nu2 : c->P.nu1, npost = tr ? c->P.nu1 : c->P.nu2, order = tr ? 1 : 0;
+    smooth(l, npre, order, zero);
+    op(CP_DEFECT, l, cur[l], 0);
+    op(CP_RESTRICT, l, 0, 0);
+    cur[l - 1] = 0;
+    if (type == 0) {
+      cycle(l - 1, tr ? 1 : 0, tr, true);
+      if (l - 1 > 1) cycle(l - 1, tr ? 0 : 1, tr, false);
+    } else {
+      cycle(l - 1, 1, tr, true);
+    }
+    op(CP_PROLONG, l, cur[l], cur[l - 1]);
+    smooth(l, npost, order, false);
+  }
+  // coarse correction at level lc requested by a type-`type` cycle at lc + 1
+  void sub(int lc, int type, int tr) {
+    op(CP_LOAD_G, lc, 0, 0);
+    cur[lc] = 0;
+    if (type == 0) {
+      cycle(lc, tr ? 1 : 0, tr, true);
+      if (lc > 1) cycle(lc, tr ? 0 : 1, tr, false);
+    } else {
+      cycle(lc, 1, tr, true);
+    }
+    op(CP_STORE_U, lc, cur[lc], 0);
+  }
+  // one F-cycle on the finest grid L (= lc)
+  void fine(int L, int zero, int tr) {
+    op(CP_LOAD_G, L, 0, 0);
+    if (!zero) op(CP_LOAD_U, L, 0, 0);
+    cur[L] = 0;
+    cycle(L, 0, tr, zero != 0);
+    op(CP_STORE_U, L, cur[L], 0);
+  }
+};
+
 // One cycle at level l on (u = current buffer of level l, g).  type 0 = F, 1 = V.
 template <typename T>
 static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool zero_start) {
@@ -373,18 +506,24 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
   int npre = transposed ? c->P.nu2 : c->P.nu1, npost = transposed ? c->P.nu1 : c->P.nu2;
   int order = transposed ? 1 : 0;
   smooth<T>(S, l, g, npre, order, zero_start);
-  launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
-  launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
+  if (c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP)) {
+    launch_defect_restrict2d<T>(S.lc, L, Lc, c->kind, D.u[c->cur[l]], g, Dc.g);
+  } else {
+    launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
+    launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
+  }
   c->cur[l - 1] = 0;
-  if (type == 0) {
+  if (l - 1 == c->lcut) {
+    // the whole coarse correction below level l in one single-CTA launch
+    launch_csk<T>(S, prog_id_sub(type, transposed), Dc.g, nullptr, Dc.u[0]);
+  } else if (type == 0) {
     int first = transposed ? 1 : 0, second = transposed ? 0 : 1;
     cycle<T>(S, l - 1, Dc.g, first, transposed, true);
     if (l - 1 > 1) cycle<T>(S, l - 1, Dc.g, second, transposed, false);
   } else {
     cycle<T>(S, l - 1, Dc.g, 1, transposed, true);
   }
-  launch_prolong_add<T>(S.lc, L, Lc, Dc.u[c->cur[l - 1]], D.u[c->cur[l]], (T)c->P.omega_corr);
-  smooth<T>(S, l, g, npost, order, false);
+  smooth<T>(S, l, g, npost, order, false, &Lc, Dc.u[c->cur[l - 1]]);
 }
 
 // Ensure the finest level's current buffer is buffer 0 at the end of a cycle.
@@ -404,7 +543,8 @@ static void emit_fp64_cycle(Sched &S, int transposed) {
   mg_ctx *c = S.c;
   int L = c->L;
   c->cur[L] = 0;
-  cycle<double>(S, L, c->d64[L].g, 0, transposed, false);
+  if (c->lcut == L) launch_csk<double>(S, prog_id_fine(0, transposed), c->d64[L].g, c->d64[L].u[0], c->d64[L].u[0]);
+  else cycle<double>(S, L, c->d64[L].g, 0, transposed, false);
   finest_to_zero<double>(S);
   launch_defect_norm<double>(S.lc, lev64(c, L), c->kind, c->d64[L].u[0], c->d64[L].g, c->partials,
                              norm_parts_count(), c->scal + 1);
@@ -417,7 +557,10 @@ static void emit_mixed_step(Sched &S, int transposed) {
   int L = c->L;
   for (int q = 0; q < c->P.inner_cycles; ++q) {
     c->cur[L] = 0;
-    cycle<float>(S, L, c->d32[L].g, 0, transposed, q == 0);
+    if (c->lcut == L)
+      launch_csk<float>(S, prog_id_fine(q == 0 ? 1 : 0, transposed), c->d32[L].g, c->d32[L].u[0], c->d32[L].u[0]);
+    else
+      cycle<float>(S, L, c->d32[L].g, 0, transposed, q == 0);
     finest_to_zero<float>(S);
   }
   launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
@@ -549,6 +692,54 @@ static mg_status setup_levels(mg_ctx *c) {
       for (int k = 0; k < c->nc; ++k) launch_gj_step(lc, c->Ainv, c->gjcol, c->nc, k);
     }
     CK(cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
+  }
+  // single-CTA coarse kernel: level views, programs, coarsest indices in the compact layout
+  if (c->lcut) {
+    std::vector<char> tab((size_t)(MAXLEV + 1) * 512, 0);
+    long long gp[MAXLEV + 1], gpl[MAXLEV + 1];
+    for (int l = 1; l <= c->lcut; ++l) {
+      gp[l] = c->geo[l].pitch;
+      gpl[l] = c->geo[l].plane;
+    }
+    if (c->mixed) {
+      std::vector<Lev<float>> lv(MAXLEV + 1);
+      for (int l = 1; l <= c->lcut; ++l) lv[l] = lev32(c, l);
+      c->csk_smem = coarse_fill_levels<float>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind);
+    } else {
+      std::vector<Lev<double>> lv(MAXLEV + 1);
+      for (int l = 1; l <= c->lcut; ++l) lv[l] = lev64(c, l);
+      c->csk_smem = coarse_fill_levels<double>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind);
+    }
+    std::vector<int4> all;
+    for (int pid = 0; pid < 8; ++pid) {
+      ProgBuilder pb{c};
+      if (pid < 4) {
+        if (c->lcut != L) continue;
+        pb.fine(L, pid / 2, pid % 2);
+      } else {
+        if (c->lcut == L) continue;
+        pb.sub(c->lcut, (pid - 4) / 2, (pid - 4) % 2);
+      }
+      c->prog_off[pid] = (int)all.size();
+      c->prog_len[pid] = (int)pb.ops.size();
+      all.insert(all.end(), pb.ops.begin(), pb.ops.end());
+    }
+    if (all.size() > 32768) {
+      c->err = "coarse program too long";
+      return MG_EINVAL;
+    }
+    const LevGeom &g1 = c->geo[1];
+    std::vector<long long> cs;
+    int kz0 = P.dim == 3 ? 1 : 0, kz1 = P.dim == 3 ? g1.n[2] - 2 : 0;
+    int j0 = P.periodic_y ? 0 : 1, j1 = P.periodic_y ? g1.n[1] - 1 : g1.n[1] - 2;
+    for (int k = kz0; k <= kz1; ++k)
+      for (int j = j0; j <= j1; ++j)
+        for (int i = 1; i <= g1.n[0] - 2; ++i) cs.push_back(((long long)k * g1.n[1] + j) * g1.n[0] + i);
+    CK(cudaMemcpyAsync(c->slev, tab.data(), tab.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->prog, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice, c->stream));
+    if (!cs.empty())
+      CK(cudaMemcpyAsync(c->cidx_s, cs.data(), sizeof(long long) * cs.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
   }
   CK(cudaMemsetAsync(c->scal, 0, sizeof(double) * 16, c->stream));
   mg_status st = last_launch(c);

@@ -164,6 +164,28 @@ void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const lo
                            int nc, double *A);
 void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep);
 
+// fused 2-D kernels (kernels_fast.cu): a whole red-black sweep out of place (mode 0: plain,
+// 1: from a zero iterate, 2: u + omega_corr P ec applied while staging u), and the defect
+// fused with full-weighting restriction
+template <typename T>
+void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
+                 int mode, const Lev<T> *C, const T *ec, T omega_corr);
+template <typename T>
+void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
+                              T *gc);
+
+// single-CTA coarse cycle (kernels_coarse.cu): levs = device table of shared-memory level
+// views (filled by coarse_fill_levels), prog = program of CoarseOp steps
+template <typename T>
+void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, const int4 *prog, int nops, int lcut,
+                         const T *g_in, const T *u_in, T *u_out, const double *Ainv, const long long *cidx_smem,
+                         int nc, T omega, T omega_corr, size_t smem_bytes);
+template <typename T>
+size_t coarse_slev_size();
+template <typename T>
+size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long long *gpitch, const long long *gplane,
+                          int kind);
+
 // setup
 void launch_coarsen_sep(const Launch &lc, const double *fsx, const double *fsy, const double *fsz, int nf0,
                         double *csx, double *csy, double *csz, int nc0);

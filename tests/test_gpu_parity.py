@@ -72,6 +72,10 @@ CASES = [
     (3, (33, 17, 33), False, inputs.CONST, 3, "rbgs", 1.0),
     (3, (33, 16, 17), True, inputs.SEPARABLE, 3, "jacobi", 0.8),
     (3, (17, 17, 17), False, inputs.CELL, 3, "zebra_x", 1.0),
+    # every grid fits the single-CTA coarse cycle (the whole F-cycle runs in one launch)
+    (2, (33, 33), False, inputs.CONST, 4, "rbgs", 1.0),
+    (2, (17, 33), False, inputs.CELL, 3, "zebra_y", 1.0),
+    (2, (33, 16), True, inputs.SEPARABLE, 3, "jacobi", 0.8),
 ]
 
 
@@ -229,3 +233,58 @@ def test_nonfinite_rhs_reports_divergence():
     b[5, 5] = np.nan
     x, info = s.solve(b, tol=1e-10)
     assert info["status"] == "MG_EDIVERGED"
+
+
+# ---------------------------------------------------------------------------------------
+# alternative kernel paths give the same iterates
+# ---------------------------------------------------------------------------------------
+from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH  # noqa: E402
+
+FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP = 4, 8
+
+
+@pytest.mark.parametrize("flags", [FLAG_NO_GRAPH, FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP,
+                                   FLAG_NO_FUSED_COARSE | FLAG_NO_FUSED_SWEEP | FLAG_NO_GRAPH])
+@pytest.mark.parametrize("smoother", ["rbgs", "jacobi"])
+def test_kernel_paths_agree(flags, smoother):
+    rng = np.random.default_rng(11)
+    sp = spec_of(2, (257, 129), False, inputs.CONST, rng, eps=0.5)
+    om = 0.8 if smoother == "jacobi" else 1.0
+    a = Solver(sp, levels=7, smoother=smoother, omega=om, max_cycles=3)
+    b = Solver(sp, levels=7, smoother=smoother, omega=om, max_cycles=3, flags=flags)
+    xa, ia = a.solve(sp.b, tol=0.0)
+    xb, ib = b.solve(sp.b, tol=0.0)
+    assert rel(xa, xb.cpu().numpy()) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# mixed precision: FP32 cycles, FP64 defect / update / coarsest solve
+# ---------------------------------------------------------------------------------------
+MIXED = [
+    (2, (257, 257), False, inputs.CONST, 8, "rbgs", 1.0, 1.0),
+    (2, (257, 129), False, inputs.CONST, 7, "zebra_y", 1.0, 1e-3),
+    (2, (129, 128), True, inputs.SEPARABLE, 7, "rbgs", 1.0, 1.0),
+    (2, (129, 129), False, inputs.CELL, 7, "rbgs", 1.0, 1.0),
+    (3, (33, 33, 33), False, inputs.CONST, 4, "rbgs", 1.0, 1.0),
+    (2, (65, 65), False, inputs.CONST, 6, "jacobi", 0.8, 1.0),
+]
+
+
+@pytest.mark.parametrize("dim,n,per,kind,L,sm,om,eps", MIXED)
+def test_mixed_precision_reaches_fp64_residual(dim, n, per, kind, L, sm, om, eps):
+    """The refined solution meets the 1e-10 relative residual computed independently in FP64
+    (by the oracle's operator); its distance to the FP64 oracle solution is reported."""
+    rng = np.random.default_rng(12)
+    sp = spec_of(dim, n, per, kind, rng, eps=eps)
+    o = oracle_of(sp, L, sm, om)
+    s = Solver(sp, levels=L, smoother=sm, omega=om, precision="mixed", max_cycles=40)
+    x, info = s.solve(sp.b, tol=1e-10)
+    xn = x.cpu().numpy()
+    rr = o.norm(o.defect(xn, sp.b)) / o.norm(sp.b)
+    assert info["status"] == "MG_OK" and rr <= 1e-10, (info, rr)
+    assert abs(rr - info["relres"]) <= 1e-3 * rr + 1e-16
+    xo, st, co, rro, ho = o.solve(sp.b, tol=1e-13, maxit=200)
+    err = rel(xn, xo)
+    print(f"mixed vs FP64 oracle: max rel err {err:.2e}, refinement steps {info['cycles']} (FP64 cycles to 1e-10: "
+          f"{int(np.argmax(ho <= 1e-10))})")
+    assert err <= 1e-6
