@@ -24,20 +24,40 @@ struct SLev {
 template <typename T>
 __device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + off : nullptr; }
 
-// loop over the unknowns of a level (node index p, coordinates i, j, k)
-#define FOR_UNK(Lv, ...)                                                    \
-  {                                                                         \
-    int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows(), nz_ = (Lv).zrows();          \
-    int tot_ = nx_ * ny_ * nz_;                                             \
-    for (int t_ = threadIdx.x; t_ < tot_; t_ += blockDim.x) {               \
-      int i = 1 + t_ % nx_;                                                 \
-      int r_ = t_ / nx_;                                                    \
-      int j = (Lv).ylo() + r_ % ny_;                                        \
-      int k = ((Lv).dim == 3 ? 1 : 0) + r_ / ny_;                           \
-      long long p = (long long)k * (Lv).plane + (long long)j * (Lv).pitch + i; \
-      __VA_ARGS__                                                           \
-    }                                                                       \
+// loop over the unknowns of a level (node index p, coordinates i, j, k): warp w of the
+// CTA takes rows w, w + 32, ..., its lanes the x positions of the row (no divisions per node)
+#define FOR_UNK(Lv, ...)                                                                    \
+  {                                                                                         \
+    int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows();                                              \
+    int rows_ = ny_ * (Lv).zrows();                                                         \
+    for (int r_ = (int)(threadIdx.x >> 5); r_ < rows_; r_ += (int)(blockDim.x >> 5)) {      \
+      int j = (Lv).ylo() + (DIM == 3 ? r_ % ny_ : r_);                                      \
+      int k = DIM == 3 ? 1 + r_ / ny_ : 0;                                                  \
+      long long rowp_ = (long long)k * (Lv).plane + (long long)j * (Lv).pitch;              \
+      for (int i = 1 + (int)(threadIdx.x & 31); i <= nx_; i += 32) {                        \
+        long long p = rowp_ + i;                                                            \
+        __VA_ARGS__                                                                         \
+      }                                                                                     \
+    }                                                                                       \
   }
+// the same over the unknowns of one colour ((i + j + k) % 2 == colour)
+#define FOR_COLOUR(Lv, colour, ...)                                                         \
+  {                                                                                         \
+    int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows();                                              \
+    int rows_ = ny_ * (Lv).zrows();                                                         \
+    for (int r_ = (int)(threadIdx.x >> 5); r_ < rows_; r_ += (int)(blockDim.x >> 5)) {      \
+      int j = (Lv).ylo() + (DIM == 3 ? r_ % ny_ : r_);                                      \
+      int k = DIM == 3 ? 1 + r_ / ny_ : 0;                                                  \
+      long long rowp_ = (long long)k * (Lv).plane + (long long)j * (Lv).pitch;              \
+      int par_ = ((colour) + j + k + 1) & 1;                                                \
+      for (int i = 1 + par_ + 2 * (int)(threadIdx.x & 31); i <= nx_; i += 64) {             \
+        long long p = rowp_ + i;                                                            \
+        __VA_ARGS__                                                                         \
+      }                                                                                     \
+    }                                                                                       \
+  }
+
+static constexpr int CSK_STAGED_OPS = 1024;   // program steps staged in shared memory
 
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
@@ -48,6 +68,19 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
                                                        T omega_corr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *pool = reinterpret_cast<T *>(smem_raw);
+  // stage the level table and the program in shared memory (each step reads them)
+  __shared__ SLev<T> s_levs[17];
+  __shared__ int4 s_prog[CSK_STAGED_OPS];
+  {
+    const int *src = reinterpret_cast<const int *>(levs);
+    int *dst = reinterpret_cast<int *>(s_levs);
+    int nwords = (int)((lc + 1) * sizeof(SLev<T>) / sizeof(int));
+    for (int t = threadIdx.x; t < nwords; t += blockDim.x) dst[t] = src[t];
+    int nst = nops < CSK_STAGED_OPS ? nops : CSK_STAGED_OPS;
+    for (int t = threadIdx.x; t < nst; t += blockDim.x) s_prog[t] = prog[t];
+    __syncthreads();
+    levs = s_levs;
+  }
   // zero all level arrays, load cell data
   for (int l = 1; l <= lc; ++l) {
     const SLev<T> &S = levs[l];
@@ -71,7 +104,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
   }
   __syncthreads();
   for (int op = 0; op < nops; ++op) {
-    int4 o = prog[op];
+    int4 o = op < CSK_STAGED_OPS ? s_prog[op] : prog[op];
     const SLev<T> &S = levs[o.y];
     Lev<T> L = S.L;
     if (KIND == K_CELL) {
@@ -109,14 +142,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
       case CP_RB_HALF: {   // z = colour, w = buffer
         T *u = ub[o.w];
         int colour = o.z;
-        FOR_UNK(L, {
-          if (((i + j + k) & 1) == colour) {
-            long long dm, dp;
-            yoffs(L, j, dm, dp);
-            Weights<T, DIM, KIND> w;
-            w.load(L, i, p, dm);
-            u[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]), u[p]);
-          }
+        FOR_COLOUR(L, colour, {
+          long long dm, dp;
+          yoffs(L, j, dm, dp);
+          Weights<T, DIM, KIND> w;
+          w.load(L, i, p, dm);
+          u[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]), u[p]);
         });
         break;
       }

@@ -12,53 +12,53 @@
 //    the prolongation never makes its own pass over u).
 //  * k_defect_restrict2d: d = g - A u on a fine tile and g_c = R d (full
 //    weighting) of the 32 x 8 coarse nodes it covers, without writing d.
+//
+// All loops are row-per-warp (8 warps, lanes along x): no integer division per
+// element, one bounds / periodic-wrap decision per row, 128-byte aligned
+// main-body accesses with the halo columns loaded by a few lanes.
 #include "mg_internal.cuh"
 
 namespace mg {
 
 namespace {
-constexpr int TX = 64, TY = 16, HX = TX + 4, HY = TY + 4;   // RB tile and its halo-2 extent
-constexpr int CX = 32, CY = 8;                              // coarse tile of the defect/restriction
+constexpr int TX = 64, TY = 16;   // RB output tile
+constexpr int SX = TX + 5;        // smem row stride of the u tile (halo 2 + pad)
+constexpr int CX = 32, CY = 8;    // coarse tile of the defect/restriction
 
+// row pointer of node row j, or nullptr for a row outside a Dirichlet grid; periodic rows wrap
 template <typename T>
-__device__ __forceinline__ T load_or_zero(const T *__restrict__ a, const Lev<T> &L, int i, int j) {
-  if (i < 0 || i >= L.n0) return T(0);
+__device__ __forceinline__ const T *row_ptr(const T *a, const Lev<T> &L, int j) {
   if (L.per) {
-    j = (j % L.n1 + L.n1) % L.n1;
+    j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
+    if (j < 0 || j >= L.n1) j = ((j % L.n1) + L.n1) % L.n1;   // tiny periodic grids
   } else if (j < 0 || j >= L.n1) {
-    return T(0);
+    return nullptr;
   }
-  return a[(long long)j * L.pitch + i];
+  return a + (long long)j * L.pitch;
+}
+template <typename T>
+__device__ __forceinline__ int wrap_row(const Lev<T> &L, int j) {
+  if (!L.per) return j;
+  j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
+  if (j < 0 || j >= L.n1) j = ((j % L.n1) + L.n1) % L.n1;
+  return j;
+}
+template <typename T>
+__device__ __forceinline__ bool unk_row(const Lev<T> &L, int j) {
+  return L.per ? true : (j >= 1 && j <= L.n1 - 2);   // periodic rows outside [0, n1) are wrapped copies
+}
+template <typename T>
+__device__ __forceinline__ bool owned_row(const Lev<T> &L, int j) {
+  return L.per ? (j >= 0 && j < L.n1) : (j >= 1 && j <= L.n1 - 2);
 }
 
-// node (i, j) of the staged region is an unknown (a periodic row outside [0, n1) is the
-// wrapped copy of a real row and is relaxed like it)
-template <typename T>
-__device__ __forceinline__ bool unknown2d(const Lev<T> &L, int i, int j) {
-  return i >= 1 && i <= L.n0 - 2 && (L.per ? true : (j >= 1 && j <= L.n1 - 2));
-}
-// node (i, j) is an unknown owned by this tile (real rows only)
-template <typename T>
-__device__ __forceinline__ bool owned2d(const Lev<T> &L, int i, int j) {
-  return i >= 1 && i <= L.n0 - 2 && (L.per ? (j >= 0 && j < L.n1) : (j >= 1 && j <= L.n1 - 2));
-}
-
-// wrapped row offset of node row j (j may be -1 or n1 for a periodic grid)
-template <typename T>
-__device__ __forceinline__ long long row_of(const Lev<T> &L, int j) {
-  if (L.per) j = (j % L.n1 + L.n1) % L.n1;
-  return (long long)j * L.pitch;
-}
-
-// relax node (i, j) whose stencil values sit in shared memory at (r, c) of s (row stride SX)
-template <typename T, int KIND, int SX>
-__device__ __forceinline__ T relax_smem(const Lev<T> &L, const T (*s)[SX], int r, int c, T gp, int i, int j,
-                                        T omega) {
-  long long p = row_of(L, j) + i;
-  long long dm = row_of(L, j - 1) - row_of(L, j);
+// relax node (i, j) (smem position r, c of a tile with row stride S) with its weights
+template <typename T, int KIND, int S>
+__device__ __forceinline__ T relax_at(const Lev<T> &L, const T *s, int r, int c, T gp, int i, long long p,
+                                      long long dm, T omega) {
   Weights<T, 2, KIND> w;
   w.load(L, i, p, dm);
-  T uc = s[r][c];
+  T uc = s[r * S + c];
   T sum;
   if (KIND == K_CONST) {
     sum = fma(-L.d, uc, gp);
@@ -66,10 +66,10 @@ __device__ __forceinline__ T relax_smem(const Lev<T> &L, const T (*s)[SX], int r
     T D = (w.wW + w.wE) + (w.wS + w.wN);
     sum = fma(-D, uc, gp);
   }
-  sum = fma(w.wW, s[r][c - 1], sum);
-  sum = fma(w.wE, s[r][c + 1], sum);
-  sum = fma(w.wS, s[r - 1][c], sum);
-  sum = fma(w.wN, s[r + 1][c], sum);
+  sum = fma(w.wW, s[r * S + c - 1], sum);
+  sum = fma(w.wE, s[r * S + c + 1], sum);
+  sum = fma(w.wS, s[(r - 1) * S + c], sum);
+  sum = fma(w.wN, s[(r + 1) * S + c], sum);
   return fma(omega * w.dinv, sum, uc);
 }
 }  // namespace
@@ -79,56 +79,79 @@ template <typename T, int KIND, int MODE>
 __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                               T *__restrict__ out, T omega, int first, Lev<T> C,
                                               const T *__restrict__ ec, T omega_corr) {
-  __shared__ T su[HY][HX + 1];
-  __shared__ T sg[TY + 2][TX + 3];
-  const int tid = threadIdx.x;
+  __shared__ T su[(TY + 4) * SX];        // u rows j0-2 .. j0+TY+1, columns i0-2 .. i0+TX+1 at c = 0 .. TX+3
+  __shared__ T sg[(TY + 2) * SX];        // g rows j0-1 .. j0+TY, columns i0-1 .. i0+TX at c = 1 .. TX+2
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  // stage u (halo 2) and g (halo 1)
-  for (int e = tid; e < HY * HX; e += 256) {
-    int r = e / HX, cc = e % HX;
-    int i = i0 - 2 + cc, j = j0 - 2 + r;
-    T v = T(0);
-    if (MODE != 1) v = load_or_zero(u, L, i, j);
-    if (MODE == 2 && unknown2d(L, i, j)) {
-      int jw = L.per ? (j % L.n1 + L.n1) % L.n1 : j;
-      int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = jw >> 1, J1 = (jw + 1) >> 1;
-      if (J1 >= C.n1) J1 -= C.n1;
-      long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
-      T s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
-      v = fma(omega_corr, s, v);
+  const bool xin = (i0 >= 2) && (i0 + TX + 2 <= L.n0);   // every staged column exists
+  // ---- stage u (with the optional fused correction) ----
+  for (int r = warp; r < TY + 4; r += 8) {
+    int j = j0 - 2 + r;
+    const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
+    bool corr = (MODE == 2) && unk_row(L, j);
+    int jw = wrap_row(L, j);
+    int J0 = jw >> 1, J1 = (jw + 1) >> 1;
+    if (J1 >= C.n1) J1 -= C.n1;
+    const T *e0 = ec + (long long)J0 * C.pitch, *e1 = ec + (long long)J1 * C.pitch;
+    for (int c = lane; c < TX + 4; c += 32) {
+      int i = i0 - 2 + c;
+      bool inx = xin || (i >= 0 && i < L.n0);
+      T v = (rp && inx) ? rp[i] : T(0);
+      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2) {
+        int I0 = i >> 1, I1 = (i + 1) >> 1;
+        T s = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
+        v = fma(omega_corr, s, v);
+      }
+      su[r * SX + c] = v;
     }
-    su[r][cc] = v;
   }
-  for (int e = tid; e < (TY + 2) * (TX + 2); e += 256) {
-    int r = e / (TX + 2), cc = e % (TX + 2);
-    sg[r][cc] = load_or_zero(g, L, i0 - 1 + cc, j0 - 1 + r);
+  // ---- stage g ----
+  for (int r = warp; r < TY + 2; r += 8) {
+    const T *rp = row_ptr(g, L, j0 - 1 + r);
+    for (int c = lane; c < TX + 2; c += 32) {
+      int i = i0 - 1 + c;
+      bool inx = xin || (i >= 0 && i < L.n0);
+      sg[r * SX + c + 1] = (rp && inx) ? rp[i] : T(0);
+    }
   }
   __syncthreads();
-  // first colour on the tile plus a one-node ring (33 nodes of that colour per extended row)
-  for (int e = tid; e < (TY + 2) * 33; e += 256) {
-    int rr = e / 33, q = e % 33;
+  // ---- first colour on rows j0-1 .. j0+TY, columns i0-1 .. i0+TX ----
+  for (int rr = warp; rr < TY + 2; rr += 8) {
     int j = j0 - 1 + rr;
-    int i = i0 - 1 + 2 * q + ((first + i0 + 1 + j) & 1);
-    if (i > i0 + TX || !unknown2d(L, i, j)) continue;
-    int r = rr + 1, cc = i - i0 + 2;
-    su[r][cc] = relax_smem<T, KIND, HX + 1>(L, su, r, cc, sg[rr][i - i0 + 1], i, j, omega);
+    if (!unk_row(L, j)) continue;
+    int jw = wrap_row(L, j);
+    long long rowoff = (long long)jw * L.pitch;
+    long long dm = (long long)wrap_row(L, jw - 1) * L.pitch - rowoff;
+    int par = (first + i0 + 1 + j) & 1;   // i = i0 - 1 + 2q + par has colour `first`
+    for (int q = lane; q < TX / 2 + 1; q += 32) {
+      int i = i0 - 1 + 2 * q + par;
+      if (i < 1 || i > L.n0 - 2 || i > i0 + TX) continue;
+      int r = rr + 1, c = i - i0 + 2;
+      su[r * SX + c] = relax_at<T, KIND, SX>(L, su, r, c, sg[rr * SX + c], i, rowoff + i, dm, omega);
+    }
   }
   __syncthreads();
-  // second colour on the tile
-  for (int e = tid; e < TY * 32; e += 256) {
-    int rr = e / 32, q = e % 32;
+  // ---- second colour on the tile ----
+  for (int rr = warp; rr < TY; rr += 8) {
     int j = j0 + rr;
-    int i = i0 + 2 * q + ((1 - first + i0 + j) & 1);
-    if (!owned2d(L, i, j)) continue;
-    int r = rr + 2, cc = i - i0 + 2;
-    su[r][cc] = relax_smem<T, KIND, HX + 1>(L, su, r, cc, sg[rr + 1][i - i0 + 1], i, j, omega);
+    if (!owned_row(L, j)) continue;
+    long long rowoff = (long long)j * L.pitch;
+    long long dm = (long long)wrap_row(L, j - 1) * L.pitch - rowoff;
+    int i = i0 + 2 * lane + ((1 - first + i0 + j) & 1);
+    if (i < 1 || i > L.n0 - 2) continue;
+    int r = rr + 2, c = i - i0 + 2;
+    su[r * SX + c] = relax_at<T, KIND, SX>(L, su, r, c, sg[(rr + 1) * SX + c], i, rowoff + i, dm, omega);
   }
   __syncthreads();
-  // write the tile's unknowns
-  for (int e = tid; e < TY * TX; e += 256) {
-    int rr = e / TX, cc = e % TX;
-    int i = i0 + cc, j = j0 + rr;
-    if (owned2d(L, i, j)) out[(long long)j * L.pitch + i] = su[rr + 2][cc + 2];
+  // ---- write the tile's unknowns ----
+  for (int rr = warp; rr < TY; rr += 8) {
+    int j = j0 + rr;
+    if (!owned_row(L, j)) continue;
+    T *op = out + (long long)j * L.pitch;
+    for (int c = lane; c < TX; c += 32) {
+      int i = i0 + c;
+      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + 2) * SX + c + 2];
+    }
   }
 }
 
@@ -136,48 +159,58 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, const T *__restrict__ u,
                                                            const T *__restrict__ g, T *__restrict__ gc) {
   constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;   // fine defect region
-  __shared__ T su[RY + 2][RX + 3];
-  __shared__ T sr[RY][RX + 1];
-  const int tid = threadIdx.x;
+  constexpr int US = RX + 3;                        // smem stride
+  __shared__ T su[(RY + 2) * US];
+  __shared__ T sr[RY * US];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int I0 = blockIdx.x * CX, J0 = blockIdx.y * CY;
   const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;     // fine origin of the defect region
-  for (int e = tid; e < (RY + 2) * (RX + 2); e += 256) {
-    int r = e / (RX + 2), cc = e % (RX + 2);
-    su[r][cc] = load_or_zero(u, F, fi0 - 1 + cc, fj0 - 1 + r);
-  }
-  __syncthreads();
-  for (int e = tid; e < RY * RX; e += 256) {
-    int r = e / RX, cc = e % RX;
-    int i = fi0 + cc, j = fj0 + r;
-    T d = T(0);
-    if (unknown2d(F, i, j)) {
-      long long p = row_of(F, j) + i;
-      long long dm = row_of(F, j - 1) - row_of(F, j);
-      Weights<T, 2, KIND> w;
-      w.load(F, i, p, dm);
-      T uc = su[r + 1][cc + 1];
-      T s;
-      if (KIND == K_CONST) {
-        s = fma(-F.d, uc, g[p]);
-      } else {
-        T D = (w.wW + w.wE) + (w.wS + w.wN);
-        s = fma(-D, uc, g[p]);
-      }
-      s = fma(w.wW, su[r + 1][cc], s);
-      s = fma(w.wE, su[r + 1][cc + 2], s);
-      s = fma(w.wS, su[r][cc + 1], s);
-      s = fma(w.wN, su[r + 2][cc + 1], s);
-      d = s;
+  for (int r = warp; r < RY + 2; r += 8) {
+    const T *rp = row_ptr(u, F, fj0 - 1 + r);
+    for (int c = lane; c < RX + 2; c += 32) {
+      int i = fi0 - 1 + c;
+      su[r * US + c] = (rp && i >= 0 && i < F.n0) ? rp[i] : T(0);
     }
-    sr[r][cc] = d;
   }
   __syncthreads();
-  int I = I0 + (tid & 31), J = J0 + (tid >> 5);
+  for (int r = warp; r < RY; r += 8) {
+    int j = fj0 + r;
+    bool rowok = unk_row(F, j);
+    int jw = wrap_row(F, j);
+    long long rowoff = (long long)jw * F.pitch;
+    long long dm = (long long)wrap_row(F, jw - 1) * F.pitch - rowoff;
+    for (int c = lane; c < RX; c += 32) {
+      int i = fi0 + c;
+      T d = T(0);
+      if (rowok && i >= 1 && i <= F.n0 - 2) {
+        long long p = rowoff + i;
+        Weights<T, 2, KIND> w;
+        w.load(F, i, p, dm);
+        const T *s = su + (r + 1) * US + (c + 1);
+        T uc = s[0];
+        T sum;
+        if (KIND == K_CONST) {
+          sum = fma(-F.d, uc, g[p]);
+        } else {
+          T D = (w.wW + w.wE) + (w.wS + w.wN);
+          sum = fma(-D, uc, g[p]);
+        }
+        sum = fma(w.wW, s[-1], sum);
+        sum = fma(w.wE, s[1], sum);
+        sum = fma(w.wS, s[-US], sum);
+        sum = fma(w.wN, s[US], sum);
+        d = sum;
+      }
+      sr[r * US + c] = d;
+    }
+  }
+  __syncthreads();
+  int I = I0 + lane, J = J0 + warp;
   if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
-    int r = 2 * (J - J0) + 1, cc = 2 * (I - I0) + 1;   // centre of the stencil in sr
-    auto row3 = [&](int rr) -> T { return (sr[rr][cc - 1] + sr[rr][cc + 1]) + T(2) * sr[rr][cc]; };
-    T s = ((row3(r - 1) + row3(r + 1)) + T(2) * row3(r)) * T(0.0625);
-    gc[(long long)J * C.pitch + I] = s;
+    const T *s = sr + (2 * warp + 1) * US + (2 * lane + 1);   // centre of the stencil in sr
+    auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
+    T v = ((row3(s - US) + row3(s + US)) + T(2) * row3(s)) * T(0.0625);
+    gc[(long long)J * C.pitch + I] = v;
   }
 }
 
@@ -186,7 +219,8 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
                  int mode, const Lev<T> *C, const T *ec, T omega_corr) {
   dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + TY - 1) / TY);
   Lev<T> Cv = C ? *C : L;
-#define RB_L(K, M) k_rb2d<T, K, M><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, ec, omega_corr)
+  const T *e = ec ? ec : u;
+#define RB_L(K, M) k_rb2d<T, K, M><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr)
   if (kind == K_CONST) {
     if (mode == 0) RB_L(K_CONST, 0); else if (mode == 1) RB_L(K_CONST, 1); else RB_L(K_CONST, 2);
   } else if (kind == K_SEP) {

@@ -361,6 +361,72 @@ void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst) {
   ++*lc.counter;
 }
 
+// Axis-swapped copies (y-line smoothers run as x-line smoothers on the transposed
+// problem): internal node (i', j', k) <-> caller node (i = j', j = i', k).  32 x 32 tiles
+// through shared memory keep both sides coalesced.  rows_i, cols_i: internal extent of the
+// copied array (nodes: n1 x n0; cells: ncy x ncx), pitch_i / plane_i its padded layout;
+// the caller array is compact (cols_i x rows_i per plane).
+template <typename T, typename U>
+__global__ void k_transpose_copy(const U *__restrict__ src, T *__restrict__ dst, int rows_i, int cols_i,
+                                 long long pitch_i, long long plane_i, int to_internal, double scale) {
+  __shared__ double tile[32][33];
+  int k = blockIdx.z;
+  int bx = blockIdx.x * 32, by = blockIdx.y * 32;   // internal column / row origin
+  long long cplane = (long long)rows_i * cols_i;
+  if (to_internal) {
+    // read caller rows: caller row index = internal column i', caller column = internal row j'
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      int ic = bx + r, jr = by + threadIdx.x;       // internal (col ic, row jr)
+      if (ic < cols_i && jr < rows_i) tile[r][threadIdx.x] = (double)src[k * cplane + (long long)ic * rows_i + jr];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      int jr = by + r, ic = bx + threadIdx.x;
+      if (ic < cols_i && jr < rows_i) dst[k * plane_i + (long long)jr * pitch_i + ic] = (T)(scale * tile[threadIdx.x][r]);
+    }
+  } else {
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      int jr = by + r, ic = bx + threadIdx.x;
+      if (ic < cols_i && jr < rows_i) tile[r][threadIdx.x] = (double)src[k * plane_i + (long long)jr * pitch_i + ic];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      int ic = bx + r, jr = by + threadIdx.x;
+      if (ic < cols_i && jr < rows_i) dst[k * cplane + (long long)ic * rows_i + jr] = (T)(scale * tile[threadIdx.x][r]);
+    }
+  }
+}
+
+template <typename T>
+void launch_pack_swapped(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary) {
+  dim3 gr((L.n0 + 31) / 32, (L.n1 + 31) / 32, L.dim == 3 ? L.n2 : 1), bl(32, 8);
+  k_transpose_copy<T, double><<<gr, bl, 0, lc.s>>>(src, dst, L.n1, L.n0, L.pitch, L.plane, 1, 1.0);
+  ++*lc.counter;
+  if (zero_boundary) launch_zero_boundary<T>(lc, L, dst);
+}
+template <typename T>
+void launch_unpack_swapped(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale) {
+  dim3 gr((L.n0 + 31) / 32, (L.n1 + 31) / 32, L.dim == 3 ? L.n2 : 1), bl(32, 8);
+  k_transpose_copy<double, T><<<gr, bl, 0, lc.s>>>(src, dst, L.n1, L.n0, L.pitch, L.plane, 0, scale);
+  ++*lc.counter;
+}
+void launch_cell_pack_swapped(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst) {
+  int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
+  dim3 gr((ncx + 31) / 32, (ncy + 31) / 32, ncz), bl(32, 8);
+  k_transpose_copy<double, double><<<gr, bl, 0, lc.s>>>(src_compact, dst, ncy, ncx, L.pitch, L.plane, 1, 1.0);
+  ++*lc.counter;
+}
+void launch_cell_unpack_swapped(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact) {
+  int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
+  dim3 gr((ncx + 31) / 32, (ncy + 31) / 32, ncz), bl(32, 8);
+  k_transpose_copy<double, double><<<gr, bl, 0, lc.s>>>(src, dst_compact, ncy, ncx, L.pitch, L.plane, 0, 1.0);
+  ++*lc.counter;
+}
+template void launch_pack_swapped<double>(const Launch &, const Lev<double> &, const double *, double *, int);
+template void launch_pack_swapped<float>(const Launch &, const Lev<float> &, const double *, float *, int);
+template void launch_unpack_swapped<double>(const Launch &, const Lev<double> &, const double *, double *, double);
+template void launch_unpack_swapped<float>(const Launch &, const Lev<float> &, const float *, double *, double);
+
 // cell arrays: compact (ncz, ncy, n0-1) <-> node layout of the level
 __global__ void k_cell_pack(Lev<double> L, const double *__restrict__ src, double *__restrict__ dst, int dir) {
   int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1;

@@ -82,6 +82,9 @@ struct mg_ctx {
   int prog_off[8] = {0}, prog_len[8] = {0};
   long long *cidx_s = nullptr;     // coarsest unknowns in the compact shared-memory layout
   size_t csk_smem = 0;
+  // y-line smoothers run as x-line smoothers on the axis-swapped problem: internal node
+  // (i, j, k) is the caller's (j, i, k); only the copies in and out see the difference
+  bool swap = false;
   // bookkeeping
   int cur[MAXLEV + 1];          // current u buffer per level (schedule state)
   long long launches = 0;
@@ -233,7 +236,7 @@ static size_t layout(mg_ctx *c, char *ws) {
     for (int l = 1; l <= c->L; ++l) {
       long long nodes = (long long)c->geo[l].n[0] * c->geo[l].n[1] * c->geo[l].n[2];
       total += arrays * (size_t)((nodes + 3) / 4 * 4) * es;
-      if (total > 200 * 1024 || nodes > cap) break;
+      if (total > 190 * 1024 || nodes > cap) break;   // + ~21 KB of static shared memory
       c->lcut = l;
     }
     if (c->lcut < 2) c->lcut = 0;
@@ -273,6 +276,37 @@ static Lev<double> lev64(const mg_ctx *c, int l) {
   L.k = D.k; L.ndinv = D.ndinv;
   return L;
 }
+// Line smoothers along y on constant or cell coefficients are run along x on the
+// axis-swapped problem (contiguous lines; the x-line kernel keeps a line in shared
+// memory).  Separable coefficients depend on x only and keep their y-line kernel.
+static void apply_swap(mg_ctx *c) {
+  mg_params &P = c->P;
+  bool yline = P.smoother == MG_LINE_Y || P.smoother == MG_ZEBRA_Y;
+  if (!yline || c->kind == K_SEP || P.periodic_y) return;
+  c->swap = true;
+  int t = P.n[0];
+  P.n[0] = P.n[1];
+  P.n[1] = t;
+  double a = c->K.c[0];
+  c->K.c[0] = c->K.c[1];
+  c->K.c[1] = a;
+  a = c->K.h[0];
+  c->K.h[0] = c->K.h[1];
+  c->K.h[1] = a;
+  P.smoother = P.smoother == MG_LINE_Y ? MG_LINE_X : MG_ZEBRA_X;
+}
+
+// caller layout <-> internal padded layout (transposing when the axes are swapped)
+static void pack_in(mg_ctx *c, const Launch &lc, const Lev<double> &L, const double *src, double *dst, int zb) {
+  if (c->swap) launch_pack_swapped<double>(lc, L, src, dst, zb);
+  else launch_pack<double>(lc, L, src, dst, zb);
+}
+static void unpack_out(mg_ctx *c, const Launch &lc, const Lev<double> &L, const double *src, double *dst,
+                       double scale) {
+  if (c->swap) launch_unpack_swapped<double>(lc, L, src, dst, scale);
+  else launch_unpack<double>(lc, L, src, dst, scale);
+}
+
 static Lev<float> lev32(const mg_ctx *c, int l) {
   Lev<float> L = make_lev<float>(c, l);
   const LevData<float> &D = c->d32[l];
@@ -374,11 +408,17 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
     } else {
       int dir = (c->P.smoother == MG_LINE_X || c->P.smoother == MG_ZEBRA_X) ? 0 : 1;
       int zebra = c->P.smoother >= MG_ZEBRA_X;
+      // x lines: one CTA per line (partition + PCR); y lines and very long lines: one thread per line
+      bool fast = dir == 0 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && L.n0 - 2 <= 4096;
       if (zebra) {
-        launch_line<T>(S.lc, L, c->kind, dir, 1, order, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
-        launch_line<T>(S.lc, L, c->kind, dir, 1, 1 - order, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+        for (int col = 0; col < 2; ++col) {
+          int colour = col == 0 ? order : 1 - order;
+          if (!(fast && launch_xline<T>(S.lc, L, c->kind, 1, colour, D.u[cur], g, D.u[cur], om)))
+            launch_line<T>(S.lc, L, c->kind, dir, 1, colour, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+        }
       } else {
-        launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
+        if (!(fast && launch_xline<T>(S.lc, L, c->kind, 0, 0, D.u[cur], g, D.u[1 - cur], om)))
+          launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
         cur = 1 - cur;
       }
     }
@@ -636,7 +676,8 @@ static mg_status setup_levels(mg_ctx *c) {
     }
   } else if (c->kind == K_CELL) {
     for (int l = L; l >= 1; --l) CK(cudaMemsetAsync(c->d64[l].k, 0, sizeof(double) * c->geo[l].count, c->stream));
-    launch_cell_pack(lc, lev64(c, L), c->K.k, c->d64[L].k);
+    if (c->swap) launch_cell_pack_swapped(lc, lev64(c, L), c->K.k, c->d64[L].k);
+    else launch_cell_pack(lc, lev64(c, L), c->K.k, c->d64[L].k);
     for (int l = L; l > 1; --l) launch_coarsen_cell(lc, lev64(c, l), lev64(c, l - 1), c->d64[l].k, c->d64[l - 1].k);
     for (int l = L; l >= 1; --l) {
       CK(cudaMemsetAsync(c->d64[l].ndinv, 0, sizeof(double) * c->geo[l].count, c->stream));
@@ -762,6 +803,7 @@ size_t mg_workspace_bytes(const mg_params *p, const mg_coeffs *k) {
   c->L = p->levels;
   c->kind = k->kind;
   c->mixed = p->precision == MG_MIXED;
+  apply_swap(c);
   size_t s = layout(c, nullptr);
   delete c;
   return s;
@@ -782,6 +824,7 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
   c->kind = k->kind;
   c->mixed = p->precision == MG_MIXED;
   c->stream = (cudaStream_t)p->stream;
+  apply_swap(c);
   size_t need = layout(c, nullptr);
   if (ws_bytes < need) {
     delete c;
@@ -838,6 +881,11 @@ long long mg_launch_count(const mg_ctx *c) { return c ? c->launches : 0; }
 mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]) {
   if (!c || level < 1 || level > c->L || !n) return MG_EINVAL;
   for (int d = 0; d < 3; ++d) n[d] = c->geo[level].n[d];
+  if (c->swap) {   // caller-facing axes
+    int t = n[0];
+    n[0] = n[1];
+    n[1] = t;
+  }
   return MG_OK;
 }
 
@@ -858,10 +906,16 @@ static void harvest_events(mg_ctx *c, int base, int n) {
 static mg_status load_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, const double *src, double *dst,
                           bool host) {
   if (!host) {
-    launch_pack<double>(lc, F, src, dst, 1);
+    pack_in(c, lc, F, src, dst, 1);
     return MG_OK;
   }
   size_t rows = (size_t)F.n1 * (F.dim == 3 ? F.n2 : 1);
+  if (c->swap) {   // stage the caller layout on the device, then transpose into place
+    double *stage = c->d64[c->L].r;
+    CK(cudaMemcpyAsync(stage, src, sizeof(double) * F.n0 * rows, cudaMemcpyHostToDevice, lc.s));
+    pack_in(c, lc, F, stage, dst, 1);
+    return MG_OK;
+  }
   CK(cudaMemcpy2DAsync(dst, sizeof(double) * F.pitch, src, sizeof(double) * F.n0, sizeof(double) * F.n0, rows,
                        cudaMemcpyHostToDevice, lc.s));
   launch_zero_boundary<double>(lc, F, dst);
@@ -870,10 +924,16 @@ static mg_status load_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, con
 static mg_status store_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, const double *src, double *dst,
                            bool host) {
   if (!host) {
-    launch_unpack<double>(lc, F, src, dst, 1.0);
+    unpack_out(c, lc, F, src, dst, 1.0);
     return MG_OK;
   }
   size_t rows = (size_t)F.n1 * (F.dim == 3 ? F.n2 : 1);
+  if (c->swap) {
+    double *stage = c->d64[c->L].r;
+    unpack_out(c, lc, F, src, stage, 1.0);
+    CK(cudaMemcpyAsync(dst, stage, sizeof(double) * F.n0 * rows, cudaMemcpyDeviceToHost, lc.s));
+    return MG_OK;
+  }
   CK(cudaMemcpy2DAsync(dst, sizeof(double) * F.n0, src, sizeof(double) * F.pitch, sizeof(double) * F.n0, rows,
                        cudaMemcpyDeviceToHost, lc.s));
   return MG_OK;
@@ -988,10 +1048,11 @@ mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double
   Lev<double> F = lev64(c, L);
   double *ub = c->mixed ? c->d64[L].u[0] : c->d64[L].u[1];
   double *lb = c->d64[L].r;
-  launch_pack<double>(lc, F, u, ub, 1);
-  launch_pack<double>(lc, F, lambda, lb, 1);
+  pack_in(c, lc,F, u, ub, 1);
+  pack_in(c, lc,F, lambda, lb, 1);
   launch_grad_k(lc, F, ub, lb, c->grad_tmp);
-  launch_cell_unpack(lc, F, c->grad_tmp, dk);
+  if (c->swap) launch_cell_unpack_swapped(lc, F, c->grad_tmp, dk);
+  else launch_cell_unpack(lc, F, c->grad_tmp, dk);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1003,10 +1064,10 @@ mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au) {
   Lev<double> Lv = lev64(c, level);
   LevData<double> &D = c->d64[level];
   double *ub = c->mixed ? D.u[0] : D.u[1];
-  launch_pack<double>(lc, Lv, u, ub, 1);
+  pack_in(c, lc,Lv, u, ub, 1);
   CK(cudaMemsetAsync(D.g, 0, sizeof(double) * (size_t)c->geo[level].count, c->stream));
   launch_defect<double>(lc, Lv, c->kind, ub, D.g, D.r);   // r = 0 - A u
-  launch_unpack<double>(lc, Lv, D.r, Au, -1.0);
+  unpack_out(c, lc,Lv, D.r, Au, -1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1022,12 +1083,12 @@ mg_status mg_step_smooth(mg_ctx *c, int level, const double *u, const double *g,
   Launch lc{c->stream, &c->launches};
   Lev<double> Lv = lev64(c, level);
   LevData<double> &D = c->d64[level];
-  launch_pack<double>(lc, Lv, u, D.u[0], 1);
-  launch_pack<double>(lc, Lv, g, D.g, 1);
+  pack_in(c, lc,Lv, u, D.u[0], 1);
+  pack_in(c, lc,Lv, g, D.g, 1);
   c->cur[level] = 0;
   Sched S{c, lc, false};
   smooth<double>(S, level, D.g, sweeps, order ? 1 : 0, false);
-  launch_unpack<double>(lc, Lv, D.u[c->cur[level]], out, 1.0);
+  unpack_out(c, lc,Lv, D.u[c->cur[level]], out, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1037,10 +1098,10 @@ mg_status mg_step_defect(mg_ctx *c, int level, const double *u, const double *g,
   Launch lc{c->stream, &c->launches};
   Lev<double> Lv = lev64(c, level);
   LevData<double> &D = c->d64[level];
-  launch_pack<double>(lc, Lv, u, D.u[0], 1);
-  launch_pack<double>(lc, Lv, g, D.g, 1);
+  pack_in(c, lc,Lv, u, D.u[0], 1);
+  pack_in(c, lc,Lv, g, D.g, 1);
   launch_defect<double>(lc, Lv, c->kind, D.u[0], D.g, D.r);
-  launch_unpack<double>(lc, Lv, D.r, r, 1.0);
+  unpack_out(c, lc,Lv, D.r, r, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1049,9 +1110,9 @@ mg_status mg_step_restrict(mg_ctx *c, int level, const double *r, double *gc) {
   if (need_fp64(c) || level < 2 || level > c->L || !r || !gc) return MG_EINVAL;
   Launch lc{c->stream, &c->launches};
   Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
-  launch_pack<double>(lc, F, r, c->d64[level].r, 1);
+  pack_in(c, lc,F, r, c->d64[level].r, 1);
   launch_restrict<double>(lc, F, C, c->d64[level].r, c->d64[level - 1].g);
-  launch_unpack<double>(lc, C, c->d64[level - 1].g, gc, 1.0);
+  unpack_out(c, lc,C, c->d64[level - 1].g, gc, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1060,10 +1121,10 @@ mg_status mg_step_prolong(mg_ctx *c, int level, const double *ec, const double *
   if (need_fp64(c) || level < 2 || level > c->L || !ec || !u || !u_out) return MG_EINVAL;
   Launch lc{c->stream, &c->launches};
   Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
-  launch_pack<double>(lc, C, ec, c->d64[level - 1].u[0], 1);
-  launch_pack<double>(lc, F, u, c->d64[level].u[0], 1);
+  pack_in(c, lc,C, ec, c->d64[level - 1].u[0], 1);
+  pack_in(c, lc,F, u, c->d64[level].u[0], 1);
   launch_prolong_add<double>(lc, F, C, c->d64[level - 1].u[0], c->d64[level].u[0], w);
-  launch_unpack<double>(lc, F, c->d64[level].u[0], u_out, 1.0);
+  unpack_out(c, lc,F, c->d64[level].u[0], u_out, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1072,10 +1133,10 @@ mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u) {
   if (need_fp64(c) || !g || !u) return MG_EINVAL;
   Launch lc{c->stream, &c->launches};
   Lev<double> C = lev64(c, 1);
-  launch_pack<double>(lc, C, g, c->d64[1].g, 1);
+  pack_in(c, lc,C, g, c->d64[1].g, 1);
   CK(cudaMemsetAsync(c->d64[1].u[0], 0, sizeof(double) * (size_t)c->geo[1].count, c->stream));
   launch_coarse_apply<double>(lc, c->Ainv, c->cidx, c->nc, c->d64[1].g, c->d64[1].u[0]);
-  launch_unpack<double>(lc, C, c->d64[1].u[0], u, 1.0);
+  unpack_out(c, lc,C, c->d64[1].u[0], u, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
 }
@@ -1085,13 +1146,13 @@ mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_o
   int L = c->L;
   Launch lc{c->stream, &c->launches};
   Lev<double> F = lev64(c, L);
-  launch_pack<double>(lc, F, b, c->d64[L].g, 1);
-  launch_pack<double>(lc, F, x, c->d64[L].u[0], 1);
+  pack_in(c, lc,F, b, c->d64[L].g, 1);
+  pack_in(c, lc,F, x, c->d64[L].u[0], 1);
   Sched S{c, lc, false};
   c->cur[L] = 0;
   if (transposed) cycle<double>(S, L, c->d64[L].g, 0, 1, false);
   else cycle<double>(S, L, c->d64[L].g, 0, 0, false);
-  launch_unpack<double>(lc, F, c->d64[L].u[c->cur[L]], x_out, 1.0);
+  unpack_out(c, lc,F, c->d64[L].u[c->cur[L]], x_out, 1.0);
   c->cur[L] = 0;
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);

@@ -206,6 +206,17 @@ template <typename T>
 void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst);
 template <typename T>
 void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst);
+// axis-swapped copies: caller node (i, j, k) <-> internal node (j, i, k)
+template <typename T>
+void launch_pack_swapped(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary);
+template <typename T>
+void launch_unpack_swapped(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale);
+void launch_cell_pack_swapped(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst);
+void launch_cell_unpack_swapped(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact);
+// x-line smoother, one CTA per line; returns false (nothing launched) for lines longer than it holds
+template <typename T>
+bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int colour, const T *u, const T *g, T *out,
+                  T omega);
 
 // mixed precision
 void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
