@@ -144,6 +144,13 @@ mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double
 /* Au = A_l u on level l (1..L).  u, Au: device node arrays of level l. */
 mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au);
 
+/* ||b - A_l u||_2 over the unknowns of level l (1..L; MG_MIXED contexts: level L only), the
+ * stopping quantity of the solve (section "Smoothers": the defect A x - b that C^{-1}
+ * acts on).  u, b: device node arrays of level l (Dirichlet entries ignored); out: device
+ * pointer to one double.  The reduction is deterministic (fixed-order partial sums held
+ * in the context's workspace). */
+mg_status mg_residual_norm(mg_ctx *c, int level, const double *u, const double *b, double *out);
+
 /* Level geometry: nodes per direction of level l. */
 mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]);
 

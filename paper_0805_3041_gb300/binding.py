@@ -24,7 +24,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOC
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
 
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
-           "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
+           "mg_residual_norm", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error"]
 
@@ -79,6 +79,8 @@ def load(build_if_missing: bool = True):
     L.mg_grad_coeff.restype = I
     L.mg_apply.argtypes = [P, I, P, P]
     L.mg_apply.restype = I
+    L.mg_residual_norm.argtypes = [P, I, P, P, P]
+    L.mg_residual_norm.restype = I
     L.mg_level_dims.argtypes = [P, I, C.POINTER(C.c_int)]
     L.mg_level_dims.restype = I
     L.mg_step_smooth.argtypes = [P, I, P, P, P, I, I]
@@ -270,6 +272,15 @@ class Solver:
         self._check(self.lib.mg_grad_coeff(self.ctx, C.c_void_p(u.data_ptr()), C.c_void_p(lam.data_ptr()),
                                            C.c_void_p(dk.data_ptr())))
         return dk
+
+    def residual_norm(self, u, b, l=None):
+        """||b - A_l u||_2 over the unknowns (mg_residual_norm), as a 1-element float64 tensor."""
+        l = self.levels if l is None else l
+        u, b = self._dev(u), self._dev(b)
+        out = _torch().zeros(1, dtype=_torch().float64, device=self.device)
+        self._check(self.lib.mg_residual_norm(self.ctx, l, C.c_void_p(u.data_ptr()), C.c_void_p(b.data_ptr()),
+                                              C.c_void_p(out.data_ptr())))
+        return out
 
     def apply(self, u, l=None):
         l = self.levels if l is None else l

@@ -379,6 +379,12 @@ void launch_norm_finish(const Launch &lc, const double *partials, int nparts, do
   ++*lc.counter;
 }
 
+__global__ void k_sqrt(const double *src, double *dst) { dst[0] = sqrt(src[0]); }
+void launch_sqrt(const Launch &lc, const double *src, double *dst) {
+  k_sqrt<<<1, 1, 0, lc.s>>>(src, dst);
+  ++*lc.counter;
+}
+
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out) {
   k_relres<<<1, 1, 0, lc.s>>>(sq, bsq, hist, it, relres_out);
   ++*lc.counter;

@@ -1057,6 +1057,20 @@ mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double
   return last_launch(c);
 }
 
+mg_status mg_residual_norm(mg_ctx *c, int level, const double *u, const double *b, double *out) {
+  if (!c || !u || !b || !out || level < 1 || level > c->L) return MG_EINVAL;
+  if (c->mixed && level != c->L) return MG_EINVAL;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> Lv = lev64(c, level);
+  LevData<double> &D = c->d64[level];
+  pack_in(c, lc, Lv, u, D.u[0], 1);
+  pack_in(c, lc, Lv, b, D.g, 1);
+  launch_defect_norm<double>(lc, Lv, c->kind, D.u[0], D.g, c->partials, norm_parts_count(), c->scal + 3);
+  launch_sqrt(lc, c->scal + 3, out);
+  CK(cudaStreamSynchronize(c->stream));
+  return last_launch(c);
+}
+
 mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au) {
   if (!c || !u || !Au || level < 1 || level > c->L) return MG_EINVAL;
   if (c->mixed && level != c->L) return MG_EINVAL;

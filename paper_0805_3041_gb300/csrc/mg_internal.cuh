@@ -228,5 +228,7 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
 
 // finish kernel: relres = sqrt(sq) / bnorm, history, status word
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out);
+// dst[0] = sqrt(src[0])
+void launch_sqrt(const Launch &lc, const double *src, double *dst);
 
 }  // namespace mg
