@@ -151,6 +151,28 @@ mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au);
  * in the context's workspace). */
 mg_status mg_residual_norm(mg_ctx *c, int level, const double *u, const double *b, double *out);
 
+/* ||b - A u||_2 over the unknowns of one grid, without a context and without allocating.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (for instance code whose device memory is owned entirely by another
+ * allocator or a fixed budget, or code running while its stream is being captured),
+ * and so cannot allocate the workspace mg_setup needs.
+ *   p: dim, n, periodic_y and stream are used (levels, smoother etc. are ignored);
+ *   k: MG_COEF_CONST or MG_COEF_SEPARABLE (MG_COEF_CELL returns MG_EINVAL);
+ *   u, b: device node arrays in the compact caller layout, read in place -- the
+ *         Dirichlet entries of u must hold 0; out: device pointer to one double.
+ * The per-block partial sums live in a file-scope __device__ array of 65,568 doubles
+ * (~512 KB) that every GPU touched by the library holds until the process exits; at
+ * most MG_NOALLOC_MAX_NODES nodes are accepted, larger grids return MG_EINVAL.  The
+ * first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.  The call
+ * is stream-ordered and asynchronous: *out is ready once p->stream has synchronised.
+ * All calls share the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race; each call writes every slot it later reads, nothing has
+ * to be cleared between calls. */
+#define MG_NOALLOC_MAX_NODES 2147483647LL
+mg_status mg_residual_norm_noalloc(const mg_params *p, const mg_coeffs *k, const double *u, const double *b,
+                                   double *out);
+
 /* Level geometry: nodes per direction of level l. */
 mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]);
 

@@ -24,7 +24,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOC
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
 
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
-           "mg_residual_norm", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
+           "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error"]
 
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True):
     L.mg_apply.restype = I
     L.mg_residual_norm.argtypes = [P, I, P, P, P]
     L.mg_residual_norm.restype = I
+    L.mg_residual_norm_noalloc.argtypes = [C.POINTER(Params), C.POINTER(Coeffs), P, P, P]
+    L.mg_residual_norm_noalloc.restype = I
     L.mg_level_dims.argtypes = [P, I, C.POINTER(C.c_int)]
     L.mg_level_dims.restype = I
     L.mg_step_smooth.argtypes = [P, I, P, P, P, I, I]
