@@ -79,6 +79,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
     int nst = nops < CSK_STAGED_OPS ? nops : CSK_STAGED_OPS;
     for (int t = threadIdx.x; t < nst; t += blockDim.x) s_prog[t] = prog[t];
     __syncthreads();
+    if (KIND == K_CELL && threadIdx.x == 0) {   // cell data of every level lives in the pool
+      for (int l = 1; l <= lc; ++l) {
+        s_levs[l].L.k = pool + s_levs[l].off_k;
+        s_levs[l].L.ndinv = pool + s_levs[l].off_dinv;
+      }
+    }
+    __syncthreads();
     levs = s_levs;
   }
   // zero all level arrays, load cell data
@@ -106,11 +113,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
   for (int op = 0; op < nops; ++op) {
     int4 o = op < CSK_STAGED_OPS ? s_prog[op] : prog[op];
     const SLev<T> &S = levs[o.y];
-    Lev<T> L = S.L;
-    if (KIND == K_CELL) {
-      L.k = pool + S.off_k;
-      L.ndinv = pool + S.off_dinv;
-    }
+    const Lev<T> &L = S.L;   // read in place from shared memory (cell pointers patched at start)
     T *ub[2] = {pool + S.off_u0, pool + S.off_u1};
     T *g = pool + S.off_g, *r = pool + S.off_r;
     switch (o.x) {
@@ -288,7 +291,7 @@ void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, 
   do {                                                                                                       \
     auto fn = k_coarse_cycle<T, D, K>;                                                                       \
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);                  \
-    fn<<<1, 1024, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,      \
+    fn<<<1, 512, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,       \
                                       cidx_smem, nc, omega, omega_corr);                                     \
   } while (0)
   if (dim == 2) {

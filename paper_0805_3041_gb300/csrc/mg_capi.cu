@@ -103,7 +103,8 @@ struct mg_ctx {
   std::string err;
 };
 
-static size_t padded_pitch(int n0) { return (size_t)((n0 + 31) / 32) * 32; }
+// rows padded to 128 elements: the marching kernels read 128-column strips with vector loads
+static size_t padded_pitch(int n0) { return (size_t)((n0 + 127) / 128) * 128; }
 
 static int coarsen_dims(const int nf[3], int dim, int per, int nc[3]) {
   if ((nf[0] - 1) % 2 || nf[0] < 5) return 0;
@@ -399,7 +400,8 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       cur = 1 - cur;
     } else if (rb2d) {
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
-      launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
+      if (!launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc))
+        launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
       cur = 1 - cur;
     } else if (!line) {
       int first = order;

@@ -1,7 +1,7 @@
 // mg_internal.cuh -- device-side level view, stencil helpers and kernel launchers.
 //
 // Data layout in HBM (every level, both precisions): node (i, j, k) of level l
-// lives at  base + k * plane + j * pitch + i,  pitch = round_up(n0, 32)
+// lives at  base + k * plane + j * pitch + i,  pitch = round_up(n0, 128)
 // elements, plane = pitch * n1, each array 256-byte aligned.  Dirichlet nodes
 // are stored and hold 0; kernels only ever write unknowns.  A periodic y
 // direction has n1 distinct rows and wraps.  Cell coefficients (per-cell k of
@@ -173,6 +173,11 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
 template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc);
+// column-marching form of launch_rb2d (kernels_march.cu) for constant / separable
+// coefficients; returns false (nothing launched) where it does not apply
+template <typename T>
+bool launch_rb2d_march(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega,
+                       int first, int mode, const Lev<T> *C, const T *ec, T omega_corr);
 
 // single-CTA coarse cycle (kernels_coarse.cu): levs = device table of shared-memory level
 // views (filled by coarse_fill_levels), prog = program of CoarseOp steps

@@ -65,19 +65,23 @@ def test_gradient_matches_oracle():
 def test_finite_differences_lognormal_1025(precision):
     """Inverse problem of the differentiation study: 1025^2 nodes, k log-normal (correlation
     16 cells), u_obs = u(k_ref) + 1 % noise, L = ||u - u_obs||^2; dL/dk on 64 random cells
-    against central differences with delta = 1e-6 k_c."""
+    against central differences with delta = 1e-3 k_c.  The solves stop at 1e-10: this
+    smooth-solution problem reaches its FP64 rounding floor of the residual near 2e-11, so
+    the step is large enough that the solve error (~1e-10 relative in L) stays far below the
+    differenced signal, and small enough that the O(delta^2) truncation is ~1e-6."""
     n, L = 1025, 10
+    tol = 1e-10
     sp = inputs.diffusion_cells(n=n, seed_k=5)
     kref = inputs.lognormal_cells(n - 1, corr=16.0, seed=6)
     f = torch.tensor(sp.b, device="cuda")
     with torch.no_grad():
-        uref = diffusion_solve(torch.tensor(kref, device="cuda"), f, levels=L, tol=1e-13)
+        uref = diffusion_solve(torch.tensor(kref, device="cuda"), f, levels=L, tol=tol)
     noise = torch.tensor(inputs.observation_noise((n, n), seed=7), device="cuda")
     uobs = uref + 0.01 * uref.pow(2).mean().sqrt() * noise
     m = _mask(n)
 
     def loss(kt):
-        u = diffusion_solve(kt, f, levels=L, tol=1e-13, precision=precision)
+        u = diffusion_solve(kt, f, levels=L, tol=tol, precision=precision)
         return (((u - uobs) * m) ** 2).sum()
 
     k = torch.tensor(sp.k, device="cuda", requires_grad=True)
@@ -88,7 +92,7 @@ def test_finite_differences_lognormal_1025(precision):
     errs = []
     with torch.no_grad():
         for c in cells:
-            d = 1e-6 * float(sp.k[c])
+            d = 1e-3 * float(sp.k[c])
             kp = torch.tensor(sp.k, device="cuda")
             km = kp.clone()
             kp[c] += d
