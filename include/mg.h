@@ -85,6 +85,9 @@ typedef struct {
   int inner_cycles;       /* MG_MIXED: single-precision F-cycles per refinement step (>= 1) */
   void *stream;           /* cudaStream_t; NULL = legacy default stream */
   unsigned flags;         /* MG_FLAG_* */
+  int coarse_cut_nodes;   /* grids with at most this many nodes run inside the single-CTA coarse
+                             cycle (0: 5000 in single precision, 1200 in FP64; it must also fit in
+                             shared memory) -- a tuning knob of the autotuner */
 } mg_params;
 
 typedef struct {

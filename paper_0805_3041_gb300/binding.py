@@ -33,7 +33,8 @@ class Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("periodic_y", C.c_int), ("levels", C.c_int),
                 ("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_corr", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
-                ("inner_cycles", C.c_int), ("stream", C.c_void_p), ("flags", C.c_uint)]
+                ("inner_cycles", C.c_int), ("stream", C.c_void_p), ("flags", C.c_uint),
+                ("coarse_cut_nodes", C.c_int)]
 
 
 class Coeffs(C.Structure):
@@ -130,7 +131,8 @@ class Solver:
     """
 
     def __init__(self, spec, levels, smoother="rbgs", omega=1.0, nu1=2, nu2=2, omega_corr=1.0,
-                 precision="fp64", max_cycles=100, inner_cycles=1, flags=0, device="cuda", stream=None):
+                 precision="fp64", max_cycles=100, inner_cycles=1, flags=0, device="cuda", stream=None,
+                 coarse_cut_nodes=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the multigrid solver needs a CUDA GPU; no CPU path exists")
@@ -154,6 +156,7 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p.stream = self.stream.cuda_stream
         p.flags = int(flags)
+        p.coarse_cut_nodes = int(coarse_cut_nodes)
         self.params = p
         k = Coeffs()
         k.kind = int(spec.kind)

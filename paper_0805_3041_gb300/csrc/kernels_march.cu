@@ -142,9 +142,17 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
       if (io >= 0 && io < L.pitch) R.gout = gp[io];
     }
     if (MODE == 2 && unk_row(j)) {
+      // coarse values of the thread's columns: coarse columns c0 .. c0 + NV/2 of rows J0, J1
+      int J0 = jw >> 1, J1 = (jw + 1) >> 1;
+      if (J1 >= C.n1) J1 -= C.n1;
+      const T *e0 = ec + (long long)J0 * C.pitch, *e1 = ec + (long long)J1 * C.pitch;
+      const int c0 = i0 >> 1;
+      T s[NV / 2 + 1];
+#pragma unroll
+      for (int q = 0; q <= NV / 2; ++q) s[q] = (c0 + q < C.n0) ? e0[c0 + q] + e1[c0 + q] : T(0);
 #pragma unroll
       for (int e = 0; e < NV; ++e)
-        if (act[e]) R.u[e] += corr(i0 + e, jw);
+        if (act[e]) R.u[e] += omega_corr * ((s[e >> 1] + s[(e + 1) >> 1]) * T(0.25));
       if (edge) {
         if (oact) R.out += corr(io, jw);
         if (io2 >= 1 && io2 <= L.n0 - 2) R.out2 += corr(io2, jw);
@@ -153,23 +161,39 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
   };
   auto is_first = [&](int i, int j) { return ((i + j) & 1) == first; };
 
+  // Relax the elements of one colour of a row (o = c elsewhere): in each pair (2k, 2k+1) of
+  // the thread's columns exactly one node has that colour, the one with index parity p, so
+  // operands are selected instead of relaxing both and discarding one.
+  auto relax_sel = [&](T (&o)[NV], const T (&c)[NV], T left, T right, const T (&n)[NV], const T (&s)[NV],
+                       const T (&gg)[NV], int p, bool rowok) {
+#pragma unroll
+    for (int k = 0; k < NV / 2; ++k) {
+      const int a = 2 * k, b = 2 * k + 1;
+      T cc = p ? c[b] : c[a];
+      T wv = p ? c[a] : (a > 0 ? c[a - 1] : left);
+      T ev = p ? (b + 1 < NV ? c[b + 1] : right) : c[b];
+      T nn = p ? n[b] : n[a], ss = p ? s[b] : s[a], gv = p ? gg[b] : gg[a];
+      T r = fma(-(p ? CD(b) : CD(a)), cc, gv);
+      r = fma(p ? CW(b) : CW(a), wv, r);
+      r = fma(p ? CE(b) : CE(a), ev, r);
+      T y = p ? CY(b) : CY(a);
+      r = fma(y, nn, r);
+      r = fma(y, ss, r);
+      T nv = fma(p ? CO(b) : CO(a), r, cc);
+      bool on = rowok && (p ? act[b] : act[a]);
+      o[a] = (!p && on) ? nv : c[a];
+      o[b] = (p && on) ? nv : c[b];
+    }
+  };
+
   // ---- first colour relaxed on row j (Rm, R, Rp = rows j-1, j, j+1) -> H (+ outside value ho) ----
   auto half_row = [&](T (&H)[NV], T &ho, const RowW<T> &Rm, const RowW<T> &R, const RowW<T> &Rp, int j) {
     T left = __shfl_up_sync(FULL, R.u[NV - 1], 1), right = __shfl_down_sync(FULL, R.u[0], 1);
     if (lane == 0) left = R.out;
     if (lane == 31) right = R.out;
     bool rowu = unk_row(j);
-#pragma unroll
-    for (int e = 0; e < NV; ++e) {
-      T wv = e > 0 ? R.u[e - 1] : left, ev = e < NV - 1 ? R.u[e + 1] : right;
-      T s = fma(-CD(e), R.u[e], R.g[e]);
-      s = fma(CW(e), wv, s);
-      s = fma(CE(e), ev, s);
-      s = fma(CY(e), Rm.u[e], s);
-      s = fma(CY(e), Rp.u[e], s);
-      T nv = fma(CO(e), s, R.u[e]);
-      H[e] = (rowu && act[e] && is_first(i0 + e, j)) ? nv : R.u[e];
-    }
+    // first-colour columns of row j have index parity (first + j) % 2 (i0 is even)
+    relax_sel(H, R.u, left, right, Rm.u, Rp.u, R.g, (first + j) & 1, rowu);
     ho = R.out;
     if (edge && rowu && oact && is_first(io, j)) {
       T w_ = lane == 0 ? R.out2 : R.u[NV - 1], e_ = lane == 0 ? R.u[0] : R.out2;
@@ -203,18 +227,9 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
     T hl = __shfl_up_sync(FULL, Hc[NV - 1], 1), hr = __shfl_down_sync(FULL, Hc[0], 1);
     if (lane == 0) hl = hoc;
     if (lane == 31) hr = hoc;
+    // the second colour's own values are still the old ones in Hc
     T O[NV];
-#pragma unroll
-    for (int e = 0; e < NV; ++e) {
-      T wv = e > 0 ? Hc[e - 1] : hl, ev = e < NV - 1 ? Hc[e + 1] : hr;
-      T s = fma(-CD(e), W0.u[e], W0.g[e]);
-      s = fma(CW(e), wv, s);
-      s = fma(CE(e), ev, s);
-      s = fma(CY(e), Hm[e], s);
-      s = fma(CY(e), Hp[e], s);
-      T nv = fma(CO(e), s, W0.u[e]);
-      O[e] = (act[e] && !is_first(i0 + e, j)) ? nv : Hc[e];
-    }
+    relax_sel(O, Hc, hl, hr, Hm, Hp, W0.g, 1 - ((first + j) & 1), true);
     vstore<T>(out + (long long)j * L.pitch + i0, O);   // rows j0 .. j1-1 are real unknown rows
 #pragma unroll
     for (int e = 0; e < NV; ++e) {

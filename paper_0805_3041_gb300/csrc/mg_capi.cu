@@ -234,6 +234,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   if (!(P.flags & MG_FLAG_NO_FUSED_COARSE)) {
     size_t es = c->mixed ? 4 : 8, arrays = 4 + (c->kind == K_CELL ? 2 : 0), total = 0;
     long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
+    if (P.coarse_cut_nodes > 0) cap = P.coarse_cut_nodes;
     for (int l = 1; l <= c->L; ++l) {
       long long nodes = (long long)c->geo[l].n[0] * c->geo[l].n[1] * c->geo[l].n[2];
       total += arrays * (size_t)((nodes + 3) / 4 * 4) * es;
