@@ -220,29 +220,46 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
     half_row(Hm, hom, Wa, Wb, W0, j0 - 1);
     half_row(Hc, hoc, Wb, W0, W1, j0);
   }
-  for (int j = j0; j < j1; ++j) {
-    load_row(W3, j + 3);                    // prefetch, consumed in the next iteration
-    half_row(Hp, hop, W0, W1, W2, j + 1);
-    // second colour on row j
-    T hl = __shfl_up_sync(FULL, Hc[NV - 1], 1), hr = __shfl_down_sync(FULL, Hc[0], 1);
-    if (lane == 0) hl = hoc;
-    if (lane == 31) hr = hoc;
-    // the second colour's own values are still the old ones in Hc
+  // One output row.  The window rotates by renaming: the loop below is unrolled over the
+  // 12 rotations of (4 row slots, 3 half-row slots), so no registers are copied.
+  auto step = [&](RowW<T> &w0, RowW<T> &w1, RowW<T> &w2, RowW<T> &w3, T (&hm)[NV], T &hom_, T (&hc)[NV], T &hoc_,
+                  T (&hp)[NV], T &hop_, int j) {
+    (void)hom_;
+    load_row(w3, j + 3);                    // prefetch, consumed by the next row
+    half_row(hp, hop_, w0, w1, w2, j + 1);
+    T hl = __shfl_up_sync(FULL, hc[NV - 1], 1), hr = __shfl_down_sync(FULL, hc[0], 1);
+    if (lane == 0) hl = hoc_;
+    if (lane == 31) hr = hoc_;
+    // second colour on row j; its own values are still the old ones in hc
     T O[NV];
-    relax_sel(O, Hc, hl, hr, Hm, Hp, W0.g, 1 - ((first + j) & 1), true);
+    relax_sel(O, hc, hl, hr, hm, hp, w0.g, 1 - ((first + j) & 1), true);
     vstore<T>(out + (long long)j * L.pitch + i0, O);   // rows j0 .. j1-1 are real unknown rows
-#pragma unroll
-    for (int e = 0; e < NV; ++e) {
-      Hm[e] = Hc[e];
-      Hc[e] = Hp[e];
-    }
-    hom = hoc;
-    hoc = hop;
-    W0 = W1;
-    W1 = W2;
-    W2 = W3;
+  };
+  for (int j = j0; j < j1; j += 12) {
+    step(W0, W1, W2, W3, Hm, hom, Hc, hoc, Hp, hop, j);
+    if (j + 1 >= j1) break;
+    step(W1, W2, W3, W0, Hc, hoc, Hp, hop, Hm, hom, j + 1);
+    if (j + 2 >= j1) break;
+    step(W2, W3, W0, W1, Hp, hop, Hm, hom, Hc, hoc, j + 2);
+    if (j + 3 >= j1) break;
+    step(W3, W0, W1, W2, Hm, hom, Hc, hoc, Hp, hop, j + 3);
+    if (j + 4 >= j1) break;
+    step(W0, W1, W2, W3, Hc, hoc, Hp, hop, Hm, hom, j + 4);
+    if (j + 5 >= j1) break;
+    step(W1, W2, W3, W0, Hp, hop, Hm, hom, Hc, hoc, j + 5);
+    if (j + 6 >= j1) break;
+    step(W2, W3, W0, W1, Hm, hom, Hc, hoc, Hp, hop, j + 6);
+    if (j + 7 >= j1) break;
+    step(W3, W0, W1, W2, Hc, hoc, Hp, hop, Hm, hom, j + 7);
+    if (j + 8 >= j1) break;
+    step(W0, W1, W2, W3, Hp, hop, Hm, hom, Hc, hoc, j + 8);
+    if (j + 9 >= j1) break;
+    step(W1, W2, W3, W0, Hm, hom, Hc, hoc, Hp, hop, j + 9);
+    if (j + 10 >= j1) break;
+    step(W2, W3, W0, W1, Hc, hoc, Hp, hop, Hm, hom, j + 10);
+    if (j + 11 >= j1) break;
+    step(W3, W0, W1, W2, Hp, hop, Hm, hom, Hc, hoc, j + 11);
   }
-  (void)hom;
 #undef CW
 #undef CE
 #undef CY
