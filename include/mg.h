@@ -44,7 +44,7 @@ typedef enum {
   MG_ECUDA = 3,      /* a CUDA call failed; see mg_last_error */
   MG_ENOCONV = 4,    /* max_cycles reached before the tolerance; x holds the last iterate */
   MG_EDIVERGED = 5,  /* the residual norm became non-finite */
-  MG_ETIMEOUT = 6,   /* a bounded device wait gave up (reserved) */
+  MG_ETIMEOUT = 6,   /* a bounded device wait gave up; the output is not the solution */
   MG_EBOUNDS = 7     /* a device-side check found an out-of-range index (reserved) */
 } mg_status;
 
@@ -70,6 +70,8 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 #define MG_FLAG_TIMING   2u   /* record CUDA events around every finest-level smoothing launch */
 #define MG_FLAG_NO_FUSED_COARSE 4u  /* run every grid with per-step kernels (no single-CTA coarse cycle) */
 #define MG_FLAG_NO_FUSED_SWEEP  8u  /* 2-D: red-black half-sweep kernels and a separate defect / restriction */
+#define MG_FLAG_NO_TMA          16u /* 2-D FP32 red-black sweeps: register-marching kernel instead of the
+                                       TMA-fed one (same arithmetic, same results) */
 
 typedef struct {
   int dim;                /* 2 or 3 */
@@ -88,6 +90,8 @@ typedef struct {
   int coarse_cut_nodes;   /* grids with at most this many nodes run inside the single-CTA coarse
                              cycle (0: 5000 in single precision, 1200 in FP64; it must also fit in
                              shared memory) -- a tuning knob of the autotuner */
+  int sweep_rows;         /* rows one warp marches through in the fused 2-D red-black sweeps of
+                             single precision (0: 64) -- a tuning knob; results do not depend on it */
 } mg_params;
 
 typedef struct {

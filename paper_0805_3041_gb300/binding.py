@@ -18,7 +18,7 @@ SMOOTHERS = {"jacobi": JACOBI, "rbgs": RBGS, "line_x": LINE_X, "line_y": LINE_Y,
              "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y}
 CONST, SEPARABLE, CELL = 0, 1, 2
 FP64, MIXED = 0, 1
-FLAG_NO_GRAPH, FLAG_TIMING = 1, 2
+FLAG_NO_GRAPH, FLAG_TIMING, FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP, FLAG_NO_TMA = 1, 2, 4, 8, 16
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_corr", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
                 ("inner_cycles", C.c_int), ("stream", C.c_void_p), ("flags", C.c_uint),
-                ("coarse_cut_nodes", C.c_int)]
+                ("coarse_cut_nodes", C.c_int), ("sweep_rows", C.c_int)]
 
 
 class Coeffs(C.Structure):
@@ -132,7 +132,7 @@ class Solver:
 
     def __init__(self, spec, levels, smoother="rbgs", omega=1.0, nu1=2, nu2=2, omega_corr=1.0,
                  precision="fp64", max_cycles=100, inner_cycles=1, flags=0, device="cuda", stream=None,
-                 coarse_cut_nodes=0):
+                 coarse_cut_nodes=0, sweep_rows=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the multigrid solver needs a CUDA GPU; no CPU path exists")
@@ -157,6 +157,7 @@ class Solver:
         p.stream = self.stream.cuda_stream
         p.flags = int(flags)
         p.coarse_cut_nodes = int(coarse_cut_nodes)
+        p.sweep_rows = int(sweep_rows)
         self.params = p
         k = Coeffs()
         k.kind = int(spec.kind)

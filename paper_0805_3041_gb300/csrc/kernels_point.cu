@@ -379,6 +379,41 @@ void launch_norm_finish(const Launch &lc, const double *partials, int nparts, do
   ++*lc.counter;
 }
 
+// End of a cycle inside a device-side solve loop (a CUDA-graph WHILE node): record the
+// relative residual, count the cycle and set the loop condition.  st[0] = cycles done,
+// st[1] = status (0 running / converged, 4 no convergence, 5 non-finite, 6 a bounded
+// device wait gave up), st[2] = set by a kernel whose wait gave up.  init = 1 for the
+// check before the first cycle.  ||b|| = 0 stops at once (x = 0); a non-finite ||b||
+// gives a non-finite relative residual.
+__global__ void k_step_end(cudaGraphConditionalHandle h, const double *sq, const double *bsq, double *hist, int *st,
+                           const double *tol, int maxit, int init) {
+  double b = bsq[0];
+  double rel = b == 0.0 ? 0.0 : sqrt(sq[0]) / sqrt(b);
+  int it = init ? 0 : st[0] + 1;
+  st[0] = it;
+  if (hist) hist[it] = rel;
+  int go = 1, status = 0;
+  if (st[2]) {
+    go = 0;
+    status = 6;
+  } else if (!(rel == rel) || rel > 1.7976931348623157e308) {
+    go = 0;
+    status = 5;
+  } else if (rel <= tol[0] || b == 0.0) {
+    go = 0;
+  } else if (it >= maxit) {
+    go = 0;
+    status = 4;
+  }
+  st[1] = status;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
+                     double *hist, int *st, const double *tol, int maxit, int init) {
+  k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init);
+  ++*lc.counter;
+}
+
 __global__ void k_sqrt(const double *src, double *dst) { dst[0] = sqrt(src[0]); }
 void launch_sqrt(const Launch &lc, const double *src, double *dst) {
   k_sqrt<<<1, 1, 0, lc.s>>>(src, dst);

@@ -91,6 +91,9 @@ struct mg_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // forward / transposed cycle + check
+  cudaGraphExec_t lexec[2] = {nullptr, nullptr};   // whole solve: device-side WHILE loop
+  long long loop_init_kernels[2] = {0, 0}, loop_body_kernels[2] = {0, 0};
+  int *st = nullptr;                               // device: cycles done, status of the loop
   long long graph_kernels[2] = {0, 0};
   double *h_relres = nullptr;   // pinned
   // timing of finest-level smoothing launches
@@ -133,7 +136,7 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y)) return MG_EINVAL;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
-  if (p->max_cycles < 0) return MG_EINVAL;
+  if (p->max_cycles < 0 || p->sweep_rows < 0) return MG_EINVAL;
   if (k->kind < MG_COEF_CONST || k->kind > MG_COEF_CELL) return MG_EINVAL;
   if (k->kind == MG_COEF_SEPARABLE && (!k->sx || !k->sy || (p->dim == 3 && !k->sz))) return MG_EINVAL;
   if (k->kind == MG_COEF_CELL && !k->k) return MG_EINVAL;
@@ -221,6 +224,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   c->partials = b.take<double>((size_t)norm_parts_count());
   c->scal = b.take<double>(16);
   c->hist = b.take<double>((size_t)P.max_cycles + 2);
+  c->st = b.take<int>(8);
   // coarsest grid
   const LevGeom &g1 = c->geo[1];
   long long nc = (long long)(g1.n[0] - 2) * (P.periodic_y ? g1.n[1] : g1.n[1] - 2) * (P.dim == 3 ? g1.n[2] - 2 : 1);
@@ -353,6 +357,8 @@ struct Sched {
   bool timing;
   int ev_base = 0;      // first event of this schedule's range in the pool
   int *ev_next = nullptr;
+  bool loop = false;    // emitting into a device-side solve loop: end cycles with launch_step_end
+  cudaGraphConditionalHandle loop_h = 0;
 };
 
 static void record_event(Sched &S) {
@@ -363,6 +369,19 @@ static void record_event(Sched &S) {
   // "external" so that a stream capture turns the record into an event-record node
   cudaEventRecordWithFlags(c->ev[idx], S.lc.s, cudaEventRecordExternal);
   ++*S.ev_next;
+}
+
+// One fused 2-D red-black sweep in FP32 through the TMA-fed kernel, where it applies.
+template <typename T>
+static bool sweep_tma(Sched &, const Lev<T> &, const T *, const T *, T *, T, int, int, const Lev<T> *, const T *, T) {
+  return false;
+}
+template <>
+bool sweep_tma<float>(Sched &S, const Lev<float> &L, const float *u, const float *g, float *out, float om, int order,
+                      int mode, const Lev<float> *Cp, const float *ec, float oc) {
+  mg_ctx *c = S.c;
+  if (c->P.flags & MG_FLAG_NO_TMA) return false;
+  return launch_rb2d_tma(S.lc, L, c->kind, u, g, out, om, order, mode, Cp, ec, oc, c->st + 2, c->P.sweep_rows);
 }
 
 // `sweeps` smoothing steps on level l.  With ec != nullptr the coarse-grid correction
@@ -401,7 +420,8 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       cur = 1 - cur;
     } else if (rb2d) {
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
-      if (!launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc))
+      if (!sweep_tma<T>(S, L, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc) &&
+          !launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc))
         launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
       cur = 1 - cur;
     } else if (!line) {
@@ -591,7 +611,9 @@ static void emit_fp64_cycle(Sched &S, int transposed) {
   finest_to_zero<double>(S);
   launch_defect_norm<double>(S.lc, lev64(c, L), c->kind, c->d64[L].u[0], c->d64[L].g, c->partials,
                              norm_parts_count(), c->scal + 1);
-  launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+  if (S.loop) launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4,
+                              c->P.max_cycles, 0);
+  else launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
 }
 
 // Mixed form: FP32 inner F-cycles on r32 from zero, FP64 update, FP64 defect and check.
@@ -609,7 +631,89 @@ static void emit_mixed_step(Sched &S, int transposed) {
   launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
   launch_defect64_to32(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
                        c->scal + 1);
-  launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+  if (S.loop) launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4,
+                              c->P.max_cycles, 0);
+  else launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+}
+
+// Initial check of a device-side solve: ||b||^2, the defect of the start vector, and the
+// loop condition (the packed b and x already sit in the finest-level buffers).
+static void emit_solve_init(Sched &S) {
+  mg_ctx *c = S.c;
+  int L = c->L;
+  Lev<double> F64 = lev64(c, L);
+  if (c->mixed) {
+    launch_norm_parts<double>(S.lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
+    launch_defect64_to32(S.lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                         c->scal + 1);
+  } else {
+    launch_norm_parts<double>(S.lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
+    launch_defect_norm<double>(S.lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
+                               c->scal + 1);
+  }
+  launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4, c->P.max_cycles, 1);
+}
+
+// The whole solve as one graph: the initial check, then a WHILE node whose body is one
+// cycle (FP64) or refinement step (MG_MIXED) ending in the convergence test, which sets the
+// loop condition on the device.  One launch and one synchronisation per solve.
+static mg_status build_loop_graph(mg_ctx *c, int transposed) {
+  if (c->lexec[transposed]) return MG_OK;
+  long long before = c->launches;
+  cudaGraph_t graph = nullptr, body = nullptr;
+  cudaGraphConditionalHandle h;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, 0);
+  if (e == cudaSuccess) {
+    Sched S{c, Launch{c->cap, &c->launches}, false};
+    S.loop = true;
+    S.loop_h = h;
+    emit_solve_init(S);
+    e = cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+  }
+  cudaGraphNode_t cnode;
+  cudaGraphNodeParams cp = {};
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp);
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(c->cap, &cnode, nullptr, 1,
+                                                                cudaStreamSetCaptureDependencies);
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) {
+    c->loop_init_kernels[transposed] = c->launches - before;
+    body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      long long b0 = c->launches;
+      Sched S{c, Launch{c->cap, &c->launches}, false};
+      S.loop = true;
+      S.loop_h = h;
+      if (c->mixed) emit_mixed_step(S, transposed);
+      else emit_fp64_cycle(S, transposed);
+      c->loop_body_kernels[transposed] = c->launches - b0;
+      cudaGraph_t bout = body;
+      e = cudaStreamEndCapture(c->cap, &bout);
+    }
+  }
+  c->launches = before;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->lexec[transposed], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->err = std::string("solve-loop graph: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    c->lexec[transposed] = nullptr;
+    return MG_ECUDA;
+  }
+  return MG_OK;
 }
 
 static mg_status build_graph(mg_ctx *c, int transposed) {
@@ -647,6 +751,7 @@ static mg_status setup_levels(mg_ctx *c) {
   Launch lc{c->stream, &c->launches};
   const mg_params &P = c->P;
   int L = c->L;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(int) * 8, c->stream));   // loop state and the device-wait flag
   // geometry constants per level
   for (int l = L; l >= 1; --l) {
     LevGeom &g = c->geo[l];
@@ -857,6 +962,8 @@ void mg_destroy(mg_ctx *c) {
   if (!c) return;
   for (int t = 0; t < 2; ++t)
     if (c->gexec[t]) cudaGraphExecDestroy(c->gexec[t]);
+  for (int t = 0; t < 2; ++t)
+    if (c->lexec[t]) cudaGraphExecDestroy(c->lexec[t]);
   for (auto &e : c->ev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->h_relres) cudaFreeHost(c->h_relres);
@@ -953,6 +1060,48 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   bool launched = false;
   Lev<double> F64 = lev64(c, L);
   mg_status lst;
+  if (use_graph && !timing) {
+    // the whole solve on the device: copy in, one graph launch, copy out, one synchronisation
+    mg_status st = build_loop_graph(c, transposed);
+    if (st) return st;
+    if ((lst = load_vec(c, lc, F64, b, c->mixed ? c->b64 : c->d64[L].g, host))) return lst;
+    if ((lst = load_vec(c, lc, F64, x, c->mixed ? c->x64 : c->d64[L].u[0], host))) return lst;
+    c->h_relres[3] = tol;
+    CK(cudaMemcpyAsync(c->scal + 4, c->h_relres + 3, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaGraphLaunch(c->lexec[transposed], c->stream));
+    double *xin = c->mixed ? c->x64 : c->d64[L].u[0];
+    std::vector<double> hbuf((size_t)c->P.max_cycles + 2);
+    int sth[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(sth, c->st, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hbuf.data(), c->hist, sizeof(double) * hbuf.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if ((st = last_launch(c))) return st;
+    int cycles = sth[0];
+    c->launches += c->loop_init_kernels[transposed] + (long long)cycles * c->loop_body_kernels[transposed];
+    if (c->h_relres[0] == 0.0) {   // b = 0: x = 0
+      CK(cudaMemsetAsync(xin, 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
+    }
+    if ((lst = store_vec(c, lc, F64, xin, x, host))) return lst;
+    CK(cudaStreamSynchronize(c->stream));
+    if ((st = last_launch(c))) return st;
+    mg_status result = sth[1] == 4 ? MG_ENOCONV : sth[1] == 5 ? MG_EDIVERGED : MG_OK;
+    if (sth[2] || sth[1] == 6) {   // a bounded device wait gave up: clear the flag, report it
+      CK(cudaMemsetAsync(c->st + 2, 0, sizeof(int), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      result = MG_ETIMEOUT;
+    }
+    if (rep) {
+      rep->cycles = cycles;
+      rep->relres = hbuf[cycles];
+      rep->rate = (cycles > 0 && hbuf[0] > 0.0) ? std::pow(hbuf[cycles] / hbuf[0], 1.0 / cycles) : 0.0;
+      rep->status = result;
+      if (rep->history)
+        for (int t = 0; t <= cycles && t < rep->history_cap; ++t) rep->history[t] = hbuf[t];
+      rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return result;
+  }
   if (c->mixed) {
     if ((lst = load_vec(c, lc, F64, b, c->b64, host))) return lst;
     if ((lst = load_vec(c, lc, F64, x, c->x64, host))) return lst;
@@ -1013,9 +1162,16 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     else CK(cudaMemsetAsync(c->d64[L].u[0], 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
   }
   if ((lst = store_vec(c, lc, F64, c->mixed ? c->x64 : c->d64[L].u[0], x, host))) return lst;
+  int wait_flag = 0;
+  CK(cudaMemcpyAsync(&wait_flag, c->st + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   mg_status st = last_launch(c);
   if (st) return st;
+  if (wait_flag) {   // a bounded device wait gave up: clear the flag, report it
+    CK(cudaMemsetAsync(c->st + 2, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    result = MG_ETIMEOUT;
+  }
   if (rep) {
     rep->cycles = it;
     rep->relres = hist.back();

@@ -179,6 +179,14 @@ template <typename T>
 bool launch_rb2d_march(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega,
                        int first, int mode, const Lev<T> *C, const T *ec, T omega_corr);
 
+// the same sweep in FP32 with rows streamed by TMA bulk copies into a shared-memory ring
+// (kernels_tma.cu); rc = rows per warp (0: default).  A wait that gives up sets *err.
+// Returns false (nothing launched) where it does not apply.
+bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const float *u, const float *g, float *out,
+                     float omega, int first, int mode, const Lev<float> *C, const float *ec, float omega_corr,
+                     int *err, int rc);
+size_t rb2d_tma_smem(int mode);
+
 // single-CTA coarse cycle (kernels_coarse.cu): levs = device table of shared-memory level
 // views (filled by coarse_fill_levels), prog = program of CoarseOp steps
 template <typename T>
@@ -235,5 +243,8 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out);
 // dst[0] = sqrt(src[0])
 void launch_sqrt(const Launch &lc, const double *src, double *dst);
+// end of a cycle of a device-side solve loop: history, cycle count, status, WHILE condition
+void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
+                     double *hist, int *st, const double *tol, int maxit, int init);
 
 }  // namespace mg
