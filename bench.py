@@ -32,7 +32,7 @@ METRIC = "F-cycle time-to-1e-10-residual & smoother/defect HBM GB/s vs 8 TB/s pe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4097)
@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="extra MG_FLAG_* bits for the solver (1 = kernel-by-kernel launches, for profilers)")
     return ap.parse_args()
 
 
@@ -60,7 +62,7 @@ FP64_TFLOPS_MEASURED = 1.197
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in the background."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -74,7 +76,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -168,11 +170,16 @@ def run_reference(args):
         return
     sp, levels, omega = make_problem(args)
     cyc = oracle_cycles_to_tol(args, levels, omega)
-    ts = oracle_cycle_time(args, levels, omega, sp, reps=args.warmup + args.steps)[args.warmup:]
+    # one oracle cycle per step; the whole run is kept to about four minutes of oracle time
+    first = oracle_cycle_time(args, levels, omega, sp, reps=1)[0]
+    budget = max(1, int(240.0 / max(first, 1e-3)) - 1)
+    warm = min(args.warmup - 1, budget // 4) if args.warmup > 1 else 0
+    timed = max(1, min(args.steps, budget - warm))
+    ts = oracle_cycle_time(args, levels, omega, sp, reps=warm + timed)[warm:]
     per_cycle = float(np.mean(ts))
     value = per_cycle * cyc * 1e3
-    sample = (f"one oracle F-cycle + residual check on the full {args.n}^2 grid per step, x{cyc} cycles "
-              f"(the oracle's cycle count to {args.tol:g} on 513^2, same eps/smoother)")
+    sample = (f"one oracle F-cycle + residual check on the full {args.n}^2 grid per step ({timed} timed), x{cyc} "
+              f"cycles (the oracle's cycle count to {args.tol:g} on 513^2, same eps/smoother)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -204,9 +211,9 @@ def run_ours(args):
     # the measured solver runs the whole solve as one device-side graph loop; a second context
     # with CUDA events around every finest-level smoothing launch times the dominant kernel
     s = Solver(sp, levels=levels, smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu,
-               precision=args.precision, max_cycles=100, device=dev)
+               precision=args.precision, max_cycles=100, flags=args.flags, device=dev)
     st = Solver(sp, levels=levels, smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu,
-                precision=args.precision, max_cycles=100, flags=FLAG_TIMING, device=dev)
+                precision=args.precision, max_cycles=100, flags=FLAG_TIMING | args.flags, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():

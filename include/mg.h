@@ -90,8 +90,12 @@ typedef struct {
   int coarse_cut_nodes;   /* grids with at most this many nodes run inside the single-CTA coarse
                              cycle (0: 5000 in single precision, 1200 in FP64; it must also fit in
                              shared memory) -- a tuning knob of the autotuner */
-  int sweep_rows;         /* rows one warp marches through in the fused 2-D red-black sweeps of
-                             single precision (0: 64) -- a tuning knob; results do not depend on it */
+  int sweep_rows;         /* rows one CTA marches through in the fused 2-D red-black sweeps of
+                             single precision (0: from the occupancy) -- a tuning knob; results do
+                             not depend on it */
+  int tile_nodes;         /* 2-D grids with at most this many nodes smooth with the one-pass tile
+                             kernel instead of the row-streaming ones (0: 263169 = 513^2, -1:
+                             never) -- a tuning knob; results do not depend on it */
 } mg_params;
 
 typedef struct {
@@ -199,8 +203,10 @@ mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u);
 mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed);
 
 /* Mean duration (ms) of the finest-level smoothing launches recorded since the
- * last call (MG_FLAG_TIMING), their count, and the algorithmic bytes one such
- * launch moves.  Resets the record. */
+ * last call (MG_FLAG_TIMING), their count, and the mean algorithmic bytes of one
+ * such launch: per unknown, read u and g and write u (3 words), 2 words for a sweep
+ * whose iterate starts at zero, plus one read of the coarse correction (per coarse
+ * unknown) for a sweep that folds it in.  Resets the record. */
 mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *bytes_per_launch);
 
 /* Number of kernels the library launched since the context was created. */

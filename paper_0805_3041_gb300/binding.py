@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_corr", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
                 ("inner_cycles", C.c_int), ("stream", C.c_void_p), ("flags", C.c_uint),
-                ("coarse_cut_nodes", C.c_int), ("sweep_rows", C.c_int)]
+                ("coarse_cut_nodes", C.c_int), ("sweep_rows", C.c_int), ("tile_nodes", C.c_int)]
 
 
 class Coeffs(C.Structure):
@@ -132,7 +132,7 @@ class Solver:
 
     def __init__(self, spec, levels, smoother="rbgs", omega=1.0, nu1=2, nu2=2, omega_corr=1.0,
                  precision="fp64", max_cycles=100, inner_cycles=1, flags=0, device="cuda", stream=None,
-                 coarse_cut_nodes=0, sweep_rows=0):
+                 coarse_cut_nodes=0, sweep_rows=0, tile_nodes=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the multigrid solver needs a CUDA GPU; no CPU path exists")
@@ -158,6 +158,7 @@ class Solver:
         p.flags = int(flags)
         p.coarse_cut_nodes = int(coarse_cut_nodes)
         p.sweep_rows = int(sweep_rows)
+        p.tile_nodes = int(tile_nodes)
         self.params = p
         k = Coeffs()
         k.kind = int(spec.kind)

@@ -102,7 +102,9 @@ struct mg_ctx {
   int ev_used = 0;
   int ev_graph_n[2] = {0, 0};
   double t_sum_ms = 0.0;
+  double t_sum_bytes = 0.0;
   long long t_count = 0;
+  std::vector<double> ev_bytes;   // algorithmic bytes of the launch opened by each pool event
   std::string err;
 };
 
@@ -136,7 +138,7 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y)) return MG_EINVAL;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
-  if (p->max_cycles < 0 || p->sweep_rows < 0) return MG_EINVAL;
+  if (p->max_cycles < 0 || p->sweep_rows < 0 || p->tile_nodes < -1) return MG_EINVAL;
   if (k->kind < MG_COEF_CONST || k->kind > MG_COEF_CELL) return MG_EINVAL;
   if (k->kind == MG_COEF_SEPARABLE && (!k->sx || !k->sy || (p->dim == 3 && !k->sz))) return MG_EINVAL;
   if (k->kind == MG_COEF_CELL && !k->k) return MG_EINVAL;
@@ -361,11 +363,18 @@ struct Sched {
   cudaGraphConditionalHandle loop_h = 0;
 };
 
-static void record_event(Sched &S) {
+// unknowns of level l (periodic y: every row is unknown)
+static double level_unknowns(const mg_ctx *c, int l) {
+  const LevGeom &g = c->geo[l];
+  return (double)(g.n[0] - 2) * (c->P.periodic_y ? g.n[1] : g.n[1] - 2) * (c->P.dim == 3 ? g.n[2] - 2 : 1);
+}
+
+static void record_event(Sched &S, double bytes = 0.0) {
   mg_ctx *c = S.c;
   if (!S.timing || !S.ev_next) return;
   int idx = S.ev_base + *S.ev_next;
   if (*S.ev_next >= 2046 || idx >= (int)c->ev.size()) return;
+  c->ev_bytes[idx] = bytes;
   // "external" so that a stream capture turns the record into an event-record node
   cudaEventRecordWithFlags(c->ev[idx], S.lc.s, cudaEventRecordExternal);
   ++*S.ev_next;
@@ -409,9 +418,15 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
   bool fine = (l == c->L) && S.timing;
   int odd_guard = 0;
   if (zero_start && !jac && !rb2d) cudaMemsetAsync(D.u[cur], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+  // algorithmic bytes of one sweep: read u and g, write u (2 arrays when the iterate starts
+  // at zero and is not read; plus one read of the coarse correction when it is folded in)
+  const double es = sizeof(T), unk = level_unknowns(c, l);
   for (int s = 0; s < sweeps; ++s) {
     if (fine && S.ev_next && *S.ev_next < 2046) {
-      record_event(S);
+      bool zero = zero_start && s == 0 && (jac || rb2d);
+      bool fold = rb2d && ec && s == 0;
+      double bytes = es * unk * (zero ? 2.0 : 3.0) + (fold ? es * level_unknowns(c, l - 1) : 0.0);
+      record_event(S, bytes);
       odd_guard = 1;
     }
     if (jac) {
@@ -420,8 +435,12 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       cur = 1 - cur;
     } else if (rb2d) {
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
-      if (!sweep_tma<T>(S, L, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc) &&
-          !launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc))
+      // small grids: one pass over tiles (launch latency bound); large: row streaming
+      const long long tile_max = c->P.tile_nodes == 0 ? 263169 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
+      const bool small = tile_max >= 0 && (long long)L.n0 * L.n1 <= tile_max;
+      if (small || (!sweep_tma<T>(S, L, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc) &&
+                    !launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec,
+                                          oc)))
         launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
       cur = 1 - cur;
     } else if (!line) {
@@ -947,6 +966,7 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
   }
   if (p->flags & MG_FLAG_TIMING) {
     c->ev.resize(6144);
+    c->ev_bytes.assign(6144, 0.0);
     for (auto &e : c->ev) cudaEventCreate(&e);
   }
   st = setup_levels(c);
@@ -1005,6 +1025,7 @@ static void harvest_events(mg_ctx *c, int base, int n) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[t], c->ev[t + 1]) == cudaSuccess) {
       c->t_sum_ms += ms;
+      c->t_sum_bytes += c->ev_bytes[t];
       c->t_count++;
     }
   }
@@ -1335,14 +1356,10 @@ mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *by
   if (!c) return MG_EINVAL;
   if (mean_ms) *mean_ms = c->t_count ? c->t_sum_ms / c->t_count : 0.0;
   if (launches) *launches = (int)c->t_count;
-  if (bytes_per_launch) {
-    // algorithmic bytes of one finest-level smoothing sweep: read u, g, write u
-    const LevGeom &g = c->geo[c->L];
-    double unk = (double)(g.n[0] - 2) * (c->P.periodic_y ? g.n[1] : g.n[1] - 2) * (c->P.dim == 3 ? g.n[2] - 2 : 1);
-    double es = c->mixed ? 4.0 : 8.0;
-    *bytes_per_launch = 3.0 * es * unk;
-  }
+  // mean algorithmic bytes of the timed launches (each recorded with its sweep's kind)
+  if (bytes_per_launch) *bytes_per_launch = c->t_count ? c->t_sum_bytes / c->t_count : 0.0;
   c->t_sum_ms = 0.0;
+  c->t_sum_bytes = 0.0;
   c->t_count = 0;
   return MG_OK;
 }

@@ -7,7 +7,9 @@ FP32 roundings amplified by three cycles) and equality is reported.  Shapes cove
 strip), periodic y with separable coefficients, row counts that leave a ragged last chunk
 of rows, several chunk heights, and the sweep that folds in the coarse-grid correction
 (every post-smoothing).  The mixed solve through the TMA sweep must meet 1e-10 in the
-oracle's FP64 residual.
+oracle's FP64 residual.  Solvers here pass tile_nodes=-1 so that even small grids take the
+row-streaming kernels; the last test checks the one-pass tile kernel used below the default
+threshold against them.
 """
 import numpy as np
 import pytest
@@ -38,8 +40,8 @@ CASES = [
 def test_tma_sweep_matches_marching_sweep(dim, n, per, kind, L, eps):
     rng = np.random.default_rng(21)
     sp = spec_of(dim, n, per, kind, rng, eps=eps)
-    a = Solver(sp, levels=L, smoother="rbgs", precision="mixed", max_cycles=3)
-    b = Solver(sp, levels=L, smoother="rbgs", precision="mixed", max_cycles=3, flags=FLAG_NO_TMA)
+    a = Solver(sp, levels=L, smoother="rbgs", precision="mixed", max_cycles=3, tile_nodes=-1)
+    b = Solver(sp, levels=L, smoother="rbgs", precision="mixed", max_cycles=3, flags=FLAG_NO_TMA, tile_nodes=-1)
     xa, ia = a.solve(sp.b, tol=0.0)
     xb, ib = b.solve(sp.b, tol=0.0)
     d = rel(xa, xb.cpu().numpy())
@@ -53,8 +55,8 @@ def test_tma_sweep_chunk_heights(rows):
     """Rows per warp from 1 (prologue-only chunks) to more than the grid has."""
     rng = np.random.default_rng(22)
     sp = spec_of(2, (257, 97), False, inputs.CONST, rng, eps=0.7)
-    a = Solver(sp, levels=6, smoother="rbgs", precision="mixed", max_cycles=3, sweep_rows=rows)
-    b = Solver(sp, levels=6, smoother="rbgs", precision="mixed", max_cycles=3, flags=FLAG_NO_TMA)
+    a = Solver(sp, levels=6, smoother="rbgs", precision="mixed", max_cycles=3, sweep_rows=rows, tile_nodes=-1)
+    b = Solver(sp, levels=6, smoother="rbgs", precision="mixed", max_cycles=3, flags=FLAG_NO_TMA, tile_nodes=-1)
     xa, _ = a.solve(sp.b, tol=0.0)
     xb, _ = b.solve(sp.b, tol=0.0)
     assert rel(xa, xb.cpu().numpy()) <= 1e-6
@@ -64,8 +66,23 @@ def test_tma_mixed_solve_meets_tolerance_in_fp64():
     rng = np.random.default_rng(23)
     sp = spec_of(2, (513, 513), False, inputs.CONST, rng, eps=1.0)
     o = oracle_of(sp, 9, "rbgs", 1.0)
-    s = Solver(sp, levels=9, smoother="rbgs", precision="mixed", max_cycles=40)
+    s = Solver(sp, levels=9, smoother="rbgs", precision="mixed", max_cycles=40, tile_nodes=-1)
     x, info = s.solve(sp.b, tol=1e-10)
     xn = x.cpu().numpy()
     rr = o.norm(o.defect(xn, sp.b)) / o.norm(sp.b)
     assert info["status"] == "MG_OK" and rr <= 1e-10, (info, rr)
+
+
+@pytest.mark.parametrize("kind,per", [(inputs.CONST, False), (inputs.SEPARABLE, True)])
+def test_tile_sweep_matches_streaming_sweep(kind, per):
+    """Grids at or below the tile threshold smooth with the one-pass tile kernel; it performs
+    the same relaxations as the row-streaming sweep (in a different FMA order)."""
+    rng = np.random.default_rng(24)
+    sp = spec_of(2, (257, 256 if per else 257), per, kind, rng, eps=0.5)
+    a = Solver(sp, levels=7, smoother="rbgs", precision="mixed", max_cycles=3, tile_nodes=-1)
+    b = Solver(sp, levels=7, smoother="rbgs", precision="mixed", max_cycles=3, tile_nodes=1 << 30)
+    xa, _ = a.solve(sp.b, tol=0.0)
+    xb, _ = b.solve(sp.b, tol=0.0)
+    d = rel(xa, xb.cpu().numpy())
+    print(f"tile vs streaming sweep after 3 steps: max rel difference {d:.3e}")
+    assert d <= 1e-6
