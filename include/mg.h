@@ -147,6 +147,37 @@ mg_status mg_solve_host(mg_ctx *c, const double *b_host, double *x_host, double 
  * cycle in reverse order, each transposed).  Same conventions as mg_solve. */
 mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep);
 
+/* ---- Batched solves -------------------------------------------------------------
+ * The paper solves one problem at a time; solving many independent problems together
+ * is an addition of this library.  Each instance has its own context (its own sizes,
+ * coefficients, smoother, precision and max_cycles) and its own b / x (device
+ * pointers, layout as for mg_solve).  The whole batch runs as ONE CUDA graph launch on
+ * the first context's stream: every instance is an independent branch (copy b and
+ * x in, initial check, a device-side loop of cycles or refinement steps that stops on
+ * that instance's own test, copy x out), so instances of very different sizes proceed
+ * concurrently and the host synchronises once.
+ *
+ * mg_batch_create: builds and instantiates the graph for count contexts and their
+ *   b[i] / x[i] (host arrays of device pointers; the pointer values are kept).  The
+ *   contexts, b[i] and x[i] must stay valid until mg_batch_destroy.  MG_EINVAL for a
+ *   NULL argument, count < 1, a context used twice, contexts on different devices or
+ *   a context made with MG_FLAG_NO_GRAPH or MG_FLAG_TIMING.  The batch uses no device
+ *   memory of its own (each instance works in its context's workspace); it owns a
+ *   small pinned host buffer for the tolerance and the per-instance reports.
+ * mg_batch_solve: solves every instance to ||b_i - A_i x_i|| / ||b_i|| <= tol from
+ *   the start vectors in x[i]; reps (NULL, or count reports) receives each instance's
+ *   report.  Returns MG_OK when every instance converged, else the status of the
+ *   first instance (in index order) that did not (MG_ENOCONV, MG_EDIVERGED,
+ *   MG_ETIMEOUT); the x[i] hold each instance's last iterate either way.
+ * mg_solve_batched: create, solve and destroy in one call (the graph is built on
+ *   every call; keep a batch to solve the same set repeatedly). */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, mg_batch **out);
+mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps);
+void mg_batch_destroy(mg_batch *bt);
+mg_status mg_solve_batched(mg_ctx *const *cs, int count, const double *const *b, double *const *x, double tol,
+                           mg_report *reps);
+
 /* MG_COEF_CELL only: dk[c] = -sum over the edges e of cell c of
  * (d w_e / d k_c) (u_p - u_q)(lambda_p - lambda_q), i.e. dL/dk for a loss L
  * whose gradient in u is A^T lambda.  dk: device cell array, overwritten. */

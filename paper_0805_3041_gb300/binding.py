@@ -26,7 +26,8 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
            "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
-           "mg_status_str", "mg_last_error"]
+           "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_solve", "mg_batch_destroy",
+           "mg_solve_batched"]
 
 
 class Params(C.Structure):
@@ -107,6 +108,13 @@ def load(build_if_missing: bool = True):
     L.mg_status_str.restype = C.c_char_p
     L.mg_last_error.argtypes = [P]
     L.mg_last_error.restype = C.c_char_p
+    L.mg_batch_create.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), C.POINTER(P)]
+    L.mg_batch_create.restype = I
+    L.mg_batch_solve.argtypes = [P, D, C.POINTER(Report)]
+    L.mg_batch_solve.restype = I
+    L.mg_batch_destroy.argtypes = [P]
+    L.mg_solve_batched.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), D, C.POINTER(Report)]
+    L.mg_solve_batched.restype = I
     _lib = L
     return L
 
@@ -348,3 +356,80 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.mg_launch_count(self.ctx))
+
+
+def _batch_args(solvers, bs, xs):
+    n = len(solvers)
+    if n < 1 or len(bs) != n or len(xs) != n:
+        raise ValueError("solvers, bs and xs must have the same non-zero length")
+    for s, b, x in zip(solvers, bs, xs):
+        for t in (b, x):
+            if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+                raise ValueError("b and x must be contiguous float64 CUDA tensors")
+            if tuple(t.shape) != tuple(s.shape):
+                raise ValueError(f"tensor shape {tuple(t.shape)} does not match the solver's {tuple(s.shape)}")
+    cs = (C.c_void_p * n)(*[s.ctx for s in solvers])
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    return n, cs, bp, xp
+
+
+def _batch_reports(solvers, n):
+    hists = [np.zeros(s.max_cycles + 2, dtype=np.float64) for s in solvers]
+    reps = (Report * n)()
+    for r, h in zip(reps, hists):
+        r.history = h.ctypes.data
+        r.history_cap = len(h)
+    return reps, hists
+
+
+def _batch_infos(reps, hists):
+    return [dict(status=STATUS[r.status], cycles=r.cycles, relres=r.relres, rate=r.rate, seconds=r.seconds,
+                 history=h[:r.cycles + 1].copy()) for r, h in zip(reps, hists)]
+
+
+class Batch:
+    """Several independent solves as one CUDA graph (mg_batch_create / mg_batch_solve):
+    solvers[i] solves its problem with right-hand side bs[i] and start vector / solution
+    xs[i] (contiguous float64 CUDA tensors of the solver's shape, kept by reference).
+    The graph is built once; solve() launches it and returns one info dict per instance."""
+
+    def __init__(self, solvers, bs, xs):
+        self.lib = load()
+        self.solvers, self.bs, self.xs = list(solvers), list(bs), list(xs)
+        n, cs, bp, xp = _batch_args(self.solvers, self.bs, self.xs)
+        self.n = n
+        h = C.c_void_p()
+        st = self.lib.mg_batch_create(cs, n, bp, xp, C.byref(h))
+        if st != OK:
+            raise MGError(st, self.lib.mg_last_error(self.solvers[0].ctx).decode())
+        self.handle = h.value
+
+    def solve(self, tol=1e-10):
+        reps, hists = _batch_reports(self.solvers, self.n)
+        st = self.lib.mg_batch_solve(self.handle, float(tol), reps)
+        if st not in (OK, ENOCONV, EDIVERGED):
+            raise MGError(st, self.lib.mg_last_error(self.solvers[0].ctx).decode())
+        return _batch_infos(reps, hists)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.mg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(solvers, bs, xs, tol=1e-10):
+    """mg_solve_batched: build, launch and free the batch graph in one call."""
+    lib = load()
+    n, cs, bp, xp = _batch_args(solvers, bs, xs)
+    reps, hists = _batch_reports(solvers, n)
+    st = lib.mg_solve_batched(cs, n, bp, xp, float(tol), reps)
+    if st not in (OK, ENOCONV, EDIVERGED):
+        raise MGError(st, lib.mg_last_error(solvers[0].ctx).decode())
+    return _batch_infos(reps, hists)

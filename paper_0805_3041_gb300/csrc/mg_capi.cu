@@ -9,6 +9,7 @@
 // cycle (adjoint solves) runs the same steps in reverse order, each transposed.
 #include <chrono>
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -90,6 +91,8 @@ struct mg_ctx {
   long long launches = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap2 = nullptr;  // captures the body of a device-side solve loop
+  int dev = 0;                  // the device the context was set up on
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // forward / transposed cycle + check
   cudaGraphExec_t lexec[2] = {nullptr, nullptr};   // whole solve: device-side WHILE loop
   long long loop_init_kernels[2] = {0, 0}, loop_body_kernels[2] = {0, 0};
@@ -673,26 +676,25 @@ static void emit_solve_init(Sched &S) {
   launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4, c->P.max_cycles, 1);
 }
 
-// The whole solve as one graph: the initial check, then a WHILE node whose body is one
-// cycle (FP64) or refinement step (MG_MIXED) ending in the convergence test, which sets the
-// loop condition on the device.  One launch and one synchronisation per solve.
-static mg_status build_loop_graph(mg_ctx *c, int transposed) {
-  if (c->lexec[transposed]) return MG_OK;
-  long long before = c->launches;
-  cudaGraph_t graph = nullptr, body = nullptr;
+// Into the graph that stream s is capturing: the initial check, then a WHILE node whose
+// body is one cycle (FP64) or refinement step (MG_MIXED) ending in the convergence test,
+// which sets the loop condition on the device.  The body is captured on c->cap2.  The
+// kernel counts of the initial part and of one body go to init_k / body_k.
+static cudaError_t capture_loop(mg_ctx *c, cudaStream_t s, int transposed, long long *init_k, long long *body_k) {
+  cudaGraph_t graph = nullptr;
   cudaGraphConditionalHandle h;
-  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t *deps = nullptr;
   size_t ndeps = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+  long long before = c->launches;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, 0);
   if (e == cudaSuccess) {
-    Sched S{c, Launch{c->cap, &c->launches}, false};
+    Sched S{c, Launch{s, &c->launches}, false};
     S.loop = true;
     S.loop_h = h;
     emit_solve_init(S);
-    e = cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+    e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
   }
   cudaGraphNode_t cnode;
   cudaGraphNodeParams cp = {};
@@ -703,27 +705,38 @@ static mg_status build_loop_graph(mg_ctx *c, int transposed) {
     cp.conditional.size = 1;
     e = cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp);
   }
-  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(c->cap, &cnode, nullptr, 1,
-                                                                cudaStreamSetCaptureDependencies);
-  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
-  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess) {
-    c->loop_init_kernels[transposed] = c->launches - before;
-    body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    *init_k = c->launches - before;
+    e = cudaStreamBeginCaptureToGraph(c->cap2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       long long b0 = c->launches;
-      Sched S{c, Launch{c->cap, &c->launches}, false};
+      Sched S{c, Launch{c->cap2, &c->launches}, false};
       S.loop = true;
       S.loop_h = h;
       if (c->mixed) emit_mixed_step(S, transposed);
       else emit_fp64_cycle(S, transposed);
-      c->loop_body_kernels[transposed] = c->launches - b0;
-      cudaGraph_t bout = body;
-      e = cudaStreamEndCapture(c->cap, &bout);
+      *body_k = c->launches - b0;
+      cudaGraph_t bout = cp.conditional.phGraph_out[0];
+      e = cudaStreamEndCapture(c->cap2, &bout);
     }
   }
   c->launches = before;
+  return e;
+}
+
+// The whole solve as one graph (capture_loop on the context's own capture stream).  One
+// launch and one synchronisation per solve.
+static mg_status build_loop_graph(mg_ctx *c, int transposed) {
+  if (c->lexec[transposed]) return MG_OK;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = capture_loop(c, c->cap, transposed, &c->loop_init_kernels[transposed],
+                               &c->loop_body_kernels[transposed]);
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&c->lexec[transposed], graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
@@ -958,7 +971,8 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
     return MG_EINVAL;
   }
   layout(c, (char *)workspace);
-  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaGetDevice(&c->dev) != cudaSuccess || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&c->h_relres, sizeof(double) * 4) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -986,6 +1000,7 @@ void mg_destroy(mg_ctx *c) {
     if (c->lexec[t]) cudaGraphExecDestroy(c->lexec[t]);
   for (auto &e : c->ev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
   if (c->h_relres) cudaFreeHost(c->h_relres);
   delete c;
 }
@@ -1218,6 +1233,172 @@ mg_status mg_solve_host(mg_ctx *c, const double *b_host, double *x_host, double 
 mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double tol, mg_report *rep) {
   if (!c || !g || !lambda || !(tol >= 0.0)) return MG_EINVAL;
   return run_solve(c, g, lambda, tol, rep, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// batched solves: one graph, one independent branch per instance
+// ---------------------------------------------------------------------------------------
+struct mg_batch {
+  std::vector<mg_ctx *> cs;
+  std::vector<const double *> b;
+  std::vector<double *> x;
+  cudaGraphExec_t exec = nullptr;
+  double *host = nullptr;        // pinned: [0] tolerance, then one report row per instance
+  int stride = 0;                // doubles per report row: loop state (2), ||b||^2 (1), history
+  std::vector<long long> loop_init, loop_body, extra;   // kernel counts per instance
+};
+
+static void batch_free(mg_batch *bt) {
+  if (!bt) return;
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->host) cudaFreeHost(bt->host);
+  delete bt;
+}
+
+mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, mg_batch **out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (!cs || !b || !x || count < 1) return MG_EINVAL;
+  int maxc = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!cs[i] || !b[i] || !x[i]) return MG_EINVAL;
+    if (cs[i]->P.flags & (MG_FLAG_NO_GRAPH | MG_FLAG_TIMING)) return MG_EINVAL;
+    if (cs[i]->dev != cs[0]->dev) return MG_EINVAL;
+    maxc = std::max(maxc, cs[i]->P.max_cycles);
+  }
+  {
+    std::vector<mg_ctx *> sorted(cs, cs + count);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return MG_EINVAL;
+  }
+  mg_batch *bt = new (std::nothrow) mg_batch();
+  if (!bt) return MG_ENOMEM;
+  bt->cs.assign(cs, cs + count);
+  bt->b.assign(b, b + count);
+  bt->x.assign(x, x + count);
+  bt->stride = 3 + maxc + 2;
+  bt->loop_init.assign(count, 0);
+  bt->loop_body.assign(count, 0);
+  bt->extra.assign(count, 0);
+  mg_ctx *c0 = cs[0];
+  if (cudaMallocHost(&bt->host, sizeof(double) * (1 + (size_t)count * bt->stride)) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(bt);
+    return MG_ECUDA;
+  }
+  // capture: fork one branch per instance from the root stream, join them at the end
+  cudaStream_t root = nullptr;
+  std::vector<cudaEvent_t> evs(count + 1, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking);
+  for (int i = 0; i <= count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+  bool capturing = e == cudaSuccess;
+  if (e == cudaSuccess) e = cudaEventRecord(evs[count], root);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    mg_ctx *c = cs[i];
+    cudaStream_t s = c->cap;
+    Launch lc{s, &c->launches};
+    Lev<double> F64 = lev64(c, c->L);
+    double *row = bt->host + 1 + (size_t)i * bt->stride;
+    long long k0 = c->launches;
+    e = cudaStreamWaitEvent(s, evs[count], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal + 4, bt->host, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      load_vec(c, lc, F64, b[i], c->mixed ? c->b64 : c->d64[c->L].g, false);
+      load_vec(c, lc, F64, x[i], c->mixed ? c->x64 : c->d64[c->L].u[0], false);
+      e = capture_loop(c, s, 0, &bt->loop_init[i], &bt->loop_body[i]);
+    }
+    if (e == cudaSuccess) {
+      store_vec(c, lc, F64, c->mixed ? c->x64 : c->d64[c->L].u[0], x[i], false);
+      e = cudaMemcpyAsync(row, c->st, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(row + 2, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(row + 3, c->hist, sizeof(double) * (c->P.max_cycles + 2), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(root, evs[i], 0);
+    bt->extra[i] = c->launches - k0;
+    c->launches = k0;
+  }
+  if (capturing) {
+    cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (root) cudaStreamDestroy(root);
+  if (e != cudaSuccess) {
+    c0->err = std::string("batched graph: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    bt->exec = nullptr;
+    batch_free(bt);
+    return MG_ECUDA;
+  }
+  *out = bt;
+  return MG_OK;
+}
+
+mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps) {
+  if (!bt || !(tol >= 0.0)) return MG_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  mg_ctx *c = bt->cs[0];
+  const int count = (int)bt->cs.size();
+  bt->host[0] = tol;
+  CK(cudaGraphLaunch(bt->exec, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  mg_status result = MG_OK;
+  bool fixups = false;
+  for (int i = 0; i < count; ++i) {
+    mg_ctx *ci = bt->cs[i];
+    const double *row = bt->host + 1 + (size_t)i * bt->stride;
+    int st3[3];
+    std::memcpy(st3, row, sizeof(st3));
+    const int cycles = st3[0];
+    const double bsq = row[2];
+    const double *hist = row + 3;
+    ci->launches += bt->extra[i] + bt->loop_init[i] + (long long)cycles * bt->loop_body[i];
+    mg_status si = st3[1] == 4 ? MG_ENOCONV : st3[1] == 5 ? MG_EDIVERGED : MG_OK;
+    if (st3[2] || st3[1] == 6) {   // a bounded device wait gave up: clear the flag, report it
+      CK(cudaMemsetAsync(ci->st + 2, 0, sizeof(int), c->stream));
+      fixups = true;
+      si = MG_ETIMEOUT;
+    }
+    if (bsq == 0.0) {   // b = 0: x = 0
+      const int *n = ci->P.n;
+      size_t nodes = (size_t)n[0] * n[1] * (ci->P.dim == 3 ? n[2] : 1);
+      CK(cudaMemsetAsync(bt->x[i], 0, sizeof(double) * nodes, c->stream));
+      fixups = true;
+    }
+    if (si != MG_OK && result == MG_OK) result = si;
+    if (reps) {
+      mg_report &r = reps[i];
+      r.cycles = cycles;
+      r.relres = hist[cycles];
+      r.rate = (cycles > 0 && hist[0] > 0.0) ? std::pow(hist[cycles] / hist[0], 1.0 / cycles) : 0.0;
+      r.status = si;
+      if (r.history)
+        for (int t = 0; t <= cycles && t < r.history_cap; ++t) r.history[t] = hist[t];
+      r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+  if (fixups) CK(cudaStreamSynchronize(c->stream));
+  return result;
+}
+
+void mg_batch_destroy(mg_batch *bt) { batch_free(bt); }
+
+mg_status mg_solve_batched(mg_ctx *const *cs, int count, const double *const *b, double *const *x, double tol,
+                           mg_report *reps) {
+  if (!(tol >= 0.0)) return MG_EINVAL;
+  mg_batch *bt = nullptr;
+  mg_status st = mg_batch_create(cs, count, b, x, &bt);
+  if (st) return st;
+  st = mg_batch_solve(bt, tol, reps);
+  mg_batch_destroy(bt);
+  return st;
 }
 
 mg_status mg_grad_coeff(mg_ctx *c, const double *u, const double *lambda, double *dk) {
