@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="aniso", choices=["aniso", "batched"],
+                    help="aniso: the 4097^2 anisotropic solve (default); batched: 256 uneven instances in one graph")
+    ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--flags", type=int, default=0,
                     help="extra MG_FLAG_* bits for the solver (1 = kernel-by-kernel launches, for profilers)")
     return ap.parse_args()
@@ -317,10 +320,119 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------------------
+# batched workload: 256 independent instances of uneven size and anisotropy, one graph
+# --------------------------------------------------------------------------------------
+def run_batched(args):
+    import torch
+    from paper_0805_3041_gb300 import inputs
+    from paper_0805_3041_gb300.autotune import Autotuner
+    from paper_0805_3041_gb300.binding import Solver, Batch
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    specs = inputs.batched(count=args.count, seed=4)
+    tuner = Autotuner(path=os.path.join(ROOT, "paper_0805_3041_gb300", "tuned_gb300.json"))
+    t0 = time.perf_counter()
+    cfgs = [tuner.choose(sp) for sp in specs]
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solvers = [Solver(sp, levels=inputs.max_levels(sp.n), precision="mixed", max_cycles=100, device=dev, **cfg)
+               for sp, cfg in zip(specs, cfgs)]
+    bs = [torch.from_numpy(sp.b).to(dev) for sp in specs]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = Batch(solvers, bs, xs)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)), out
+
+    def batch_solve():
+        for x in xs:
+            x.zero_()
+        return batch.solve(tol=args.tol)
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    launches0 = sum(s.launch_count() for s in solvers)
+    ms, infos = timed(batch_solve, args.steps, args.warmup)
+    launches = (sum(s.launch_count() for s in solvers) - launches0) // max(1, args.steps + args.warmup) * args.steps
+    clk = clocks.stop()
+    assert all(i["status"] == "MG_OK" for i in infos), [i["status"] for i in infos]
+
+    def sequential(solver_list):
+        out = []
+        for s, b, x in zip(solver_list, bs, xs):
+            x.zero_()
+            out.append(s.solve_into(b, x, tol=args.tol))
+        return out
+
+    seq_ms, seq = timed(lambda: sequential(solvers), max(1, args.steps // 4), 1)
+    fp64 = [Solver(sp, levels=inputs.max_levels(sp.n), precision="fp64", max_cycles=100, device=dev, **cfg)
+            for sp, cfg in zip(specs, cfgs)]
+    f64_ms, f64 = timed(lambda: sequential(fp64), max(1, args.steps // 4), 1)
+
+    # end to end: host copies of every b and x around the batch solve
+    bh = [torch.from_numpy(sp.b).pin_memory() for sp in specs]
+    xh = [torch.zeros(sp.shape, dtype=torch.float64).pin_memory() for sp in specs]
+    e2e = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        for b, h in zip(bs, bh):
+            b.copy_(h, non_blocking=True)
+        infos_e = batch_solve()
+        for x, h in zip(xs, xh):
+            h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e.append((time.perf_counter() - t1) * 1e3)
+    nbytes = sum(sp.b.nbytes for sp in specs)
+    nodes = sum(sp.b.size for sp in specs)
+    classes = {}
+    for cfg in cfgs:
+        k = f"{cfg['smoother']}/nu{cfg['nu1']}"
+        classes[k] = classes.get(k, 0) + 1
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{args.count} independent 2-D anisotropic Poisson instances, N uniform over "
+                                   f"{{65,129,257,513,1025}}, eps log-uniform [1e-3,1], f~U[-1,1] seed 4, x0=0, "
+                                   f"mixed precision to {args.tol:g}, one CUDA graph launch per batch, "
+                                   f"autotuned schedule per class",
+                       "instances": args.count, "nodes": int(nodes), "schedules": classes,
+                       "l2": "L2 flushed between steps"},
+            "cycles_max": max(i["cycles"] for i in infos), "relres_max": max(i["relres"] for i in infos),
+            "sequential_mixed_ms": seq_ms, "sequential_fp64_ms": f64_ms,
+            "fp64_relres_max": max(i["relres"] for i in f64),
+            "setup_s": setup_s, "tune_s": tune_s, "roofline": None,
+            "e2e": {"value": float(np.median(e2e)), "unit": "ms", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 
