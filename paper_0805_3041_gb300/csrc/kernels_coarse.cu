@@ -24,18 +24,19 @@ struct SLev {
 template <typename T>
 __device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + off : nullptr; }
 
-// loop over the unknowns of a level (node index p, coordinates i, j, k): warp w of the
-// CTA takes rows w, w + 32, ..., its lanes the x positions of the row (no divisions per node)
+// loop over the unknowns of a level (node index p, coordinates i, j, k): working warp wid_
+// of nw_ takes rows wid_, wid_ + nw_, ..., its lanes the x positions of the row (no
+// divisions per node)
 #define FOR_UNK(Lv, ...)                                                                    \
   {                                                                                         \
     int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows();                                              \
     int rows_ = ny_ * (Lv).zrows();                                                         \
-    for (int r_ = (int)(threadIdx.x >> 5); r_ < rows_; r_ += (int)(blockDim.x >> 5)) {      \
+    for (int r_ = wid_; r_ < rows_; r_ += nw_) {                                            \
       int j = (Lv).ylo() + (DIM == 3 ? r_ % ny_ : r_);                                      \
       int k = DIM == 3 ? 1 + r_ / ny_ : 0;                                                  \
-      long long rowp_ = (long long)k * (Lv).plane + (long long)j * (Lv).pitch;              \
+      int rowp_ = k * (int)(Lv).plane + j * (int)(Lv).pitch;                                \
       for (int i = 1 + (int)(threadIdx.x & 31); i <= nx_; i += 32) {                        \
-        long long p = rowp_ + i;                                                            \
+        int p = rowp_ + i;                                                                  \
         __VA_ARGS__                                                                         \
       }                                                                                     \
     }                                                                                       \
@@ -45,13 +46,13 @@ __device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + 
   {                                                                                         \
     int nx_ = (Lv).n0 - 2, ny_ = (Lv).yrows();                                              \
     int rows_ = ny_ * (Lv).zrows();                                                         \
-    for (int r_ = (int)(threadIdx.x >> 5); r_ < rows_; r_ += (int)(blockDim.x >> 5)) {      \
+    for (int r_ = wid_; r_ < rows_; r_ += nw_) {                                            \
       int j = (Lv).ylo() + (DIM == 3 ? r_ % ny_ : r_);                                      \
       int k = DIM == 3 ? 1 + r_ / ny_ : 0;                                                  \
-      long long rowp_ = (long long)k * (Lv).plane + (long long)j * (Lv).pitch;              \
+      int rowp_ = k * (int)(Lv).plane + j * (int)(Lv).pitch;                                \
       int par_ = ((colour) + j + k + 1) & 1;                                                \
       for (int i = 1 + par_ + 2 * (int)(threadIdx.x & 31); i <= nx_; i += 64) {             \
-        long long p = rowp_ + i;                                                            \
+        int p = rowp_ + i;                                                                  \
         __VA_ARGS__                                                                         \
       }                                                                                     \
     }                                                                                       \
@@ -110,6 +111,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
     }
   }
   __syncthreads();
+  const int wid_ = (int)(threadIdx.x >> 5), nw_ = (int)(blockDim.x >> 5);
+  const int tid_ = (int)threadIdx.x, nthr_ = (int)blockDim.x;
   for (int op = 0; op < nops; ++op) {
     int4 o = op < CSK_STAGED_OPS ? s_prog[op] : prog[op];
     const SLev<T> &S = levs[o.y];
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         const T *src = o.z >= 0 ? ub[o.z] : nullptr;
         T *dst = ub[o.w];
         FOR_UNK(L, {
-          long long dm, dp;
+          int dm, dp;
           yoffs(L, j, dm, dp);
           Weights<T, DIM, KIND> w;
           w.load(L, i, p, dm);
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         T *u = ub[o.w];
         int colour = o.z;
         FOR_COLOUR(L, colour, {
-          long long dm, dp;
+          int dm, dp;
           yoffs(L, j, dm, dp);
           Weights<T, DIM, KIND> w;
           w.load(L, i, p, dm);
@@ -159,15 +162,15 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         T *src = ub[o.w & 15], *dst = ub[(o.w >> 4) & 15];
         T *cps = r, *dps = ub[(o.w >> 8) & 15];
         int nlines = dir == 0 ? (int)L.unk_rows() : (L.n0 - 2) * L.zrows();
-        for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
+        for (int t = tid_; t < nlines; t += nthr_) {
           int m, a_fixed, kk;
-          long long base, stride;
+          int base, stride;
           if (dir == 0) {
             int jj, k2;
             row_jk(L, t, jj, k2);
             if (zebra && ((jj + k2) & 1) != colour) continue;
             m = L.n0 - 2;
-            base = (long long)k2 * L.plane + (long long)jj * L.pitch + 1;
+            base = k2 * (int)L.plane + jj * (int)L.pitch + 1;
             stride = 1;
             a_fixed = jj;
             kk = k2;
@@ -176,18 +179,18 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
             int ii = 1 + t % nx, k2 = (DIM == 3 ? 1 : 0) + t / nx;
             if (zebra && ((ii + k2) & 1) != colour) continue;
             m = L.n1 - 2;
-            base = (long long)k2 * L.plane + L.pitch + ii;
-            stride = L.pitch;
+            base = k2 * (int)L.plane + (int)L.pitch + ii;
+            stride = (int)L.pitch;
             a_fixed = ii;
             kk = k2;
           }
           (void)kk;
           T cprev = T(0), dprev = T(0);
           for (int s = 0; s < m; ++s) {
-            long long p = base + s * stride;
+            int p = base + s * stride;
             int i = dir == 0 ? 1 + s : a_fixed;
             int j = dir == 0 ? a_fixed : 1 + s;
-            long long dm, dp;
+            int dm, dp;
             yoffs(L, j, dm, dp);
             Weights<T, DIM, KIND> w;
             w.load(L, i, p, dm);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
           }
           T x = T(0);
           for (int s = m - 1; s >= 0; --s) {
-            long long p = base + s * stride;
+            int p = base + s * stride;
             x = dps[p] - cps[p] * x;
             dst[p] = fma(omega, x, src[p]);
           }
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
       case CP_DEFECT: {   // z = buffer
         const T *u = ub[o.z];
         FOR_UNK(L, {
-          long long dm, dp;
+          int dm, dp;
           yoffs(L, j, dm, dp);
           Weights<T, DIM, KIND> w;
           w.load(L, i, p, dm);
@@ -231,14 +234,14 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         T *gc = pool + Cs.off_g;
         FOR_UNK(C, {
           int I = i, J = j, K = k;
-          long long dm, dp;
+          int dm, dp;
           yoffs(L, 2 * J, dm, dp);
-          long long pf = (long long)(2 * K) * L.plane + (long long)(2 * J) * L.pitch + 2 * I;
-          auto row3 = [&](long long c) -> T { return (r[c - 1] + r[c + 1]) + T(2) * r[c]; };
-          auto plane3 = [&](long long c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
+          int pf = (2 * K) * (int)L.plane + (2 * J) * (int)L.pitch + 2 * I;
+          auto row3 = [&](int c) -> T { return (r[c - 1] + r[c + 1]) + T(2) * r[c]; };
+          auto plane3 = [&](int c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
           T s;
           if (DIM == 2) s = plane3(pf) * T(0.0625);
-          else s = ((plane3(pf - L.plane) + plane3(pf + L.plane)) + T(2) * plane3(pf)) * T(0.015625);
+          else s = ((plane3(pf - (int)L.plane) + plane3(pf + (int)L.plane)) + T(2) * plane3(pf)) * T(0.015625);
           gc[p] = s;
         });
         break;
@@ -252,12 +255,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
           int I0 = i >> 1, I1 = (i + 1) >> 1;
           int J0 = j >> 1, J1 = (j + 1) >> 1;
           if (J1 >= C.n1) J1 -= C.n1;
-          long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+          int a0 = J0 * (int)C.pitch, a1 = J1 * (int)C.pitch;
           T s;
           if (DIM == 2) {
             s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
           } else {
-            long long z0 = (long long)(k >> 1) * C.plane, z1 = (long long)((k + 1) >> 1) * C.plane;
+            int z0 = (k >> 1) * (int)C.plane, z1 = ((k + 1) >> 1) * (int)C.plane;
             T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
             T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
             s = (s0 + s1) * T(0.125);
@@ -268,8 +271,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
       }
       case CP_COARSE: {   // level 1: u[z] = A^{-1} g, one warp per row of the dense inverse
         T *u = ub[o.z];
-        int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int row = warp; row < nc; row += nw) {
+        const int lane = threadIdx.x & 31;
+        for (int row = wid_; row < nc; row += nw_) {
           const double *arow = Ainv + (long long)row * nc;
           double s = 0.0;
           for (int c = lane; c < nc; c += 32) s = fma(arow[c], (double)g[cidx_smem[c]], s);

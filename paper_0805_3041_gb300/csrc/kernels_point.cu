@@ -206,47 +206,60 @@ __global__ void k_relres(const double *sq, const double *bsq, double *hist, int 
 // mixed precision: r32 = (float)(b - A x) with the defect in FP64, plus norm partials;
 // refinement update x += (double)c
 // ---------------------------------------------------------------------------------------
-template <int DIM, int KIND>
+// The defect is FP64-pipe bound on this GPU (5 DFMA per unknown for the 5-point stencil):
+// the R rows of a thread are a compile-time count (RT > 0) where it can be, so their FMA
+// chains interleave, and the squares of the norm are taken of the FP32 result on the FP32
+// pipe (at most R terms per thread; the block and grid sums stay FP64) -- the norm only
+// drives the stopping test.
+template <int DIM, int KIND, int RT>
 __global__ void __launch_bounds__(BX *BY) k_defect64_to32(Lev<double> L, const double *__restrict__ x,
                                                           const double *__restrict__ b, float *__restrict__ r32,
                                                           long long pitch32, long long plane32,
-                                                          double *__restrict__ partials, int R) {
+                                                          double *__restrict__ partials, int Rrt) {
+  const int R = RT > 0 ? RT : Rrt;
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
-  double acc = 0.0;
+  float acc = 0.f;
   if (i <= L.n0 - 2) {
+#pragma unroll
     for (int q = 0; q < R; ++q) {
       long long r = r0 + q;
-      if (r >= nr) break;
-      int j, k;
-      row_jk(L, r, j, k);
-      long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
-      yoffs(L, j, dm, dp);
-      Weights<double, DIM, KIND> w;
-      w.load(L, i, p, dm);
-      double s = residual_at<double, DIM, KIND>(L, w, x, p, dm, dp, b[p]);
-      r32[(long long)k * plane32 + (long long)j * pitch32 + i] = (float)s;
-      acc = fma(s, s, acc);
+      if (r < nr) {
+        int j, k;
+        row_jk(L, r, j, k);
+        long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+        yoffs(L, j, dm, dp);
+        Weights<double, DIM, KIND> w;
+        w.load(L, i, p, dm);
+        double s = residual_at<double, DIM, KIND>(L, w, x, p, dm, dp, b[p]);
+        float s32 = (float)s;
+        r32[(long long)k * plane32 + (long long)j * pitch32 + i] = s32;
+        acc = fmaf(s32, s32, acc);
+      }
     }
   }
-  double bs = block_sum(acc);
+  double bs = block_sum((double)acc);
   if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
 }
 
+template <int RT>
 __global__ void __launch_bounds__(BX *BY) k_ir_update(Lev<double> L, double *__restrict__ x, const float *__restrict__ c,
-                                                      long long pitch32, long long plane32, int R) {
+                                                      long long pitch32, long long plane32, int Rrt) {
+  const int R = RT > 0 ? RT : Rrt;
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
+#pragma unroll
   for (int q = 0; q < R; ++q) {
     long long r = r0 + q;
-    if (r >= nr) return;
-    int j, k;
-    row_jk(L, r, j, k);
-    long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
-    x[p] += (double)c[(long long)k * plane32 + (long long)j * pitch32 + i];
+    if (r < nr) {
+      int j, k;
+      row_jk(L, r, j, k);
+      long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
+      x[p] += (double)c[(long long)k * plane32 + (long long)j * pitch32 + i];
+    }
   }
 }
 
@@ -431,15 +444,22 @@ void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, cons
   int R = norm_R(rows, L.xunk(), nparts);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   long long p32 = L.pitch, pl32 = L.plane;   // the FP32 finest level uses the same element pitch
+#define D64_R(D, K)                                                                                          \
+  do {                                                                                                       \
+    if (R == 4) k_defect64_to32<D, K, 4><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);         \
+    else if (R == 1) k_defect64_to32<D, K, 1><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);    \
+    else k_defect64_to32<D, K, 0><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);                \
+  } while (0)
   if (L.dim == 2) {
-    if (kind == K_CONST) k_defect64_to32<2, K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
-    else if (kind == K_SEP) k_defect64_to32<2, K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
-    else k_defect64_to32<2, K_CELL><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    if (kind == K_CONST) D64_R(2, K_CONST);
+    else if (kind == K_SEP) D64_R(2, K_SEP);
+    else D64_R(2, K_CELL);
   } else {
-    if (kind == K_CONST) k_defect64_to32<3, K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
-    else if (kind == K_SEP) k_defect64_to32<3, K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
-    else k_defect64_to32<3, K_CELL><<<gr, bl, 0, lc.s>>>(L, x, b, r32, p32, pl32, partials, R);
+    if (kind == K_CONST) D64_R(3, K_CONST);
+    else if (kind == K_SEP) D64_R(3, K_SEP);
+    else D64_R(3, K_CELL);
   }
+#undef D64_R
   ++*lc.counter;
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
@@ -448,7 +468,8 @@ void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const f
   long long rows = L.unk_rows();
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  k_ir_update<<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
+  if (R == 4) k_ir_update<4><<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
+  else k_ir_update<0><<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
   ++*lc.counter;
 }
 

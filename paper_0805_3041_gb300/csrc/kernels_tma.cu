@@ -298,6 +298,16 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     const float *slot = slot_of(j);
     const float4 g4 = *reinterpret_cast<const float4 *>(slot + SEGW + c0);
     const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+    if (MODE == 1) {
+      // zero iterate: the residual of a first-colour node is g, its new value omega/D g
+      // (the same rounding as the general chain with zero operands); the rest stays 0
+      const bool rowu = unk(j);
+      const int p = (first + j) & 1;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) H.h[e] = (rowu && K.act[e] && (e & 1) == p) ? fmaf(K.O[e], gg[e], 0.f) : 0.f;
+      H.ho = (oact && rowu && (((io + j) & 1) == first)) ? fmaf(oO, slot[SEGW + co], 0.f) : 0.f;
+      return;
+    }
     float left = __shfl_up_sync(FULL, R.u[3], 1), right = __shfl_down_sync(FULL, R.u[0], 1);
     if (lane == 0) left = R.out;
     if (lane == 31) right = R.out;

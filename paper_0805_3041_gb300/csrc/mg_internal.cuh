@@ -36,13 +36,13 @@ struct Lev {
 };
 
 // Offsets of the y neighbours of row j (periodic wrap).
-template <typename T>
-__device__ __forceinline__ void yoffs(const Lev<T> &L, int j, long long &dm, long long &dp) {
-  dm = -L.pitch;
-  dp = L.pitch;
+template <typename T, typename IT>
+__device__ __forceinline__ void yoffs(const Lev<T> &L, int j, IT &dm, IT &dp) {
+  dm = -(IT)L.pitch;
+  dp = (IT)L.pitch;
   if (L.per) {
-    if (j == 0) dm = (long long)(L.n1 - 1) * L.pitch;
-    if (j == L.n1 - 1) dp = -(long long)(L.n1 - 1) * L.pitch;
+    if (j == 0) dm = (IT)(L.n1 - 1) * (IT)L.pitch;
+    if (j == L.n1 - 1) dp = -(IT)(L.n1 - 1) * (IT)L.pitch;
   }
 }
 
@@ -58,7 +58,8 @@ __device__ __forceinline__ void row_jk(const Lev<T> &L, long long r, int &j, int
 template <typename T, int DIM, int KIND>
 struct Weights {
   T wW, wE, wS, wN, wB, wF, dinv;
-  __device__ __forceinline__ void load(const Lev<T> &L, int i, long long p, long long dm) {
+  template <typename IT>
+  __device__ __forceinline__ void load(const Lev<T> &L, int i, IT p, IT dm) {
     if (KIND == K_CONST) {
       wW = wE = L.cx;
       wS = wN = L.cy;
@@ -81,7 +82,7 @@ struct Weights {
         wN = L.ay * (nw + ne);
         wB = wF = T(0);
       } else {
-        long long pl = L.plane;
+        IT pl = (IT)L.plane;
         T sw0 = k[p - pl + dm - 1], se0 = k[p - pl + dm], nw0 = k[p - pl - 1], ne0 = k[p - pl];
         T sw1 = k[p + dm - 1], se1 = k[p + dm], nw1 = k[p - 1], ne1 = k[p];
         wW = L.ax * ((sw0 + nw0) + (sw1 + nw1));
@@ -96,10 +97,11 @@ struct Weights {
   }
 };
 
-// r_p = g_p - (A u)_p  =  g_p - D u_p + sum_q w_pq u_q, written as an FMA chain.
-template <typename T, int DIM, int KIND>
+// r_p = g_p - (A u)_p  =  g_p - D u_p + sum_q w_pq u_q, written as an FMA chain.  IT is the
+// index type: 64-bit for global arrays, 32-bit for shared-memory ones.
+template <typename T, int DIM, int KIND, typename IT>
 __device__ __forceinline__ T residual_at(const Lev<T> &L, const Weights<T, DIM, KIND> &w, const T *__restrict__ u,
-                                         long long p, long long dm, long long dp, T gp) {
+                                         IT p, IT dm, IT dp, T gp) {
   T up = u[p];
   T s;
   if (KIND == K_CONST) {
@@ -114,8 +116,8 @@ __device__ __forceinline__ T residual_at(const Lev<T> &L, const Weights<T, DIM, 
   s = fma(w.wS, u[p + dm], s);
   s = fma(w.wN, u[p + dp], s);
   if (DIM == 3) {
-    s = fma(w.wB, u[p - L.plane], s);
-    s = fma(w.wF, u[p + L.plane], s);
+    s = fma(w.wB, u[p - (IT)L.plane], s);
+    s = fma(w.wF, u[p + (IT)L.plane], s);
   }
   return s;
 }
