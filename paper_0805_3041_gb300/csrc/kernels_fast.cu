@@ -155,6 +155,80 @@ __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u,
   }
 }
 
+// NS complete sweeps in one pass (temporal blocking, for small latency-bound grids): u is
+// staged with a halo of 2 NS and g with 2 NS - 1; half-sweep h (colours alternating from
+// `first`) relaxes the tile plus a ring of width 2 NS - 1 - h, so every node of the tile
+// ends with exactly the values NS successive sweeps give.  MODE applies to the first sweep
+// (1: zero iterate, 2: coarse-grid correction folded in), as in k_rb2d.
+template <typename T, int KIND, int MODE, int NS>
+__global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
+                                                 T *__restrict__ out, T omega, int first, Lev<T> C,
+                                                 const T *__restrict__ ec, T omega_corr) {
+  constexpr int H = 2 * NS;                 // halo of the u tile
+  constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
+  constexpr int SXN = TX + 2 * H + 1;       // smem row stride
+  __shared__ T su[RW * SXN];
+  __shared__ T sg[RW * SXN];                // same indexing as su (outer ring unused)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  // ---- stage u (with the optional fused correction) and g ----
+  for (int r = warp; r < RW; r += 8) {
+    int j = j0 - H + r;
+    const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
+    const T *gp = row_ptr(g, L, j);
+    bool corr = (MODE == 2) && unk_row(L, j);
+    int jw = wrap_row(L, j);
+    int J0 = jw >> 1, J1 = (jw + 1) >> 1;
+    if (J1 >= C.n1) J1 -= C.n1;
+    const T *e0 = ec + (long long)J0 * C.pitch, *e1 = ec + (long long)J1 * C.pitch;
+    for (int c = lane; c < TX + 2 * H; c += 32) {
+      int i = i0 - H + c;
+      bool inx = i >= 0 && i < L.n0;
+      T v = (rp && inx) ? rp[i] : T(0);
+      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2) {
+        int I0 = i >> 1, I1 = (i + 1) >> 1;
+        T s = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
+        v = fma(omega_corr, s, v);
+      }
+      su[r * SXN + c] = v;
+      sg[r * SXN + c] = (gp && inx) ? gp[i] : T(0);
+    }
+  }
+  __syncthreads();
+  // ---- 2 NS half-sweeps on shrinking regions ----
+#pragma unroll 1
+  for (int h = 0; h < 2 * NS; ++h) {
+    const int col = (h & 1) ? 1 - first : first, w = 2 * NS - 1 - h;
+    for (int rr = warp; rr < TY + 2 * w; rr += 8) {
+      int j = j0 - w + rr;
+      if (!unk_row(L, j)) continue;
+      int jw = wrap_row(L, j);
+      long long rowoff = (long long)jw * L.pitch;
+      long long dm = (long long)wrap_row(L, jw - 1) * L.pitch - rowoff;
+      int ib = i0 - w;                               // first column of the region
+      int par = (col + ib + j) & 1;                  // i = ib + 2q + par has colour col
+      int r = j - (j0 - H);
+      for (int q = lane; 2 * q + par < TX + 2 * w; q += 32) {
+        int i = ib + 2 * q + par;
+        if (i < 1 || i > L.n0 - 2) continue;
+        int c = i - (i0 - H);
+        su[r * SXN + c] = relax_at<T, KIND, SXN>(L, su, r, c, sg[r * SXN + c], i, rowoff + i, dm, omega);
+      }
+    }
+    __syncthreads();
+  }
+  // ---- write the tile's unknowns ----
+  for (int rr = warp; rr < TY; rr += 8) {
+    int j = j0 + rr;
+    if (!owned_row(L, j)) continue;
+    T *op = out + (long long)j * L.pitch;
+    for (int c = lane; c < TX; c += 32) {
+      int i = i0 + c;
+      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + H) * SXN + c + H];
+    }
+  }
+}
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, const T *__restrict__ u,
                                                            const T *__restrict__ g, T *__restrict__ gc) {
@@ -233,6 +307,24 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
 }
 
 template <typename T>
+void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
+                   int mode, const Lev<T> *C, const T *ec, T omega_corr) {
+  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + TY - 1) / TY);
+  Lev<T> Cv = C ? *C : L;
+  const T *e = ec ? ec : u;
+#define RB2_L(K, M) k_rb2d_ns<T, K, M, 2><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr)
+  if (kind == K_CONST) {
+    if (mode == 0) RB2_L(K_CONST, 0); else if (mode == 1) RB2_L(K_CONST, 1); else RB2_L(K_CONST, 2);
+  } else if (kind == K_SEP) {
+    if (mode == 0) RB2_L(K_SEP, 0); else if (mode == 1) RB2_L(K_SEP, 1); else RB2_L(K_SEP, 2);
+  } else {
+    if (mode == 0) RB2_L(K_CELL, 0); else if (mode == 1) RB2_L(K_CELL, 1); else RB2_L(K_CELL, 2);
+  }
+#undef RB2_L
+  ++*lc.counter;
+}
+
+template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc) {
   dim3 gr((C.n0 + CX - 1) / CX, (C.n1 + CY - 1) / CY);
@@ -246,6 +338,10 @@ template void launch_rb2d<double>(const Launch &, const Lev<double> &, int, cons
                                   double, int, int, const Lev<double> *, const double *, double);
 template void launch_rb2d<float>(const Launch &, const Lev<float> &, int, const float *, const float *, float *, float,
                                  int, int, const Lev<float> *, const float *, float);
+template void launch_rb2d_2<double>(const Launch &, const Lev<double> &, int, const double *, const double *, double *,
+                                    double, int, int, const Lev<double> *, const double *, double);
+template void launch_rb2d_2<float>(const Launch &, const Lev<float> &, int, const float *, const float *, float *,
+                                   float, int, int, const Lev<float> *, const float *, float);
 template void launch_defect_restrict2d<double>(const Launch &, const Lev<double> &, const Lev<double> &, int,
                                                const double *, const double *, double *);
 template void launch_defect_restrict2d<float>(const Launch &, const Lev<float> &, const Lev<float> &, int,

@@ -438,9 +438,16 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       cur = 1 - cur;
     } else if (rb2d) {
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
-      // small grids: one pass over tiles (launch latency bound); large: row streaming
+      // small grids: one pass over tiles (launch latency bound), two sweeps per pass where
+      // two remain (not on a timed finest level); large: row streaming
       const long long tile_max = c->P.tile_nodes == 0 ? 263169 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
       const bool small = tile_max >= 0 && (long long)L.n0 * L.n1 <= tile_max;
+      if (small && sweeps - s >= 2 && !fine) {
+        launch_rb2d_2<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
+        cur = 1 - cur;
+        ++s;   // the second sweep of the pair
+        continue;
+      }
       if (small || (!sweep_tma<T>(S, L, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc) &&
                     !launch_rb2d_march<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec,
                                           oc)))

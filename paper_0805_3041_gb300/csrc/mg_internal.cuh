@@ -172,6 +172,10 @@ void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep);
 template <typename T>
 void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
                  int mode, const Lev<T> *C, const T *ec, T omega_corr);
+// two complete sweeps in one pass (temporal blocking, small grids); mode applies to the first
+template <typename T>
+void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
+                   int mode, const Lev<T> *C, const T *ec, T omega_corr);
 template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc);
