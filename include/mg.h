@@ -94,8 +94,8 @@ typedef struct {
                              single precision (0: from the occupancy) -- a tuning knob; results do
                              not depend on it */
   int tile_nodes;         /* 2-D grids with at most this many nodes smooth with the one-pass tile
-                             kernel instead of the row-streaming ones (0: 263169 = 513^2, -1:
-                             never) -- a tuning knob; results do not depend on it */
+                             kernels instead of the row-streaming ones (0: 1050625 = 1025^2,
+                             -1: never) -- a tuning knob; results do not depend on it */
 } mg_params;
 
 typedef struct {

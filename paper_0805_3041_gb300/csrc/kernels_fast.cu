@@ -229,6 +229,110 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
   }
 }
 
+// NS sweeps, then the defect and its full-weighting restriction, in one pass (small grids:
+// the pre-smoothing of a level visit and the restriction that follows it).  The sweeps
+// run as in k_rb2d_ns on regions 2 nodes wider (halo 2 NS + 2), so the smoothed u is exact
+// on the tile plus a ring of 2; the defect is formed on the tile plus a ring of 1 and
+// restricted to the tile's 32 x 8 coarse nodes (coarse node I sits at fine 2I).  Writes
+// the tile of u and the coarse g; the fine defect is never stored.
+template <typename T, int KIND, int MODE, int NS>
+__global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T *__restrict__ u,
+                                                    const T *__restrict__ g, T *__restrict__ out, T omega, int first,
+                                                    T *__restrict__ gc) {
+  constexpr int H = 2 * NS + 2;             // halo of the u tile
+  constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
+  constexpr int SXN = TX + 2 * H + 1;       // smem row stride
+  constexpr int DS = TX + 3;                // stride of the defect tile (rows j0-1 .. j0+TY)
+  __shared__ T su[RW * SXN];
+  __shared__ T sg[RW * SXN];
+  __shared__ T sr[(TY + 2) * DS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  for (int r = warp; r < RW; r += 8) {
+    int j = j0 - H + r;
+    const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
+    const T *gp = row_ptr(g, L, j);
+    for (int c = lane; c < TX + 2 * H; c += 32) {
+      int i = i0 - H + c;
+      bool inx = i >= 0 && i < L.n0;
+      su[r * SXN + c] = (rp && inx) ? rp[i] : T(0);
+      sg[r * SXN + c] = (gp && inx) ? gp[i] : T(0);
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int h = 0; h < 2 * NS; ++h) {
+    const int col = (h & 1) ? 1 - first : first, w = 2 * NS + 1 - h;
+    for (int rr = warp; rr < TY + 2 * w; rr += 8) {
+      int j = j0 - w + rr;
+      if (!unk_row(L, j)) continue;
+      int jw = wrap_row(L, j);
+      long long rowoff = (long long)jw * L.pitch;
+      long long dm = (long long)wrap_row(L, jw - 1) * L.pitch - rowoff;
+      int ib = i0 - w;
+      int par = (col + ib + j) & 1;
+      int r = j - (j0 - H);
+      for (int q = lane; 2 * q + par < TX + 2 * w; q += 32) {
+        int i = ib + 2 * q + par;
+        if (i < 1 || i > L.n0 - 2) continue;
+        int c = i - (i0 - H);
+        su[r * SXN + c] = relax_at<T, KIND, SXN>(L, su, r, c, sg[r * SXN + c], i, rowoff + i, dm, omega);
+      }
+    }
+    __syncthreads();
+  }
+  // ---- defect on rows j0-1 .. j0+TY, columns i0-1 .. i0+TX ----
+  for (int rr = warp; rr < TY + 2; rr += 8) {
+    int j = j0 - 1 + rr;
+    bool rowok = unk_row(L, j);
+    int jw = wrap_row(L, j);
+    long long rowoff = (long long)jw * L.pitch;
+    long long dm = (long long)wrap_row(L, jw - 1) * L.pitch - rowoff;
+    int r = j - (j0 - H);
+    for (int cc = lane; cc < TX + 2; cc += 32) {
+      int i = i0 - 1 + cc;
+      T d = T(0);
+      if (rowok && i >= 1 && i <= L.n0 - 2) {
+        long long p = rowoff + i;
+        Weights<T, 2, KIND> wt;
+        wt.load(L, i, p, dm);
+        const T *sp = su + r * SXN + (i - (i0 - H));
+        T uc = sp[0];
+        T sum;
+        if (KIND == K_CONST) {
+          sum = fma(-L.d, uc, sg[r * SXN + (i - (i0 - H))]);
+        } else {
+          T D = (wt.wW + wt.wE) + (wt.wS + wt.wN);
+          sum = fma(-D, uc, sg[r * SXN + (i - (i0 - H))]);
+        }
+        sum = fma(wt.wW, sp[-1], sum);
+        sum = fma(wt.wE, sp[1], sum);
+        sum = fma(wt.wS, sp[-SXN], sum);
+        sum = fma(wt.wN, sp[SXN], sum);
+        d = sum;
+      }
+      sr[rr * DS + cc] = d;
+    }
+  }
+  __syncthreads();
+  // ---- the tile of u, and the coarse g ----
+  for (int rr = warp; rr < TY; rr += 8) {
+    int j = j0 + rr;
+    if (!owned_row(L, j)) continue;
+    T *op = out + (long long)j * L.pitch;
+    for (int c = lane; c < TX; c += 32) {
+      int i = i0 + c;
+      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + H) * SXN + c + H];
+    }
+  }
+  int I = (i0 >> 1) + lane, J = (j0 >> 1) + warp;
+  if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
+    const T *sp = sr + (2 * warp + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
+    auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
+    gc[(long long)J * C.pitch + I] = ((row3(sp - DS) + row3(sp + DS)) + T(2) * row3(sp)) * T(0.0625);
+  }
+}
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, const T *__restrict__ u,
                                                            const T *__restrict__ g, T *__restrict__ gc) {
@@ -325,6 +429,22 @@ void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
 }
 
 template <typename T>
+void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int kind, const T *u, const T *g, T *out,
+                      T omega, int first, int mode, T *gc) {
+  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + TY - 1) / TY);
+#define RB2D_L(K, M) k_rb2d_ns_dr<T, K, M, 2><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc)
+  if (kind == K_CONST) {
+    if (mode == 1) RB2D_L(K_CONST, 1); else RB2D_L(K_CONST, 0);
+  } else if (kind == K_SEP) {
+    if (mode == 1) RB2D_L(K_SEP, 1); else RB2D_L(K_SEP, 0);
+  } else {
+    if (mode == 1) RB2D_L(K_CELL, 1); else RB2D_L(K_CELL, 0);
+  }
+#undef RB2D_L
+  ++*lc.counter;
+}
+
+template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc) {
   dim3 gr((C.n0 + CX - 1) / CX, (C.n1 + CY - 1) / CY);
@@ -342,6 +462,10 @@ template void launch_rb2d_2<double>(const Launch &, const Lev<double> &, int, co
                                     double, int, int, const Lev<double> *, const double *, double);
 template void launch_rb2d_2<float>(const Launch &, const Lev<float> &, int, const float *, const float *, float *,
                                    float, int, int, const Lev<float> *, const float *, float);
+template void launch_rb2d_2_dr<double>(const Launch &, const Lev<double> &, const Lev<double> &, int, const double *,
+                                       const double *, double *, double, int, int, double *);
+template void launch_rb2d_2_dr<float>(const Launch &, const Lev<float> &, const Lev<float> &, int, const float *,
+                                      const float *, float *, float, int, int, float *);
 template void launch_defect_restrict2d<double>(const Launch &, const Lev<double> &, const Lev<double> &, int,
                                                const double *, const double *, double *);
 template void launch_defect_restrict2d<float>(const Launch &, const Lev<float> &, const Lev<float> &, int,

@@ -440,7 +440,7 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
       // small grids: one pass over tiles (launch latency bound), two sweeps per pass where
       // two remain (not on a timed finest level); large: row streaming
-      const long long tile_max = c->P.tile_nodes == 0 ? 263169 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
+      const long long tile_max = c->P.tile_nodes == 0 ? 1050625 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
       const bool small = tile_max >= 0 && (long long)L.n0 * L.n1 <= tile_max;
       if (small && sweeps - s >= 2 && !fine) {
         launch_rb2d_2<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
@@ -597,10 +597,20 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
   Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
   int npre = transposed ? c->P.nu2 : c->P.nu1, npost = transposed ? c->P.nu1 : c->P.nu2;
   int order = transposed ? 1 : 0;
-  smooth<T>(S, l, g, npre, order, zero_start);
-  if (c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP)) {
+  const long long tile_max = c->P.tile_nodes == 0 ? 1050625 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
+  const bool fused2d = c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP);
+  if (fused2d && c->P.smoother == MG_RBGS && npre == 2 && tile_max >= 0 && (long long)L.n0 * L.n1 <= tile_max &&
+      !(S.timing && l == c->L)) {
+    // small grid: both pre-smoothing sweeps, the defect and the restriction in one pass
+    int &cu = c->cur[l];
+    launch_rb2d_2_dr<T>(S.lc, L, Lc, c->kind, D.u[cu], g, D.u[1 - cu], (T)c->P.omega, order, zero_start ? 1 : 0,
+                        Dc.g);
+    cu = 1 - cu;
+  } else if (fused2d) {
+    smooth<T>(S, l, g, npre, order, zero_start);
     launch_defect_restrict2d<T>(S.lc, L, Lc, c->kind, D.u[c->cur[l]], g, Dc.g);
   } else {
+    smooth<T>(S, l, g, npre, order, zero_start);
     launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
     launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
   }

@@ -176,6 +176,11 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
 template <typename T>
 void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
                    int mode, const Lev<T> *C, const T *ec, T omega_corr);
+// two sweeps, then the defect and its full-weighting restriction into the coarse g, in one pass
+// (small grids; mode 0 or 1)
+template <typename T>
+void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int kind, const T *u, const T *g, T *out,
+                      T omega, int first, int mode, T *gc);
 template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc);
