@@ -116,7 +116,10 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
   for (int op = 0; op < nops; ++op) {
     int4 o = op < CSK_STAGED_OPS ? s_prog[op] : prog[op];
     const SLev<T> &S = levs[o.y];
-    const Lev<T> &L = S.L;   // read in place from shared memory (cell pointers patched at start)
+    // a register copy of the level view: the steps store through pool pointers, which the
+    // compiler cannot prove distinct from the level table, so fields read in place would be
+    // reloaded after every store
+    const Lev<T> L = S.L;
     T *ub[2] = {pool + S.off_u0, pool + S.off_u1};
     T *g = pool + S.off_g, *r = pool + S.off_r;
     switch (o.x) {
