@@ -16,7 +16,9 @@ enum CoarseOp {
   CP_DEFECT = 8,    // r_y = g_y - A u_y[a]
   CP_RESTRICT = 9,  // g_{y-1} = R r_y
   CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b]
-  CP_COARSE = 11    // u_1[a] = A_1^{-1} g_1
+  CP_COARSE = 11,   // u_1[a] = A_1^{-1} g_1
+  CP_RB_ZERO = 12   // u_y[b] = first half sweep of colour a from a zero iterate (replaces ZERO_U +
+                    // RB_HALF with the same arithmetic: the residual of a zero iterate is g)
 };
 
 }  // namespace mg

@@ -272,6 +272,22 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         });
         break;
       }
+      case CP_RB_ZERO: {   // z = colour, w = buffer: first half sweep from a zero iterate
+        T *u = ub[o.w];
+        const int colour = o.z;
+        FOR_UNK(L, {
+          T v = T(0);
+          if (((i + j + k) & 1) == colour) {
+            int dm, dp;
+            yoffs(L, j, dm, dp);
+            Weights<T, DIM, KIND> w;
+            w.load(L, i, p, dm);
+            v = fma(omega * w.dinv, g[p], T(0));   // the residual of a zero iterate is g
+          }
+          u[p] = v;
+        });
+        break;
+      }
       case CP_COARSE: {   // level 1: u[z] = A^{-1} g, one warp per row of the dense inverse
         T *u = ub[o.z];
         const int lane = threadIdx.x & 31;

@@ -522,14 +522,20 @@ struct ProgBuilder {
       }
       return;
     }
-    if (zero) op(CP_ZERO_U, l, cu, 0);
     if (sm == MG_RBGS) {
-      for (int s = 0; s < sweeps; ++s) {
+      int s0 = 0;
+      if (zero) {   // the first half sweep from a zero iterate sets every unknown
+        op(CP_RB_ZERO, l, order, cu);
+        op(CP_RB_HALF, l, 1 - order, cu);
+        s0 = 1;
+      }
+      for (int s = s0; s < sweeps; ++s) {
         op(CP_RB_HALF, l, order, cu);
         op(CP_RB_HALF, l, 1 - order, cu);
       }
       return;
     }
+    if (zero) op(CP_ZERO_U, l, cu, 0);
     int dir = (sm == MG_LINE_X || sm == MG_ZEBRA_X) ? 0 : 1;
     bool zebra = sm >= MG_ZEBRA_X;
     for (int s = 0; s < sweeps; ++s) {
