@@ -49,9 +49,17 @@ __device__ __forceinline__ void yoffs(const Lev<T> &L, int j, IT &dm, IT &dp) {
 // Row index r in [0, unk_rows) -> (j, k) of an unknown row.
 template <typename T>
 __device__ __forceinline__ void row_jk(const Lev<T> &L, long long r, int &j, int &k) {
-  int yr = L.yrows();
-  j = L.ylo() + (int)(r % yr);
-  k = (L.dim == 3 ? 1 : 0) + (int)(r / yr);
+  // row counts fit in 32 bits; 2-D needs no division, 3-D a 32-bit one (a 64-bit integer
+  // division is a long software sequence on the GPU)
+  const int rr = (int)r;
+  if (L.dim == 2) {
+    j = L.ylo() + rr;
+    k = 0;
+  } else {
+    const int yr = L.yrows(), q = rr / yr;
+    j = L.ylo() + (rr - q * yr);
+    k = 1 + q;
+  }
 }
 
 // Edge weights around node p = (i, j, k): W, E (x), S, N (y), B, F (z), and 1/D.
