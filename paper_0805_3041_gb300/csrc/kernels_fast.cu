@@ -23,7 +23,9 @@ namespace mg {
 namespace {
 constexpr int TX = 64, TY = 16;   // RB output tile
 constexpr int SX = TX + 5;        // smem row stride of the u tile (halo 2 + pad)
-constexpr int CX = 32, CY = 8;    // coarse tile of the defect/restriction
+constexpr int CX = 32;            // coarse tile of the defect/restriction: CX x CY_OF(T)
+template <typename T>
+struct CYOf { static constexpr int v = sizeof(T) == 8 ? 8 : 16; };   // FP64 within 48 KB static smem
 
 // row pointer of node row j, or nullptr for a row outside a Dirichlet grid; periodic rows wrap
 template <typename T>
@@ -336,18 +338,24 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, const T *__restrict__ u,
                                                            const T *__restrict__ g, T *__restrict__ gc) {
+  constexpr int CY = CYOf<T>::v;
   constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;   // fine defect region
   constexpr int US = RX + 3;                        // smem stride
   __shared__ T su[(RY + 2) * US];
+  __shared__ T sgf[RY * US];
   __shared__ T sr[RY * US];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int I0 = blockIdx.x * CX, J0 = blockIdx.y * CY;
   const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;     // fine origin of the defect region
+  // u (with a ring of 1) and g in one round of loads
   for (int r = warp; r < RY + 2; r += 8) {
     const T *rp = row_ptr(u, F, fj0 - 1 + r);
+    const T *gp = (r >= 1 && r <= RY) ? row_ptr(g, F, fj0 - 1 + r) : nullptr;
     for (int c = lane; c < RX + 2; c += 32) {
       int i = fi0 - 1 + c;
-      su[r * US + c] = (rp && i >= 0 && i < F.n0) ? rp[i] : T(0);
+      bool inx = i >= 0 && i < F.n0;
+      su[r * US + c] = (rp && inx) ? rp[i] : T(0);
+      if (r >= 1 && r <= RY && c >= 1 && c <= RX) sgf[(r - 1) * US + (c - 1)] = (gp && inx) ? gp[i] : T(0);
     }
   }
   __syncthreads();
@@ -368,10 +376,10 @@ __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, c
         T uc = s[0];
         T sum;
         if (KIND == K_CONST) {
-          sum = fma(-F.d, uc, g[p]);
+          sum = fma(-F.d, uc, sgf[r * US + c]);
         } else {
           T D = (w.wW + w.wE) + (w.wS + w.wN);
-          sum = fma(-D, uc, g[p]);
+          sum = fma(-D, uc, sgf[r * US + c]);
         }
         sum = fma(w.wW, s[-1], sum);
         sum = fma(w.wE, s[1], sum);
@@ -383,12 +391,14 @@ __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, c
     }
   }
   __syncthreads();
-  int I = I0 + lane, J = J0 + warp;
-  if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
-    const T *s = sr + (2 * warp + 1) * US + (2 * lane + 1);   // centre of the stencil in sr
-    auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
-    T v = ((row3(s - US) + row3(s + US)) + T(2) * row3(s)) * T(0.0625);
-    gc[(long long)J * C.pitch + I] = v;
+  for (int cy = warp; cy < CY; cy += 8) {
+    int I = I0 + lane, J = J0 + cy;
+    if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
+      const T *s = sr + (2 * cy + 1) * US + (2 * lane + 1);   // centre of the stencil in sr
+      auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
+      T v = ((row3(s - US) + row3(s + US)) + T(2) * row3(s)) * T(0.0625);
+      gc[(long long)J * C.pitch + I] = v;
+    }
   }
 }
 
@@ -447,7 +457,7 @@ void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int ki
 template <typename T>
 void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C, int kind, const T *u, const T *g,
                               T *gc) {
-  dim3 gr((C.n0 + CX - 1) / CX, (C.n1 + CY - 1) / CY);
+  dim3 gr((C.n0 + CX - 1) / CX, (C.n1 + CYOf<T>::v - 1) / CYOf<T>::v);
   if (kind == K_CONST) k_defect_restrict2d<T, K_CONST><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   else if (kind == K_SEP) k_defect_restrict2d<T, K_SEP><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   else k_defect_restrict2d<T, K_CELL><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);

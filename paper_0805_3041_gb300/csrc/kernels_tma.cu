@@ -422,6 +422,298 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
     band_sweep<KIND, MODE, false>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err);
 }
 
+// ---------------------------------------------------------------------------------------
+// The defect d = g - A u of a fine level and its full-weighting restriction g_c = R d
+// (Wallis 2008, section "The Multigrid Technique"), streamed the same way: a CTA owns a band
+// of coarse rows [J0, J1) of a 256-coarse-column group (512 fine columns); the producer warp
+// streams fine rows 2 J0 - 2 .. 2 J1 of u and g through the ring; each compute warp keeps
+// three u rows in registers, forms the defect of the middle row (4 columns per lane, x
+// neighbours by shuffles, the strip-edge lane also forms the defect one column to the left),
+// folds it into the row sums (d_{i-1} + d_{i+1}) + 2 d_i at its two coarse columns, and
+// writes coarse row J when the defect of fine row 2J + 1 is done.  The fine defect is never
+// stored: 8 B read per fine unknown and 1 B written (FP32).  Same arithmetic, in the same
+// order, as the tile kernel k_defect_restrict2d.
+template <int KIND, bool IN>
+__device__ __forceinline__ void band_dr(const Lev<float> L, const Lev<float> C, const float *__restrict__ u,
+                                        const float *__restrict__ g, float *__restrict__ gc, int J0, int J1, int s0,
+                                        float *ring, uint64_t *full, uint64_t *empty, int *err) {
+  constexpr int SLOT = 2 * SEGW;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sw = s0 + 128 * warp;
+  const int i0 = sw + 4 * lane;
+  const int c0 = 4 + 128 * warp + 4 * lane;
+  const bool edge = lane == 0 || lane == 31;
+  const int io = lane == 0 ? sw - 1 : sw + 128;
+  const int co = lane == 0 ? c0 - 1 : c0 + 4, co2 = lane == 0 ? c0 - 2 : c0 + 5;
+
+  Coef K;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = i0 + e;
+    K.act[e] = i >= 1 && i <= L.n0 - 2;
+    if (KIND == K_CONST) {
+      K.W[e] = L.cx; K.E[e] = L.cx; K.Y[e] = L.cy; K.D[e] = L.d; K.O[e] = 0.f;
+    } else {
+      const int ic = K.act[e] ? i : 1;
+      K.W[e] = L.sx[ic - 1]; K.E[e] = L.sx[ic]; K.Y[e] = L.sy[ic];
+      K.D[e] = (K.W[e] + K.E[e]) + (K.Y[e] + K.Y[e]);
+      K.O[e] = 0.f;
+    }
+  }
+  // the extra defect of lane 0 at column sw - 1
+  const bool oact = lane == 0 && io >= 1 && io <= L.n0 - 2;
+  float oW = L.cx, oE = L.cx, oY = L.cy, oD = L.d;
+  if (KIND == K_SEP && lane == 0) {
+    const int ic = oact ? io : 1;
+    oW = L.sx[ic - 1]; oE = L.sx[ic]; oY = L.sy[ic];
+    oD = (oW + oE) + (oY + oY);
+  }
+
+  const int cs = max(0, s0 - 4), ce = min((int)L.pitch, s0 + 128 * NW + 4);
+  const int doff = cs - (s0 - 4);
+  const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
+
+  auto valid = [&](int j) { return IN || L.per || (j >= 0 && j < L.n1); };
+  auto unk = [&](int j) { return IN || L.per || (j >= 1 && j <= L.n1 - 2); };
+  auto wrap = [&](int j) -> int {
+    if (IN || !L.per) return j;
+    j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
+    if (j < 0 || j >= L.n1) j = ((j % L.n1) + L.n1) % L.n1;
+    return j;
+  };
+  const int jfirst = 2 * J0 - 2, jlast = 2 * J1;   // fine rows streamed
+  auto slot_of = [&](int j) -> const float * { return ring + ((j - jfirst) & (RING - 1)) * SLOT; };
+  const int jv0 = valid(jfirst) ? jfirst : (valid(jfirst + 1) ? jfirst + 1 : jfirst + 2);
+  auto full_parity = [&](int j) -> uint32_t { return (uint32_t)(((j - jv0) >> RING_LOG) & 1); };
+  auto empty_parity = [&](int j) -> uint32_t { return (uint32_t)(((j - jfirst) >> RING_LOG) & 1); };
+
+  auto issue = [&](int j) {
+    if (!valid(j)) return;
+    const int k = j - jfirst;
+    float *slot = ring + (k & (RING - 1)) * SLOT;
+    uint64_t *bar = &full[k & (RING - 1)];
+    const long long ro = (long long)wrap(j) * L.pitch;
+    mbar_expect_tx(bar, 2u * seg_bytes);
+    tma_load_1d(slot + doff, u + ro + cs, seg_bytes, bar);
+    tma_load_1d(slot + SEGW + doff, g + ro + cs, seg_bytes, bar);
+  };
+  if (warp == NW) {   // producer (lane 0): as in band_sweep
+    if (lane != 0) return;
+    int r = jfirst;
+    bool ok = true;
+    for (; r <= jlast; ++r) {
+      if (r - RING >= jfirst &&
+          !mbar_wait(&empty[(r - jfirst) & (RING - 1)], empty_parity(r - RING), WAIT_CYCLES)) {
+        ok = false;
+        break;
+      }
+      issue(r);
+    }
+    for (int q = max(jfirst, jlast - RING + 1); q <= jlast && ok; ++q)
+      ok = mbar_wait(&empty[(q - jfirst) & (RING - 1)], empty_parity(q), WAIT_CYCLES);
+    if (!ok) {
+      atomicExch(err, 1);
+      for (int q = max(jfirst, r - RING); q < r; ++q)
+        if (valid(q)) mbar_wait(&full[(q - jfirst) & (RING - 1)], full_parity(q), DRAIN_CYCLES);
+    }
+    return;
+  }
+  auto arrive_row = [&](int j) -> bool {
+    bool ok = true;
+    if (valid(j)) ok = mbar_wait(&full[(j - jfirst) & (RING - 1)], full_parity(j), WAIT_CYCLES);
+    return __all_sync(FULL, ok);
+  };
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[(j - jfirst) & (RING - 1)]);
+  };
+  auto load_row = [&](URow &R, int j) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) R.u[e] = 0.f;
+    R.out = 0.f;
+    R.out2 = 0.f;
+    if (!valid(j)) return;
+    const float *slot = slot_of(j);
+    const float4 v = *reinterpret_cast<const float4 *>(slot + c0);
+    R.u[0] = v.x; R.u[1] = v.y; R.u[2] = v.z; R.u[3] = v.w;
+    if (edge) {
+      R.out = slot[co];
+      R.out2 = slot[co2];
+    }
+  };
+  // row sums (d_{i-1} + d_{i+1}) + 2 d_i of the defect of fine row j at the lane's coarse columns
+  // (fine 4L and 4L + 2 of the strip)
+  auto defect_row3 = [&](const URow &Rm, const URow &R, const URow &Rp, int j, float &ra, float &rb) {
+    const bool rowu = unk(j);
+    const float4 g4 = *reinterpret_cast<const float4 *>(slot_of(j) + SEGW + c0);
+    const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+    float left = __shfl_up_sync(FULL, R.u[3], 1), right = __shfl_down_sync(FULL, R.u[0], 1);
+    if (lane == 0) left = R.out;
+    if (lane == 31) right = R.out;
+    float d[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float wv = e > 0 ? R.u[e - 1] : left, ev = e < 3 ? R.u[e + 1] : right;
+      float s = fmaf(-K.D[e], R.u[e], gg[e]);
+      s = fmaf(K.W[e], wv, s);
+      s = fmaf(K.E[e], ev, s);
+      s = fmaf(K.Y[e], Rm.u[e], s);
+      s = fmaf(K.Y[e], Rp.u[e], s);
+      d[e] = (rowu && K.act[e]) ? s : 0.f;
+    }
+    // defect at column 4L - 1: the left lane's d[3]; lane 0 forms its own
+    float dl = __shfl_up_sync(FULL, d[3], 1);
+    if (lane == 0) {
+      dl = 0.f;
+      if (oact && rowu) {
+        const float gl = slot_of(j)[SEGW + co];
+        float s = fmaf(-oD, R.out, gl);
+        s = fmaf(oW, R.out2, s);
+        s = fmaf(oE, R.u[0], s);
+        s = fmaf(oY, Rm.out, s);
+        s = fmaf(oY, Rp.out, s);
+        dl = s;
+      }
+    }
+    ra = (dl + d[1]) + 2.f * d[0];
+    rb = (d[1] + d[3]) + 2.f * d[2];
+  };
+  auto store_coarse = [&](int J, float va, float vb) {
+    const bool Jok = C.per ? (J >= 0 && J < C.n1) : (J >= 1 && J <= C.n1 - 2);
+    if (!Jok) return;
+    const int I = (sw >> 1) + 2 * lane;
+    float *rowp = gc + (long long)J * C.pitch;
+    if (I >= 1 && I <= C.n0 - 2) rowp[I] = va;
+    if (I + 1 >= 1 && I + 1 <= C.n0 - 2) rowp[I + 1] = vb;
+  };
+
+  URow A, B, Cr;
+  float pa = 0.f, pb = 0.f, ea = 0.f, eb = 0.f;   // row sums of fine rows 2J - 1 (odd) and 2J (even)
+  bool ok = arrive_row(jfirst) && arrive_row(jfirst + 1);
+  if (ok) {
+    load_row(A, jfirst);
+    load_row(B, jfirst + 1);
+  }
+  // fine row jf arrives -> defect of row jf - 1 (rows A = jf-2, B = jf-1, Cr = jf)
+  auto step = [&](URow &Um, URow &Uc, URow &Up, int jf) -> bool {
+    if (!arrive_row(jf)) return false;
+    load_row(Up, jf);
+    const int jd = jf - 1;   // row of the defect
+    float ra, rb;
+    defect_row3(Um, Uc, Up, jd, ra, rb);
+    const int rel = jd - (2 * J0 - 1);   // 0, 1, 2, ... : rows 2J0-1, 2J0, 2J0+1, ...
+    if (rel == 0) {
+      pa = ra;
+      pb = rb;
+    } else if (rel & 1) {
+      ea = ra;
+      eb = rb;
+    } else {   // jd = 2J + 1 with J = J0 + rel / 2 - 1
+      const int J = J0 + rel / 2 - 1;
+      store_coarse(J, ((pa + ra) + 2.f * ea) * 0.0625f, ((pb + rb) + 2.f * eb) * 0.0625f);
+      pa = ra;
+      pb = rb;
+    }
+    release(jf - 2);
+    return true;
+  };
+  if (ok) {
+    for (int jf = jfirst + 2; jf <= jlast; jf += 3) {
+      if (!(ok = step(A, B, Cr, jf))) break;
+      if (jf + 1 > jlast) break;
+      if (!(ok = step(B, Cr, A, jf + 1))) break;
+      if (jf + 2 > jlast) break;
+      if (!(ok = step(Cr, A, B, jf + 2))) break;
+    }
+  }
+  if (ok) {
+    release(jlast - 1);
+    release(jlast);
+  } else if (lane == 0) {
+    atomicExch(err, 1);
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(32 * (NW + 1)) k_defect_restrict_tma(Lev<float> L, Lev<float> C,
+                                                                       const float *__restrict__ u,
+                                                                       const float *__restrict__ g,
+                                                                       float *__restrict__ gc, int RCc, int ngroups,
+                                                                       int *err) {
+  constexpr int SLOT = 2 * SEGW;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  float *ring = reinterpret_cast<float *>(tma_smem);
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + RING * SLOT);
+  uint64_t *empty = full + RING;
+  const int grp = blockIdx.x % ngroups, band = blockIdx.x / ngroups;
+  const int Jlo = C.per ? 0 : 1, Jhi = C.per ? C.n1 - 1 : C.n1 - 2;   // coarse unknown rows
+  const int J0 = Jlo + band * RCc;
+  if (J0 > Jhi) return;
+  const int J1 = min(J0 + RCc, Jhi + 1);
+  const int s0 = grp * 128 * NW;
+  const int nact = min(NW, (int)(L.pitch - s0) / 128);
+  for (int t = threadIdx.x; t < RING * SLOT; t += 32 * (NW + 1)) ring[t] = 0.f;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RING; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nact);
+    }
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp < NW && warp >= nact) return;
+  const bool interior = L.per ? (2 * J0 - 2 >= 0 && 2 * J1 <= L.n1 - 1) : (2 * J0 - 2 >= 1 && 2 * J1 <= L.n1 - 2);
+  if (interior) band_dr<KIND, true>(L, C, u, g, gc, J0, J1, s0, ring, full, empty, err);
+  else band_dr<KIND, false>(L, C, u, g, gc, J0, J1, s0, ring, full, empty, err);
+}
+
+bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev<float> &C, int kind,
+                                const float *u, const float *g, float *gc, int *err, int rc) {
+  if (L.dim != 2 || kind == K_CELL || L.pitch % 128 != 0 || L.n0 < 5 || !err) return false;
+  if (((uintptr_t)u | (uintptr_t)g) & 15) return false;
+  const int crows = C.per ? C.n1 : C.n1 - 2;
+  if (crows <= 0) return false;
+  const int nstrips = (int)(L.pitch / 128);
+  const int ngroups = (nstrips + NW - 1) / NW;
+  const size_t smem = rb2d_tma_smem(0);
+  const int ki = kind == K_CONST ? 0 : 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static thread_local int occ_dev = -1, occ[2] = {0, 0}, sms = 0;
+  if (occ_dev != dev) {
+    occ_dev = dev;
+    occ[0] = occ[1] = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (occ[ki] <= 0) {
+    if (kind == K_CONST) {
+      cudaFuncSetAttribute(k_defect_restrict_tma<K_CONST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[ki], k_defect_restrict_tma<K_CONST>, 32 * (NW + 1), smem);
+    } else {
+      cudaFuncSetAttribute(k_defect_restrict_tma<K_SEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[ki], k_defect_restrict_tma<K_SEP>, 32 * (NW + 1), smem);
+    }
+    if (occ[ki] <= 0) occ[ki] = 1;
+  }
+  int RCc = rc;
+  if (RCc <= 0) {
+    const long long slots = (long long)std::max(sms, 1) * occ[ki];
+    const long long nb = std::max<long long>(1, slots / ngroups);
+    RCc = (int)std::max<long long>(4, (crows + nb - 1) / nb);
+  }
+  const int nbands = (crows + RCc - 1) / RCc;
+  const unsigned blocks = (unsigned)((long long)ngroups * nbands);
+  if (kind == K_CONST)
+    k_defect_restrict_tma<K_CONST><<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, C, u, g, gc, RCc, ngroups, err);
+  else
+    k_defect_restrict_tma<K_SEP><<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, C, u, g, gc, RCc, ngroups, err);
+  ++*lc.counter;
+  return true;
+}
+
 size_t rb2d_tma_smem(int mode) {
   const int slot = 2 * SEGW + (mode == 2 ? 2 * CSEGW : 0);
   return (size_t)RING * slot * sizeof(float) + 2 * RING * sizeof(uint64_t);

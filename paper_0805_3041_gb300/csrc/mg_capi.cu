@@ -396,6 +396,19 @@ bool sweep_tma<float>(Sched &S, const Lev<float> &L, const float *u, const float
   return launch_rb2d_tma(S.lc, L, c->kind, u, g, out, om, order, mode, Cp, ec, oc, c->st + 2, c->P.sweep_rows);
 }
 
+// The fused defect + restriction in FP32 through the TMA-fed kernel, where it applies.
+template <typename T>
+static bool defect_restrict_tma(Sched &, const Lev<T> &, const Lev<T> &, const T *, const T *, T *) {
+  return false;
+}
+template <>
+bool defect_restrict_tma<float>(Sched &S, const Lev<float> &L, const Lev<float> &C, const float *u, const float *g,
+                                float *gc) {
+  mg_ctx *c = S.c;
+  if (c->P.flags & MG_FLAG_NO_TMA) return false;
+  return launch_defect_restrict_tma(S.lc, L, C, c->kind, u, g, gc, c->st + 2, 0);
+}
+
 // `sweeps` smoothing steps on level l.  With ec != nullptr the coarse-grid correction
 // u += omega_l P ec is applied first -- folded into the first fused red-black sweep when
 // there is one, as its own kernel otherwise.
@@ -614,7 +627,8 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
     cu = 1 - cu;
   } else if (fused2d) {
     smooth<T>(S, l, g, npre, order, zero_start);
-    launch_defect_restrict2d<T>(S.lc, L, Lc, c->kind, D.u[c->cur[l]], g, Dc.g);
+    if (!defect_restrict_tma<T>(S, L, Lc, D.u[c->cur[l]], g, Dc.g))
+      launch_defect_restrict2d<T>(S.lc, L, Lc, c->kind, D.u[c->cur[l]], g, Dc.g);
   } else {
     smooth<T>(S, l, g, npre, order, zero_start);
     launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);

@@ -205,6 +205,10 @@ bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const floa
                      float omega, int first, int mode, const Lev<float> *C, const float *ec, float omega_corr,
                      int *err, int rc);
 size_t rb2d_tma_smem(int mode);
+// the fused defect + full-weighting restriction (2-D, FP32, constant or separable
+// coefficients) streamed the same way; rc = coarse rows per CTA (0: from the occupancy)
+bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev<float> &C, int kind,
+                                const float *u, const float *g, float *gc, int *err, int rc);
 
 // single-CTA coarse cycle (kernels_coarse.cu): levs = device table of shared-memory level
 // views (filled by coarse_fill_levels), prog = program of CoarseOp steps
