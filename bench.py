@@ -63,6 +63,12 @@ def measured_peaks():
 # (1.19-1.20 TFLOP/s = 0.6 T FMA instructions/s over 152 SMs at ~1.95 GHz).
 FP64_TFLOPS_MEASURED = 1.197
 
+# DRAM bytes (read + write) per launch of the finest-level red-black sweep of the 4097^2
+# mixed solve, from one ncu capture of the current k_rb2d_tma: the mean of the cycle's four
+# launches (zero start 93.2 MB, plain 181.6 MB, correction folded in 205.5 MB, plain 181.7 MB).
+# It must be re-measured, or set to None, whenever that kernel changes.
+FINEST_SWEEP_TRAFFIC = 165.5e6
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms in the background."""
@@ -291,7 +297,11 @@ def run_ours(args):
     else:
         achieved = kern_bytes / (kern_ms * 1e-3) / 1e9 if kern_ms else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                "traffic": FINEST_SWEEP_TRAFFIC if args.n == 4097 and args.smoother == "rbgs" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of the four "
+                                  "finest-level sweeps of one refinement step (zero start, plain, correction "
+                                  "folded in, plain)",
                 "kernel": "finest-level smoothing sweep (FP32)", "peak_source": src,
                 "launch_ms": kern_ms, "launches": kern_n, "bytes_per_launch": kern_bytes}
 
