@@ -120,24 +120,25 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
     // compiler cannot prove distinct from the level table, so fields read in place would be
     // reloaded after every store
     const Lev<T> L = S.L;
-    T *ub[2] = {pool + S.off_u0, pool + S.off_u1};
+    T *const ub0 = pool + S.off_u0, *const ub1 = pool + S.off_u1;
+    auto ub = [&](int b) -> T * { return b ? ub1 : ub0; };   // no runtime-indexed array (local memory)
     T *g = pool + S.off_g, *r = pool + S.off_r;
     switch (o.x) {
       case CP_LOAD_G:
         FOR_UNK(L, { g[p] = g_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
         break;
       case CP_LOAD_U:
-        FOR_UNK(L, { ub[o.z][p] = u_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
+        FOR_UNK(L, { ub(o.z)[p] = u_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
         break;
       case CP_STORE_U:
-        FOR_UNK(L, { u_out[(long long)k * S.gplane + (long long)j * S.gpitch + i] = ub[o.z][p]; });
+        FOR_UNK(L, { u_out[(long long)k * S.gplane + (long long)j * S.gpitch + i] = ub(o.z)[p]; });
         break;
       case CP_ZERO_U:
-        FOR_UNK(L, { ub[o.z][p] = T(0); });
+        FOR_UNK(L, { ub(o.z)[p] = T(0); });
         break;
       case CP_JACOBI: {   // z = src, w = dst; src < 0: zero iterate
-        const T *src = o.z >= 0 ? ub[o.z] : nullptr;
-        T *dst = ub[o.w];
+        const T *src = o.z >= 0 ? ub(o.z) : nullptr;
+        T *dst = ub(o.w);
         FOR_UNK(L, {
           int dm, dp;
           yoffs(L, j, dm, dp);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         break;
       }
       case CP_RB_HALF: {   // z = colour, w = buffer
-        T *u = ub[o.w];
+        T *u = ub(o.w);
         int colour = o.z;
         FOR_COLOUR(L, colour, {
           int dm, dp;
@@ -162,8 +163,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
       }
       case CP_LINE: {   // z = dir | zebra << 1 | colour << 2, w = src | dst << 4 | scratch << 8
         int dir = o.z & 1, zebra = (o.z >> 1) & 1, colour = (o.z >> 2) & 1;
-        T *src = ub[o.w & 15], *dst = ub[(o.w >> 4) & 15];
-        T *cps = r, *dps = ub[(o.w >> 8) & 15];
+        T *src = ub(o.w & 15), *dst = ub((o.w >> 4) & 15);
+        T *cps = r, *dps = ub((o.w >> 8) & 15);
         int nlines = dir == 0 ? (int)L.unk_rows() : (L.n0 - 2) * L.zrows();
         for (int t = tid_; t < nlines; t += nthr_) {
           int m, a_fixed, kk;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         break;
       }
       case CP_DEFECT: {   // z = buffer
-        const T *u = ub[o.z];
+        const T *u = ub(o.z);
         FOR_UNK(L, {
           int dm, dp;
           yoffs(L, j, dm, dp);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
         const T *ec = (o.w ? pool + Cs.off_u1 : pool + Cs.off_u0);
-        T *uf = ub[o.z];
+        T *uf = ub(o.z);
         FOR_UNK(L, {
           int I0 = i >> 1, I1 = (i + 1) >> 1;
           int J0 = j >> 1, J1 = (j + 1) >> 1;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         break;
       }
       case CP_RB_ZERO: {   // z = colour, w = buffer: first half sweep from a zero iterate
-        T *u = ub[o.w];
+        T *u = ub(o.w);
         const int colour = o.z;
         FOR_UNK(L, {
           T v = T(0);
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         break;
       }
       case CP_COARSE: {   // level 1: u[z] = A^{-1} g, one warp per row of the dense inverse
-        T *u = ub[o.z];
+        T *u = ub(o.z);
         const int lane = threadIdx.x & 31;
         for (int row = wid_; row < nc; row += nw_) {
           const double *arow = Ainv + (long long)row * nc;
