@@ -256,6 +256,17 @@ static void lev_smooth(or_hier *H, lev_t *v, double *u, const double *g, int swe
       case OR_LINE_Y: sweep_line(v, u, g, H->omega, 1, 0, first, v->r); break;
       case OR_ZEBRA_X: sweep_line(v, u, g, H->omega, 0, 1, first, v->r); break;
       case OR_ZEBRA_Y: sweep_line(v, u, g, H->omega, 1, 1, first, v->r); break;
+      /* ADI / GSADI (sections "The choice of C" and "Coordinate systems": TRIx then TRIy, GSTRIx
+       * then GSTRIy): the x-line sweep then the y-line sweep.  The transposed cycle (BLACK_FIRST)
+       * runs the composition in reverse order, each zebra part with its colours reversed. */
+      case OR_ADI:
+        sweep_line(v, u, g, H->omega, first ? 1 : 0, 0, first, v->r);
+        sweep_line(v, u, g, H->omega, first ? 0 : 1, 0, first, v->r);
+        break;
+      case OR_GSADI:
+        sweep_line(v, u, g, H->omega, first ? 1 : 0, 1, first, v->r);
+        sweep_line(v, u, g, H->omega, first ? 0 : 1, 1, first, v->r);
+        break;
     }
     v->nsmooth++;
   }
@@ -585,8 +596,10 @@ int or_create(const or_config *cfg, or_hier **out) {
   *out = NULL;
   if (cfg->dim != 2 && cfg->dim != 3) return OR_EINVAL;
   if (cfg->levels < 1 || cfg->levels > OR_MAXLEV) return OR_EINVAL;
-  if (cfg->smoother < OR_JACOBI || cfg->smoother > OR_ZEBRA_Y) return OR_EINVAL;
-  if (cfg->periodic_y && (cfg->smoother == OR_LINE_Y || cfg->smoother == OR_ZEBRA_Y)) return OR_EINVAL;
+  if (cfg->smoother < OR_JACOBI || cfg->smoother > OR_GSADI) return OR_EINVAL;
+  if (cfg->periodic_y && (cfg->smoother == OR_LINE_Y || cfg->smoother == OR_ZEBRA_Y || cfg->smoother == OR_ADI ||
+                          cfg->smoother == OR_GSADI))
+    return OR_EINVAL;
   if (cfg->n[0] < 3 || cfg->n[1] < (cfg->periodic_y ? 2 : 3) || (cfg->dim == 3 && cfg->n[2] < 3)) return OR_EINVAL;
   if (cfg->periodic_y && (cfg->n[1] % 2)) return OR_EINVAL;
   or_hier *H = (or_hier *)calloc(1, sizeof(or_hier));

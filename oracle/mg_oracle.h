@@ -25,7 +25,9 @@ extern "C" {
 #endif
 
 enum { OR_CONST = 0, OR_SEPARABLE = 1, OR_CELL = 2 };
-enum { OR_JACOBI = 0, OR_RBGS = 1, OR_LINE_X = 2, OR_LINE_Y = 3, OR_ZEBRA_X = 4, OR_ZEBRA_Y = 5 };
+enum { OR_JACOBI = 0, OR_RBGS = 1, OR_LINE_X = 2, OR_LINE_Y = 3, OR_ZEBRA_X = 4, OR_ZEBRA_Y = 5,
+       OR_ADI = 6,     /* alternating directions: x-line Jacobi sweep, then y-line Jacobi sweep */
+       OR_GSADI = 7 }; /* zebra x-line Gauss-Seidel, then zebra y-line Gauss-Seidel */
 enum { OR_RED_FIRST = 0, OR_BLACK_FIRST = 1 };
 enum { OR_CYCLE_F = 0, OR_CYCLE_V = 1 };
 enum { OR_COARSE_EXACT = 0, OR_COARSE_SMOOTH = 1 };
@@ -46,7 +48,7 @@ typedef struct {
   const double *k;    /* OR_CELL: per-cell coefficient, (n0-1) x ncy [x (n2-1)], x fastest;
                          ncy = n1 if periodic_y else n1-1 */
   int levels;         /* number of grids L (>= 1) */
-  int smoother;       /* OR_JACOBI ... OR_ZEBRA_Y */
+  int smoother;       /* OR_JACOBI ... OR_GSADI */
   double omega;       /* smoother damping / relaxation parameter */
   int nu1, nu2;       /* pre- and post-smoothing steps */
   double omega_corr;  /* omega_l of the coarse-grid correction */

@@ -26,14 +26,14 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _LOCK = threading.Lock()
 
 CONST, SEPARABLE, CELL = 0, 1, 2
-JACOBI, RBGS, LINE_X, LINE_Y, ZEBRA_X, ZEBRA_Y = range(6)
+JACOBI, RBGS, LINE_X, LINE_Y, ZEBRA_X, ZEBRA_Y, ADI, GSADI = range(8)
 RED_FIRST, BLACK_FIRST = 0, 1
 CYCLE_F, CYCLE_V = 0, 1
 COARSE_EXACT, COARSE_SMOOTH = 0, 1
 OK, EINVAL, ENOMEM, ENOCONV, EDIVERGED = 0, 1, 2, 4, 5
 
 SMOOTHERS = {"jacobi": JACOBI, "rbgs": RBGS, "line_x": LINE_X, "line_y": LINE_Y,
-             "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y}
+             "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y, "adi": ADI, "gsadi": GSADI}
 
 
 def build(force: bool = False) -> str:

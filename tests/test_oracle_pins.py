@@ -268,6 +268,43 @@ def test_line_jacobi_mode_multiplier(direction):
         assert np.max(np.abs(out - (1 - omega * lam / c) * v * o.unknown_mask())) <= 1e-12
 
 
+@pytest.mark.parametrize("eps", [1.0, 1e-3])
+def test_adi_mode_multiplier_is_product_of_line_multipliers(eps):
+    """One ADI sweep (x-line Jacobi, then y-line Jacobi) maps a sine mode of the constant
+    operator to itself times (1 - omega lambda / c_x)(1 - omega lambda / c_y): each line
+    sweep is diagonal in the sine basis with the multipliers of the line-Jacobi pin."""
+    n, omega = 17, 0.7
+    o = orc.Oracle(const_problem(n, eps), levels=1, smoother="adi", omega=omega)
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    wx, wy = eps / h ** 2, 1 / h ** 2
+    for p, q in [(1, 1), (4, 13), (15, 2), (9, 9)]:
+        v = np.outer(np.sin(q * math.pi * x), np.sin(p * math.pi * x))
+        sx, sy = math.sin(p * math.pi * h / 2) ** 2, math.sin(q * math.pi * h / 2) ** 2
+        lam = 4 * wx * sx + 4 * wy * sy
+        cx, cy = 2 * wy + 4 * wx * sx, 2 * wx + 4 * wy * sy
+        mult = (1 - omega * lam / cx) * (1 - omega * lam / cy)
+        out = o.smooth(v, np.zeros_like(v), 1)
+        assert np.max(np.abs(out - mult * v * o.unknown_mask())) <= 1e-12
+
+
+def test_gsadi_is_zebra_x_then_zebra_y():
+    """GSADI equals a zebra x-line sweep followed by a zebra y-line sweep (order matters:
+    the reverse composition, which the transposed cycle uses, differs)."""
+    rng = np.random.default_rng(17)
+    prob = _small(2, False, 2, 17, rng)
+    kw = dict(levels=1, omega=1.0)
+    g = orc.Oracle(prob, smoother="gsadi", **kw)
+    zx, zy = orc.Oracle(prob, smoother="zebra_x", **kw), orc.Oracle(prob, smoother="zebra_y", **kw)
+    u = rand_field(g, rng)
+    b = rand_field(g, rng)
+    both = g.smooth(u, b, 1)
+    assert np.array_equal(both, zy.smooth(zx.smooth(u, b, 1), b, 1))
+    rev = zx.smooth(zy.smooth(u, b, 1, order=1), b, 1, order=1)
+    assert np.array_equal(g.smooth(u, b, 1, order=1), rev)
+    assert np.max(np.abs(rev - both)) > 1e-6 * np.max(np.abs(both))
+
+
 def test_thomas_matches_dense():
     rng = np.random.default_rng(9)
     m = 37
@@ -366,6 +403,8 @@ CASES = [
     (2, False, 0, "rbgs", 5, 2), (2, False, 2, "jacobi", 9, 3), (2, True, 1, "zebra_x", 17, 4),
     (2, False, 2, "zebra_y", 17, 4), (2, False, 0, "line_y", 17, 3), (3, False, 0, "rbgs", 5, 2),
     (3, True, 1, "zebra_x", 9, 3), (3, False, 2, "jacobi", 9, 2),
+    (2, False, 0, "adi", 17, 3), (2, False, 2, "gsadi", 17, 4), (3, False, 1, "adi", 9, 3),
+    (3, False, 0, "gsadi", 9, 2),
 ]
 
 
