@@ -55,7 +55,11 @@ typedef enum {
   MG_LINE_X = 2,   /* TRIx: C = tridiagonal part of A along x lines, all lines at once       */
   MG_LINE_Y = 3,   /* TRIy: the same along y lines (the paper's "virtually transposed" TRI) */
   MG_ZEBRA_X = 4,  /* GSTRIx: x lines in two colours by parity of (j + k), even first       */
-  MG_ZEBRA_Y = 5   /* GSTRIy: y lines in two colours by parity of (i + k), even first       */
+  MG_ZEBRA_Y = 5,  /* GSTRIy: y lines in two colours by parity of (i + k), even first       */
+  MG_ADI = 6,      /* ADI: a TRIx sweep then a TRIy sweep (sections "The choice of C",
+                      "Coordinate systems"); the transposed cycle runs y then x               */
+  MG_GSADI = 7     /* GSADI: a GSTRIx sweep then a GSTRIy sweep; transposed: y then x, each
+                      with its colours reversed.  ADI / GSADI need a non-periodic y        */
 } mg_smoother;
 
 typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2 } mg_coef_kind;

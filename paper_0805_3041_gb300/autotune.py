@@ -3,10 +3,10 @@
 For a problem class -- grid size and anisotropy -- it times candidate configurations on
 the device and keeps the fastest one that reaches the tolerance:
 
-1. the smoothing schedule: point red-black Gauss-Seidel, zebra y-line Gauss-Seidel or
-   damped y-line Jacobi, each with nu1 = nu2 = 1 or 2 (for -eps u_xx - u_yy the point
-   smoother slows down as eps falls, the y-line smoothers do not: Wallis 2008, section
-   "Anisotropies");
+1. the smoothing schedule: point red-black Gauss-Seidel, zebra y-line Gauss-Seidel, damped
+   y-line Jacobi, or the alternating-direction GSADI / ADI, with nu1 = nu2 = 1 or 2 (for
+   -eps u_xx - u_yy the point smoother slows down as eps falls, the y-line smoothers do
+   not: Wallis 2008, section "Anisotropies");
 2. then, for the chosen schedule, the kernel knobs that do not change the results: the
    single-CTA coarse-cycle cut-off (coarse_cut_nodes), the size below which the tile sweep
    replaces the row-streaming one (tile_nodes) and the rows per CTA of the streaming
@@ -30,6 +30,8 @@ SCHEDULES = [
     dict(smoother="zebra_y", omega=1.0, nu1=1, nu2=1),
     dict(smoother="zebra_y", omega=1.0, nu1=2, nu2=2),
     dict(smoother="line_y", omega=0.7, nu1=2, nu2=2),
+    dict(smoother="gsadi", omega=1.0, nu1=1, nu2=1),
+    dict(smoother="adi", omega=0.8, nu1=2, nu2=2),
 ]
 KNOBS = [
     dict(),

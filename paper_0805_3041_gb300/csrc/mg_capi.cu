@@ -137,8 +137,10 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (!p || !k) return MG_EINVAL;
   if (p->dim != 2 && p->dim != 3) return MG_EINVAL;
   if (p->levels < 1 || p->levels > MAXLEV) return MG_EINVAL;
-  if (p->smoother < MG_JACOBI || p->smoother > MG_ZEBRA_Y) return MG_EINVAL;
-  if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y)) return MG_EINVAL;
+  if (p->smoother < MG_JACOBI || p->smoother > MG_GSADI) return MG_EINVAL;
+  if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y || p->smoother == MG_ADI ||
+                        p->smoother == MG_GSADI))
+    return MG_EINVAL;   // lines across the periodic direction are cyclic systems: not supported
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
   if (p->max_cycles < 0 || p->sweep_rows < 0 || p->tile_nodes < -1) return MG_EINVAL;
@@ -471,20 +473,30 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, first);
       launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, 1 - first);
     } else {
-      int dir = (c->P.smoother == MG_LINE_X || c->P.smoother == MG_ZEBRA_X) ? 0 : 1;
-      int zebra = c->P.smoother >= MG_ZEBRA_X;
+      // one line sweep in direction dir: line Jacobi out of place, or zebra (both colours) in place.
       // x lines: one CTA per line (partition + PCR); y lines and very long lines: one thread per line
-      bool fast = dir == 0 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && L.n0 - 2 <= 4096;
-      if (zebra) {
-        for (int col = 0; col < 2; ++col) {
-          int colour = col == 0 ? order : 1 - order;
-          if (!(fast && launch_xline<T>(S.lc, L, c->kind, 1, colour, D.u[cur], g, D.u[cur], om)))
-            launch_line<T>(S.lc, L, c->kind, dir, 1, colour, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+      auto line_pass = [&](int dir, bool zebra) {
+        bool fast = dir == 0 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && L.n0 - 2 <= 4096;
+        if (zebra) {
+          for (int col = 0; col < 2; ++col) {
+            int colour = col == 0 ? order : 1 - order;
+            if (!(fast && launch_xline<T>(S.lc, L, c->kind, 1, colour, D.u[cur], g, D.u[cur], om)))
+              launch_line<T>(S.lc, L, c->kind, dir, 1, colour, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+          }
+        } else {
+          if (!(fast && launch_xline<T>(S.lc, L, c->kind, 0, 0, D.u[cur], g, D.u[1 - cur], om)))
+            launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
+          cur = 1 - cur;
         }
+      };
+      const int sm = c->P.smoother;
+      if (sm == MG_ADI || sm == MG_GSADI) {
+        // x lines then y lines; the transposed cycle (order 1) runs the composition reversed
+        const int d0 = order ? 1 : 0;
+        line_pass(d0, sm == MG_GSADI);
+        line_pass(1 - d0, sm == MG_GSADI);
       } else {
-        if (!(fast && launch_xline<T>(S.lc, L, c->kind, 0, 0, D.u[cur], g, D.u[1 - cur], om)))
-          launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
-        cur = 1 - cur;
+        line_pass((sm == MG_LINE_X || sm == MG_ZEBRA_X) ? 0 : 1, sm == MG_ZEBRA_X || sm == MG_ZEBRA_Y);
       }
     }
     if (fine && odd_guard) {
@@ -549,9 +561,7 @@ struct ProgBuilder {
       return;
     }
     if (zero) op(CP_ZERO_U, l, cu, 0);
-    int dir = (sm == MG_LINE_X || sm == MG_ZEBRA_X) ? 0 : 1;
-    bool zebra = sm >= MG_ZEBRA_X;
-    for (int s = 0; s < sweeps; ++s) {
+    auto pass = [&](int dir, bool zebra) {
       if (zebra) {
         int bufs = cu | (cu << 4) | ((1 - cu) << 8);
         op(CP_LINE, l, dir | 2 | (order << 2), bufs);
@@ -559,6 +569,15 @@ struct ProgBuilder {
       } else {
         op(CP_LINE, l, dir, cu | ((1 - cu) << 4) | ((1 - cu) << 8));
         cu = 1 - cu;
+      }
+    };
+    for (int s = 0; s < sweeps; ++s) {
+      if (sm == MG_ADI || sm == MG_GSADI) {   // x then y lines (reversed in the transposed cycle)
+        const int d0 = order ? 1 : 0;
+        pass(d0, sm == MG_GSADI);
+        pass(1 - d0, sm == MG_GSADI);
+      } else {
+        pass((sm == MG_LINE_X || sm == MG_ZEBRA_X) ? 0 : 1, sm == MG_ZEBRA_X || sm == MG_ZEBRA_Y);
       }
     }
   }

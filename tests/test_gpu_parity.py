@@ -72,10 +72,16 @@ CASES = [
     (3, (33, 17, 33), False, inputs.CONST, 3, "rbgs", 1.0),
     (3, (33, 16, 17), True, inputs.SEPARABLE, 3, "jacobi", 0.8),
     (3, (17, 17, 17), False, inputs.CELL, 3, "zebra_x", 1.0),
+    # alternating-direction line smoothers (x lines then y lines)
+    (2, (65, 65), False, inputs.CONST, 4, "adi", 0.8),
+    (2, (129, 65), False, inputs.SEPARABLE, 5, "gsadi", 1.0),
+    (2, (65, 33), False, inputs.CELL, 4, "gsadi", 1.0),
+    (3, (17, 17, 17), False, inputs.CONST, 3, "adi", 0.8),
     # every grid fits the single-CTA coarse cycle (the whole F-cycle runs in one launch)
     (2, (33, 33), False, inputs.CONST, 4, "rbgs", 1.0),
     (2, (17, 33), False, inputs.CELL, 3, "zebra_y", 1.0),
     (2, (33, 16), True, inputs.SEPARABLE, 3, "jacobi", 0.8),
+    (2, (33, 33), False, inputs.CONST, 3, "gsadi", 1.0),
 ]
 
 
