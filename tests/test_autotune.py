@@ -23,7 +23,7 @@ def test_tune_picks_fastest_converging_schedule_then_knobs():
         calls.append(dict(cfg))
         if cfg["smoother"] == "rbgs":
             return math.inf                       # does not converge (strong anisotropy)
-        t = {"zebra_y": 2.0, "line_y": 3.0}[cfg["smoother"]] + 0.1 * cfg["nu1"]
+        t = {"zebra_y": 2.0, "line_y": 3.0, "gsadi": 2.5, "adi": 4.0}[cfg["smoother"]] + 0.1 * cfg["nu1"]
         if cfg.get("tile_nodes") == -1:
             t -= 0.05
         return t
