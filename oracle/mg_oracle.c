@@ -509,6 +509,36 @@ void or_cycle(or_hier *H, int l, double *u, const double *g, int type, int trans
   lev_smooth(H, v, u, g, npost, order);
 }
 
+/* Nested-iteration start vector (section "Start-Vector Choice": begin the solution on the
+ * coarsest level and work up to the finest).  Reading: the right-hand side is restricted to
+ * every level by full weighting (its Dirichlet entries taken as 0), the coarsest level is
+ * solved exactly, and on each finer level the bilinear / trilinear interpolation of the
+ * coarser solution is improved by ncyc F-cycles.  x receives the finest-level result. */
+void or_fmg_start(or_hier *H, const double *b, double *x, int ncyc) {
+  int L = H->L;
+  double **bl = (double **)calloc((size_t)L + 1, sizeof(double *));
+  lev_t *vL = &H->lev[L];
+  bl[L] = (double *)calloc(nodes(vL), sizeof(double));
+  FOR_NODES(vL) if (is_unk(vL, i, j, k)) bl[L][nid(vL, i, j, k)] = b[nid(vL, i, j, k)];
+  for (int l = L; l > 1; --l) {
+    bl[l - 1] = (double *)calloc(nodes(&H->lev[l - 1]), sizeof(double));
+    lev_restrict(&H->lev[l], &H->lev[l - 1], bl[l], bl[l - 1]);
+  }
+  double *xc = (double *)calloc(nodes(&H->lev[1]), sizeof(double));
+  or_coarse_solve(H, bl[1], xc);
+  for (int l = 2; l <= L; ++l) {
+    double *xf = (double *)calloc(nodes(&H->lev[l]), sizeof(double));
+    lev_prolong_add(&H->lev[l], &H->lev[l - 1], xc, xf, 1.0);
+    for (int q = 0; q < ncyc; ++q) or_cycle(H, l, xf, bl[l], OR_CYCLE_F, 0);
+    free(xc);
+    xc = xf;
+  }
+  memcpy(x, xc, nodes(vL) * sizeof(double));
+  free(xc);
+  for (int l = 1; l <= L; ++l) free(bl[l]);
+  free(bl);
+}
+
 int or_solve(or_hier *H, const double *b, double *x, double tol, int maxit, int transposed, double *hist,
              int hist_cap, int *cycles, double *relres) {
   lev_t *v = &H->lev[H->L];

@@ -77,6 +77,9 @@ void or_restrict(const or_hier *H, int lf, const double *rf, double *gc);
 void or_prolong_add(const or_hier *H, int lf, const double *ec, double *uf, double w);
 void or_coarse_solve(or_hier *H, const double *g, double *u);
 void or_cycle(or_hier *H, int l, double *u, const double *g, int type, int transposed);
+/* nested-iteration start vector: coarsest level exact, then on each finer level the
+ * interpolated coarser solution improved by ncyc F-cycles (section "Start-Vector Choice") */
+void or_fmg_start(or_hier *H, const double *b, double *x, int ncyc);
 int  or_solve(or_hier *H, const double *b, double *x, double tol, int maxit, int transposed,
               double *hist, int hist_cap, int *cycles, double *relres);
 void or_grad_k(const or_hier *H, const double *u, const double *lam, double *dk);

@@ -88,6 +88,8 @@ def lib():
         L.or_prolong_add.argtypes = [P, C.c_int, P, P, C.c_double]
         L.or_coarse_solve.argtypes = [P, P, P]
         L.or_cycle.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
+        L.or_fmg_start.argtypes = [P, P, P, C.c_int]
+        L.or_fmg_start.restype = None
         L.or_solve.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, C.c_int,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_solve.restype = C.c_int
@@ -255,9 +257,19 @@ class Oracle:
         lib().or_cycle(self._h, l, _ptr(u), _ptr(g), cycle, int(transposed))
         return u
 
-    def solve(self, b, x0=None, tol=1e-10, maxit=100, transposed=False):
-        """F-cycles until ||b - A x|| / ||b|| <= tol.  Returns (x, status, cycles, relres, history)."""
+    def fmg_start(self, b, ncyc=1):
+        """Nested-iteration start vector (or_fmg_start)."""
         b = np.ascontiguousarray(b, dtype=np.float64)
+        x = self.zeros()
+        lib().or_fmg_start(self._h, _ptr(b), _ptr(x), int(ncyc))
+        return x
+
+    def solve(self, b, x0=None, tol=1e-10, maxit=100, transposed=False, start="given"):
+        """F-cycles until ||b - A x|| / ||b|| <= tol from x0 (zero if None), or from the
+        nested-iteration start when start == "fmg".  Returns (x, status, cycles, relres, history)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if start == "fmg":
+            x0 = self.fmg_start(b)
         x = self.zeros() if x0 is None else np.array(x0, dtype=np.float64, copy=True, order="C")
         hist = np.zeros(maxit + 1, dtype=np.float64)
         cyc = C.c_int()

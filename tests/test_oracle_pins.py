@@ -507,6 +507,47 @@ def test_manufactured_closed_form_solution():
     assert np.linalg.norm(x - exact) <= 2e-10 * np.linalg.norm(exact)
 
 
+def test_fmg_start_on_one_level_is_the_exact_solution():
+    """With a single level the nested iteration is the coarsest (exact) solve."""
+    rng = np.random.default_rng(30)
+    o = orc.Oracle(_small(2, False, 2, 17, rng), levels=1)
+    A, m = dense_matrix(o, 1)
+    b = rand_field(o, rng)
+    x = o.fmg_start(b)
+    ref = np.linalg.solve(A, b[m])
+    assert np.max(np.abs(x[m] - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_fmg_start_reaches_the_discretisation_error():
+    """Nested iteration (one F-cycle per level) lands within the discretisation error of the
+    closed-form discrete solution of the 129^2 sin(pi x) sin(pi y) problem: its algebraic
+    error is far below the O(h^2) difference between the discrete and continuous solutions,
+    while one F-cycle from zero is not."""
+    n = 129
+    h = 1.0 / (n - 1)
+    xs = np.arange(n) * h
+    S = np.outer(np.sin(math.pi * xs), np.sin(math.pi * xs))
+    b = 2 * math.pi ** 2 * S
+    exact = (2 * math.pi ** 2 * h ** 2 / (8 * math.sin(math.pi * h / 2) ** 2)) * S
+    exact[0, :] = exact[-1, :] = exact[:, 0] = exact[:, -1] = 0.0
+    o = orc.Oracle(const_problem(n), levels=6, smoother="jacobi", omega=0.8)
+    x = o.fmg_start(b)
+    disc = np.linalg.norm(exact - S * o.unknown_mask()) / np.linalg.norm(exact)   # ~ pi^2 h^2 / 12
+    err = np.linalg.norm(x - exact) / np.linalg.norm(exact)
+    one = np.linalg.norm(o.cycle(o.zeros(), b) - exact) / np.linalg.norm(exact)
+    assert err <= 0.5 * disc < one
+
+
+@pytest.mark.parametrize("smoother,eps", [("rbgs", 1.0), ("zebra_y", 1e-3)])
+def test_fmg_start_saves_outer_cycles(smoother, eps):
+    rng = np.random.default_rng(31)
+    o = orc.Oracle(const_problem(129, eps), levels=6, smoother=smoother)
+    b = rand_field(o, rng)
+    _, st0, c0, r0, _ = o.solve(b, tol=1e-10)
+    _, st1, c1, r1, _ = o.solve(b, tol=1e-10, start="fmg")
+    assert st0 == st1 == orc.OK and r1 <= 1e-10 and c1 < c0
+
+
 def test_solve_reports_no_convergence():
     o = orc.Oracle(const_problem(33, 1e-4), levels=5, smoother="jacobi", omega=0.8)
     b = rand_field(o, np.random.default_rng(0))
