@@ -76,6 +76,11 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 #define MG_FLAG_NO_FUSED_SWEEP  8u  /* 2-D: red-black half-sweep kernels and a separate defect / restriction */
 #define MG_FLAG_NO_TMA          16u /* 2-D FP32 red-black sweeps: register-marching kernel instead of the
                                        TMA-fed one (same arithmetic, same results) */
+#define MG_FLAG_FMG_START       32u /* ignore the caller's x: start from nested iteration (Wallis 2008,
+                                       section "Start-Vector Choice"): b restricted to every level, the
+                                       coarsest level solved exactly, then on each finer level the
+                                       interpolated solution improved by one F-cycle.  Its cycles are
+                                       not counted in mg_report.cycles.  MG_MIXED runs it in FP32 */
 
 typedef struct {
   int dim;                /* 2 or 3 */

@@ -14,11 +14,12 @@ enum CoarseOp {
   CP_RB_HALF = 6,   // red-black half sweep of colour a on u_y[b], in place
   CP_LINE = 7,      // a = dir | zebra << 1 | colour << 2,  b = src | dst << 4 | scratch << 8
   CP_DEFECT = 8,    // r_y = g_y - A u_y[a]
-  CP_RESTRICT = 9,  // g_{y-1} = R r_y
+  CP_RESTRICT = 9,  // g_{y-1} = R r_y  (a = 1: R g_y, the right-hand side itself)
   CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b]
   CP_COARSE = 11,   // u_1[a] = A_1^{-1} g_1
-  CP_RB_ZERO = 12   // u_y[b] = first half sweep of colour a from a zero iterate (replaces ZERO_U +
+  CP_RB_ZERO = 12,  // u_y[b] = first half sweep of colour a from a zero iterate (replaces ZERO_U +
                     // RB_HALF with the same arithmetic: the residual of a zero iterate is g)
+  CP_INTERP = 13    // u_y[a] = P u_{y-1}[b]  (interpolation of a coarse solution, weight 1)
 };
 
 }  // namespace mg

@@ -232,16 +232,17 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         });
         break;
       }
-      case CP_RESTRICT: {   // level y -> y-1 (r of level y into g of level y-1)
+      case CP_RESTRICT: {   // level y -> y-1 (r of level y, or g when z = 1, into g of level y-1)
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
         T *gc = pool + Cs.off_g;
+        const T *rs = o.z ? g : r;
         FOR_UNK(C, {
           int I = i, J = j, K = k;
           int dm, dp;
           yoffs(L, 2 * J, dm, dp);
           int pf = (2 * K) * (int)L.plane + (2 * J) * (int)L.pitch + 2 * I;
-          auto row3 = [&](int c) -> T { return (r[c - 1] + r[c + 1]) + T(2) * r[c]; };
+          auto row3 = [&](int c) -> T { return (rs[c - 1] + rs[c + 1]) + T(2) * rs[c]; };
           auto plane3 = [&](int c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
           T s;
           if (DIM == 2) s = plane3(pf) * T(0.0625);
@@ -250,11 +251,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         });
         break;
       }
-      case CP_PROLONG: {   // level y (fine), z = fine buffer, w = coarse buffer
+      case CP_PROLONG:     // level y (fine), z = fine buffer, w = coarse buffer
+      case CP_INTERP: {
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
         const T *ec = (o.w ? pool + Cs.off_u1 : pool + Cs.off_u0);
         T *uf = ub(o.z);
+        const bool interp = o.x == CP_INTERP;
         FOR_UNK(L, {
           int I0 = i >> 1, I1 = (i + 1) >> 1;
           int J0 = j >> 1, J1 = (j + 1) >> 1;
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
             T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
             s = (s0 + s1) * T(0.125);
           }
-          uf[p] = fma(omega_corr, s, uf[p]);
+          uf[p] = interp ? s : fma(omega_corr, s, uf[p]);
         });
         break;
       }

@@ -80,7 +80,7 @@ struct mg_ctx {
   int lcut = 0;
   void *slev = nullptr;            // device table of shared-memory level views
   int4 *prog = nullptr;            // device programs
-  int prog_off[8] = {0}, prog_len[8] = {0};
+  int prog_off[9] = {0}, prog_len[9] = {0};
   long long *cidx_s = nullptr;     // coarsest unknowns in the compact shared-memory layout
   size_t csk_smem = 0;
   // y-line smoothers run as x-line smoothers on the axis-swapped problem: internal node
@@ -517,6 +517,7 @@ static void coarse_solve(Sched &S, const T *g) {
 // (when every grid fits in shared memory), 4..7 the coarse correction below lcut + 1.
 static int prog_id_fine(int zero, int tr) { return zero * 2 + tr; }
 static int prog_id_sub(int type, int tr) { return 4 + type * 2 + tr; }
+static const int PROG_FMG = 8;   // nested iteration on levels 1..lcut
 
 template <typename T>
 static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out) {
@@ -612,6 +613,20 @@ struct ProgBuilder {
     }
     op(CP_STORE_U, lc, cur[lc], 0);
   }
+  // nested iteration on levels 1..lc: g_lc loaded and restricted down to level 1, solved
+  // there, then on each finer level the interpolated solution improved by one F-cycle
+  void fmg(int lc) {
+    op(CP_LOAD_G, lc, 0, 0);
+    for (int l = lc; l > 1; --l) op(CP_RESTRICT, l, 1, 0);
+    cur[1] = 0;
+    op(CP_COARSE, 1, 0, 0);
+    for (int l = 2; l <= lc; ++l) {
+      cur[l] = 0;
+      op(CP_INTERP, l, 0, cur[l - 1]);
+      cycle(l, 0, 0, false);
+    }
+    op(CP_STORE_U, lc, cur[lc], 0);
+  }
   // one F-cycle on the finest grid L (= lc)
   void fine(int L, int zero, int tr) {
     op(CP_LOAD_G, L, 0, 0);
@@ -679,6 +694,53 @@ static void finest_to_zero(Sched &S) {
   }
 }
 
+// Nested iteration (Wallis 2008, section "Start-Vector Choice") on the levels of precision T:
+// g of the finest level holds the right-hand side (zero on the boundary); it is restricted
+// level by level into g of every coarser level, the coarsest level is solved exactly, and on
+// each finer level l the interpolated coarse solution (u_l = P u_{l-1}) is improved by one
+// F-cycle with g_l.  The cycle at level l overwrites g only below l, so each level's
+// restricted right-hand side is still in place when its turn comes.  Levels 1..lcut run as
+// one single-CTA launch.  Afterwards buffer 0 of the finest level holds the start vector.
+template <typename T>
+static void emit_fmg(Sched &S) {
+  mg_ctx *c = S.c;
+  const int L = c->L, lo = c->lcut >= 2 ? c->lcut : 1;
+  for (int l = L; l > lo; --l)
+    launch_restrict<T>(S.lc, LevOf<T>::get(c, l), LevOf<T>::get(c, l - 1), LevOf<T>::data(c, l).g,
+                       LevOf<T>::data(c, l - 1).g);
+  for (int l = 1; l <= lo; ++l) c->cur[l] = 0;
+  if (lo == 1) coarse_solve<T>(S, LevOf<T>::data(c, 1).g);
+  else launch_csk<T>(S, PROG_FMG, LevOf<T>::data(c, lo).g, nullptr, LevOf<T>::data(c, lo).u[0]);
+  for (int l = lo + 1; l <= L; ++l) {
+    LevData<T> &D = LevOf<T>::data(c, l), &Dc = LevOf<T>::data(c, l - 1);
+    cudaMemsetAsync(D.u[0], 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+    launch_prolong_add<T>(S.lc, LevOf<T>::get(c, l), LevOf<T>::get(c, l - 1), Dc.u[c->cur[l - 1]], D.u[0], T(1));
+    c->cur[l] = 0;
+    cycle<T>(S, l, D.g, 0, 0, false);
+  }
+  finest_to_zero<T>(S);
+}
+
+// MG_FLAG_FMG_START: the start vector of a solve from nested iteration, in place of the
+// caller's x (the packed b already sits in the finest-level buffers).  FP64 contexts run it
+// on the FP64 levels; MG_MIXED contexts run it on the FP32 levels from (float) b and widen
+// the result into x.  The operator is symmetric, so an adjoint solve uses the same start.
+static void emit_fmg_start(Sched &S) {
+  mg_ctx *c = S.c;
+  const int L = c->L;
+  if (c->mixed) {
+    Lev<double> F64 = lev64(c, L);
+    cudaMemsetAsync(c->x64, 0, sizeof(double) * (size_t)c->geo[L].count, S.lc.s);
+    // g32 = (float)(b - A 0) = (float) b
+    launch_defect64_to32(S.lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                         c->scal + 1);
+    emit_fmg<float>(S);
+    launch_ir_update(S.lc, F64, c->x64, c->d32[L].u[0]);
+  } else {
+    emit_fmg<double>(S);
+  }
+}
+
 // FP64 form: one F-cycle on the finest level followed by the residual check.
 static void emit_fp64_cycle(Sched &S, int transposed) {
   mg_ctx *c = S.c;
@@ -720,6 +782,7 @@ static void emit_solve_init(Sched &S) {
   mg_ctx *c = S.c;
   int L = c->L;
   Lev<double> F64 = lev64(c, L);
+  if (c->P.flags & MG_FLAG_FMG_START) emit_fmg_start(S);
   if (c->mixed) {
     launch_norm_parts<double>(S.lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
     launch_defect64_to32(S.lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
@@ -948,9 +1011,12 @@ static mg_status setup_levels(mg_ctx *c) {
       c->csk_smem = coarse_fill_levels<double>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind);
     }
     std::vector<int4> all;
-    for (int pid = 0; pid < 8; ++pid) {
+    for (int pid = 0; pid < 9; ++pid) {
       ProgBuilder pb{c};
-      if (pid < 4) {
+      if (pid == PROG_FMG) {
+        if (c->lcut < 2) continue;
+        pb.fmg(c->lcut);
+      } else if (pid < 4) {
         if (c->lcut != L) continue;
         pb.fine(L, pid / 2, pid % 2);
       } else {
@@ -1197,11 +1263,19 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   if (c->mixed) {
     if ((lst = load_vec(c, lc, F64, b, c->b64, host))) return lst;
     if ((lst = load_vec(c, lc, F64, x, c->x64, host))) return lst;
+    if (c->P.flags & MG_FLAG_FMG_START) {
+      Sched S{c, lc, false};
+      emit_fmg_start(S);
+    }
     launch_norm_parts<double>(lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
     launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
   } else {
     if ((lst = load_vec(c, lc, F64, b, c->d64[L].g, host))) return lst;
     if ((lst = load_vec(c, lc, F64, x, c->d64[L].u[0], host))) return lst;
+    if (c->P.flags & MG_FLAG_FMG_START) {
+      Sched S{c, lc, false};
+      emit_fmg_start(S);
+    }
     launch_norm_parts<double>(lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
     launch_defect_norm<double>(lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
                                c->scal + 1);
