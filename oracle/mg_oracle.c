@@ -44,6 +44,7 @@ struct or_hier {
   lev_t lev[OR_MAXLEV + 1];   /* lev[1] coarsest ... lev[L] finest */
   int smoother, nu1, nu2, coarse_mode, coarse_sweeps, dense_max;
   double omega, omega_corr;
+  int adaptive_corr;
   /* coarsest-grid direct solver */
   int nc;                     /* number of coarsest unknowns */
   size_t *cidx;               /* node index of each coarsest unknown */
@@ -479,6 +480,35 @@ void or_coarse_solve(or_hier *H, const double *g, double *u) {
 /* the cycle                                                                 */
 /* ------------------------------------------------------------------------- */
 
+/* Adaptive weight of the coarse-grid correction (section "Multigrid", the omega_l chosen to
+ * minimise the error in the energy norm).  With u* = A^-1 g, the corrected iterate
+ * u + w P e has energy error ||u* - u - w P e||_A^2, a quadratic in w whose minimum is at
+ * w = (A (u* - u), P e) / (A P e, P e) = (d, P e) / (A P e, P e) with d = g - A u, the
+ * defect of the iterate before the correction.  Reading: the printed formula writes the
+ * restriction symbol and mixes the iterate superscripts; the operator applied to the coarse
+ * correction can only be the interpolation P (it maps level l-1 to level l), so that is the
+ * formula taken.  Inner products run over the unknowns of level l. */
+double or_adaptive_omega(const or_hier *H, int l, const double *u, const double *g, const double *e) {
+  const lev_t *v = &H->lev[l], *c = &H->lev[l - 1];
+  size_t n = nodes(v);
+  double *pe = (double *)calloc(n, sizeof(double));
+  double *ape = (double *)calloc(n, sizeof(double));
+  double *d = (double *)calloc(n, sizeof(double));
+  lev_prolong_add(v, c, e, pe, 1.0);   /* P e (zero on the Dirichlet nodes) */
+  lev_apply(v, pe, ape);               /* A P e */
+  lev_defect(v, u, g, d);              /* d = g - A u */
+  double num = 0.0, den = 0.0;
+  FOR_NODES(v) if (is_unk(v, i, j, k)) {
+    size_t p = nid(v, i, j, k);
+    num += d[p] * pe[p];
+    den += ape[p] * pe[p];
+  }
+  free(pe);
+  free(ape);
+  free(d);
+  return den > 0.0 ? num / den : 1.0;
+}
+
 /* MG(l, u, g) with the F-cycle recursion: the coarse problem is solved by an
  * F-cycle started from zero followed by a V-cycle (skipped when the coarse grid
  * is the coarsest, whose direct solve is already exact); a V-cycle recurses
@@ -505,7 +535,8 @@ void or_cycle(or_hier *H, int l, double *u, const double *g, int type, int trans
   } else {
     or_cycle(H, l - 1, c->u, c->g, OR_CYCLE_V, transposed);
   }
-  lev_prolong_add(v, c, c->u, u, H->omega_corr); /* u + omega_l P u_{l-1} */
+  double w = H->adaptive_corr ? or_adaptive_omega(H, l, u, g, c->u) : H->omega_corr;
+  lev_prolong_add(v, c, c->u, u, w);          /* u + omega_l P u_{l-1} */
   lev_smooth(H, v, u, g, npost, order);
 }
 
@@ -640,6 +671,7 @@ int or_create(const or_config *cfg, or_hier **out) {
   H->nu1 = cfg->nu1;
   H->nu2 = cfg->nu2;
   H->omega_corr = cfg->omega_corr;
+  H->adaptive_corr = cfg->adaptive_corr ? 1 : 0;
   H->coarse_mode = cfg->coarse_mode;
   H->coarse_sweeps = cfg->coarse_sweeps;
   H->dense_max = cfg->dense_max > 0 ? cfg->dense_max : 1024;

@@ -55,6 +55,8 @@ typedef struct {
   int coarse_mode;    /* OR_COARSE_EXACT (direct / CG) or OR_COARSE_SMOOTH */
   int coarse_sweeps;  /* sweeps used by OR_COARSE_SMOOTH */
   int dense_max;      /* largest coarsest-grid unknown count solved by dense Cholesky */
+  int adaptive_corr;  /* 1: omega_l of every correction chosen to minimise the energy norm of
+                         the error (or_adaptive_omega); omega_corr is then ignored */
 } or_config;
 
 typedef struct or_hier or_hier;
@@ -77,6 +79,9 @@ void or_restrict(const or_hier *H, int lf, const double *rf, double *gc);
 void or_prolong_add(const or_hier *H, int lf, const double *ec, double *uf, double w);
 void or_coarse_solve(or_hier *H, const double *g, double *u);
 void or_cycle(or_hier *H, int l, double *u, const double *g, int type, int transposed);
+/* energy-optimal correction weight at level l >= 2 for iterate u, right-hand side g and
+ * coarse correction e: (g - A u, P e) / (A P e, P e); 1 when P e = 0 */
+double or_adaptive_omega(const or_hier *H, int l, const double *u, const double *g, const double *e);
 /* nested-iteration start vector: coarsest level exact, then on each finer level the
  * interpolated coarser solution improved by ncyc F-cycles (section "Start-Vector Choice") */
 void or_fmg_start(or_hier *H, const double *b, double *x, int ncyc);

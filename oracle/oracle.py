@@ -56,7 +56,8 @@ class _Config(C.Structure):
                 ("sx", C.c_void_p), ("sy", C.c_void_p), ("sz", C.c_void_p), ("k", C.c_void_p),
                 ("levels", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("omega_corr", C.c_double),
-                ("coarse_mode", C.c_int), ("coarse_sweeps", C.c_int), ("dense_max", C.c_int)]
+                ("coarse_mode", C.c_int), ("coarse_sweeps", C.c_int), ("dense_max", C.c_int),
+                ("adaptive_corr", C.c_int)]
 
 
 _lib = None
@@ -89,6 +90,8 @@ def lib():
         L.or_coarse_solve.argtypes = [P, P, P]
         L.or_cycle.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
         L.or_fmg_start.argtypes = [P, P, P, C.c_int]
+        L.or_adaptive_omega.argtypes = [P, C.c_int, P, P, P]
+        L.or_adaptive_omega.restype = C.c_double
         L.or_fmg_start.restype = None
         L.or_solve.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, C.c_int,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -134,7 +137,8 @@ class Oracle:
     """One multigrid hierarchy of the oracle."""
 
     def __init__(self, prob: Problem, levels=2, smoother="rbgs", omega=1.0, nu1=2, nu2=2,
-                 omega_corr=1.0, coarse_mode=COARSE_EXACT, coarse_sweeps=2, dense_max=1024):
+                 omega_corr=1.0, coarse_mode=COARSE_EXACT, coarse_sweeps=2, dense_max=1024,
+                 adaptive_corr=False):
         self.prob = prob
         cfg = _Config()
         cfg.dim = prob.dim
@@ -157,6 +161,7 @@ class Oracle:
         cfg.coarse_mode = coarse_mode
         cfg.coarse_sweeps = coarse_sweeps
         cfg.dense_max = dense_max
+        cfg.adaptive_corr = int(bool(adaptive_corr))
         h = C.c_void_p()
         st = lib().or_create(C.byref(cfg), C.byref(h))
         if st != OK:
@@ -256,6 +261,13 @@ class Oracle:
         g = np.ascontiguousarray(g, dtype=np.float64)
         lib().or_cycle(self._h, l, _ptr(u), _ptr(g), cycle, int(transposed))
         return u
+
+    def adaptive_omega(self, u, g, e, l=None):
+        """Energy-optimal correction weight at level l for iterate u, right-hand side g and
+        coarse correction e (or_adaptive_omega)."""
+        l = self.levels if l is None else l
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, g, e)]
+        return lib().or_adaptive_omega(self._h, l, *[_ptr(a) for a in arrs])
 
     def fmg_start(self, b, ncyc=1):
         """Nested-iteration start vector (or_fmg_start)."""

@@ -612,3 +612,95 @@ def test_adjoint_solution_matches_dense():
     lam, st, *_ = o.solve(g, tol=1e-13, maxit=100, transposed=True)
     ref = np.linalg.solve(A.T, g[m])
     assert st == orc.OK and np.max(np.abs(lam[m] - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------------------
+# adaptive correction weight omega_l (energy-norm optimal)
+# --------------------------------------------------------------------------------------
+
+def _interp_1d(nf, periodic):
+    """Dense 1-D linear interpolation from the coarse to the fine nodes (numpy, independent
+    of the oracle): even fine nodes copy, odd ones average their two coarse neighbours."""
+    nc = nf // 2 if periodic else (nf - 1) // 2 + 1
+    P = np.zeros((nf, nc))
+    for i in range(nf):
+        if i % 2 == 0:
+            P[i, i // 2] = 1.0
+        else:
+            P[i, (i - 1) // 2] = 0.5
+            P[i, ((i + 1) // 2) % nc] += 0.5
+    return P
+
+
+def _interp(o):
+    """P of the finest level of `o` on full node arrays, rows of non-unknowns zero."""
+    p = o.prob
+    Px, Py = _interp_1d(p.n[0], False), _interp_1d(p.n[1], p.periodic_y)
+    P = np.kron(Py, Px) if p.dim == 2 else np.kron(_interp_1d(p.n[2], False), np.kron(Py, Px))
+    return P * o.unknown_mask().reshape(-1)[:, None]
+
+
+ADAPT_CASES = [(2, False, 0), (2, False, 2), (2, True, 1), (3, False, 2)]
+
+
+@pytest.mark.parametrize("dim,per,kind_idx", ADAPT_CASES)
+def test_adaptive_omega_is_one_when_the_correction_is_the_error(dim, per, kind_idx):
+    """If u = u* - P e0 with g = A u*, the correction P e0 removes the whole error, so the
+    energy-optimal weight is exactly 1 (and 1/2 for 2 e0, -1 for -e0)."""
+    rng = np.random.default_rng(40)
+    o = orc.Oracle(_small(dim, per, kind_idx, 9, rng), levels=2)
+    ustar = rand_field(o, rng)
+    e0 = rand_field(o, rng, 1)
+    u = ustar - (_interp(o) @ e0.reshape(-1)).reshape(o.shape())
+    g = o.apply(ustar)
+    for s, want in [(1.0, 1.0), (2.0, 0.5), (-1.0, -1.0)]:
+        assert abs(o.adaptive_omega(u, g, s * e0) - want) <= 1e-11
+
+
+@pytest.mark.parametrize("dim,per,kind_idx", ADAPT_CASES)
+def test_adaptive_omega_minimises_the_energy_error(dim, per, kind_idx):
+    """Brute force: with u* from a dense solve, the energy error E(w) = ||u* - u - w P e||_A^2
+    is a parabola in w; its vertex from three samples is the oracle's weight."""
+    rng = np.random.default_rng(41)
+    o = orc.Oracle(_small(dim, per, kind_idx, 9, rng), levels=2)
+    A, m = dense_matrix(o)
+    u, g, e = rand_field(o, rng), rand_field(o, rng), rand_field(o, rng, 1)
+    ustar = np.zeros(o.shape())
+    ustar[m] = np.linalg.solve(A, g[m])
+    pe = (_interp(o) @ e.reshape(-1)).reshape(o.shape())
+
+    def energy(w):
+        err = (ustar - u - w * pe)[m]
+        return err @ A @ err
+
+    e0, e1, e2 = energy(0.0), energy(1.0), energy(2.0)
+    vertex = 0.5 * (3 * e0 - 4 * e1 + e2) / (e0 - 2 * e1 + e2)   # argmin of the parabola through w = 0, 1, 2
+    w = o.adaptive_omega(u, g, e)
+    assert abs(w - vertex) <= 1e-9 * max(1.0, abs(vertex))
+    assert energy(w) <= min(e0, e1)
+
+
+@pytest.mark.parametrize("dim,per,kind_idx,smoother,n,levels", CASES[:8])
+def test_adaptive_fcycle_converges_to_dense_solution(dim, per, kind_idx, smoother, n, levels):
+    rng = np.random.default_rng(42)
+    prob = _small(dim, per, kind_idx, n, rng)
+    omega = 0.8 if smoother in ("jacobi", "line_y") else 1.0
+    o = orc.Oracle(prob, levels=levels, smoother=smoother, omega=omega, adaptive_corr=True, omega_corr=0.3)
+    A, m = dense_matrix(o)
+    b = rand_field(o, rng)
+    x, st, cyc, rr, hist = o.solve(b, tol=1e-13, maxit=200)
+    assert st == orc.OK
+    ref = np.linalg.solve(A, b[m])
+    assert np.max(np.abs(x[m] - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+def test_adaptive_weight_repairs_a_badly_damped_correction():
+    """omega_corr is ignored under the adaptive rule: a correction damped to 0.3 converges
+    slowly with the fixed weight and at the undamped rate (or better) with the adaptive one."""
+    o_fix = orc.Oracle(const_problem(65), levels=5, smoother="rbgs", nu1=1, nu2=1, omega_corr=0.3)
+    o_one = orc.Oracle(const_problem(65), levels=5, smoother="rbgs", nu1=1, nu2=1)
+    o_ad = orc.Oracle(const_problem(65), levels=5, smoother="rbgs", nu1=1, nu2=1, omega_corr=0.3,
+                      adaptive_corr=True)
+    b = rand_field(o_one, np.random.default_rng(43))
+    cyc = {k: o.solve(b, tol=1e-10)[2] for k, o in (("fix", o_fix), ("one", o_one), ("ad", o_ad))}
+    assert cyc["ad"] <= cyc["one"] < cyc["fix"]
