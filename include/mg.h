@@ -81,6 +81,10 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        coarsest level solved exactly, then on each finer level the
                                        interpolated solution improved by one F-cycle.  Its cycles are
                                        not counted in mg_report.cycles.  MG_MIXED runs it in FP32 */
+#define MG_FLAG_ADAPTIVE_CORR   64u /* every coarse-grid correction added with the weight that minimises
+                                       the energy norm of the error (Wallis 2008, section "Multigrid"):
+                                       omega_l = (g - A u, P e) / (A P e, P e) on the iterate u before
+                                       the correction; omega_corr is ignored */
 
 typedef struct {
   int dim;                /* 2 or 3 */

@@ -60,6 +60,20 @@ __device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + 
 
 static constexpr int CSK_STAGED_OPS = 1024;   // program steps staged in shared memory
 
+// bilinear / trilinear interpolation of the coarse array ec at fine node (i, j, k)
+template <typename T, int DIM>
+__device__ __forceinline__ T interp_at(const Lev<T> &C, const T *ec, int i, int j, int k) {
+  int I0 = i >> 1, I1 = (i + 1) >> 1;
+  int J0 = j >> 1, J1 = (j + 1) >> 1;
+  if (J1 >= C.n1) J1 -= C.n1;
+  int a0 = J0 * (int)C.pitch, a1 = J1 * (int)C.pitch;
+  if (DIM == 2) return ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
+  int z0 = (k >> 1) * (int)C.plane, z1 = ((k + 1) >> 1) * (int)C.plane;
+  T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
+  T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
+  return (s0 + s1) * T(0.125);
+}
+
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
                                                        int nops, int lc, const T *__restrict__ g_in,
@@ -72,6 +86,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
   // stage the level table and the program in shared memory (each step reads them)
   __shared__ SLev<T> s_levs[17];
   __shared__ int4 s_prog[CSK_STAGED_OPS];
+  __shared__ double s_red[2][32];   // warp totals of the adaptive-weight inner products
   {
     const int *src = reinterpret_cast<const int *>(levs);
     int *dst = reinterpret_cast<int *>(s_levs);
@@ -259,21 +274,46 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         T *uf = ub(o.z);
         const bool interp = o.x == CP_INTERP;
         FOR_UNK(L, {
-          int I0 = i >> 1, I1 = (i + 1) >> 1;
-          int J0 = j >> 1, J1 = (j + 1) >> 1;
-          if (J1 >= C.n1) J1 -= C.n1;
-          int a0 = J0 * (int)C.pitch, a1 = J1 * (int)C.pitch;
-          T s;
-          if (DIM == 2) {
-            s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
-          } else {
-            int z0 = (k >> 1) * (int)C.plane, z1 = ((k + 1) >> 1) * (int)C.plane;
-            T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
-            T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
-            s = (s0 + s1) * T(0.125);
-          }
+          T s = interp_at<T, DIM>(C, ec, i, j, k);
           uf[p] = interp ? s : fma(omega_corr, s, uf[p]);
         });
+        break;
+      }
+      case CP_ADAPT: {   // z = fine buffer, w = coarse buffer (scaled in place)
+        const SLev<T> &Cs = levs[o.y - 1];
+        Lev<T> C = Cs.L;
+        T *ec = o.w ? pool + Cs.off_u1 : pool + Cs.off_u0;
+        const T *u = ub(o.z);
+        FOR_UNK(L, { r[p] = interp_at<T, DIM>(C, ec, i, j, k); });   // P e (r is zero off the unknowns)
+        __syncthreads();
+        double a0 = 0.0, a1 = 0.0;
+        FOR_UNK(L, {
+          int dm, dp;
+          yoffs(L, j, dm, dp);
+          Weights<T, DIM, KIND> w;
+          w.load(L, i, p, dm);
+          double d = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+          double ape = -(double)residual_at<T, DIM, KIND>(L, w, r, p, dm, dp, T(0));
+          a0 = fma(d, (double)r[p], a0);
+          a1 = fma(ape, (double)r[p], a1);
+        });
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+          a0 += __shfl_down_sync(0xffffffffu, a0, o2);
+          a1 += __shfl_down_sync(0xffffffffu, a1, o2);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          s_red[0][wid_] = a0;
+          s_red[1][wid_] = a1;
+        }
+        __syncthreads();
+        double num = 0.0, den = 0.0;   // every thread sums the warp totals in the same order
+        for (int q = 0; q < nw_; ++q) {
+          num += s_red[0][q];
+          den += s_red[1][q];
+        }
+        const T f = (T)(den > 0.0 ? num / den : 1.0);
+        const int cc = (int)(C.plane * C.n2);
+        for (int t = tid_; t < cc; t += nthr_) ec[t] *= f;
         break;
       }
       case CP_RB_ZERO: {   // z = colour, w = buffer: first half sweep from a zero iterate

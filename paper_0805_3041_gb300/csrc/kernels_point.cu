@@ -211,6 +211,81 @@ __global__ void __launch_bounds__(1024) k_norm_finish(const double *__restrict__
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// adaptive correction weight (Wallis 2008, section "Multigrid": omega_l chosen to minimise
+// the energy norm of the error): omega = (d, P e) / (A P e, P e) with d = g - A u
+// ---------------------------------------------------------------------------------------
+
+// per block the partial sums of d . Pe (partials[b]) and (A Pe) . Pe (partials[nb + b]) over
+// the unknowns; pe holds P e, zero off the unknowns
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
+                                                      const T *__restrict__ pe, double *__restrict__ partials, int R) {
+  int i = 1 + blockIdx.x * BX + threadIdx.x;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  long long nr = L.unk_rows();
+  double a0 = 0.0, a1 = 0.0;
+  if (i <= L.n0 - 2) {
+    for (int q = 0; q < R; ++q) {
+      long long r = r0 + q;
+      if (r >= nr) break;
+      int j, k;
+      row_jk(L, r, j, k);
+      long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+      yoffs(L, j, dm, dp);
+      Weights<T, DIM, KIND> w;
+      w.load(L, i, p, dm);
+      double d = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+      double ape = -(double)residual_at<T, DIM, KIND>(L, w, pe, p, dm, dp, T(0));
+      double v = (double)pe[p];
+      a0 = fma(d, v, a0);
+      a1 = fma(ape, v, a1);
+    }
+  }
+  const int nb = (int)(gridDim.x * gridDim.y), b = blockIdx.y * gridDim.x + blockIdx.x;
+  double s0 = block_sum(a0);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[b] = s0;
+  __syncthreads();   // block_sum's shared slots are reused
+  double s1 = block_sum(a1);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[nb + b] = s1;
+}
+
+// single block: omega = sum(num) / sum(den) in a fixed order; 1 when P e = 0 (den = 0)
+__global__ void __launch_bounds__(1024) k_corr_omega(const double *__restrict__ partials, int n, double *out) {
+  __shared__ double red[2][32];
+  double a0 = 0.0, a1 = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    a0 += partials[t];
+    a1 += partials[n + t];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a0;
+    red[1][threadIdx.x >> 5] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    bool in = threadIdx.x < (blockDim.x >> 5);
+    double s0 = in ? red[0][threadIdx.x] : 0.0, s1 = in ? red[1][threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    }
+    if (threadIdx.x == 0) out[0] = s1 > 0.0 ? s0 / s1 : 1.0;
+  }
+}
+
+// e *= omega over a whole node array
+template <typename T>
+__global__ void k_scale_by(T *__restrict__ e, long long n, const double *__restrict__ w) {
+  const T f = (T)w[0];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    e[t] *= f;
+}
+
 // relres = sqrt(sq) / sqrt(bsq), recorded in the device history
 __global__ void k_relres(const double *sq, const double *bsq, double *hist, int it, double *out) {
   double rel = sqrt(sq[0]) / sqrt(bsq[0]);
@@ -403,6 +478,26 @@ void launch_norm_parts(const Launch &lc, const Lev<T> &L, const T *v, double *pa
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
 
+template <typename T>
+void launch_corr_weight(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, const T *pe,
+                        double *partials, int nparts, double *omega) {
+  long long rows = L.unk_rows();
+  int R = norm_R(rows, L.xunk(), nparts / 2);
+  dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
+  DISPATCH_DK(L.dim, kind, k_corr_dots, <<<gr, bl, 0, lc.s>>>(L, u, g, pe, partials, R));
+  ++*lc.counter;
+  k_corr_omega<<<1, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), omega);
+  ++*lc.counter;
+}
+
+template <typename T>
+void launch_scale_by(const Launch &lc, T *e, long long n, const double *omega) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_scale_by<T><<<(unsigned)blocks, 256, 0, lc.s>>>(e, n, omega);
+  ++*lc.counter;
+}
+
 void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq) {
   k_norm_finish<<<1, 1024, 0, lc.s>>>(partials, nparts, out_sq);
   ++*lc.counter;
@@ -506,7 +601,10 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
   template void launch_defect<T>(const Launch &, const Lev<T> &, int, const T *, const T *, T *);           \
   template void launch_defect_norm<T>(const Launch &, const Lev<T> &, int, const T *, const T *, double *, int, \
                                       double *);                                                              \
-  template void launch_norm_parts<T>(const Launch &, const Lev<T> &, const T *, double *, int, double *);
+  template void launch_norm_parts<T>(const Launch &, const Lev<T> &, const T *, double *, int, double *);      \
+  template void launch_corr_weight<T>(const Launch &, const Lev<T> &, int, const T *, const T *, const T *,    \
+                                      double *, int, double *);                                               \
+  template void launch_scale_by<T>(const Launch &, T *, long long, const double *);
 INST(double)
 INST(float)
 

@@ -358,6 +358,11 @@ static mg_status last_launch(mg_ctx *c) {
 // ---------------------------------------------------------------------------------------
 // the cycle schedule
 // ---------------------------------------------------------------------------------------
+// MG_FLAG_ADAPTIVE_CORR: the coarse correction is scaled by its energy-optimal weight
+// before it is added, which is then added with weight 1
+static bool adaptive_corr(const mg_ctx *c) { return (c->P.flags & MG_FLAG_ADAPTIVE_CORR) != 0; }
+static double corr_weight(const mg_ctx *c) { return adaptive_corr(c) ? 1.0 : c->P.omega_corr; }
+
 struct Sched {
   mg_ctx *c;
   Launch lc;
@@ -420,7 +425,7 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
   mg_ctx *c = S.c;
   LevData<T> &D = LevOf<T>::data(c, l);
   Lev<T> L = LevOf<T>::get(c, l);
-  T om = (T)c->P.omega, oc = (T)c->P.omega_corr;
+  T om = (T)c->P.omega, oc = (T)corr_weight(c);
   int &cur = c->cur[l];
   bool jac = c->P.smoother == MG_JACOBI;
   bool line = c->P.smoother >= MG_LINE_X;
@@ -523,7 +528,7 @@ template <typename T>
 static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out) {
   mg_ctx *c = S.c;
   launch_coarse_cycle<T>(S.lc, c->P.dim, c->kind, c->slev, c->prog + c->prog_off[pid], c->prog_len[pid], c->lcut,
-                         g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)c->P.omega_corr,
+                         g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)corr_weight(c),
                          c->csk_smem);
 }
 
@@ -598,6 +603,7 @@ struct ProgBuilder {
     } else {
       cycle(l - 1, 1, tr, true);
     }
+    if (adaptive_corr(c)) op(CP_ADAPT, l, cur[l], cur[l - 1]);
     op(CP_PROLONG, l, cur[l], cur[l - 1]);
     smooth(l, npost, order, false);
   }
@@ -636,6 +642,22 @@ struct ProgBuilder {
     op(CP_STORE_U, L, cur[L], 0);
   }
 };
+
+// Adaptive correction weight at level l (Wallis 2008, section "Multigrid": omega_l that
+// minimises the energy norm of the error): P e into r_l, omega = (g - A u, P e) / (A P e, P e),
+// then the coarse correction e scaled by omega in place, so that the correction added next
+// (with weight 1) is omega P e.
+template <typename T>
+static void emit_adapt(Sched &S, int l, const T *g) {
+  mg_ctx *c = S.c;
+  LevData<T> &D = LevOf<T>::data(c, l), &Dc = LevOf<T>::data(c, l - 1);
+  Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
+  T *e = Dc.u[c->cur[l - 1]];
+  cudaMemsetAsync(D.r, 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
+  launch_prolong_add<T>(S.lc, L, Lc, e, D.r, T(1));
+  launch_corr_weight<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r, c->partials, norm_parts_count(), c->scal + 8);
+  launch_scale_by<T>(S.lc, e, (long long)c->geo[l - 1].count, c->scal + 8);
+}
 
 // One cycle at level l on (u = current buffer of level l, g).  type 0 = F, 1 = V.
 template <typename T>
@@ -679,6 +701,7 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
   } else {
     cycle<T>(S, l - 1, Dc.g, 1, transposed, true);
   }
+  if (adaptive_corr(c)) emit_adapt<T>(S, l, g);
   smooth<T>(S, l, g, npost, order, false, &Lc, Dc.u[c->cur[l - 1]]);
 }
 

@@ -258,6 +258,14 @@ bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int co
 void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
                           float *r32, double *partials, int nparts, double *out_sq);
 void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c);
+// adaptive correction weight: omega = (g - A u, pe) / (A pe, pe) over the unknowns of L
+// (pe = P e, zero off the unknowns), written to *omega; partials: nparts doubles of scratch
+template <typename T>
+void launch_corr_weight(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, const T *pe,
+                        double *partials, int nparts, double *omega);
+// e[0..n) *= *omega
+template <typename T>
+void launch_scale_by(const Launch &lc, T *e, long long n, const double *omega);
 
 // gradient with respect to the cell field
 void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, const double *lam, double *dk);
