@@ -20,8 +20,8 @@ enum CoarseOp {
   CP_RB_ZERO = 12,  // u_y[b] = first half sweep of colour a from a zero iterate (replaces ZERO_U +
                     // RB_HALF with the same arithmetic: the residual of a zero iterate is g)
   CP_INTERP = 13,   // u_y[a] = P u_{y-1}[b]  (interpolation of a coarse solution, weight 1)
-  CP_ADAPT = 14     // u_{y-1}[b] *= omega = (g_y - A u_y[a], P e) / (A P e, P e), e = u_{y-1}[b]
-                    // (energy-optimal correction weight; r_y holds P e afterwards)
+  CP_ADAPT = 14     // u_y[a] += omega P e, e = u_{y-1}[b], omega = (g_y - A u_y[a], P e) / (A P e, P e)
+                    // (the energy-optimal correction weight; r_y holds P e afterwards)
 };
 
 }  // namespace mg

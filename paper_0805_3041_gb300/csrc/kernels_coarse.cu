@@ -279,31 +279,31 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         });
         break;
       }
-      case CP_ADAPT: {   // z = fine buffer, w = coarse buffer (scaled in place)
+      case CP_ADAPT: {   // z = fine buffer, w = coarse buffer: u_y[z] += omega P e with its own weight
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
-        T *ec = o.w ? pool + Cs.off_u1 : pool + Cs.off_u0;
-        const T *u = ub(o.z);
+        const T *ec = o.w ? pool + Cs.off_u1 : pool + Cs.off_u0;
+        T *u = ub(o.z);
         FOR_UNK(L, { r[p] = interp_at<T, DIM>(C, ec, i, j, k); });   // P e (r is zero off the unknowns)
         __syncthreads();
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = T(0), a1 = T(0);   // per-thread sums in the level's precision
         FOR_UNK(L, {
           int dm, dp;
           yoffs(L, j, dm, dp);
           Weights<T, DIM, KIND> w;
           w.load(L, i, p, dm);
-          double d = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
-          double ape = -(double)residual_at<T, DIM, KIND>(L, w, r, p, dm, dp, T(0));
-          a0 = fma(d, (double)r[p], a0);
-          a1 = fma(ape, (double)r[p], a1);
+          T d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+          T ape = -residual_at<T, DIM, KIND>(L, w, r, p, dm, dp, T(0));
+          a0 = fma(d, r[p], a0);
+          a1 = fma(ape, r[p], a1);
         });
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
           a0 += __shfl_down_sync(0xffffffffu, a0, o2);
           a1 += __shfl_down_sync(0xffffffffu, a1, o2);
         }
         if ((threadIdx.x & 31) == 0) {
-          s_red[0][wid_] = a0;
-          s_red[1][wid_] = a1;
+          s_red[0][wid_] = (double)a0;
+          s_red[1][wid_] = (double)a1;
         }
         __syncthreads();
         double num = 0.0, den = 0.0;   // every thread sums the warp totals in the same order
@@ -311,9 +311,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
           num += s_red[0][q];
           den += s_red[1][q];
         }
-        const T f = (T)(den > 0.0 ? num / den : 1.0);
-        const int cc = (int)(C.plane * C.n2);
-        for (int t = tid_; t < cc; t += nthr_) ec[t] *= f;
+        const T wgt = (T)(den > 0.0 ? num / den : 1.0);
+        FOR_UNK(L, { u[p] = fma(wgt, r[p], u[p]); });
         break;
       }
       case CP_RB_ZERO: {   // z = colour, w = buffer: first half sweep from a zero iterate

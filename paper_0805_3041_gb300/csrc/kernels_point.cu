@@ -216,15 +216,26 @@ __global__ void __launch_bounds__(1024) k_norm_finish(const double *__restrict__
 // the energy norm of the error): omega = (d, P e) / (A P e, P e) with d = g - A u
 // ---------------------------------------------------------------------------------------
 
-// per block the partial sums of d . Pe (partials[b]) and (A Pe) . Pe (partials[nb + b]) over
-// the unknowns; pe holds P e, zero off the unknowns
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v);
+template <>
+__device__ __forceinline__ double block_sum_t<double>(double v) { return block_sum(v); }
+template <>
+__device__ __forceinline__ float block_sum_t<float>(float v) { return block_sum_f(v); }
+
+// Sums of d . Pe and (A Pe) . Pe over the unknowns (pe holds P e, zero off the unknowns),
+// accumulated per thread in the level's precision (FP64 throughput is the limit in FP32
+// levels otherwise), one FP64 partial pair per block.  The last block to finish sums the
+// partials in a fixed order, writes omega = sum1 / sum2 (1 when P e = 0) and re-arms the
+// counter.
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
-                                                      const T *__restrict__ pe, double *__restrict__ partials, int R) {
+                                                      const T *__restrict__ pe, double *__restrict__ partials,
+                                                      unsigned *__restrict__ count, double *__restrict__ omega, int R) {
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
-  double a0 = 0.0, a1 = 0.0;
+  T a0 = T(0), a1 = T(0);
   if (i <= L.n0 - 2) {
     for (int q = 0; q < R; ++q) {
       long long r = r0 + q;
@@ -235,46 +246,39 @@ __global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restr
       yoffs(L, j, dm, dp);
       Weights<T, DIM, KIND> w;
       w.load(L, i, p, dm);
-      double d = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
-      double ape = -(double)residual_at<T, DIM, KIND>(L, w, pe, p, dm, dp, T(0));
-      double v = (double)pe[p];
+      T d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+      T ape = -residual_at<T, DIM, KIND>(L, w, pe, p, dm, dp, T(0));
+      T v = pe[p];
       a0 = fma(d, v, a0);
       a1 = fma(ape, v, a1);
     }
   }
   const int nb = (int)(gridDim.x * gridDim.y), b = blockIdx.y * gridDim.x + blockIdx.x;
-  double s0 = block_sum(a0);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[b] = s0;
+  const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
+  double s0 = (double)block_sum_t<T>(a0);
   __syncthreads();   // block_sum's shared slots are reused
-  double s1 = block_sum(a1);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[nb + b] = s1;
-}
-
-// single block: omega = sum(num) / sum(den) in a fixed order; 1 when P e = 0 (den = 0)
-__global__ void __launch_bounds__(1024) k_corr_omega(const double *__restrict__ partials, int n, double *out) {
-  __shared__ double red[2][32];
-  double a0 = 0.0, a1 = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    a0 += partials[t];
-    a1 += partials[n + t];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_down_sync(0xffffffffu, a0, o);
-    a1 += __shfl_down_sync(0xffffffffu, a1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = a0;
-    red[1][threadIdx.x >> 5] = a1;
+  double s1 = (double)block_sum_t<T>(a1);
+  __shared__ bool last;
+  if (t0) {
+    partials[b] = s0;
+    partials[nb + b] = s1;
+    __threadfence();
+    last = atomicAdd(count, 1u) == (unsigned)nb - 1u;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    bool in = threadIdx.x < (blockDim.x >> 5);
-    double s0 = in ? red[0][threadIdx.x] : 0.0, s1 = in ? red[1][threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, o);
-      s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    }
-    if (threadIdx.x == 0) out[0] = s1 > 0.0 ? s0 / s1 : 1.0;
+  if (!last) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  double n0 = 0.0, n1 = 0.0;
+  for (int t = tid; t < nb; t += nt) {
+    n0 += __ldcg(partials + t);
+    n1 += __ldcg(partials + nb + t);
+  }
+  n0 = block_sum(n0);
+  __syncthreads();
+  n1 = block_sum(n1);
+  if (t0) {
+    omega[0] = n1 > 0.0 ? n0 / n1 : 1.0;
+    count[0] = 0u;
   }
 }
 
@@ -480,13 +484,11 @@ void launch_norm_parts(const Launch &lc, const Lev<T> &L, const T *v, double *pa
 
 template <typename T>
 void launch_corr_weight(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, const T *pe,
-                        double *partials, int nparts, double *omega) {
+                        double *partials, int nparts, unsigned *count, double *omega) {
   long long rows = L.unk_rows();
-  int R = norm_R(rows, L.xunk(), nparts / 2);
+  int R = norm_R(rows, L.xunk(), nparts / 2 < 4096 ? nparts / 2 : 4096);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  DISPATCH_DK(L.dim, kind, k_corr_dots, <<<gr, bl, 0, lc.s>>>(L, u, g, pe, partials, R));
-  ++*lc.counter;
-  k_corr_omega<<<1, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), omega);
+  DISPATCH_DK(L.dim, kind, k_corr_dots, <<<gr, bl, 0, lc.s>>>(L, u, g, pe, partials, count, omega, R));
   ++*lc.counter;
 }
 
@@ -603,7 +605,7 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
                                       double *);                                                              \
   template void launch_norm_parts<T>(const Launch &, const Lev<T> &, const T *, double *, int, double *);      \
   template void launch_corr_weight<T>(const Launch &, const Lev<T> &, int, const T *, const T *, const T *,    \
-                                      double *, int, double *);                                               \
+                                      double *, int, unsigned *, double *);                                   \
   template void launch_scale_by<T>(const Launch &, T *, long long, const double *);
 INST(double)
 INST(float)

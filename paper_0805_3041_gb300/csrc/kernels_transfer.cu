@@ -81,6 +81,50 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, cons
   }
 }
 
+// out = P ec on every node of F: the interpolation at the unknowns, zero on the Dirichlet
+// nodes (the whole node array is written, so no clearing pass is needed)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(BX *BY) k_interp(Lev<T> F, Lev<T> C, const T *__restrict__ ec,
+                                                   T *__restrict__ out, int R) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  if (i >= F.n0) return;
+  long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
+  const int nrows = F.n1 * (DIM == 3 ? F.n2 : 1);
+  const bool xin = i >= 1 && i <= F.n0 - 2;
+  const int I0 = i >> 1, I1 = (i + 1) >> 1;
+  for (int q = 0; q < R; ++q) {
+    long long r = r0 + q;
+    if (r >= nrows) return;
+    const int j = DIM == 3 ? (int)r % F.n1 : (int)r, k = DIM == 3 ? (int)r / F.n1 : 0;
+    const bool unk = xin && (F.per || (j >= 1 && j <= F.n1 - 2)) && (DIM == 2 || (k >= 1 && k <= F.n2 - 2));
+    T s = T(0);
+    if (unk) {
+      int J0 = j >> 1, J1 = (j + 1) >> 1;
+      if (J1 >= C.n1) J1 -= C.n1;   // periodic wrap
+      long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+      if (DIM == 2) {
+        s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
+      } else {
+        long long z0 = (long long)(k >> 1) * C.plane, z1 = (long long)((k + 1) >> 1) * C.plane;
+        T s0 = (ec[z0 + a0 + I0] + ec[z0 + a0 + I1]) + (ec[z0 + a1 + I0] + ec[z0 + a1 + I1]);
+        T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
+        s = (s0 + s1) * T(0.125);
+      }
+    }
+    out[(long long)k * F.plane + (long long)j * F.pitch + i] = s;
+  }
+}
+
+template <typename T>
+void launch_interp(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *ec, T *out) {
+  long long rows = (long long)F.n1 * (F.dim == 3 ? F.n2 : 1);
+  int R = rpt(rows);
+  dim3 gr = grid2(F.n0, rows, R), bl(BX, BY);
+  if (F.dim == 2) k_interp<T, 2><<<gr, bl, 0, lc.s>>>(F, C, ec, out, R);
+  else k_interp<T, 3><<<gr, bl, 0, lc.s>>>(F, C, ec, out, R);
+  ++*lc.counter;
+}
+
 template <typename T>
 void launch_restrict(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *rf, T *gc) {
   long long rows = C.unk_rows();
@@ -453,6 +497,7 @@ void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *sr
 #define INST(T)                                                                                              \
   template void launch_restrict<T>(const Launch &, const Lev<T> &, const Lev<T> &, const T *, T *);          \
   template void launch_prolong_add<T>(const Launch &, const Lev<T> &, const Lev<T> &, const T *, T *, T);    \
+  template void launch_interp<T>(const Launch &, const Lev<T> &, const Lev<T> &, const T *, T *);           \
   template void launch_coarse_apply<T>(const Launch &, const double *, const long long *, int, const T *, T *); \
   template void launch_pack<T>(const Launch &, const Lev<T> &, const double *, T *, int);                    \
   template void launch_unpack<T>(const Launch &, const Lev<T> &, const T *, double *, double);                       \

@@ -97,6 +97,7 @@ struct mg_ctx {
   cudaGraphExec_t lexec[2] = {nullptr, nullptr};   // whole solve: device-side WHILE loop
   long long loop_init_kernels[2] = {0, 0}, loop_body_kernels[2] = {0, 0};
   int *st = nullptr;                               // device: cycles done, status of the loop
+  unsigned *cnt = nullptr;                         // device: block counter of last-block reductions (zero at rest)
   long long graph_kernels[2] = {0, 0};
   double *h_relres = nullptr;   // pinned
   // timing of finest-level smoothing launches
@@ -232,6 +233,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   c->scal = b.take<double>(16);
   c->hist = b.take<double>((size_t)P.max_cycles + 2);
   c->st = b.take<int>(8);
+  c->cnt = b.take<unsigned>(8);
   // coarsest grid
   const LevGeom &g1 = c->geo[1];
   long long nc = (long long)(g1.n[0] - 2) * (P.periodic_y ? g1.n[1] : g1.n[1] - 2) * (P.dim == 3 ? g1.n[2] - 2 : 1);
@@ -603,8 +605,8 @@ struct ProgBuilder {
     } else {
       cycle(l - 1, 1, tr, true);
     }
-    if (adaptive_corr(c)) op(CP_ADAPT, l, cur[l], cur[l - 1]);
-    op(CP_PROLONG, l, cur[l], cur[l - 1]);
+    if (adaptive_corr(c)) op(CP_ADAPT, l, cur[l], cur[l - 1]);   // the correction with its own weight
+    else op(CP_PROLONG, l, cur[l], cur[l - 1]);
     smooth(l, npost, order, false);
   }
   // coarse correction at level lc requested by a type-`type` cycle at lc + 1
@@ -653,9 +655,9 @@ static void emit_adapt(Sched &S, int l, const T *g) {
   LevData<T> &D = LevOf<T>::data(c, l), &Dc = LevOf<T>::data(c, l - 1);
   Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
   T *e = Dc.u[c->cur[l - 1]];
-  cudaMemsetAsync(D.r, 0, sizeof(T) * (size_t)c->geo[l].count, S.lc.s);
-  launch_prolong_add<T>(S.lc, L, Lc, e, D.r, T(1));
-  launch_corr_weight<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r, c->partials, norm_parts_count(), c->scal + 8);
+  launch_interp<T>(S.lc, L, Lc, e, D.r);
+  launch_corr_weight<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r, c->partials, norm_parts_count(), c->cnt,
+                        c->scal + 8);
   launch_scale_by<T>(S.lc, e, (long long)c->geo[l - 1].count, c->scal + 8);
 }
 
@@ -926,6 +928,7 @@ static mg_status setup_levels(mg_ctx *c) {
   const mg_params &P = c->P;
   int L = c->L;
   CK(cudaMemsetAsync(c->st, 0, sizeof(int) * 8, c->stream));   // loop state and the device-wait flag
+  CK(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned) * 8, c->stream));
   // geometry constants per level
   for (int l = L; l >= 1; --l) {
     LevGeom &g = c->geo[l];

@@ -259,10 +259,14 @@ void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, cons
                           float *r32, double *partials, int nparts, double *out_sq);
 void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c);
 // adaptive correction weight: omega = (g - A u, pe) / (A pe, pe) over the unknowns of L
-// (pe = P e, zero off the unknowns), written to *omega; partials: nparts doubles of scratch
+// (pe = P e, zero off the unknowns), written to *omega; partials: nparts doubles of scratch;
+// count: a device counter that is zero between launches (the kernel re-arms it)
 template <typename T>
 void launch_corr_weight(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, const T *pe,
-                        double *partials, int nparts, double *omega);
+                        double *partials, int nparts, unsigned *count, double *omega);
+// out = P ec on every node of F (zero off the unknowns of F)
+template <typename T>
+void launch_interp(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *ec, T *out);
 // e[0..n) *= *omega
 template <typename T>
 void launch_scale_by(const Launch &lc, T *e, long long n, const double *omega);
