@@ -172,6 +172,59 @@ def cylinder_3d(nr=257, nt=256, nz=257, r0=0.1, r1=1.0, seed=3, noise=0.1):
                        sz=r / hz ** 2, b=b, x0=np.zeros_like(b))
 
 
+def stretched_x(n=129, ny=None, beta=3.0, dim=2, manufactured=False, seed=12):
+    """-Laplace u = f on the unit square (cube) on a grid stretched in x (section "Anisotropies":
+    refinement in one direction), y (and z) uniform.
+
+    Nodes x_i = (exp(beta s_i) - 1) / (exp(beta) - 1), s_i = i / (n - 1): spacings grow
+    geometrically away from x = 0 (ratio exp(beta h0) between neighbours, exp(beta) end to end);
+    the even nodes form the same family on the coarser grid.  Finite-volume form on the dual
+    cells, divided by the nominal h0 = 1 / (n - 1) times hy (hy hz in 3-D) so that a uniform grid
+    gives the usual 1/h^2 weights:
+
+        x-edge (i, i+1): 1 / (hx_{i+1/2} h0),  y-edge at x_i: hbar_i / (h0 hy^2),
+        z-edge at x_i: hbar_i / (h0 hz^2),     right-hand side: f_i hbar_i / h0,
+
+    hbar_i = (hx_{i-1/2} + hx_{i+1/2}) / 2 the dual-cell width.  The weights depend on x only:
+    a separable-coefficient problem.  manufactured=True takes f = d pi^2 prod sin(pi x_d) (exact
+    solution prod sin(pi x_d)); otherwise f is uniform in [-1, 1].
+    """
+    ny = n if ny is None else ny
+    nz = n if dim == 3 else 1
+    s = np.arange(n) / (n - 1)
+    x = np.expm1(beta * s) / np.expm1(beta) if beta != 0 else s
+    hx = np.diff(x)
+    hbar = np.empty(n)
+    hbar[1:-1] = 0.5 * (hx[:-1] + hx[1:])
+    hbar[0], hbar[-1] = 0.5 * hx[0], 0.5 * hx[-1]
+    h0 = 1.0 / (n - 1)
+    hy = 1.0 / (ny - 1)
+    hz = 1.0 / (nz - 1) if dim == 3 else 1.0
+    y = hy * np.arange(ny)
+    if dim == 2:
+        shape = (ny, n)
+        if manufactured:
+            f = 2 * math.pi ** 2 * np.outer(np.sin(math.pi * y), np.sin(math.pi * x))
+        else:
+            f = np.random.default_rng(seed).uniform(-1.0, 1.0, shape)
+        scale = hbar[None, :] / h0
+    else:
+        z = hz * np.arange(nz)
+        shape = (nz, ny, n)
+        if manufactured:
+            f = 3 * math.pi ** 2 * np.einsum("k,j,i->kji", np.sin(math.pi * z), np.sin(math.pi * y),
+                                             np.sin(math.pi * x))
+        else:
+            f = np.random.default_rng(seed).uniform(-1.0, 1.0, shape)
+        scale = hbar[None, None, :] / h0
+    b = _zero_boundary(f * scale, dim, False)
+    sp = ProblemSpec(name=f"stretched_x{n}_b{beta:g}", dim=dim, n=(n, ny, nz), periodic_y=False, kind=SEPARABLE,
+                     h=(h0, hy, hz), sx=1.0 / (hx * h0), sy=hbar / (h0 * hy ** 2),
+                     sz=(hbar / (h0 * hz ** 2)) if dim == 3 else np.zeros(n), b=b, x0=np.zeros_like(b))
+    sp.x_nodes = x
+    return sp
+
+
 def poisson_3d(n=33, seed=11):
     """-Laplace u = f on the unit cube, f uniform[-1, 1]."""
     h = 1.0 / (n - 1)

@@ -704,3 +704,53 @@ def test_adaptive_weight_repairs_a_badly_damped_correction():
     b = rand_field(o_one, np.random.default_rng(43))
     cyc = {k: o.solve(b, tol=1e-10)[2] for k, o in (("fix", o_fix), ("one", o_one), ("ad", o_ad))}
     assert cyc["ad"] <= cyc["one"] < cyc["fix"]
+
+
+# --------------------------------------------------------------------------------------
+# stretched grids (section "Anisotropies": refinement in one direction)
+# --------------------------------------------------------------------------------------
+
+def _stretched_oracle(sp, smoother="rbgs", omega=1.0, levels=None):
+    p = orc.Problem(dim=sp.dim, n=sp.n, periodic_y=False, kind=orc.SEPARABLE, h=sp.h, sx=sp.sx, sy=sp.sy, sz=sp.sz)
+    return orc.Oracle(p, levels=levels or inputs.max_levels(sp.n, dim=sp.dim), smoother=smoother, omega=omega)
+
+
+@pytest.mark.parametrize("beta", [2.0, 4.0])
+def test_stretched_grid_discretisation_is_second_order(beta):
+    """Manufactured solution sin(pi x) sin(pi y) on x-stretched grids: the max-norm error of
+    the discrete solution falls by ~4 per halving of the nominal spacing."""
+    errs = []
+    for n in (33, 65, 129):
+        sp = inputs.stretched_x(n, beta=beta, manufactured=True)
+        x, st, c, rr, h = _stretched_oracle(sp, "gsadi").solve(sp.b, tol=1e-11, maxit=100)
+        assert st == orc.OK
+        exact = np.outer(np.sin(math.pi * np.linspace(0, 1, n)), np.sin(math.pi * sp.x_nodes))
+        errs.append(np.abs(x - exact).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 3.7 <= a / b <= 4.3
+
+
+def test_stretched_grid_coarse_levels_are_the_coarse_stretched_grid():
+    """The coarsening rule (harmonic mean along an edge, x1/4) reproduces the x-edge weights of
+    the stretched grid built directly on the even nodes: series resistances add."""
+    fine = inputs.stretched_x(129, beta=5.0)
+    coarse = inputs.stretched_x(65, beta=5.0)
+    o = _stretched_oracle(fine, levels=2)
+    cc = o.level_coeffs(1)
+    n = 65
+    assert np.allclose(cc[:n - 1], coarse.sx, rtol=1e-13)
+
+
+def test_stretched_grid_needs_alternating_lines():
+    """Strong stretching makes the cells thin in x at one end and thin in y at the other: point
+    Gauss-Seidel stalls, x-lines alone slow down, the alternating GSADI keeps its rate."""
+    out = {}
+    for n in (65, 129):
+        sp = inputs.stretched_x(n, beta=6.0)
+        for sm in ("rbgs", "zebra_x", "gsadi"):
+            x, st, c, rr, h = _stretched_oracle(sp, sm).solve(sp.b, tol=1e-10, maxit=40)
+            out[(n, sm)] = (st, c)
+    for n in (65, 129):
+        assert out[(n, "gsadi")][0] == orc.OK and out[(n, "gsadi")][1] <= 7
+        assert out[(n, "rbgs")][0] == orc.ENOCONV
+        assert out[(n, "zebra_x")][0] == orc.ENOCONV
