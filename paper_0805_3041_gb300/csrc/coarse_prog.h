@@ -11,14 +11,15 @@ enum CoarseOp {
   CP_STORE_U = 3,   // global u <- u_y[a] (unknowns)
   CP_ZERO_U = 4,    // u_y[a] = 0
   CP_JACOBI = 5,    // u_y[b] = u_y[a] + omega D^-1 (g - A u_y[a]);  a < 0: from a zero iterate
-  CP_RB_HALF = 6,   // red-black half sweep of colour a on u_y[b], in place
+  CP_RB_HALF = 6,   // red-black half sweeps on u_y[b], in place: a = first colour | zero << 1 |
+                    // (count - 1) << 2, colours alternating, one barrier between them; zero: the
+                    // first half sweep starts from a zero iterate and sets every unknown
   CP_LINE = 7,      // a = dir | zebra << 1 | colour << 2,  b = src | dst << 4 | scratch << 8
-  CP_DEFECT = 8,    // r_y = g_y - A u_y[a]
+  CP_DEFECT = 8,    // r_y = g_y - A u_y[a]; b = 1: then g_{y-1} = R r_y in the same step
   CP_RESTRICT = 9,  // g_{y-1} = R r_y  (a = 1: R g_y, the right-hand side itself)
-  CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b]
+  CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b & 1]; b >> 1 = d + 1: then the red-black sweeps
+                    // of descriptor d (as CP_RB_HALF) on u_y[a] in the same step
   CP_COARSE = 11,   // u_1[a] = A_1^{-1} g_1
-  CP_RB_ZERO = 12,  // u_y[b] = first half sweep of colour a from a zero iterate (replaces ZERO_U +
-                    // RB_HALF with the same arithmetic: the residual of a zero iterate is g)
   CP_INTERP = 13,   // u_y[a] = P u_{y-1}[b]  (interpolation of a coarse solution, weight 1)
   CP_ADAPT = 14     // u_y[a] += omega P e, e = u_{y-1}[b], omega = (g_y - A u_y[a], P e) / (A P e, P e)
                     // (the energy-optimal correction weight; r_y holds P e afterwards)

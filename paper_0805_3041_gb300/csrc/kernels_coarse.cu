@@ -138,12 +138,40 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
     T *const ub0 = pool + S.off_u0, *const ub1 = pool + S.off_u1;
     auto ub = [&](int b) -> T * { return b ? ub1 : ub0; };   // no runtime-indexed array (local memory)
     T *g = pool + S.off_g, *r = pool + S.off_r;
+    // unknowns of this level from a global array: every thread issues a batch of loads before
+    // its shared-memory stores (one load at a time is latency-bound)
+    auto load_unk = [&](T *dst, const T *__restrict__ src) {
+      const int nx = L.n0 - 2, ny = L.yrows(), tot = nx * ny * L.zrows();
+      constexpr int B = 8;
+      for (int t0 = tid_; t0 < tot; t0 += B * nthr_) {
+        T v[B];
+        int pp[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+          const int t = t0 + q * nthr_;
+          pp[q] = -1;
+          if (t < tot) {
+            const int i = 1 + t % nx, rr = t / nx;
+            const int j = L.ylo() + (DIM == 3 ? rr % ny : rr), k = DIM == 3 ? 1 + rr / ny : 0;
+            pp[q] = k * (int)L.plane + j * (int)L.pitch + i;
+            v[q] = src[(long long)k * S.gplane + (long long)j * S.gpitch + i];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+          if (pp[q] >= 0) dst[pp[q]] = v[q];
+      }
+    };
+    int rb_desc = -1;            // red-black sweeps run after the switch (RB_HALF, or fused after PROLONG)
+    T *rb_u = nullptr;
+    const T *rs_src = nullptr;   // restriction run after the switch (RESTRICT, or fused after DEFECT)
+    bool sync_first = false;     // a barrier before the deferred part (it reads what the step wrote)
     switch (o.x) {
       case CP_LOAD_G:
-        FOR_UNK(L, { g[p] = g_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
+        load_unk(g, g_in);
         break;
       case CP_LOAD_U:
-        FOR_UNK(L, { ub(o.z)[p] = u_in[(long long)k * S.gplane + (long long)j * S.gpitch + i]; });
+        load_unk(ub(o.z), u_in);
         break;
       case CP_STORE_U:
         FOR_UNK(L, { u_out[(long long)k * S.gplane + (long long)j * S.gpitch + i] = ub(o.z)[p]; });
@@ -164,18 +192,10 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         });
         break;
       }
-      case CP_RB_HALF: {   // z = colour, w = buffer
-        T *u = ub(o.w);
-        int colour = o.z;
-        FOR_COLOUR(L, colour, {
-          int dm, dp;
-          yoffs(L, j, dm, dp);
-          Weights<T, DIM, KIND> w;
-          w.load(L, i, p, dm);
-          u[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]), u[p]);
-        });
+      case CP_RB_HALF:   // z = sweep descriptor, w = buffer (the sweeps run after the switch)
+        rb_desc = o.z;
+        rb_u = ub(o.w);
         break;
-      }
       case CP_LINE: {   // z = dir | zebra << 1 | colour << 2, w = src | dst << 4 | scratch << 8
         int dir = o.z & 1, zebra = (o.z >> 1) & 1, colour = (o.z >> 2) & 1;
         T *src = ub(o.w & 15), *dst = ub((o.w >> 4) & 15);
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         }
         break;
       }
-      case CP_DEFECT: {   // z = buffer
+      case CP_DEFECT: {   // z = buffer; w = 1: the restriction of r follows in the same step
         const T *u = ub(o.z);
         FOR_UNK(L, {
           int dm, dp;
@@ -245,38 +265,31 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
           w.load(L, i, p, dm);
           r[p] = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
         });
+        if (o.w) {
+          rs_src = r;
+          sync_first = true;
+        }
         break;
       }
-      case CP_RESTRICT: {   // level y -> y-1 (r of level y, or g when z = 1, into g of level y-1)
-        const SLev<T> &Cs = levs[o.y - 1];
-        Lev<T> C = Cs.L;
-        T *gc = pool + Cs.off_g;
-        const T *rs = o.z ? g : r;
-        FOR_UNK(C, {
-          int I = i, J = j, K = k;
-          int dm, dp;
-          yoffs(L, 2 * J, dm, dp);
-          int pf = (2 * K) * (int)L.plane + (2 * J) * (int)L.pitch + 2 * I;
-          auto row3 = [&](int c) -> T { return (rs[c - 1] + rs[c + 1]) + T(2) * rs[c]; };
-          auto plane3 = [&](int c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
-          T s;
-          if (DIM == 2) s = plane3(pf) * T(0.0625);
-          else s = ((plane3(pf - (int)L.plane) + plane3(pf + (int)L.plane)) + T(2) * plane3(pf)) * T(0.015625);
-          gc[p] = s;
-        });
+      case CP_RESTRICT:   // level y -> y-1: r of level y, or g when z = 1 (runs after the switch)
+        rs_src = o.z ? g : r;
         break;
-      }
-      case CP_PROLONG:     // level y (fine), z = fine buffer, w = coarse buffer
+      case CP_PROLONG:     // level y (fine), z = fine buffer, w = coarse buffer | (sweeps + 1) << 1
       case CP_INTERP: {
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
-        const T *ec = (o.w ? pool + Cs.off_u1 : pool + Cs.off_u0);
+        const T *ec = ((o.w & 1) ? pool + Cs.off_u1 : pool + Cs.off_u0);
         T *uf = ub(o.z);
         const bool interp = o.x == CP_INTERP;
         FOR_UNK(L, {
           T s = interp_at<T, DIM>(C, ec, i, j, k);
           uf[p] = interp ? s : fma(omega_corr, s, uf[p]);
         });
+        if (o.w >> 1) {   // the post-smoothing red-black sweeps follow in the same step
+          rb_desc = (o.w >> 1) - 1;
+          rb_u = uf;
+          sync_first = true;
+        }
         break;
       }
       case CP_ADAPT: {   // z = fine buffer, w = coarse buffer: u_y[z] += omega P e with its own weight
@@ -315,22 +328,6 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         FOR_UNK(L, { u[p] = fma(wgt, r[p], u[p]); });
         break;
       }
-      case CP_RB_ZERO: {   // z = colour, w = buffer: first half sweep from a zero iterate
-        T *u = ub(o.w);
-        const int colour = o.z;
-        FOR_UNK(L, {
-          T v = T(0);
-          if (((i + j + k) & 1) == colour) {
-            int dm, dp;
-            yoffs(L, j, dm, dp);
-            Weights<T, DIM, KIND> w;
-            w.load(L, i, p, dm);
-            v = fma(omega * w.dinv, g[p], T(0));   // the residual of a zero iterate is g
-          }
-          u[p] = v;
-        });
-        break;
-      }
       case CP_COARSE: {   // level 1: u[z] = A^{-1} g, one warp per row of the dense inverse
         T *u = ub(o.z);
         const int lane = threadIdx.x & 31;
@@ -342,6 +339,55 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
           if (lane == 0) u[cidx_smem[row]] = (T)s;
         }
         break;
+      }
+    }
+    if (rs_src) {   // full weighting of rs_src into g of level y-1
+      if (sync_first) __syncthreads();
+      const SLev<T> &Cs = levs[o.y - 1];
+      Lev<T> C = Cs.L;
+      T *gc = pool + Cs.off_g;
+      const T *rs = rs_src;
+      FOR_UNK(C, {
+        int I = i, J = j, K = k;
+        int dm, dp;
+        yoffs(L, 2 * J, dm, dp);
+        int pf = (2 * K) * (int)L.plane + (2 * J) * (int)L.pitch + 2 * I;
+        auto row3 = [&](int c) -> T { return (rs[c - 1] + rs[c + 1]) + T(2) * rs[c]; };
+        auto plane3 = [&](int c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
+        T s;
+        if (DIM == 2) s = plane3(pf) * T(0.0625);
+        else s = ((plane3(pf - (int)L.plane) + plane3(pf + (int)L.plane)) + T(2) * plane3(pf)) * T(0.015625);
+        gc[p] = s;
+      });
+    }
+    if (rb_desc >= 0) {   // red-black half sweeps on rb_u, in place, one barrier between them
+      if (sync_first) __syncthreads();
+      T *u = rb_u;
+      const int nh = 1 + (rb_desc >> 2);
+      for (int h = 0; h < nh; ++h) {
+        const int colour = (rb_desc + h) & 1;
+        if (h == 0 && (rb_desc & 2)) {   // from a zero iterate: sets every unknown (its residual is g)
+          FOR_UNK(L, {
+            T v = T(0);
+            if (((i + j + k) & 1) == colour) {
+              int dm, dp;
+              yoffs(L, j, dm, dp);
+              Weights<T, DIM, KIND> w;
+              w.load(L, i, p, dm);
+              v = fma(omega * w.dinv, g[p], T(0));
+            }
+            u[p] = v;
+          });
+        } else {
+          FOR_COLOUR(L, colour, {
+            int dm, dp;
+            yoffs(L, j, dm, dp);
+            Weights<T, DIM, KIND> w;
+            w.load(L, i, p, dm);
+            u[p] = fma(omega * w.dinv, residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]), u[p]);
+          });
+        }
+        if (h + 1 < nh) __syncthreads();
       }
     }
     __syncthreads();

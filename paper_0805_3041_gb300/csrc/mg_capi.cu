@@ -541,6 +541,8 @@ struct ProgBuilder {
   std::vector<int4> ops;
   int cur[MAXLEV + 1] = {0};
   void op(int code, int lev, int a, int b) { ops.push_back(make_int4(code, lev, a, b)); }
+  // descriptor of `sweeps` red-black sweeps starting with colour `order` (CP_RB_HALF)
+  static int rb_desc(int sweeps, int order, bool zero) { return order | (zero ? 2 : 0) | ((2 * sweeps - 1) << 2); }
   void smooth(int l, int sweeps, int order, bool zero) {
     int &cu = cur[l];
     int sm = c->P.smoother;
@@ -555,17 +557,8 @@ struct ProgBuilder {
       }
       return;
     }
-    if (sm == MG_RBGS) {
-      int s0 = 0;
-      if (zero) {   // the first half sweep from a zero iterate sets every unknown
-        op(CP_RB_ZERO, l, order, cu);
-        op(CP_RB_HALF, l, 1 - order, cu);
-        s0 = 1;
-      }
-      for (int s = s0; s < sweeps; ++s) {
-        op(CP_RB_HALF, l, order, cu);
-        op(CP_RB_HALF, l, 1 - order, cu);
-      }
+    if (sm == MG_RBGS) {   // all 2 * sweeps half sweeps in one step
+      op(CP_RB_HALF, l, rb_desc(sweeps, order, zero), cu);
       return;
     }
     if (zero) op(CP_ZERO_U, l, cu, 0);
@@ -596,8 +589,7 @@ struct ProgBuilder {
     }
     int npre = tr ? c->P.nu2 : c->P.nu1, npost = tr ? c->P.nu1 : c->P.nu2, order = tr ? 1 : 0;
     smooth(l, npre, order, zero);
-    op(CP_DEFECT, l, cur[l], 0);
-    op(CP_RESTRICT, l, 0, 0);
+    op(CP_DEFECT, l, cur[l], 1);   // defect and its restriction in one step
     cur[l - 1] = 0;
     if (type == 0) {
       cycle(l - 1, tr ? 1 : 0, tr, true);
@@ -605,9 +597,15 @@ struct ProgBuilder {
     } else {
       cycle(l - 1, 1, tr, true);
     }
-    if (adaptive_corr(c)) op(CP_ADAPT, l, cur[l], cur[l - 1]);   // the correction with its own weight
-    else op(CP_PROLONG, l, cur[l], cur[l - 1]);
-    smooth(l, npost, order, false);
+    if (adaptive_corr(c)) {   // the correction with its own weight
+      op(CP_ADAPT, l, cur[l], cur[l - 1]);
+      smooth(l, npost, order, false);
+    } else if (c->P.smoother == MG_RBGS && npost > 0) {   // correction and post-smoothing in one step
+      op(CP_PROLONG, l, cur[l], cur[l - 1] | ((rb_desc(npost, order, false) + 1) << 1));
+    } else {
+      op(CP_PROLONG, l, cur[l], cur[l - 1]);
+      smooth(l, npost, order, false);
+    }
   }
   // coarse correction at level lc requested by a type-`type` cycle at lc + 1
   void sub(int lc, int type, int tr) {
