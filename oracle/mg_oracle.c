@@ -35,6 +35,7 @@ typedef struct {
   int dim, n[3], per, kind;
   double h[3], c[3];
   double *sx, *sy, *sz, *k;   /* owned copies of the coefficients of this level */
+  double *ex, *ey, *ez;       /* OR_EDGE: per-node weights of the +x, +y, +z edges */
   double *u, *g, *r;          /* work vectors of this level (full node arrays) */
   long nsmooth;
 } lev_t;
@@ -83,6 +84,7 @@ static double kcell(const lev_t *v, int i, int j, int k) {
  * edge is the mean of the cells touching it divided by h^2 (finite-volume flux
  * over the dual face); it is linear in k. */
 static double wx_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i+1,j,k) */
+  if (v->kind == OR_EDGE) return v->ex[nid(v, i, j, k)];
   if (v->kind == OR_CONST) return v->c[0];
   if (v->kind == OR_SEPARABLE) return v->sx[i];
   if (v->dim == 2) return (kcell(v, i, j - 1, 0) + kcell(v, i, j, 0)) / (2.0 * v->h[0] * v->h[0]);
@@ -90,6 +92,7 @@ static double wx_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i+1,j,k
          (4.0 * v->h[0] * v->h[0]);
 }
 static double wy_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i,j+1,k) */
+  if (v->kind == OR_EDGE) return v->ey[nid(v, i, j, k)];
   if (v->kind == OR_CONST) return v->c[1];
   if (v->kind == OR_SEPARABLE) return v->sy[i];
   if (v->dim == 2) return (kcell(v, i - 1, j, 0) + kcell(v, i, j, 0)) / (2.0 * v->h[1] * v->h[1]);
@@ -97,6 +100,7 @@ static double wy_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i,j+1,k
          (4.0 * v->h[1] * v->h[1]);
 }
 static double wz_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i,j,k+1) */
+  if (v->kind == OR_EDGE) return v->ez[nid(v, i, j, k)];
   if (v->kind == OR_CONST) return v->c[2];
   if (v->kind == OR_SEPARABLE) return v->sz[i];
   return (kcell(v, i - 1, j - 1, k) + kcell(v, i, j - 1, k) + kcell(v, i - 1, j, k) + kcell(v, i, j, k)) /
@@ -328,6 +332,8 @@ static void lev_prolong_add(const lev_t *f, const lev_t *c, const double *ec, do
 /* ------------------------------------------------------------------------- */
 
 static double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+/* the same, 0 for an edge that does not exist on the finer grid (both weights 0) */
+static double harm0(double a, double b) { return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0; }
 
 static int coarsen(const lev_t *f, lev_t *c) {
   memset(c, 0, sizeof(*c));
@@ -363,6 +369,24 @@ static int coarsen(const lev_t *f, lev_t *c) {
     for (int I = 0; I < n0; ++I) {
       c->sy[I] = 0.25 * f->sy[2 * I];
       c->sz[I] = 0.25 * f->sz[2 * I];
+    }
+  } else if (f->kind == OR_EDGE) {
+    /* the same rule edge by edge: a coarse edge spans two fine edges in series (harmonic mean),
+     * and takes the fine line through its end nodes (injection across), times 1/4 */
+    size_t N = nodes(c);
+    c->ex = (double *)calloc(N, sizeof(double));
+    c->ey = (double *)calloc(N, sizeof(double));
+    c->ez = (double *)calloc(N, sizeof(double));
+    if (!c->ex || !c->ey || !c->ez) return OR_ENOMEM;
+    FOR_NODES(c) {
+      size_t P = nid(c, i, j, k);
+      int kk = (c->dim == 3) ? 2 * k : 0;
+      if (i < c->n[0] - 1)
+        c->ex[P] = 0.25 * harm0(f->ex[nid(f, 2 * i, 2 * j, kk)], f->ex[nid(f, 2 * i + 1, 2 * j, kk)]);
+      if (c->per || j < c->n[1] - 1)
+        c->ey[P] = 0.25 * harm0(f->ey[nid(f, 2 * i, 2 * j, kk)], f->ey[nid(f, 2 * i, 2 * j + 1, kk)]);
+      if (c->dim == 3 && k < c->n[2] - 1)
+        c->ez[P] = 0.25 * harm0(f->ez[nid(f, 2 * i, 2 * j, kk)], f->ez[nid(f, 2 * i, 2 * j, kk + 1)]);
     }
   } else {
     int cx = c->n[0] - 1, cy = ncells_y(c), cz = (c->dim == 3) ? c->n[2] - 1 : 1;
@@ -641,6 +665,7 @@ void or_grad_k(const or_hier *H, const double *u, const double *lam, double *dk)
 
 static void free_level(lev_t *v) {
   free(v->sx); free(v->sy); free(v->sz); free(v->k);
+  free(v->ex); free(v->ey); free(v->ez);
   free(v->u); free(v->g); free(v->r);
   memset(v, 0, sizeof(*v));
 }
@@ -697,6 +722,16 @@ int or_create(const or_config *cfg, or_hier **out) {
     f->k = (double *)malloc(sizeof(double) * nk);
     if (!f->k) { or_destroy(H); return OR_ENOMEM; }
     memcpy(f->k, cfg->k, sizeof(double) * nk);
+  } else if (cfg->kind == OR_EDGE) {
+    size_t N = nodes(f);
+    if (!cfg->ex || !cfg->ey || (cfg->dim == 3 && !cfg->ez)) { or_destroy(H); return OR_EINVAL; }
+    f->ex = (double *)calloc(N, sizeof(double));
+    f->ey = (double *)calloc(N, sizeof(double));
+    f->ez = (double *)calloc(N, sizeof(double));
+    if (!f->ex || !f->ey || !f->ez) { or_destroy(H); return OR_ENOMEM; }
+    memcpy(f->ex, cfg->ex, sizeof(double) * N);
+    memcpy(f->ey, cfg->ey, sizeof(double) * N);
+    if (cfg->dim == 3) memcpy(f->ez, cfg->ez, sizeof(double) * N);
   } else if (cfg->kind != OR_CONST) {
     or_destroy(H);
     return OR_EINVAL;
@@ -733,6 +768,13 @@ int or_level_unknowns(const or_hier *H, int l) {
 void or_level_coeffs(const or_hier *H, int l, double *out) {
   const lev_t *v = &H->lev[l];
   if (v->kind == OR_CONST) { for (int d = 0; d < 3; ++d) out[d] = v->c[d]; return; }
+  if (v->kind == OR_EDGE) {   /* ex, ey, ez back to back */
+    size_t N = nodes(v);
+    memcpy(out, v->ex, sizeof(double) * N);
+    memcpy(out + N, v->ey, sizeof(double) * N);
+    memcpy(out + 2 * N, v->ez, sizeof(double) * N);
+    return;
+  }
   if (v->kind == OR_SEPARABLE) {
     int n0 = v->n[0];
     memcpy(out, v->sx, sizeof(double) * (size_t)n0);

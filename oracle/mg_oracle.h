@@ -24,7 +24,7 @@
 extern "C" {
 #endif
 
-enum { OR_CONST = 0, OR_SEPARABLE = 1, OR_CELL = 2 };
+enum { OR_CONST = 0, OR_SEPARABLE = 1, OR_CELL = 2, OR_EDGE = 3 };
 enum { OR_JACOBI = 0, OR_RBGS = 1, OR_LINE_X = 2, OR_LINE_Y = 3, OR_ZEBRA_X = 4, OR_ZEBRA_Y = 5,
        OR_ADI = 6,     /* alternating directions: x-line Jacobi sweep, then y-line Jacobi sweep */
        OR_GSADI = 7 }; /* zebra x-line Gauss-Seidel, then zebra y-line Gauss-Seidel */
@@ -39,7 +39,7 @@ typedef struct {
   int dim;            /* 2 or 3 */
   int n[3];           /* nodes per direction on the finest grid (n[2] ignored in 2D) */
   int periodic_y;     /* 1: y direction periodic with n[1] distinct nodes */
-  int kind;           /* OR_CONST / OR_SEPARABLE / OR_CELL */
+  int kind;           /* OR_CONST / OR_SEPARABLE / OR_CELL / OR_EDGE */
   double h[3];        /* mesh widths (used by OR_CELL) */
   double c[3];        /* OR_CONST: edge weight per direction */
   const double *sx;   /* OR_SEPARABLE: sx[i] = weight of x-edge (i, i+1), length n0-1 */
@@ -57,6 +57,9 @@ typedef struct {
   int dense_max;      /* largest coarsest-grid unknown count solved by dense Cholesky */
   int adaptive_corr;  /* 1: omega_l of every correction chosen to minimise the energy norm of
                          the error (or_adaptive_omega); omega_corr is then ignored */
+  const double *ex;   /* OR_EDGE: full node arrays, x fastest: ex[p] = weight of the edge from node */
+  const double *ey;   /* p to its +x neighbour, ey[p] to +y (periodic: the last row's edge wraps to */
+  const double *ez;   /* row 0), ez[p] to +z (3-D); entries with no such edge are ignored */
 } or_config;
 
 typedef struct or_hier or_hier;

@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _LOCK = threading.Lock()
 
-CONST, SEPARABLE, CELL = 0, 1, 2
+CONST, SEPARABLE, CELL, EDGE = 0, 1, 2, 3
 JACOBI, RBGS, LINE_X, LINE_Y, ZEBRA_X, ZEBRA_Y, ADI, GSADI = range(8)
 RED_FIRST, BLACK_FIRST = 0, 1
 CYCLE_F, CYCLE_V = 0, 1
@@ -57,7 +57,7 @@ class _Config(C.Structure):
                 ("levels", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("omega_corr", C.c_double),
                 ("coarse_mode", C.c_int), ("coarse_sweeps", C.c_int), ("dense_max", C.c_int),
-                ("adaptive_corr", C.c_int)]
+                ("adaptive_corr", C.c_int), ("ex", C.c_void_p), ("ey", C.c_void_p), ("ez", C.c_void_p)]
 
 
 _lib = None
@@ -113,7 +113,7 @@ class Problem:
     """Operator description on the finest grid (see ``mg_oracle.h``)."""
 
     def __init__(self, dim=2, n=(129, 129, 1), periodic_y=False, kind=CONST, h=(1.0, 1.0, 1.0),
-                 c=(1.0, 1.0, 1.0), sx=None, sy=None, sz=None, k=None):
+                 c=(1.0, 1.0, 1.0), sx=None, sy=None, sz=None, k=None, ex=None, ey=None, ez=None):
         self.dim = dim
         self.n = tuple(int(v) for v in n) + (1,) * (3 - len(n))
         if dim == 2:
@@ -126,6 +126,10 @@ class Problem:
         self.sy = None if sy is None else np.ascontiguousarray(sy, dtype=np.float64)
         self.sz = None if sz is None else np.ascontiguousarray(sz, dtype=np.float64)
         self.k = None if k is None else np.ascontiguousarray(k, dtype=np.float64)
+        # EDGE: full node arrays (numpy node shape), weight of the edge to the +x / +y / +z neighbour
+        self.ex = None if ex is None else np.ascontiguousarray(ex, dtype=np.float64)
+        self.ey = None if ey is None else np.ascontiguousarray(ey, dtype=np.float64)
+        self.ez = None if ez is None else np.ascontiguousarray(ez, dtype=np.float64)
 
     @property
     def shape(self):
@@ -148,7 +152,7 @@ class Oracle:
         cfg.h = (C.c_double * 3)(*prob.h)
         cfg.c = (C.c_double * 3)(*prob.c)
         self._keep = []
-        for name in ("sx", "sy", "sz", "k"):
+        for name in ("sx", "sy", "sz", "k", "ex", "ey", "ez"):
             arr = getattr(prob, name)
             if arr is not None:
                 self._keep.append(arr)
@@ -307,6 +311,8 @@ class Oracle:
             out = np.zeros(3)
         elif p.kind == SEPARABLE:
             out = np.zeros(3 * n[0])
+        elif p.kind == EDGE:
+            out = np.zeros(3 * n[0] * n[1] * n[2])
         else:
             cy = n[1] if p.periodic_y else n[1] - 1
             out = np.zeros((n[0] - 1) * cy * (n[2] - 1 if p.dim == 3 else 1))

@@ -22,7 +22,7 @@ from typing import Optional
 
 import numpy as np
 
-CONST, SEPARABLE, CELL = 0, 1, 2
+CONST, SEPARABLE, CELL, EDGE = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -34,7 +34,9 @@ class ProblemSpec:
       CONST:     ``c`` = edge weight per direction (units 1/h^2),
       SEPARABLE: ``sx[i]`` weight of x-edge (i, i+1); ``sy[i]``, ``sz[i]`` weights of
                  the y- and z-edges at x-index i (mapped polar / cylindrical grids),
-      CELL:      ``k`` one coefficient per cell, weights k_avg / h^2 formed by the solver.
+      CELL:      ``k`` one coefficient per cell, weights k_avg / h^2 formed by the solver,
+      EDGE:      ``ex``, ``ey`` (, ``ez``) full node arrays: the weight of the edge from each node
+                 to its +x, +y (, +z) neighbour (periodic y: the last row's edge wraps to row 0).
     """
     name: str
     dim: int
@@ -47,6 +49,9 @@ class ProblemSpec:
     sy: Optional[np.ndarray] = None
     sz: Optional[np.ndarray] = None
     k: Optional[np.ndarray] = None
+    ex: Optional[np.ndarray] = None
+    ey: Optional[np.ndarray] = None
+    ez: Optional[np.ndarray] = None
     b: Optional[np.ndarray] = None
     x0: Optional[np.ndarray] = None
 
@@ -222,6 +227,79 @@ def stretched_x(n=129, ny=None, beta=3.0, dim=2, manufactured=False, seed=12):
                      h=(h0, hy, hz), sx=1.0 / (hx * h0), sy=hbar / (h0 * hy ** 2),
                      sz=(hbar / (h0 * hz ** 2)) if dim == 3 else np.zeros(n), b=b, x0=np.zeros_like(b))
     sp.x_nodes = x
+    return sp
+
+
+def _stretched_nodes(n, beta):
+    """Nodes (e^{beta s} - 1) / (e^beta - 1), s = i / (n - 1), their spacings, and the dual-cell
+    widths (half a spacing at the two ends)."""
+    s = np.arange(n) / (n - 1)
+    x = np.expm1(beta * s) / np.expm1(beta) if beta != 0 else s
+    hx = np.diff(x)
+    hbar = np.empty(n)
+    hbar[1:-1] = 0.5 * (hx[:-1] + hx[1:])
+    hbar[0], hbar[-1] = 0.5 * hx[0], 0.5 * hx[-1]
+    return x, hx, hbar
+
+
+def stretched_xy(n=129, ny=None, beta_x=3.0, beta_y=-3.0, manufactured=False, seed=13):
+    """-Laplace u = f on the unit square on a grid refined in both directions (section
+    "Anisotropies": combinations of one-direction refinements), nodes as in stretched_x per axis
+    (beta < 0 clusters at the far end).  Finite-volume weights divided by the nominal cell area
+    h0x h0y: x-edge (i, i+1) at row j: hbar_y(j) / (hx_{i+1/2} h0x h0y), y-edge (j, j+1) at
+    column i: hbar_x(i) / (hy_{j+1/2} h0x h0y), right-hand side f hbar_x hbar_y / (h0x h0y).  The
+    weights vary in both directions: an edge-weight (EDGE) problem."""
+    ny = n if ny is None else ny
+    x, hx, hbx = _stretched_nodes(n, beta_x)
+    y, hy, hby = _stretched_nodes(ny, beta_y)
+    h0x, h0y = 1.0 / (n - 1), 1.0 / (ny - 1)
+    area = h0x * h0y
+    ex = np.zeros((ny, n))
+    ey = np.zeros((ny, n))
+    ex[:, :-1] = hby[:, None] / (hx[None, :] * area)
+    ey[:-1, :] = hbx[None, :] / (hy[:, None] * area)
+    if manufactured:
+        f = 2 * math.pi ** 2 * np.outer(np.sin(math.pi * y), np.sin(math.pi * x))
+    else:
+        f = np.random.default_rng(seed).uniform(-1.0, 1.0, (ny, n))
+    b = _zero_boundary(f * np.outer(hby, hbx) / area, 2, False)
+    sp = ProblemSpec(name=f"stretched_xy{n}x{ny}", dim=2, n=(n, ny, 1), periodic_y=False, kind=EDGE,
+                     h=(h0x, h0y, 1.0), ex=ex, ey=ey, b=b, x0=np.zeros_like(b))
+    sp.x_nodes, sp.y_nodes = x, y
+    return sp
+
+
+def spherical_shell(nr=129, nt=129, r0=0.5, r1=1.0, t0=math.pi / 8, t1=7 * math.pi / 8, manufactured=False,
+                    seed=14):
+    """Axisymmetric Poisson problem in spherical coordinates (r, theta) on the shell
+    r0 <= r <= r1 between the cones theta = t0 and t1, mapped to the unit square (x = r,
+    y = theta), zero Dirichlet data.  Multiplied by the volume factor r^2 sin(theta), the
+    operator is -d/dr(r^2 sin(theta) du/dr) - d/dtheta(sin(theta) du/dtheta) = r^2 sin(theta) f,
+    whose 5-point form has edge weights r_{i+1/2}^2 sin(theta_j) / h_r^2 (x-edges) and
+    sin(theta_{j+1/2}) / h_t^2 (y-edges): they vary in both directions (EDGE).
+    manufactured=True takes u = sin(pi (r - r0) / (r1 - r0)) sin(pi (theta - t0) / (t1 - t0))
+    and f = -Laplace u in spherical coordinates; otherwise f is uniform in [-1, 1]."""
+    hr, ht = (r1 - r0) / (nr - 1), (t1 - t0) / (nt - 1)
+    r = r0 + hr * np.arange(nr)
+    t = t0 + ht * np.arange(nt)
+    rh = r0 + hr * (np.arange(nr - 1) + 0.5)
+    th = t0 + ht * (np.arange(nt - 1) + 0.5)
+    ex = np.zeros((nt, nr))
+    ey = np.zeros((nt, nr))
+    ex[:, :-1] = np.outer(np.sin(t), rh ** 2) / hr ** 2
+    ey[:-1, :] = np.outer(np.sin(th), np.ones(nr)) / ht ** 2
+    T, R = np.meshgrid(t, r, indexing="ij")
+    if manufactured:
+        a, c = math.pi / (r1 - r0), math.pi / (t1 - t0)
+        Rf, Rd, Rdd = np.sin(a * (R - r0)), a * np.cos(a * (R - r0)), -a * a * np.sin(a * (R - r0))
+        Tf, Td, Tdd = np.sin(c * (T - t0)), c * np.cos(c * (T - t0)), -c * c * np.sin(c * (T - t0))
+        f = -(Tf * (Rdd + 2.0 * Rd / R) + Rf / R ** 2 * (Tdd + Td * np.cos(T) / np.sin(T)))
+    else:
+        f = np.random.default_rng(seed).uniform(-1.0, 1.0, (nt, nr))
+    b = _zero_boundary(R ** 2 * np.sin(T) * f, 2, False)
+    sp = ProblemSpec(name=f"spherical_{nr}x{nt}", dim=2, n=(nr, nt, 1), periodic_y=False, kind=EDGE,
+                     h=(hr, ht, 1.0), ex=ex, ey=ey, b=b, x0=np.zeros_like(b))
+    sp.r_nodes, sp.t_nodes = r, t
     return sp
 
 

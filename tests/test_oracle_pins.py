@@ -86,7 +86,27 @@ def _kinds(dim, periodic_y, rng):
     kshape = (cy, n[0] - 1) if dim == 2 else (n[2] - 1, cy, n[0] - 1)
     out.append(orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.CELL, h=h,
                            k=np.exp(rng.standard_normal(kshape))))
+    out.append(_random_edge_problem(dim, n, periodic_y, h, rng))
     return out
+
+
+def _random_edge_problem(dim, n, periodic_y, h, rng):
+    """Edge weights log-normal and independent edge by edge (varying in every direction)."""
+    shape = (n[1], n[0]) if dim == 2 else (n[2], n[1], n[0])
+    w = [np.exp(0.5 * rng.standard_normal(shape)) for _ in range(3)]
+    return orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.EDGE, h=h, ex=w[0], ey=w[1],
+                       ez=w[2] if dim == 3 else None)
+
+
+def _edge_of_separable(p):
+    """The separable problem p written as per-edge weights (the same operator)."""
+    shape = (p.n[1], p.n[0]) if p.dim == 2 else (p.n[2], p.n[1], p.n[0])
+    ex, ey, ez = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    ex[..., :-1] = p.sx[: p.n[0] - 1]
+    ey[...] = p.sy
+    ez[...] = p.sz
+    return orc.Problem(dim=p.dim, n=p.n, periodic_y=p.periodic_y, kind=orc.EDGE, h=p.h, ex=ex, ey=ey,
+                       ez=ez if p.dim == 3 else None)
 
 
 @pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False), (3, True)])
@@ -405,6 +425,9 @@ CASES = [
     (3, True, 1, "zebra_x", 9, 3), (3, False, 2, "jacobi", 9, 2),
     (2, False, 0, "adi", 17, 3), (2, False, 2, "gsadi", 17, 4), (3, False, 1, "adi", 9, 3),
     (3, False, 0, "gsadi", 9, 2),
+    # edge weights varying in every direction
+    (2, True, 3, "zebra_x", 17, 4), (2, False, 3, "gsadi", 17, 3), (3, False, 3, "rbgs", 9, 2),
+    (3, True, 3, "jacobi", 9, 3),
 ]
 
 
@@ -419,6 +442,8 @@ def _small(dim, periodic_y, kind_idx, n, rng):
     if p.kind == orc.SEPARABLE:
         return orc.Problem(dim=dim, n=nn, periodic_y=periodic_y, kind=orc.SEPARABLE, h=h,
                            sx=rng.uniform(0.5, 2, n - 1), sy=rng.uniform(0.5, 2, n), sz=rng.uniform(0.5, 2, n))
+    if p.kind == orc.EDGE:
+        return _random_edge_problem(dim, nn, periodic_y, h, rng)
     cy = ny if periodic_y else ny - 1
     ks = (cy, n - 1) if dim == 2 else (n - 1, cy, n - 1)
     return orc.Problem(dim=dim, n=nn, periodic_y=periodic_y, kind=orc.CELL, h=h, k=np.exp(rng.standard_normal(ks)))
@@ -754,3 +779,65 @@ def test_stretched_grid_needs_alternating_lines():
         assert out[(n, "gsadi")][0] == orc.OK and out[(n, "gsadi")][1] <= 7
         assert out[(n, "rbgs")][0] == orc.ENOCONV
         assert out[(n, "zebra_x")][0] == orc.ENOCONV
+
+
+# --------------------------------------------------------------------------------------
+# edge-weight coefficients (per-edge weights varying in every direction)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False), (3, True)])
+def test_edge_kind_reproduces_separable_on_every_level(dim, periodic_y):
+    """Separable weights written edge by edge give the same operator on every level (the
+    coarsening rule reduces to the separable one: the harmonic mean of two equal weights) and
+    the same F-cycle, up to rounding: a transposed or shifted index in the edge arrays would
+    break it, since sx and sy vary in x."""
+    rng = np.random.default_rng(50)
+    sep = _kinds(dim, periodic_y, rng)[1]
+    edge = _edge_of_separable(sep)
+    a = orc.Oracle(sep, levels=3, smoother="rbgs")
+    b = orc.Oracle(edge, levels=3, smoother="rbgs")
+    def close(p, q):
+        return np.abs(p - q).max() <= 1e-14 * np.abs(q).max()
+
+    for l in (1, 2, 3):
+        u = rand_field(a, rng, l)
+        assert close(b.apply(u, l), a.apply(u, l))
+        assert close(b.diag(l), a.diag(l))
+    f = rand_field(a, rng)
+    x = a.zeros()
+    y = b.zeros()
+    for _ in range(3):
+        x, y = a.cycle(x, f), b.cycle(y, f)
+    assert np.abs(x - y).max() <= 1e-13 * np.abs(x).max()
+
+
+def _second_order_errors(make, exact_of, sizes=(33, 65, 129)):
+    errs = []
+    for n in sizes:
+        sp = make(n)
+        p = orc.Problem(dim=2, n=sp.n, periodic_y=False, kind=orc.EDGE, h=sp.h, ex=sp.ex, ey=sp.ey)
+        o = orc.Oracle(p, levels=inputs.max_levels(sp.n), smoother="gsadi")
+        x, st, c, rr, h = o.solve(sp.b, tol=1e-11, maxit=100)
+        assert st == orc.OK
+        errs.append(np.abs(x - exact_of(sp)).max())
+    return errs
+
+
+def test_two_direction_stretched_grid_is_second_order():
+    errs = _second_order_errors(lambda n: inputs.stretched_xy(n, beta_x=3.0, beta_y=-2.0, manufactured=True),
+                                lambda sp: np.outer(np.sin(math.pi * sp.y_nodes), np.sin(math.pi * sp.x_nodes)))
+    for a, b in zip(errs, errs[1:]):
+        assert 3.7 <= a / b <= 4.3
+
+
+def test_spherical_shell_is_second_order():
+    """Manufactured axisymmetric solution on the spherical shell (r^2 sin(theta) weights):
+    second-order convergence confirms the mapped weights and the right-hand-side factor."""
+    def exact(sp):
+        r, t = sp.r_nodes, sp.t_nodes
+        a = np.sin(math.pi * (r - r[0]) / (r[-1] - r[0]))
+        c = np.sin(math.pi * (t - t[0]) / (t[-1] - t[0]))
+        return np.outer(c, a)
+    errs = _second_order_errors(lambda n: inputs.spherical_shell(n, n, manufactured=True), exact)
+    for a, b in zip(errs, errs[1:]):
+        assert 3.7 <= a / b <= 4.3
