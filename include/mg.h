@@ -62,7 +62,7 @@ typedef enum {
                       with its colours reversed.  ADI / GSADI need a non-periodic y        */
 } mg_smoother;
 
-typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2 } mg_coef_kind;
+typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2, MG_COEF_EDGE = 3 } mg_coef_kind;
 
 /* MG_FP64: every step in double precision.
  * MG_MIXED: iterative refinement -- the FP64 defect r = b - A x drives one or
@@ -119,6 +119,15 @@ typedef struct {
   const double *sy;       /* MG_COEF_SEPARABLE (device): weight of the y-edges at x-index i, length n0 */
   const double *sz;       /* MG_COEF_SEPARABLE (device): weight of the z-edges at x-index i (3-D) */
   const double *k;        /* MG_COEF_CELL (device): coefficient per cell of -div(k grad u) */
+  /* MG_COEF_EDGE (device): full node arrays of the finest grid, x fastest (the layout of b):
+     ex[p] = weight of the edge from node p to its +x neighbour, ey[p] to +y (periodic y: the
+     last row's edge wraps to row 0), ez[p] to +z (3-D only; may be NULL in 2-D).  Entries of
+     edges that do not exist are ignored; every edge touching an unknown must weigh > 0.  Any
+     symmetric 5-/7-point operator in edge form, e.g. a grid refined in two directions or a
+     mapped geometry whose weights vary in both directions (section "Anisotropies").  Coarse
+     weights: harmonic mean of the two fine edges along a coarse edge, times 1/4.  y-line
+     smoothing uses the one-thread-per-line kernel (no axis swap). */
+  const double *ex, *ey, *ez;
 } mg_coeffs;
 
 typedef struct {

@@ -42,7 +42,8 @@ class Params(C.Structure):
 
 class Coeffs(C.Structure):
     _fields_ = [("kind", C.c_int), ("h", C.c_double * 3), ("c", C.c_double * 3),
-                ("sx", C.c_void_p), ("sy", C.c_void_p), ("sz", C.c_void_p), ("k", C.c_void_p)]
+                ("sx", C.c_void_p), ("sy", C.c_void_p), ("sz", C.c_void_p), ("k", C.c_void_p),
+                ("ex", C.c_void_p), ("ey", C.c_void_p), ("ez", C.c_void_p)]
 
 
 class Report(C.Structure):
@@ -175,7 +176,7 @@ class Solver:
         k.h = (C.c_double * 3)(*[float(v) for v in spec.h])
         k.c = (C.c_double * 3)(*[float(v) for v in (spec.c if spec.c is not None else (0, 0, 0))])
         self._coef_tensors = []
-        for name in ("sx", "sy", "sz", "k"):
+        for name in ("sx", "sy", "sz", "k", "ex", "ey", "ez"):
             arr = getattr(spec, name, None)
             if arr is not None:
                 t = torch.as_tensor(np.ascontiguousarray(arr, dtype=np.float64) if isinstance(arr, np.ndarray)

@@ -15,10 +15,12 @@ namespace mg {
 
 template <typename T>
 struct SLev {
-  Lev<T> L;              // smem view: pitch = n0, k / ndinv point into shared memory
+  Lev<T> L;              // smem view: pitch = n0, k / ndinv / ex.. point into shared memory
   int off_u0, off_u1, off_g, off_r, off_k, off_dinv;   // element offsets into the smem pool
+  int off_ex, off_ey, off_ez;                          // edge weights (-1: not held)
   long long gpitch, gplane;                            // padded global layout of this level
   const T *gk, *gdinv;                                 // global cell data (loaded at start)
+  const T *gex, *gey, *gez;                            // global edge weights (loaded at start)
 };
 
 template <typename T>
@@ -101,6 +103,14 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         s_levs[l].L.ndinv = pool + s_levs[l].off_dinv;
       }
     }
+    if (KIND == K_EDGE && threadIdx.x == 0) {   // so do the edge weights
+      for (int l = 1; l <= lc; ++l) {
+        s_levs[l].L.ex = pool + s_levs[l].off_ex;
+        s_levs[l].L.ey = pool + s_levs[l].off_ey;
+        s_levs[l].L.ez = DIM == 3 ? pool + s_levs[l].off_ez : nullptr;
+        s_levs[l].L.ndinv = pool + s_levs[l].off_dinv;
+      }
+    }
     __syncthreads();
     levs = s_levs;
   }
@@ -121,6 +131,17 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         int i = t % S.L.n0, rr = t / S.L.n0, j = rr % S.L.n1, k = rr / S.L.n1;
         long long gp = (long long)k * S.gplane + (long long)j * S.gpitch + i;
         kk[t] = S.gk[gp];
+        dv[t] = S.gdinv[gp];
+      }
+    }
+    if (KIND == K_EDGE) {
+      T *wx = pool + S.off_ex, *wy = pool + S.off_ey, *dv = pool + S.off_dinv;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        int i = t % S.L.n0, rr = t / S.L.n0, j = rr % S.L.n1, k = rr / S.L.n1;
+        long long gp = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+        wx[t] = S.gex[gp];
+        wy[t] = S.gey[gp];
+        if (DIM == 3) pool[S.off_ez + t] = S.gez[gp];
         dv[t] = S.gdinv[gp];
       }
     }
@@ -408,11 +429,13 @@ void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, 
   if (dim == 2) {
     if (kind == K_CONST) CC_LAUNCH(2, K_CONST);
     else if (kind == K_SEP) CC_LAUNCH(2, K_SEP);
-    else CC_LAUNCH(2, K_CELL);
+    else if (kind == K_CELL) CC_LAUNCH(2, K_CELL);
+    else CC_LAUNCH(2, K_EDGE);
   } else {
     if (kind == K_CONST) CC_LAUNCH(3, K_CONST);
     else if (kind == K_SEP) CC_LAUNCH(3, K_SEP);
-    else CC_LAUNCH(3, K_CELL);
+    else if (kind == K_CELL) CC_LAUNCH(3, K_CELL);
+    else CC_LAUNCH(3, K_EDGE);
   }
 #undef CC_LAUNCH
   ++*lc.counter;
@@ -445,18 +468,26 @@ size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long lo
     s.gplane = gplane[l];
     s.gk = glev[l].k;
     s.gdinv = glev[l].ndinv;
+    s.gex = glev[l].ex;
+    s.gey = glev[l].ey;
+    s.gez = glev[l].ez;
     s.off_u0 = take(cnt);
     s.off_u1 = take(cnt);
     s.off_g = take(cnt);
     s.off_r = take(cnt);
+    s.off_k = s.off_dinv = s.off_ex = s.off_ey = s.off_ez = -1;
     if (kind == K_CELL) {
       s.off_k = take(cnt);
       s.off_dinv = take(cnt);
-    } else {
-      s.off_k = s.off_dinv = -1;
+    } else if (kind == K_EDGE) {
+      s.off_ex = take(cnt);
+      s.off_ey = take(cnt);
+      if (s.L.dim == 3) s.off_ez = take(cnt);
+      s.off_dinv = take(cnt);
     }
     s.L.k = nullptr;
     s.L.ndinv = nullptr;
+    s.L.ex = s.L.ey = s.L.ez = nullptr;
   }
   return (size_t)off * sizeof(T);
 }

@@ -414,7 +414,11 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
   } else if (kind == K_SEP) {
     if (mode == 0) RB_L(K_SEP, 0); else if (mode == 1) RB_L(K_SEP, 1); else RB_L(K_SEP, 2);
   } else {
-    if (mode == 0) RB_L(K_CELL, 0); else if (mode == 1) RB_L(K_CELL, 1); else RB_L(K_CELL, 2);
+    if (kind == K_CELL) {
+      if (mode == 0) RB_L(K_CELL, 0); else if (mode == 1) RB_L(K_CELL, 1); else RB_L(K_CELL, 2);
+    } else {
+      if (mode == 0) RB_L(K_EDGE, 0); else if (mode == 1) RB_L(K_EDGE, 1); else RB_L(K_EDGE, 2);
+    }
   }
 #undef RB_L
   ++*lc.counter;
@@ -432,7 +436,11 @@ void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
   } else if (kind == K_SEP) {
     if (mode == 0) RB2_L(K_SEP, 0); else if (mode == 1) RB2_L(K_SEP, 1); else RB2_L(K_SEP, 2);
   } else {
-    if (mode == 0) RB2_L(K_CELL, 0); else if (mode == 1) RB2_L(K_CELL, 1); else RB2_L(K_CELL, 2);
+    if (kind == K_CELL) {
+      if (mode == 0) RB2_L(K_CELL, 0); else if (mode == 1) RB2_L(K_CELL, 1); else RB2_L(K_CELL, 2);
+    } else {
+      if (mode == 0) RB2_L(K_EDGE, 0); else if (mode == 1) RB2_L(K_EDGE, 1); else RB2_L(K_EDGE, 2);
+    }
   }
 #undef RB2_L
   ++*lc.counter;
@@ -448,7 +456,11 @@ void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int ki
   } else if (kind == K_SEP) {
     if (mode == 1) RB2D_L(K_SEP, 1); else RB2D_L(K_SEP, 0);
   } else {
-    if (mode == 1) RB2D_L(K_CELL, 1); else RB2D_L(K_CELL, 0);
+    if (kind == K_CELL) {
+      if (mode == 1) RB2D_L(K_CELL, 1); else RB2D_L(K_CELL, 0);
+    } else {
+      if (mode == 1) RB2D_L(K_EDGE, 1); else RB2D_L(K_EDGE, 0);
+    }
   }
 #undef RB2D_L
   ++*lc.counter;
@@ -460,7 +472,8 @@ void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C
   dim3 gr((C.n0 + CX - 1) / CX, (C.n1 + CYOf<T>::v - 1) / CYOf<T>::v);
   if (kind == K_CONST) k_defect_restrict2d<T, K_CONST><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   else if (kind == K_SEP) k_defect_restrict2d<T, K_SEP><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
-  else k_defect_restrict2d<T, K_CELL><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
+  else if (kind == K_CELL) k_defect_restrict2d<T, K_CELL><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
+  else k_defect_restrict2d<T, K_EDGE><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   ++*lc.counter;
 }
 

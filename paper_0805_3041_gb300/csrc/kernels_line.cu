@@ -87,11 +87,13 @@ void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra
   if (L.dim == 2) {
     if (kind == K_CONST) k_line<T, 2, K_CONST><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
     else if (kind == K_SEP) k_line<T, 2, K_SEP><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
-    else k_line<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
+    else if (kind == K_CELL) k_line<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
+    else k_line<T, 2, K_EDGE><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
   } else {
     if (kind == K_CONST) k_line<T, 3, K_CONST><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
     else if (kind == K_SEP) k_line<T, 3, K_SEP><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
-    else k_line<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
+    else if (kind == K_CELL) k_line<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
+    else k_line<T, 3, K_EDGE><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2);
   }
   ++*lc.counter;
 }

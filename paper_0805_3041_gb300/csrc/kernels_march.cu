@@ -271,7 +271,7 @@ template <typename T>
 bool launch_rb2d_march(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega,
                        int first, int mode, const Lev<T> *C, const T *ec, T omega_corr) {
   constexpr int NV = Vec<T>::N;
-  if (L.dim != 2 || kind == K_CELL || L.pitch % (32 * NV) != 0) return false;
+  if (L.dim != 2 || kind == K_CELL || kind == K_EDGE || L.pitch % (32 * NV) != 0) return false;
   int rows = L.per ? L.n1 : L.n1 - 2;
   int RC = 32;
   int nstrips = (int)(L.pitch / (32 * NV));

@@ -406,11 +406,13 @@ __global__ void __launch_bounds__(BX *BY) k_grad_k(Lev<double> L, const double *
     if ((DIMV) == 2) {                                                         \
       if ((KINDV) == K_CONST) KERNEL<T, 2, K_CONST> __VA_ARGS__;               \
       else if ((KINDV) == K_SEP) KERNEL<T, 2, K_SEP> __VA_ARGS__;              \
-      else KERNEL<T, 2, K_CELL> __VA_ARGS__;                                   \
+      else if ((KINDV) == K_CELL) KERNEL<T, 2, K_CELL> __VA_ARGS__;            \
+      else KERNEL<T, 2, K_EDGE> __VA_ARGS__;                                   \
     } else {                                                                   \
       if ((KINDV) == K_CONST) KERNEL<T, 3, K_CONST> __VA_ARGS__;               \
       else if ((KINDV) == K_SEP) KERNEL<T, 3, K_SEP> __VA_ARGS__;              \
-      else KERNEL<T, 3, K_CELL> __VA_ARGS__;                                   \
+      else if ((KINDV) == K_CELL) KERNEL<T, 3, K_CELL> __VA_ARGS__;            \
+      else KERNEL<T, 3, K_EDGE> __VA_ARGS__;                                   \
     }                                                                          \
   } while (0)
 
@@ -566,11 +568,13 @@ void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, cons
   if (L.dim == 2) {
     if (kind == K_CONST) D64_R(2, K_CONST);
     else if (kind == K_SEP) D64_R(2, K_SEP);
-    else D64_R(2, K_CELL);
+    else if (kind == K_CELL) D64_R(2, K_CELL);
+    else D64_R(2, K_EDGE);
   } else {
     if (kind == K_CONST) D64_R(3, K_CONST);
     else if (kind == K_SEP) D64_R(3, K_SEP);
-    else D64_R(3, K_CELL);
+    else if (kind == K_CELL) D64_R(3, K_CELL);
+    else D64_R(3, K_EDGE);
   }
 #undef D64_R
   ++*lc.counter;

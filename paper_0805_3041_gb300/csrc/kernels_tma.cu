@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_defect_restrict_tma(Lev<float
 
 bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev<float> &C, int kind,
                                 const float *u, const float *g, float *gc, int *err, int rc) {
-  if (L.dim != 2 || kind == K_CELL || L.pitch % 128 != 0 || L.n0 < 5 || !err) return false;
+  if (L.dim != 2 || kind == K_CELL || kind == K_EDGE || L.pitch % 128 != 0 || L.n0 < 5 || !err) return false;
   if (((uintptr_t)u | (uintptr_t)g) & 15) return false;
   const int crows = C.per ? C.n1 : C.n1 - 2;
   if (crows <= 0) return false;
@@ -730,7 +730,7 @@ thread_local TmaOcc tma_occ;
 bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const float *u, const float *g, float *out,
                      float omega, int first, int mode, const Lev<float> *C, const float *ec, float omega_corr,
                      int *err, int rc) {
-  if (L.dim != 2 || kind == K_CELL || L.pitch % 128 != 0 || L.n0 < 3 || !err) return false;
+  if (L.dim != 2 || kind == K_CELL || kind == K_EDGE || L.pitch % 128 != 0 || L.n0 < 3 || !err) return false;
   if (mode == 2 && (!C || !ec || C->pitch % 128 != 0)) return false;
   // every copy starts on a 16-byte boundary: 16-byte aligned arrays, pitches of 128 floats
   if (((uintptr_t)u | (uintptr_t)g | (uintptr_t)out | (uintptr_t)(ec ? ec : u)) & 15) return false;

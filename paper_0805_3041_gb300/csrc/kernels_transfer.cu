@@ -203,11 +203,13 @@ void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const lo
   if (L.dim == 2) {
     if (kind == K_CONST) k_assemble_dense<T, 2, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else if (kind == K_SEP) k_assemble_dense<T, 2, K_SEP><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
-    else k_assemble_dense<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else if (kind == K_CELL) k_assemble_dense<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else k_assemble_dense<T, 2, K_EDGE><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
   } else {
     if (kind == K_CONST) k_assemble_dense<T, 3, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else if (kind == K_SEP) k_assemble_dense<T, 3, K_SEP><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
-    else k_assemble_dense<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else if (kind == K_CELL) k_assemble_dense<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else k_assemble_dense<T, 3, K_EDGE><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
   }
   ++*lc.counter;
 }
@@ -327,6 +329,59 @@ void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
   dim3 gr((L.xunk() + 127) / 128, gy, gz);
   if (L.dim == 2) k_cell_dinv<2><<<gr, 128, 0, lc.s>>>(L, dinv);
   else k_cell_dinv<3><<<gr, 128, 0, lc.s>>>(L, dinv);
+  ++*lc.counter;
+}
+
+// ---------------------------------------------------------------------------------------
+// edge coefficients: coarse weights edge by edge, and 1/D
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double harm0(double a, double b) { return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0; }
+
+// The coarse edge from node (I, J, K) to its +x (+y, +z) neighbour spans the two fine edges
+// from (2I, 2J, 2K) in that direction: their harmonic mean (series) times 1/4; the fine line
+// through the coarse node is taken across (injection).  Edges absent on the coarse grid are 0.
+__global__ void k_coarsen_edge(Lev<double> F, Lev<double> C, const double *__restrict__ fx,
+                               const double *__restrict__ fy, const double *__restrict__ fz, double *__restrict__ cx,
+                               double *__restrict__ cy, double *__restrict__ cz) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y, K = blockIdx.z;
+  if (I >= C.n0) return;
+  long long pc = (long long)K * C.plane + (long long)J * C.pitch + I;
+  long long pf = (long long)(C.dim == 3 ? 2 * K : 0) * F.plane + (long long)(2 * J) * F.pitch + 2 * I;
+  cx[pc] = I < C.n0 - 1 ? 0.25 * harm0(fx[pf], fx[pf + 1]) : 0.0;
+  cy[pc] = (C.per || J < C.n1 - 1) ? 0.25 * harm0(fy[pf], fy[pf + F.pitch]) : 0.0;
+  if (C.dim == 3) cz[pc] = K < C.n2 - 1 ? 0.25 * harm0(fz[pf], fz[pf + F.plane]) : 0.0;
+}
+void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *fx,
+                         const double *fy, const double *fz, double *cx, double *cy, double *cz) {
+  dim3 gr((C.n0 + 127) / 128, C.n1, C.dim == 3 ? C.n2 : 1);
+  k_coarsen_edge<<<gr, 128, 0, lc.s>>>(F, C, fx, fy, fz, cx, cy, cz);
+  ++*lc.counter;
+}
+
+// 1/D at the unknowns, D = the sum of the weights of the edges at the node
+template <int DIM>
+__global__ void k_edge_dinv(Lev<double> L, double *__restrict__ dinv) {
+  int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > L.n0 - 2) return;
+  long long r = blockIdx.y + (long long)blockIdx.z * gridDim.y;
+  if (r >= L.unk_rows()) return;
+  int j, k;
+  row_jk(L, r, j, k);
+  long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
+  yoffs(L, j, dm, dp);
+  Weights<double, DIM, K_EDGE> w;
+  w.load(L, i, p, dm);
+  double D = (w.wW + w.wE) + (w.wS + w.wN);
+  if (DIM == 3) D += w.wB + w.wF;
+  dinv[p] = 1.0 / D;
+}
+void launch_edge_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
+  long long rows = L.unk_rows();
+  unsigned gy = (unsigned)(rows < 65535 ? rows : 65535), gz = (unsigned)((rows + gy - 1) / gy);
+  dim3 gr((L.xunk() + 127) / 128, gy, gz);
+  if (L.dim == 2) k_edge_dinv<2><<<gr, 128, 0, lc.s>>>(L, dinv);
+  else k_edge_dinv<3><<<gr, 128, 0, lc.s>>>(L, dinv);
   ++*lc.counter;
 }
 

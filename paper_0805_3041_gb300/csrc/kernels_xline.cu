@@ -203,9 +203,9 @@ bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int co
     k_xline<T, D, K><<<nl, NT, smem, lc.s>>>(L, u, g, out, omega, zebra, colour);                  \
   } while (0)
   if (L.dim == 2) {
-    if (kind == K_CONST) XL(2, K_CONST); else if (kind == K_SEP) XL(2, K_SEP); else XL(2, K_CELL);
+    if (kind == K_CONST) XL(2, K_CONST); else if (kind == K_SEP) XL(2, K_SEP); else if (kind == K_CELL) XL(2, K_CELL); else XL(2, K_EDGE);
   } else {
-    if (kind == K_CONST) XL(3, K_CONST); else if (kind == K_SEP) XL(3, K_SEP); else XL(3, K_CELL);
+    if (kind == K_CONST) XL(3, K_CONST); else if (kind == K_SEP) XL(3, K_SEP); else if (kind == K_CELL) XL(3, K_CELL); else XL(3, K_EDGE);
   }
 #undef XL
   ++*lc.counter;

@@ -46,6 +46,7 @@ struct LevData {
   T *g = nullptr, *r = nullptr;
   T *sx = nullptr, *sy = nullptr, *sz = nullptr, *sdinv = nullptr;
   T *k = nullptr, *ndinv = nullptr;
+  T *ex = nullptr, *ey = nullptr, *ez = nullptr;
 };
 
 struct LevGeom {
@@ -145,7 +146,8 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
   if (p->max_cycles < 0 || p->sweep_rows < 0 || p->tile_nodes < -1) return MG_EINVAL;
-  if (k->kind < MG_COEF_CONST || k->kind > MG_COEF_CELL) return MG_EINVAL;
+  if (k->kind < MG_COEF_CONST || k->kind > MG_COEF_EDGE) return MG_EINVAL;
+  if (k->kind == MG_COEF_EDGE && (!k->ex || !k->ey || (p->dim == 3 && !k->ez))) return MG_EINVAL;
   if (k->kind == MG_COEF_SEPARABLE && (!k->sx || !k->sy || (p->dim == 3 && !k->sz))) return MG_EINVAL;
   if (k->kind == MG_COEF_CELL && !k->k) return MG_EINVAL;
   int n[3] = {p->n[0], p->n[1], p->dim == 3 ? p->n[2] : 1};
@@ -196,6 +198,11 @@ static size_t layout(mg_ctx *c, char *ws) {
     } else if (c->kind == K_CELL) {
       D.k = b.take<double>(cnt);
       D.ndinv = b.take<double>(cnt);
+    } else if (c->kind == K_EDGE) {
+      D.ex = b.take<double>(cnt);
+      D.ey = b.take<double>(cnt);
+      if (P.dim == 3) D.ez = b.take<double>(cnt);
+      D.ndinv = b.take<double>(cnt);
     }
     if (!c->mixed) {
       D.u[0] = b.take<double>(cnt);
@@ -215,6 +222,11 @@ static size_t layout(mg_ctx *c, char *ws) {
         F.sdinv = b.take<float>(n0);
       } else if (c->kind == K_CELL) {
         F.k = b.take<float>(cnt);
+        F.ndinv = b.take<float>(cnt);
+      } else if (c->kind == K_EDGE) {
+        F.ex = b.take<float>(cnt);
+        F.ey = b.take<float>(cnt);
+        if (P.dim == 3) F.ez = b.take<float>(cnt);
         F.ndinv = b.take<float>(cnt);
       }
     }
@@ -245,7 +257,8 @@ static size_t layout(mg_ctx *c, char *ws) {
   // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
   c->lcut = 0;
   if (!(P.flags & MG_FLAG_NO_FUSED_COARSE)) {
-    size_t es = c->mixed ? 4 : 8, arrays = 4 + (c->kind == K_CELL ? 2 : 0), total = 0;
+    size_t es = c->mixed ? 4 : 8, total = 0;
+    size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0);
     long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
     if (P.coarse_cut_nodes > 0) cap = P.coarse_cut_nodes;
     for (int l = 1; l <= c->L; ++l) {
@@ -289,15 +302,16 @@ static Lev<double> lev64(const mg_ctx *c, int l) {
   const LevData<double> &D = c->d64[l];
   L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
   L.k = D.k; L.ndinv = D.ndinv;
+  L.ex = D.ex; L.ey = D.ey; L.ez = D.ez;
   return L;
 }
 // Line smoothers along y on constant or cell coefficients are run along x on the
 // axis-swapped problem (contiguous lines; the x-line kernel keeps a line in shared
-// memory).  Separable coefficients depend on x only and keep their y-line kernel.
+// memory).  Separable and edge coefficients keep their y-line kernel.
 static void apply_swap(mg_ctx *c) {
   mg_params &P = c->P;
   bool yline = P.smoother == MG_LINE_Y || P.smoother == MG_ZEBRA_Y;
-  if (!yline || c->kind == K_SEP || P.periodic_y) return;
+  if (!yline || c->kind == K_SEP || c->kind == K_EDGE || P.periodic_y) return;
   c->swap = true;
   int t = P.n[0];
   P.n[0] = P.n[1];
@@ -327,6 +341,7 @@ static Lev<float> lev32(const mg_ctx *c, int l) {
   const LevData<float> &D = c->d32[l];
   L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
   L.k = D.k; L.ndinv = D.ndinv;
+  L.ex = D.ex; L.ey = D.ey; L.ez = D.ez;
   return L;
 }
 template <typename T> struct LevOf;
@@ -966,6 +981,23 @@ static mg_status setup_levels(mg_ctx *c) {
       CK(cudaMemsetAsync(c->d64[l].ndinv, 0, sizeof(double) * c->geo[l].count, c->stream));
       launch_cell_dinv(lc, lev64(c, l), c->d64[l].ndinv);
     }
+  } else if (c->kind == K_EDGE) {
+    for (int l = L; l >= 1; --l) {
+      LevData<double> &A = c->d64[l];
+      size_t bytes = sizeof(double) * (size_t)c->geo[l].count;
+      for (double *p : {A.ex, A.ey, A.ez, A.ndinv})
+        if (p) CK(cudaMemsetAsync(p, 0, bytes, c->stream));
+    }
+    Lev<double> F = lev64(c, L);
+    LevData<double> &A = c->d64[L];
+    launch_pack<double>(lc, F, c->K.ex, A.ex, 0);
+    launch_pack<double>(lc, F, c->K.ey, A.ey, 0);
+    if (P.dim == 3) launch_pack<double>(lc, F, c->K.ez, A.ez, 0);
+    for (int l = L; l > 1; --l) {
+      LevData<double> &Fd = c->d64[l], &Cd = c->d64[l - 1];
+      launch_coarsen_edge(lc, lev64(c, l), lev64(c, l - 1), Fd.ex, Fd.ey, Fd.ez, Cd.ex, Cd.ey, Cd.ez);
+    }
+    for (int l = L; l >= 1; --l) launch_edge_dinv(lc, lev64(c, l), c->d64[l].ndinv);
   }
   // work vectors start at zero (Dirichlet nodes stay zero for good)
   for (int l = L; l >= 1; --l) {
@@ -984,6 +1016,11 @@ static mg_status setup_levels(mg_ctx *c) {
         launch_to_float(lc, c->d64[l].sdinv, D.sdinv, (long long)n0);
       } else if (c->kind == K_CELL) {
         launch_to_float(lc, c->d64[l].k, D.k, (long long)cnt);
+        launch_to_float(lc, c->d64[l].ndinv, D.ndinv, (long long)cnt);
+      } else if (c->kind == K_EDGE) {
+        launch_to_float(lc, c->d64[l].ex, D.ex, (long long)cnt);
+        launch_to_float(lc, c->d64[l].ey, D.ey, (long long)cnt);
+        if (P.dim == 3) launch_to_float(lc, c->d64[l].ez, D.ez, (long long)cnt);
         launch_to_float(lc, c->d64[l].ndinv, D.ndinv, (long long)cnt);
       }
     }

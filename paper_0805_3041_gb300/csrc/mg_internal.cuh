@@ -13,7 +13,7 @@
 
 namespace mg {
 
-enum Kind { K_CONST = 0, K_SEP = 1, K_CELL = 2 };
+enum Kind { K_CONST = 0, K_SEP = 1, K_CELL = 2, K_EDGE = 3 };
 
 // Everything a kernel needs to know about one level.  Passed by value.
 template <typename T>
@@ -27,6 +27,8 @@ struct Lev {
   // cell coefficients: k per cell, 1/D per node, weight factors 1/(2h^2) (2-D) or 1/(4h^2) (3-D)
   const T *k, *ndinv;
   T ax, ay, az;
+  // edge coefficients: per node, the weights of the edges to the +x, +y, +z neighbours (1/D in ndinv)
+  const T *ex, *ey, *ez;
 
   __host__ __device__ int ylo() const { return per ? 0 : 1; }
   __host__ __device__ int yrows() const { return per ? n1 : n1 - 2; }
@@ -79,6 +81,18 @@ struct Weights {
       wS = wN = L.sy[i];
       wB = wF = L.sz[i];
       dinv = L.sdinv[i];
+    } else if (KIND == K_EDGE) {
+      wW = L.ex[p - 1];
+      wE = L.ex[p];
+      wS = L.ey[p + dm];   // the +y edge of the node below (periodic: of the last row)
+      wN = L.ey[p];
+      if (DIM == 3) {
+        wB = L.ez[p - (IT)L.plane];
+        wF = L.ez[p];
+      } else {
+        wB = wF = T(0);
+      }
+      dinv = L.ndinv[p];
     } else {
       // cells around node p: SW = (i-1, j-1), SE = (i, j-1), NW = (i-1, j), NE = (i, j)
       const T *k = L.k;
@@ -229,6 +243,10 @@ void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const
                      double *dinv);
 void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *kf, double *kc);
 void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv);
+// edge coefficients: coarse weights from the fine ones (harmonic mean along, x1/4), and 1/D
+void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *fx,
+                         const double *fy, const double *fz, double *cx, double *cy, double *cz);
+void launch_edge_dinv(const Launch &lc, const Lev<double> &L, double *dinv);
 void launch_to_float(const Launch &lc, const double *src, float *dst, long long n);
 void launch_cell_pack(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst);
 void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact);
