@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso", choices=["aniso", "batched"],
-                    help="aniso: the 4097^2 anisotropic solve (default); batched: 256 uneven instances in one graph")
+    ap.add_argument("--workload", default="aniso", choices=["aniso", "batched", "small", "annulus", "cylinder", "diff"],
+                    help="aniso: the 4097^2 anisotropic solve (default); batched: 256 uneven instances in one "
+                         "graph; small: 129^2 Poisson, Jacobi, FP64; annulus: 2049x2048 polar map; cylinder: "
+                         "257x256x257 cylindrical map; diff: 1025^2 -div(k grad u) loss and gradient")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--flags", type=int, default=0,
                     help="extra MG_FLAG_* bits for the solver (1 = kernel-by-kernel launches, for profilers)")
@@ -122,13 +124,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def default_omega(smoother, omega=None):
+    """The damping used unless --omega is given: 0.8 for point Jacobi, 0.7 for line Jacobi
+    (and ADI), 1 for the Gauss-Seidel smoothers."""
+    if omega is not None:
+        return omega
+    return 0.8 if smoother == "jacobi" else 0.7 if smoother.startswith("line") or smoother == "adi" else 1.0
+
+
 def make_problem(args):
     from paper_0805_3041_gb300 import inputs
     sp = inputs.anisotropic(n=args.n, eps=args.eps, seed_f=1)
     levels = inputs.max_levels(sp.n)
-    omega = args.omega if args.omega is not None else (0.8 if args.smoother == "jacobi" else
-                                                       0.7 if args.smoother.startswith("line") else 1.0)
-    return sp, levels, omega
+    return sp, levels, default_omega(args.smoother, args.omega)
 
 
 def workload_config(args, levels, omega):
@@ -437,12 +445,132 @@ def run_batched(args):
     batch.close()
 
 
+# --------------------------------------------------------------------------------------
+# the other study configurations: one step = one solve (diff: one loss + gradient)
+# --------------------------------------------------------------------------------------
+def config_problem(args):
+    """(spec, levels, smoother, omega, description) of a study configuration."""
+    from paper_0805_3041_gb300 import inputs
+    if args.workload == "small":
+        sp = inputs.poisson_sin(129)
+        return sp, 6, "jacobi", 0.8, "2-D Poisson 129x129, f = 2 pi^2 sin sin, x0 = 0, 6 grids, damped Jacobi 0.8"
+    if args.workload == "annulus":
+        sp = inputs.annulus_2d()
+        sm = args.smoother
+        return (sp, inputs.max_levels(sp.n, periodic_y=True), sm, default_omega(sm, args.omega),
+                "annulus r in [0.1, 1] x theta periodic mapped to 2049x2048 (separable weights), blob + noise "
+                "seed 3, x0 = 0")
+    if args.workload == "cylinder":
+        sp = inputs.cylinder_3d()
+        sm = args.smoother
+        return (sp, inputs.max_levels(sp.n, periodic_y=True, dim=3), sm, default_omega(sm, args.omega),
+                "cylinder shell (r, theta, z) mapped to 257x256x257 (separable weights), blob + noise seed 3, x0 = 0")
+    sp = inputs.diffusion_cells(1025)
+    return (sp, inputs.max_levels(sp.n), args.smoother, default_omega(args.smoother, args.omega),
+            "-div(k grad u) = f on 1025x1025, k log-normal (correlation 16 cells, seed 5), blob source; "
+            "step = forward solve + adjoint solve + gradient kernel (loss ||u - u_obs||^2)")
+
+
+def run_config(args):
+    import torch
+    from oracle import oracle as orc
+    from paper_0805_3041_gb300 import inputs
+    from paper_0805_3041_gb300.binding import Solver
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    sp, levels, smoother, omega, desc = config_problem(args)
+    prec = "fp64" if args.workload == "small" else args.precision
+    t0 = time.perf_counter()
+    s = Solver(sp, levels=levels, smoother=smoother, omega=omega, nu1=args.nu, nu2=args.nu, precision=prec,
+               max_cycles=200, flags=args.flags, device=dev)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    b = torch.from_numpy(sp.b).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    diff = args.workload == "diff"
+    if diff:   # u_obs: the solution for a reference field plus 1 % noise
+        ref = Solver(inputs.ProblemSpec(name="ref", dim=2, n=sp.n, periodic_y=False, kind=inputs.CELL, h=sp.h,
+                                        k=inputs.lognormal_cells(sp.n[0] - 1, seed=6)),
+                     levels=levels, precision="fp64", max_cycles=200, device=dev)
+        uref, _ = ref.solve(sp.b, tol=args.tol)
+        noise = torch.from_numpy(inputs.observation_noise(sp.shape)).to(dev)
+        uobs = uref + 0.01 * float(uref.pow(2).mean().sqrt()) * noise
+
+    def step():
+        x.zero_()
+        info = s.solve_into(b, x, tol=args.tol)
+        if diff:
+            lam, ia = s.solve_adjoint(2.0 * (x - uobs), tol=args.tol)
+            s.grad_coeff(x, lam)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    l0 = s.launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    launches = s.launch_count() - l0
+    clk = clocks.stop()
+    value = float(np.median(ms))
+    # end to end: host buffers through mg_solve_host (copies inside the timed region)
+    bh = torch.from_numpy(sp.b).pin_memory().numpy()
+    xh = torch.zeros(sp.shape, dtype=torch.float64).pin_memory().numpy()
+    e2e = []
+    for _ in range(max(2, args.steps // 2)):
+        xh[...] = 0.0
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        s.solve_host(bh, xh, tol=args.tol)
+        e2e.append((time.perf_counter() - t1) * 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:   # one oracle F-cycle (+ residual) on the full grid, x the GPU's cycle count
+        p = orc.Problem(dim=sp.dim, n=sp.n, periodic_y=sp.periodic_y, kind=sp.kind, h=sp.h, c=sp.c, sx=sp.sx,
+                        sy=sp.sy, sz=sp.sz, k=sp.k)
+        o = orc.Oracle(p, levels=levels, smoother=smoother, omega=omega, nu1=args.nu, nu2=args.nu, dense_max=4096)
+        t1 = time.perf_counter()
+        xo = o.cycle(np.zeros_like(sp.b), sp.b)
+        o.norm(o.defect(xo, sp.b))
+        per = time.perf_counter() - t1
+        mult = 2 if diff else 1   # the adjoint solve costs what the forward does
+        cpu = {"value": per * info["cycles"] * mult * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"1 oracle F-cycle (+ residual check) on the full grid, single thread, x {info['cycles']} "
+                         f"cycles" + (" x 2 (forward + adjoint)" if diff else "")}
+    line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": desc + f", {smoother} omega={omega:g} nu1=nu2={args.nu}, {prec}, tol {args.tol:g}",
+                       "levels": levels, "smoother": smoother, "precision": prec,
+                       "l2": "L2 flushed between steps"},
+            "cycles": info["cycles"], "relres": info["relres"], "rate": info["rate"], "setup_s": setup_s,
+            "roofline": None, "cpu_baseline": cpu,
+            "e2e": {"value": float(np.median(e2e)), "unit": "ms", "h2d_bytes_per_step": 2 * sp.b.nbytes,
+                    "d2h_bytes_per_step": sp.b.nbytes},
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload in ("small", "annulus", "cylinder", "diff"):
+        run_config(args)
     else:
         run_ours(args)
 
