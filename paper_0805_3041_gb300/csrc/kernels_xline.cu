@@ -190,12 +190,199 @@ __global__ void __launch_bounds__(NT) k_xline(Lev<T> L, const T *u, const T *__r
   }
 }
 
+// Short lines (up to 32 * WSMAX unknowns): one warp per line, WL lines per CTA.  The same
+// partition method with lane t owning a segment of <= WSMAX unknowns; the 2 x 32 reduced
+// system is solved by parallel cyclic reduction across the warp with shuffles (no block
+// barriers).  The line's right-hand side and coefficients are staged coalesced in a
+// per-warp shared-memory buffer, and the solution leaves through it.
+namespace {
+constexpr int WL = 4;        // lines (warps) per CTA
+constexpr int WSMAX = 16;    // unknowns per lane
+constexpr int WBUF = 32 * WSMAX + 32 * WSMAX / 16 + 8;
+}  // namespace
+
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(32 * WL) k_xline_warp(Lev<T> L, const T *u, const T *__restrict__ g, T *out,
+                                                         T omega, int zebra, int colour) {
+  extern __shared__ __align__(16) unsigned char xw_raw[];
+  constexpr int NB = KIND == K_CONST ? 1 : 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T *sd = reinterpret_cast<T *>(xw_raw) + (size_t)warp * NB * WBUF;
+  T *sa = sd + WBUF, *sb = sa + WBUF, *sc = sb + WBUF;
+  const long long line = (long long)blockIdx.x * WL + warp;
+  if (line >= L.unk_rows()) return;   // the whole warp
+  int j, k;
+  row_jk(L, line, j, k);
+  if (zebra && ((j + k) & 1) != colour) return;   // the whole warp
+  const int m = L.n0 - 2;
+  const long long row = (long long)k * L.plane + (long long)j * L.pitch;
+  long long dm, dp;
+  yoffs(L, j, dm, dp);
+  // 1. right-hand side (g + off-line couplings) and the line's coefficients, coalesced
+  for (int q = lane; q < m; q += 32) {
+    int i = q + 1;
+    long long p = row + i;
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    T d = g[p];
+    d = fma(w.wS, u[p + dm], d);
+    d = fma(w.wN, u[p + dp], d);
+    if (DIM == 3) {
+      d = fma(w.wB, u[p - L.plane], d);
+      d = fma(w.wF, u[p + L.plane], d);
+    }
+    sd[skew(q)] = d;
+    if (KIND != K_CONST) {
+      T D = (w.wW + w.wE) + (w.wS + w.wN);
+      if (DIM == 3) D += w.wB + w.wF;
+      sa[skew(q)] = q > 0 ? -w.wW : T(0);
+      sb[skew(q)] = D;
+      sc[skew(q)] = q < m - 1 ? -w.wE : T(0);
+    }
+  }
+  __syncwarp();
+  // 2. this lane's segment: m split over min(32, m / 2) lanes, >= 2 unknowns each (the reduced
+  // form of a one-unknown segment below is exact only for a line of one unknown)
+  const int nt = m / 2 < 32 ? (m / 2 > 0 ? m / 2 : 1) : 32;
+  int n = 0, s0 = 0;
+  if (lane < nt) {
+    const int per = m / nt, extra = m % nt;
+    n = per + (lane < extra ? 1 : 0);
+    s0 = lane * per + (lane < extra ? lane : extra);
+  }
+  auto A = [&](int q) -> T { return KIND == K_CONST ? (q > 0 ? -L.cx : T(0)) : sa[skew(q)]; };
+  auto B = [&](int q) -> T { return KIND == K_CONST ? L.d : sb[skew(q)]; };
+  auto Cc = [&](int q) -> T { return KIND == K_CONST ? (q < m - 1 ? -L.cx : T(0)) : sc[skew(q)]; };
+  T ap[WSMAX], cp[WSMAX], dpv[WSMAX];
+  // top and bottom reduced equations of the segment (identity rows for a lane without unknowns)
+  T ta = T(0), tb = T(1), tc = T(0), td = T(0);
+  T ba = T(0), bb = T(1), bc = T(0), bd = T(0);
+  if (n == 1) {   // m == 1: the line's one equation (no couplings), and x_last - x_first = 0
+    ta = A(s0); tb = B(s0); tc = Cc(s0); td = sd[skew(s0)];
+    ba = T(-1);
+  } else if (n >= 2) {
+#pragma unroll
+    for (int q = 1; q < WSMAX; ++q) {
+      if (q < n) {
+        int gq = s0 + q;
+        T a = A(gq), b = B(gq), c = Cc(gq), d = sd[skew(gq)];
+        if (q == 1) {
+          T r = T(1) / b;
+          ap[1] = a * r;
+          cp[1] = c * r;
+          dpv[1] = d * r;
+        } else {
+          T r = T(1) / (b - a * cp[q - 1]);
+          ap[q] = -r * a * ap[q - 1];
+          cp[q] = r * c;
+          dpv[q] = r * (d - a * dpv[q - 1]);
+        }
+        ba = ap[q];
+        bc = cp[q];
+        bd = dpv[q];
+      }
+    }
+#pragma unroll
+    for (int q = WSMAX - 2; q >= 1; --q) {
+      if (q <= n - 3) {
+        dpv[q] = dpv[q] - cp[q] * dpv[q + 1];
+        ap[q] = ap[q] - cp[q] * ap[q + 1];
+        cp[q] = -cp[q] * cp[q + 1];
+      }
+    }
+    T a0 = A(s0), b0 = B(s0), c0 = Cc(s0), d0 = sd[skew(s0)];
+    ta = a0;
+    if (n == 2) {
+      tb = b0; tc = c0; td = d0;
+    } else {
+      tb = b0 - c0 * ap[1];
+      tc = -c0 * cp[1];
+      td = d0 - c0 * dpv[1];
+    }
+  }
+  // 3. parallel cyclic reduction of the 64 equations (top of lane t: 2t, bottom: 2t + 1)
+  const unsigned full = 0xffffffffu;
+  auto reduce = [&](T &a, T &b, T &c, T &d, bool hl, T la, T lb, T lc, T ld, bool hr, T ra, T rb, T rc, T rd) {
+    T na = T(0), nc = T(0);
+    if (hl) {
+      T al = -a / lb;
+      na = al * la;
+      b = fma(al, lc, b);
+      d = fma(al, ld, d);
+    }
+    if (hr) {
+      T ga = -c / rb;
+      nc = ga * rc;
+      b = fma(ga, ra, b);
+      d = fma(ga, rd, d);
+    }
+    a = na;
+    c = nc;
+  };
+  {   // stride 1: the top's neighbours are the previous lane's bottom and this lane's bottom
+    T pa = __shfl_up_sync(full, ba, 1), pb = __shfl_up_sync(full, bb, 1);
+    T pc = __shfl_up_sync(full, bc, 1), pd = __shfl_up_sync(full, bd, 1);
+    T xa = __shfl_down_sync(full, ta, 1), xb = __shfl_down_sync(full, tb, 1);
+    T xc = __shfl_down_sync(full, tc, 1), xd = __shfl_down_sync(full, td, 1);
+    T ta0 = ta, tb0 = tb, tc0 = tc, td0 = td;
+    reduce(ta, tb, tc, td, lane > 0, pa, pb, pc, pd, true, ba, bb, bc, bd);
+    reduce(ba, bb, bc, bd, true, ta0, tb0, tc0, td0, lane < 31, xa, xb, xc, xd);
+  }
+#pragma unroll
+  for (int h = 1; h < 32; h <<= 1) {   // stride 2h: lanes h apart, top with top, bottom with bottom
+    T pta = __shfl_up_sync(full, ta, h), ptb = __shfl_up_sync(full, tb, h);
+    T ptc = __shfl_up_sync(full, tc, h), ptd = __shfl_up_sync(full, td, h);
+    T nta = __shfl_down_sync(full, ta, h), ntb = __shfl_down_sync(full, tb, h);
+    T ntc = __shfl_down_sync(full, tc, h), ntd = __shfl_down_sync(full, td, h);
+    T pba = __shfl_up_sync(full, ba, h), pbb = __shfl_up_sync(full, bb, h);
+    T pbc = __shfl_up_sync(full, bc, h), pbd = __shfl_up_sync(full, bd, h);
+    T nba = __shfl_down_sync(full, ba, h), nbb = __shfl_down_sync(full, bb, h);
+    T nbc = __shfl_down_sync(full, bc, h), nbd = __shfl_down_sync(full, bd, h);
+    const bool hl = lane >= h, hr = lane + h < 32;
+    reduce(ta, tb, tc, td, hl, pta, ptb, ptc, ptd, hr, nta, ntb, ntc, ntd);
+    reduce(ba, bb, bc, bd, hl, pba, pbb, pbc, pbd, hr, nba, nbb, nbc, nbd);
+  }
+  // 4. interior unknowns, damped update, write back
+  __syncwarp();
+  if (n >= 1) {
+    T x0 = td / tb, xl = bd / bb;
+    sd[skew(s0)] = x0;
+    if (n >= 2) sd[skew(s0 + n - 1)] = xl;
+#pragma unroll
+    for (int q = 1; q < WSMAX - 1; ++q)
+      if (q <= n - 2) sd[skew(s0 + q)] = dpv[q] - ap[q] * x0 - cp[q] * xl;
+  }
+  __syncwarp();
+  for (int q = lane; q < m; q += 32) {
+    long long p = row + q + 1;
+    T x = sd[skew(q)];
+    out[p] = (omega == T(1)) ? x : fma(omega, x - u[p], u[p]);
+  }
+}
+
 template <typename T>
 bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int colour, const T *u, const T *g, T *out,
                   T omega) {
   int m = L.n0 - 2;
   if (m < 1 || m > NT * SMAX) return false;
   unsigned nl = (unsigned)L.unk_rows();
+  if (m <= 32 * WSMAX) {
+    size_t smemw = sizeof(T) * (kind == K_CONST ? 1 : 4) * (size_t)WBUF * WL;
+    unsigned blocks = (nl + WL - 1) / WL;
+#define XW(D, K)                                                                                         \
+  do {                                                                                                   \
+    cudaFuncSetAttribute(k_xline_warp<T, D, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemw); \
+    k_xline_warp<T, D, K><<<blocks, 32 * WL, smemw, lc.s>>>(L, u, g, out, omega, zebra, colour);          \
+  } while (0)
+    if (L.dim == 2) {
+      if (kind == K_CONST) XW(2, K_CONST); else if (kind == K_SEP) XW(2, K_SEP); else if (kind == K_CELL) XW(2, K_CELL); else XW(2, K_EDGE);
+    } else {
+      if (kind == K_CONST) XW(3, K_CONST); else if (kind == K_SEP) XW(3, K_SEP); else if (kind == K_CELL) XW(3, K_CELL); else XW(3, K_EDGE);
+    }
+#undef XW
+    ++*lc.counter;
+    return true;
+  }
   size_t smem = sizeof(T) * ((kind == K_CONST ? 1 : 4) * (size_t)XL_SZ + 16 * NT);
 #define XL(D, K)                                                                                   \
   do {                                                                                             \
