@@ -209,6 +209,16 @@ def run_reference(args):
 # --------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------
+def max_over_ranks(value, device):
+    """The largest per-rank time over the process group (every rank gets it): replicas finish
+    together only when the slowest one does."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -261,11 +271,7 @@ def run_ours(args):
     barrier()
     launches = s.launch_count() - launches0
     clk = clocks.stop()
-    ms = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / args.steps, dev) if world > 1 else total_ms / args.steps
     # dominant kernel: the finest-level smoothing sweeps, timed with CUDA events recorded on the
     # solver's stream around each launch, over the same number of solves
     for _ in range(max(1, args.warmup)):
