@@ -76,7 +76,10 @@ __device__ __forceinline__ T interp_at(const Lev<T> &C, const T *ec, int i, int 
   return (s0 + s1) * T(0.125);
 }
 
-template <typename T, int DIM, int KIND>
+// FULL = false leaves out the line-smoother and adaptive-weight steps (programs of the point
+// smoothers with a fixed weight never hold them): a smaller kernel spends less of each step
+// fetching instructions.
+template <typename T, int DIM, int KIND, bool FULL>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
                                                        int nops, int lc, const T *__restrict__ g_in,
                                                        const T *__restrict__ u_in, T *__restrict__ u_out,
@@ -218,6 +221,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         rb_u = ub(o.w);
         break;
       case CP_LINE: {   // z = dir | zebra << 1 | colour << 2, w = src | dst << 4 | scratch << 8
+        if (!FULL) break;
         int dir = o.z & 1, zebra = (o.z >> 1) & 1, colour = (o.z >> 2) & 1;
         T *src = ub(o.w & 15), *dst = ub((o.w >> 4) & 15);
         T *cps = r, *dps = ub((o.w >> 8) & 15);
@@ -314,6 +318,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         break;
       }
       case CP_ADAPT: {   // z = fine buffer, w = coarse buffer: u_y[z] += omega P e with its own weight
+        if (!FULL) break;
         const SLev<T> &Cs = levs[o.y - 1];
         Lev<T> C = Cs.L;
         const T *ec = o.w ? pool + Cs.off_u1 : pool + Cs.off_u0;
@@ -418,10 +423,10 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
 template <typename T>
 void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, const int4 *prog, int nops, int lcut,
                          const T *g_in, const T *u_in, T *u_out, const double *Ainv, const long long *cidx_smem,
-                         int nc, T omega, T omega_corr, size_t smem_bytes) {
+                         int nc, T omega, T omega_corr, size_t smem_bytes, bool full) {
 #define CC_LAUNCH(D, K)                                                                                      \
   do {                                                                                                       \
-    auto fn = k_coarse_cycle<T, D, K>;                                                                       \
+    auto fn = full ? k_coarse_cycle<T, D, K, true> : k_coarse_cycle<T, D, K, false>;                        \
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);                  \
     fn<<<1, 512, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,       \
                                       cidx_smem, nc, omega, omega_corr);                                     \
@@ -494,10 +499,10 @@ size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long lo
 
 template void launch_coarse_cycle<double>(const Launch &, int, int, const void *, const int4 *, int, int, const double *,
                                           const double *, double *, const double *, const long long *, int, double,
-                                          double, size_t);
+                                          double, size_t, bool);
 template void launch_coarse_cycle<float>(const Launch &, int, int, const void *, const int4 *, int, int, const float *,
                                          const float *, float *, const double *, const long long *, int, float, float,
-                                         size_t);
+                                         size_t, bool);
 template size_t coarse_slev_size<double>();
 template size_t coarse_slev_size<float>();
 template size_t coarse_fill_levels<double>(void *, int, const Lev<double> *, const long long *, const long long *, int);

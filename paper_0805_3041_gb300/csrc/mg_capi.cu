@@ -546,7 +546,7 @@ static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out
   mg_ctx *c = S.c;
   launch_coarse_cycle<T>(S.lc, c->P.dim, c->kind, c->slev, c->prog + c->prog_off[pid], c->prog_len[pid], c->lcut,
                          g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)corr_weight(c),
-                         c->csk_smem);
+                         c->csk_smem, c->P.smoother > MG_RBGS || adaptive_corr(c));
 }
 
 // Host-side builder of the coarse programs: mirrors smooth() and cycle() step by step,

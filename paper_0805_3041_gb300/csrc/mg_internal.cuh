@@ -229,7 +229,8 @@ bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev
 template <typename T>
 void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, const int4 *prog, int nops, int lcut,
                          const T *g_in, const T *u_in, T *u_out, const double *Ainv, const long long *cidx_smem,
-                         int nc, T omega, T omega_corr, size_t smem_bytes);
+                         int nc, T omega, T omega_corr, size_t smem_bytes,
+                         bool full);
 template <typename T>
 size_t coarse_slev_size();
 template <typename T>
