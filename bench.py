@@ -48,6 +48,9 @@ def parse():
                          "graph; small: 129^2 Poisson, Jacobi, FP64; annulus: 2049x2048 polar map; cylinder: "
                          "257x256x257 cylindrical map; diff: 1025^2 -div(k grad u) loss and gradient")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="grids of the hierarchy (0: as many as the grid allows); coarsest grids above 4096 "
+                         "unknowns are solved by conjugate gradients")
     ap.add_argument("--flags", type=int, default=0,
                     help="extra MG_FLAG_* bits for the solver (1 = kernel-by-kernel launches, for profilers)")
     return ap.parse_args()
@@ -135,7 +138,7 @@ def default_omega(smoother, omega=None):
 def make_problem(args):
     from paper_0805_3041_gb300 import inputs
     sp = inputs.anisotropic(n=args.n, eps=args.eps, seed_f=1)
-    levels = inputs.max_levels(sp.n)
+    levels = args.levels or inputs.max_levels(sp.n)
     return sp, levels, default_omega(args.smoother, args.omega)
 
 
@@ -486,6 +489,8 @@ def run_config(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     sp, levels, smoother, omega, desc = config_problem(args)
+    if args.levels:
+        levels = args.levels
     prec = "fp64" if args.workload == "small" else args.precision
     t0 = time.perf_counter()
     s = Solver(sp, levels=levels, smoother=smoother, omega=omega, nu1=args.nu, nu2=args.nu, precision=prec,

@@ -77,6 +77,10 @@ struct mg_ctx {
   long long *cidx = nullptr;
   int *cmap = nullptr;
   double *Ainv = nullptr, *gjcol = nullptr;
+  // coarsest grids above the dense limit: conjugate gradients (FP64 x, r, p, A p on level 1)
+  bool cg_mode = false;
+  double *cgw = nullptr;
+  int cg_max_it = 0;
   // single-CTA coarse kernel: every grid <= lcut in shared memory (lcut = 0: not used)
   int lcut = 0;
   void *slev = nullptr;            // device table of shared-memory level views
@@ -135,6 +139,8 @@ static int coarsen_dims(const int nf[3], int dim, int per, int nc[3]) {
   return 1;
 }
 
+static const long long kDenseCoarseMax = 4096;   // coarsest unknowns solved with a dense inverse
+
 static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (!p || !k) return MG_EINVAL;
   if (p->dim != 2 && p->dim != 3) return MG_EINVAL;
@@ -159,9 +165,9 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
     if (!coarsen_dims(n, p->dim, p->periodic_y, c)) return MG_EINVAL;
     memcpy(n, c, sizeof(n));
   }
-  // coarsest grid solved with a dense inverse
+  // coarsest grid: a dense inverse up to kDenseCoarseMax unknowns, conjugate gradients above
   long long nc = (long long)(n[0] - 2) * (p->periodic_y ? n[1] : n[1] - 2) * (p->dim == 3 ? n[2] - 2 : 1);
-  if (nc > 4096) return MG_EINVAL;
+  if (nc > (1LL << 26)) return MG_EINVAL;
   return MG_OK;
 }
 
@@ -252,11 +258,17 @@ static size_t layout(mg_ctx *c, char *ws) {
   c->nc = (int)nc;
   c->cidx = b.take<long long>((size_t)nc);
   c->cmap = b.take<int>((size_t)g1.count);
-  c->Ainv = b.take<double>((size_t)nc * nc);
-  c->gjcol = b.take<double>((size_t)nc);
+  c->cg_mode = nc > kDenseCoarseMax;
+  if (c->cg_mode) {
+    c->cgw = b.take<double>(4 * (size_t)g1.count);
+    c->cg_max_it = (int)std::min<long long>(20000, 2 * nc);
+  } else {
+    c->Ainv = b.take<double>((size_t)nc * nc);
+    c->gjcol = b.take<double>((size_t)nc);
+  }
   // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
   c->lcut = 0;
-  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE)) {
+  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode) {
     size_t es = c->mixed ? 4 : 8, total = 0;
     size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0);
     long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
@@ -528,11 +540,19 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
   }
 }
 
+// u_1 = A_1^{-1} g: the dense inverse, or conjugate gradients to 1e-14 above the dense limit
+template <typename T>
+static void coarse_solve_into(mg_ctx *c, const Launch &lc, const T *g, T *u) {
+  if (c->cg_mode)
+    launch_coarse_cg<T>(lc, lev64(c, 1), c->kind, g, u, c->cgw, c->partials, c->cg_max_it, 1e-14, c->st + 4);
+  else
+    launch_coarse_apply<T>(lc, c->Ainv, c->cidx, c->nc, g, u);
+}
 template <typename T>
 static void coarse_solve(Sched &S, const T *g) {
   mg_ctx *c = S.c;
   LevData<T> &D = LevOf<T>::data(c, 1);
-  launch_coarse_apply<T>(S.lc, c->Ainv, c->cidx, c->nc, g, D.u[c->cur[1]]);
+  coarse_solve_into<T>(c, S.lc, g, D.u[c->cur[1]]);
 }
 
 // Programs of the single-CTA coarse kernel: 0..3 run the whole cycle on the finest grid
@@ -1048,9 +1068,13 @@ static mg_status setup_levels(mg_ctx *c) {
     if (c->nc > 0) {
       CK(cudaMemcpyAsync(c->cidx, cidx.data(), sizeof(long long) * cidx.size(), cudaMemcpyHostToDevice, c->stream));
       CK(cudaMemcpyAsync(c->cmap, cmap.data(), sizeof(int) * cmap.size(), cudaMemcpyHostToDevice, c->stream));
-      CK(cudaMemsetAsync(c->Ainv, 0, sizeof(double) * (size_t)c->nc * c->nc, c->stream));
-      launch_assemble_dense<double>(lc, lev64(c, 1), c->kind, c->cidx, c->cmap, c->nc, c->Ainv);
-      for (int k = 0; k < c->nc; ++k) launch_gj_step(lc, c->Ainv, c->gjcol, c->nc, k);
+      if (c->cg_mode) {
+        CK(cudaMemsetAsync(c->cgw, 0, sizeof(double) * 4 * (size_t)c->geo[1].count, c->stream));
+      } else {
+        CK(cudaMemsetAsync(c->Ainv, 0, sizeof(double) * (size_t)c->nc * c->nc, c->stream));
+        launch_assemble_dense<double>(lc, lev64(c, 1), c->kind, c->cidx, c->cmap, c->nc, c->Ainv);
+        for (int k = 0; k < c->nc; ++k) launch_gj_step(lc, c->Ainv, c->gjcol, c->nc, k);
+      }
     }
     CK(cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
   }
@@ -1701,7 +1725,7 @@ mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u) {
   Lev<double> C = lev64(c, 1);
   pack_in(c, lc,C, g, c->d64[1].g, 1);
   CK(cudaMemsetAsync(c->d64[1].u[0], 0, sizeof(double) * (size_t)c->geo[1].count, c->stream));
-  launch_coarse_apply<double>(lc, c->Ainv, c->cidx, c->nc, c->d64[1].g, c->d64[1].u[0]);
+  coarse_solve_into<double>(c, lc, c->d64[1].g, c->d64[1].u[0]);
   unpack_out(c, lc,C, c->d64[1].u[0], u, 1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);

@@ -244,6 +244,12 @@ void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const
                      double *dinv);
 void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *kf, double *kc);
 void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv);
+// coarsest grid by FP64 conjugate gradients (one cooperative launch): u = A^{-1} g on level L to
+// ||r|| <= rtol ||g||, at most max_it iterations.  work: 4 FP64 node arrays of L, zero off the
+// unknowns; part: 2 x (blocks) doubles of scratch; iters[0] = the iterations done
+template <typename T>
+void launch_coarse_cg(const Launch &lc, const Lev<double> &L, int kind, const T *g, T *u, double *work, double *part,
+                      int max_it, double rtol, int *iters);
 // edge coefficients: coarse weights from the fine ones (harmonic mean along, x1/4), and 1/D
 void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *fx,
                          const double *fy, const double *fz, double *cx, double *cy, double *cz);
