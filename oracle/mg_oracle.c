@@ -171,6 +171,30 @@ void or_thomas(int m, const double *lo, const double *di, const double *up, cons
   free(dp);
 }
 
+/* Cyclic tridiagonal system: rows t = 0..m-1 with lo[t] x_{t-1} + di[t] x_t + up[t] x_{t+1} = d[t],
+ * indices modulo m (lo[0] couples to x_{m-1}, up[m-1] to x_0), m >= 3.  Sherman-Morrison: with
+ * gamma = -di[0], A = T + u v^T where T is A without its two corners and with di[0] - gamma and
+ * di[m-1] - up[m-1] lo[0] / gamma on the diagonal, u = (gamma, 0, .., 0, up[m-1]),
+ * v = (1, 0, .., 0, lo[0] / gamma); then x = y - (v.y / (1 + v.z)) z with T y = d, T z = u. */
+void or_cyclic_thomas(int m, const double *lo, const double *di, const double *up, const double *d, double *x) {
+  double *l2 = (double *)malloc(sizeof(double) * (size_t)m), *d2 = (double *)malloc(sizeof(double) * (size_t)m);
+  double *u2 = (double *)malloc(sizeof(double) * (size_t)m), *uu = (double *)calloc((size_t)m, sizeof(double));
+  double *y = (double *)malloc(sizeof(double) * (size_t)m), *z = (double *)malloc(sizeof(double) * (size_t)m);
+  double alpha = up[m - 1], beta = lo[0], gamma = -di[0];
+  for (int t = 0; t < m; ++t) { l2[t] = lo[t]; d2[t] = di[t]; u2[t] = up[t]; }
+  l2[0] = 0.0;
+  u2[m - 1] = 0.0;
+  d2[0] = di[0] - gamma;
+  d2[m - 1] = di[m - 1] - alpha * beta / gamma;
+  uu[0] = gamma;
+  uu[m - 1] = alpha;
+  or_thomas(m, l2, d2, u2, d, y);
+  or_thomas(m, l2, d2, u2, uu, z);
+  double fac = (y[0] + beta / gamma * y[m - 1]) / (1.0 + z[0] + beta / gamma * z[m - 1]);
+  for (int t = 0; t < m; ++t) x[t] = y[t] - fac * z[t];
+  free(l2); free(d2); free(u2); free(uu); free(y); free(z);
+}
+
 /* Jacobi, C = D: every unknown is corrected from the same old iterate */
 static void sweep_jacobi(const lev_t *v, double *u, const double *g, double omega, double *r) {
   lev_defect(v, u, g, r);
@@ -205,6 +229,16 @@ static void line_update(const lev_t *v, double *u, const double *r, double omega
     }
     or_thomas(m, lo, di, up, rhs, dx);
     for (int t = 0; t < m; ++t) u[nid(v, t + 1, a, b)] += omega * dx[t];
+  } else if (v->per) { /* periodic y-line: i = a, k = b, every row j = 0..n1-1; cyclic system */
+    m = v->n[1];
+    for (int j = 0; j < m; ++j) {
+      di[j] = diag_at(v, a, j, b);
+      lo[j] = -wy_edge(v, a, ywrap(v, j - 1), b);   /* the edge to row j-1 (row 0: to row n1-1) */
+      up[j] = -wy_edge(v, a, j, b);                  /* the edge to row j+1 (row n1-1: to row 0) */
+      rhs[j] = r[nid(v, a, j, b)];
+    }
+    or_cyclic_thomas(m, lo, di, up, rhs, dx);
+    for (int j = 0; j < m; ++j) u[nid(v, a, j, b)] += omega * dx[j];
   } else { /* y-line: i = a, k = b, unknowns j = 1..n1-2 */
     m = v->n[1] - 2;
     for (int t = 0; t < m; ++t) {
@@ -683,9 +717,9 @@ int or_create(const or_config *cfg, or_hier **out) {
   if (cfg->dim != 2 && cfg->dim != 3) return OR_EINVAL;
   if (cfg->levels < 1 || cfg->levels > OR_MAXLEV) return OR_EINVAL;
   if (cfg->smoother < OR_JACOBI || cfg->smoother > OR_GSADI) return OR_EINVAL;
-  if (cfg->periodic_y && (cfg->smoother == OR_LINE_Y || cfg->smoother == OR_ZEBRA_Y || cfg->smoother == OR_ADI ||
-                          cfg->smoother == OR_GSADI))
-    return OR_EINVAL;
+  if (cfg->periodic_y && cfg->n[1] < 4 && (cfg->smoother == OR_LINE_Y || cfg->smoother == OR_ZEBRA_Y ||
+                                            cfg->smoother == OR_ADI || cfg->smoother == OR_GSADI))
+    return OR_EINVAL;   /* cyclic line systems need >= 3 rows on every level */
   if (cfg->n[0] < 3 || cfg->n[1] < (cfg->periodic_y ? 2 : 3) || (cfg->dim == 3 && cfg->n[2] < 3)) return OR_EINVAL;
   if (cfg->periodic_y && (cfg->n[1] % 2)) return OR_EINVAL;
   or_hier *H = (or_hier *)calloc(1, sizeof(or_hier));

@@ -93,6 +93,9 @@ int  or_solve(or_hier *H, const double *b, double *x, double tol, int maxit, int
 void or_grad_k(const or_hier *H, const double *u, const double *lam, double *dk);
 void or_thomas(int m, const double *lo, const double *di, const double *up,
                const double *d, double *x);
+/* cyclic tridiagonal solve (indices modulo m: lo[0] couples to x[m-1], up[m-1] to x[0]), m >= 3 */
+void or_cyclic_thomas(int m, const double *lo, const double *di, const double *up,
+                      const double *d, double *x);
 void or_counts(const or_hier *H, long *smooth_sweeps, long *coarse_solves);
 void or_reset_counts(or_hier *H);
 

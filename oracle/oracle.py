@@ -98,6 +98,7 @@ def lib():
         L.or_solve.restype = C.c_int
         L.or_grad_k.argtypes = [P, P, P, P]
         L.or_thomas.argtypes = [C.c_int, P, P, P, P, P]
+        L.or_cyclic_thomas.argtypes = [C.c_int, P, P, P, P, P]
         L.or_counts.argtypes = [P, P, C.POINTER(C.c_long)]
         L.or_reset_counts.argtypes = [P]
         _lib = L
@@ -334,4 +335,13 @@ def thomas(lo, di, up, d):
     x = np.zeros(m)
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (lo, di, up, d)]
     lib().or_thomas(m, *[_ptr(a) for a in arrs], _ptr(x))
+    return x
+
+
+def cyclic_thomas(lo, di, up, d):
+    """Cyclic tridiagonal solve (or_cyclic_thomas): lo[0] couples row 0 to x[m-1], up[m-1] row m-1 to x[0]."""
+    m = len(di)
+    x = np.zeros(m)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (lo, di, up, d)]
+    lib().or_cyclic_thomas(m, *[_ptr(a) for a in arrs], _ptr(x))
     return x

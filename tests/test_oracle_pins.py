@@ -428,6 +428,9 @@ CASES = [
     # edge weights varying in every direction
     (2, True, 3, "zebra_x", 17, 4), (2, False, 3, "gsadi", 17, 3), (3, False, 3, "rbgs", 9, 2),
     (3, True, 3, "jacobi", 9, 3),
+    # lines across the periodic direction (cyclic tridiagonal systems)
+    (2, True, 1, "zebra_y", 17, 3), (2, True, 2, "line_y", 17, 3), (2, True, 3, "gsadi", 17, 3),
+    (3, True, 0, "adi", 9, 2),
 ]
 
 
@@ -841,3 +844,36 @@ def test_spherical_shell_is_second_order():
     errs = _second_order_errors(lambda n: inputs.spherical_shell(n, n, manufactured=True), exact)
     for a, b in zip(errs, errs[1:]):
         assert 3.7 <= a / b <= 4.3
+
+
+# --------------------------------------------------------------------------------------
+# lines across the periodic direction: cyclic tridiagonal systems
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [3, 7, 16])
+def test_cyclic_thomas_matches_dense(m):
+    rng = np.random.default_rng(60 + m)
+    lo, up = -rng.uniform(0.2, 1.0, m), -rng.uniform(0.2, 1.0, m)
+    di = 2.0 + rng.uniform(0.0, 1.0, m)
+    d = rng.standard_normal(m)
+    A = np.diag(di)
+    for t in range(m):
+        A[t, (t - 1) % m] += lo[t]
+        A[t, (t + 1) % m] += up[t]
+    assert np.allclose(orc.cyclic_thomas(lo, di, up, d), np.linalg.solve(A, d), rtol=0, atol=1e-13)
+
+
+def test_adi_is_robust_on_the_polar_map():
+    """Section "Coordinate systems": on the annulus (r-weighted polar map, theta periodic) the
+    alternating GSADI keeps its cycle count as the grid is refined, while point Gauss-Seidel and
+    theta-lines alone (cyclic systems) degrade: the strong coupling is radial."""
+    cyc = {}
+    for n in (65, 129):
+        sp = inputs.annulus_2d(nr=n, nt=n - 1)
+        p = orc.Problem(dim=2, n=sp.n, periodic_y=True, kind=orc.SEPARABLE, h=sp.h, sx=sp.sx, sy=sp.sy, sz=sp.sz)
+        for sm in ("gsadi", "zebra_y", "rbgs"):
+            o = orc.Oracle(p, levels=inputs.max_levels(sp.n, periodic_y=True), smoother=sm)
+            x, st, c, rr, h = o.solve(sp.b, tol=1e-10, maxit=100)
+            cyc[(n, sm)] = c if st == orc.OK else 10 ** 6
+    assert cyc[(65, "gsadi")] <= 7 and cyc[(129, "gsadi")] <= 7
+    assert min(cyc[(n, s)] for n in (65, 129) for s in ("zebra_y", "rbgs")) > 5 * cyc[(129, "gsadi")]
