@@ -59,7 +59,8 @@ typedef enum {
   MG_ADI = 6,      /* ADI: a TRIx sweep then a TRIy sweep (sections "The choice of C",
                       "Coordinate systems"); the transposed cycle runs y then x               */
   MG_GSADI = 7     /* GSADI: a GSTRIx sweep then a GSTRIy sweep; transposed: y then x, each
-                      with its colours reversed.  ADI / GSADI need a non-periodic y        */
+                      with its colours reversed.  y-lines across a periodic y are cyclic
+                      tridiagonal systems (solved by Sherman-Morrison)                      */
 } mg_smoother;
 
 typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2, MG_COEF_EDGE = 3 } mg_coef_kind;

@@ -16,7 +16,7 @@ from . import build as _build
 JACOBI, RBGS, LINE_X, LINE_Y, ZEBRA_X, ZEBRA_Y, ADI, GSADI = range(8)
 SMOOTHERS = {"jacobi": JACOBI, "rbgs": RBGS, "line_x": LINE_X, "line_y": LINE_Y,
              "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y, "adi": ADI, "gsadi": GSADI}
-CONST, SEPARABLE, CELL = 0, 1, 2
+CONST, SEPARABLE, CELL, EDGE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 FLAG_NO_GRAPH, FLAG_TIMING, FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP, FLAG_NO_TMA = 1, 2, 4, 8, 16
 FLAG_FMG_START = 32

@@ -47,6 +47,7 @@ struct LevData {
   T *sx = nullptr, *sy = nullptr, *sz = nullptr, *sdinv = nullptr;
   T *k = nullptr, *ndinv = nullptr;
   T *ex = nullptr, *ey = nullptr, *ez = nullptr;
+  T *t = nullptr;   // third line-solve scratch array (y-lines across a periodic y)
 };
 
 struct LevGeom {
@@ -141,14 +142,20 @@ static int coarsen_dims(const int nf[3], int dim, int per, int nc[3]) {
 
 static const long long kDenseCoarseMax = 4096;   // coarsest unknowns solved with a dense inverse
 
+// y-line smoothing across a periodic y: cyclic line systems (a third scratch array per level;
+// the single-CTA coarse kernel's line step does not take them)
+static bool periodic_ylines(const mg_params &P) {
+  return P.periodic_y && (P.smoother == MG_LINE_Y || P.smoother == MG_ZEBRA_Y || P.smoother == MG_ADI ||
+                          P.smoother == MG_GSADI);
+}
+
 static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (!p || !k) return MG_EINVAL;
   if (p->dim != 2 && p->dim != 3) return MG_EINVAL;
   if (p->levels < 1 || p->levels > MAXLEV) return MG_EINVAL;
   if (p->smoother < MG_JACOBI || p->smoother > MG_GSADI) return MG_EINVAL;
-  if (p->periodic_y && (p->smoother == MG_LINE_Y || p->smoother == MG_ZEBRA_Y || p->smoother == MG_ADI ||
-                        p->smoother == MG_GSADI))
-    return MG_EINVAL;   // lines across the periodic direction are cyclic systems: not supported
+  // lines across the periodic direction are cyclic systems (solved by Sherman-Morrison); every
+  // smoothed level then has >= 4 rows
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
   if (p->max_cycles < 0 || p->sweep_rows < 0 || p->tile_nodes < -1) return MG_EINVAL;
@@ -215,12 +222,14 @@ static size_t layout(mg_ctx *c, char *ws) {
       D.u[1] = b.take<double>(cnt);
       D.g = b.take<double>(cnt);
       D.r = b.take<double>(cnt);
+      if (periodic_ylines(P)) D.t = b.take<double>(cnt);
     } else {
       LevData<float> &F = c->d32[l];
       F.u[0] = b.take<float>(cnt);
       F.u[1] = b.take<float>(cnt);
       F.g = b.take<float>(cnt);
       F.r = b.take<float>(cnt);
+      if (periodic_ylines(P)) F.t = b.take<float>(cnt);
       if (c->kind == K_SEP) {
         F.sx = b.take<float>(n0);
         F.sy = b.take<float>(n0);
@@ -268,7 +277,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   }
   // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
   c->lcut = 0;
-  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode) {
+  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode && !periodic_ylines(P)) {
     size_t es = c->mixed ? 4 : 8, total = 0;
     size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0);
     long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
@@ -515,11 +524,11 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
           for (int col = 0; col < 2; ++col) {
             int colour = col == 0 ? order : 1 - order;
             if (!(fast && launch_xline<T>(S.lc, L, c->kind, 1, colour, D.u[cur], g, D.u[cur], om)))
-              launch_line<T>(S.lc, L, c->kind, dir, 1, colour, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur]);
+              launch_line<T>(S.lc, L, c->kind, dir, 1, colour, D.u[cur], g, D.u[cur], om, D.r, D.u[1 - cur], D.t);
           }
         } else {
           if (!(fast && launch_xline<T>(S.lc, L, c->kind, 0, 0, D.u[cur], g, D.u[1 - cur], om)))
-            launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur]);
+            launch_line<T>(S.lc, L, c->kind, dir, 0, 0, D.u[cur], g, D.u[1 - cur], om, D.r, D.u[1 - cur], D.t);
           cur = 1 - cur;
         }
       };

@@ -172,10 +172,12 @@ void launch_restrict(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T
 template <typename T>
 void launch_prolong_add(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *ec, T *uf, T w);
 // line smoother (dir 0: x lines, 1: y lines); zebra = 1 updates the lines of one colour in
-// place (out == u), zebra = 0 is line Jacobi (out != u).  s1, s2: scratch arrays of the level.
+// place (out == u), zebra = 0 is line Jacobi (out != u).  s1, s2: scratch arrays of the level;
+// s3: a third one for y-lines across a periodic y (cyclic systems), else unused.
 template <typename T>
 void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra, int colour, const T *u,
-                 const T *g, T *out, T omega, T *s1, T *s2);
+                 const T *g, T *out, T omega, T *s1, T *s2,
+                 T *s3);
 
 int norm_parts_count();
 void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq);

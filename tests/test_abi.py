@@ -44,9 +44,12 @@ def test_invalid_parameters_are_rejected_without_a_gpu():
     q.n = (C.c_int * 3)(18, 17, 1)        # not 2^m + 1 for 3 levels
     assert lib.mg_workspace_bytes(C.byref(q), C.byref(k)) == 0
     q = binding.Params.from_buffer_copy(p)
-    q.periodic_y, q.smoother = 1, binding.ZEBRA_Y   # lines across a periodic direction
+    q.periodic_y, q.smoother = 1, binding.ZEBRA_Y   # lines across a periodic direction: cyclic systems
     q.n = (C.c_int * 3)(17, 16, 1)
-    assert lib.mg_workspace_bytes(C.byref(q), C.byref(k)) == 0
+    assert lib.mg_workspace_bytes(C.byref(q), C.byref(k)) > 0
+    ke = binding.Coeffs.from_buffer_copy(k)
+    ke.kind = binding.EDGE   # edge weights without their arrays
+    assert lib.mg_workspace_bytes(C.byref(p), C.byref(ke)) == 0
     ctx = C.c_void_p()
     assert lib.mg_setup(C.byref(p), C.byref(k), None, 0, C.byref(ctx)) == binding.EINVAL
     assert lib.mg_status_str(binding.ENOCONV) == b"maximum number of cycles reached"

@@ -41,6 +41,7 @@ CASES = [
     ("2d-129x64-per-zebra_x", lambda: random_edges(2, (129, 64), True, 3), 5, "zebra_x", 1.0),
     ("2d-65x65-gsadi", lambda: random_edges(2, (65, 65), False, 4), 4, "gsadi", 1.0),
     ("2d-65x33-jacobi", lambda: random_edges(2, (65, 33), False, 5), 4, "jacobi", 0.8),
+    ("2d-129x64-per-gsadi", lambda: random_edges(2, (129, 64), True, 12), 5, "gsadi", 1.0),
     ("3d-33x17x33-rbgs", lambda: random_edges(3, (33, 17, 33), False, 6), 3, "rbgs", 1.0),
     ("3d-17x16x17-per-jacobi", lambda: random_edges(3, (17, 16, 17), True, 7), 3, "jacobi", 0.8),
     ("2d-33x33-rbgs-all-coarse", lambda: random_edges(2, (33, 33), False, 8), 4, "rbgs", 1.0),

@@ -77,6 +77,11 @@ CASES = [
     (2, (129, 65), False, inputs.SEPARABLE, 5, "gsadi", 1.0),
     (2, (65, 33), False, inputs.CELL, 4, "gsadi", 1.0),
     (3, (17, 17, 17), False, inputs.CONST, 3, "adi", 0.8),
+    # lines across the periodic direction (cyclic tridiagonal systems)
+    (2, (129, 64), True, inputs.SEPARABLE, 5, "zebra_y", 1.0),
+    (2, (65, 64), True, inputs.CELL, 4, "line_y", 0.7),
+    (2, (129, 64), True, inputs.SEPARABLE, 5, "gsadi", 1.0),
+    (3, (17, 16, 17), True, inputs.CONST, 3, "adi", 0.8),
     # every grid fits the single-CTA coarse cycle (the whole F-cycle runs in one launch)
     (2, (33, 33), False, inputs.CONST, 4, "rbgs", 1.0),
     (2, (17, 33), False, inputs.CELL, 3, "zebra_y", 1.0),
