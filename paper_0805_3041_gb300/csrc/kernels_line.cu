@@ -147,9 +147,184 @@ __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, con
   }
 }
 
+// y-lines by the partition method.  A CTA takes 32 adjacent lines (one column each: rows are
+// read coalesced) and YSEG segments of each line, one thread per segment.  A thread eliminates
+// its segment down to two equations in the segment's end unknowns (forward elimination keeping
+// the first unknown, then backward elimination keeping both ends), with the interior rows'
+// coefficients in three scratch arrays; one thread per line then solves the 2 * YSEG reduced
+// equations (cyclic when y is periodic: Sherman-Morrison as in cyclic_yline), and every thread
+// recovers its interior unknowns.  Lines need >= 2 * YSEG unknowns.
+// YC = 32 columns x YSEG = 16 segments (a shape of 8 columns x 64 segments, for more CTAs on long
+// lines, measured no faster: its 128-equation reduced solves are sequential).
+template <typename T, int DIM, int KIND, int YC, int YSEG>
+__global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, int colour, const T *u,
+                                                          const T *__restrict__ g, T *out, T omega,
+                                                          T *__restrict__ sap, T *__restrict__ scp,
+                                                          T *__restrict__ sdp) {
+  constexpr int NE = 2 * YSEG;
+  __shared__ T ra[NE][YC + 1], rb[NE][YC + 1], rc[NE][YC + 1], rd[NE][YC + 1], rz[NE][YC + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int k = DIM == 3 ? 1 + (int)blockIdx.y : 0;
+  const int nx = L.n0 - 2;
+  int i;
+  if (zebra) {
+    const int par = (((1 + k) & 1) == colour) ? 0 : 1;   // first column of this colour: 1 + par
+    i = 1 + par + 2 * ((int)blockIdx.x * YC + tx);
+  } else {
+    i = 1 + (int)blockIdx.x * YC + tx;
+  }
+  const bool act = i <= nx;
+  const bool per = L.per != 0;
+  const int m = per ? L.n1 : L.n1 - 2;
+  const int base_n = m / YSEG, extra = m % YSEG;
+  const int n = base_n + (ty < extra ? 1 : 0);
+  const int s0 = ty * base_n + (ty < extra ? ty : extra);
+  const long long plane = (long long)k * L.plane;
+  auto rowp = [&](int s) -> long long { return plane + (long long)(per ? s : s + 1) * L.pitch + i; };
+  // coefficients of row s of the line: a (to row s-1), b, c (to row s+1), d (the defect)
+  auto coef = [&](int s, T &a, T &b, T &c, T &d) {
+    const int j = per ? s : s + 1;
+    const long long p = rowp(s);
+    long long dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+    T D = (w.wW + w.wE) + (w.wS + w.wN);
+    if (DIM == 3) D += w.wB + w.wF;
+    b = KIND == K_CONST ? L.d : D;
+    a = (per || s > 0) ? -w.wS : T(0);
+    c = (per || s < m - 1) ? -w.wN : T(0);
+  };
+  T ta = T(0), tb = T(1), tc = T(0), td = T(0), ba = T(0), bb = T(1), bc = T(0), bd = T(0);
+  if (act) {
+    T a0, b0, c0, d0;
+    coef(s0, a0, b0, c0, d0);
+    T app = T(0), cpp = T(0), dpp = T(0);
+    for (int q = 1; q < n; ++q) {
+      T a, b, c, d;
+      coef(s0 + q, a, b, c, d);
+      T ap, cp, dv;
+      if (q == 1) {
+        const T r = T(1) / b;
+        ap = a * r;
+        cp = c * r;
+        dv = d * r;
+      } else {
+        const T r = T(1) / (b - a * cpp);
+        ap = -r * a * app;
+        cp = r * c;
+        dv = r * (d - a * dpp);
+      }
+      const long long p = rowp(s0 + q);
+      sap[p] = ap;
+      scp[p] = cp;
+      sdp[p] = dv;
+      app = ap;
+      cpp = cp;
+      dpp = dv;
+    }
+    ba = app;   // bottom: ap x_first + x_last + cp x_next = dp
+    bc = cpp;
+    bd = dpp;
+    // backward elimination keeping both ends: x_q = dp_q - ap_q x_first - cp_q x_last (1 <= q <= n-2)
+    T an = app, cn = cpp, dn = dpp;   // row q+1, starting at q+1 = n-1
+    for (int q = n - 2; q >= 1; --q) {
+      const long long p = rowp(s0 + q);
+      T aq = sap[p], cq = scp[p], dq = sdp[p];
+      if (q <= n - 3) {
+        dq = dq - cq * dn;
+        aq = aq - cq * an;
+        cq = -cq * cn;
+        sap[p] = aq;
+        scp[p] = cq;
+        sdp[p] = dq;
+      }
+      an = aq;
+      cn = cq;
+      dn = dq;
+    }
+    ta = a0;
+    if (n == 2) {
+      tb = b0;
+      tc = c0;
+      td = d0;
+    } else {   // row 1 of the segment, eliminated: x_1 = dn - an x_first - cn x_last
+      tb = b0 - c0 * an;
+      tc = -c0 * cn;
+      td = d0 - c0 * dn;
+    }
+  }
+  ra[2 * ty][tx] = ta; rb[2 * ty][tx] = tb; rc[2 * ty][tx] = tc; rd[2 * ty][tx] = td;
+  ra[2 * ty + 1][tx] = ba; rb[2 * ty + 1][tx] = bb; rc[2 * ty + 1][tx] = bc; rd[2 * ty + 1][tx] = bd;
+  __syncthreads();
+  if (ty == 0 && act) {   // the reduced line system of this column: NE equations
+    T alpha = T(0), beta = T(0), gamma = T(1);
+    if (per) {   // corners: equation 0 couples to the last unknown, the last to unknown 0
+      beta = ra[0][tx];
+      alpha = rc[NE - 1][tx];
+      gamma = -rb[0][tx];
+      rb[0][tx] -= gamma;
+      rb[NE - 1][tx] -= alpha * beta / gamma;
+      ra[0][tx] = T(0);
+      rc[NE - 1][tx] = T(0);
+    }
+    // Thomas on the (modified) tridiagonal system; z: right-hand side (gamma, 0, .., 0, alpha)
+    T cprev = T(0), dprev = T(0), zprev = T(0);
+    for (int e = 0; e < NE; ++e) {
+      const T a = ra[e][tx];
+      const T den = rb[e][tx] - a * cprev;
+      const T cp = rc[e][tx] / den;
+      const T dv = (rd[e][tx] - a * dprev) / den;
+      const T uz = per ? (e == 0 ? gamma : (e == NE - 1 ? alpha : T(0))) : T(0);
+      const T zv = (uz - a * zprev) / den;
+      rc[e][tx] = cp;
+      rd[e][tx] = dv;
+      rz[e][tx] = zv;
+      cprev = cp;
+      dprev = dv;
+      zprev = zv;
+    }
+    T y = T(0), z = T(0);
+    for (int e = NE - 1; e >= 0; --e) {
+      y = rd[e][tx] - rc[e][tx] * y;
+      z = rz[e][tx] - rc[e][tx] * z;
+      rd[e][tx] = y;
+      rz[e][tx] = z;
+    }
+    if (per) {
+      const T fac = (rd[0][tx] + beta / gamma * rd[NE - 1][tx]) / (T(1) + rz[0][tx] + beta / gamma * rz[NE - 1][tx]);
+      for (int e = 0; e < NE; ++e) rd[e][tx] -= fac * rz[e][tx];
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  const T x0 = rd[2 * ty][tx], xl = rd[2 * ty + 1][tx];
+  for (int q = 0; q < n; ++q) {
+    const long long p = rowp(s0 + q);
+    const T x = q == 0 ? x0 : (q == n - 1 ? xl : sdp[p] - sap[p] * x0 - scp[p] * xl);
+    out[p] = fma(omega, x, u[p]);
+  }
+}
+
 template <typename T>
 void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra, int colour, const T *u,
                  const T *g, T *out, T omega, T *s1, T *s2, T *s3) {
+  const int mrows = L.per ? L.n1 : L.n1 - 2;
+  if (dir == 1 && s3 && mrows >= 32) {
+    const int nx = L.n0 - 2;
+    const int cols = zebra ? (nx + 1) / 2 : nx;
+    dim3 gr((unsigned)((cols + 31) / 32), (unsigned)L.zrows()), bl(32, 16);
+#define YP(D, K) k_yline_part<T, D, K, 32, 16><<<gr, bl, 0, lc.s>>>(L, zebra, colour, u, g, out, omega, s3, s1, s2)
+    if (L.dim == 2) {
+      if (kind == K_CONST) YP(2, K_CONST); else if (kind == K_SEP) YP(2, K_SEP); else if (kind == K_CELL) YP(2, K_CELL); else YP(2, K_EDGE);
+    } else {
+      if (kind == K_CONST) YP(3, K_CONST); else if (kind == K_SEP) YP(3, K_SEP); else if (kind == K_CELL) YP(3, K_CELL); else YP(3, K_EDGE);
+    }
+#undef YP
+    ++*lc.counter;
+    return;
+  }
   long long nlines = dir == 0 ? L.unk_rows() : (long long)(L.n0 - 2) * L.zrows();
   int th = 64;
   unsigned bl = (unsigned)((nlines + th - 1) / th);

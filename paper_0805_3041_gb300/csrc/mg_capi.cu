@@ -179,6 +179,13 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
 }
 
 // Fill geometry; with ws == nullptr only sizes are computed.  Returns total bytes.
+// y-line smoothing on the unswapped problem (separable or edge coefficients, periodic y, ADI /
+// GSADI): the line kernels keep three scratch arrays per level
+static bool ylines_unswapped(const mg_ctx *c) {
+  const int sm = c->P.smoother;
+  return !c->swap && (sm == MG_LINE_Y || sm == MG_ZEBRA_Y || sm == MG_ADI || sm == MG_GSADI);
+}
+
 static size_t layout(mg_ctx *c, char *ws) {
   const mg_params &P = c->P;
   Bump b{ws, 0};
@@ -222,14 +229,14 @@ static size_t layout(mg_ctx *c, char *ws) {
       D.u[1] = b.take<double>(cnt);
       D.g = b.take<double>(cnt);
       D.r = b.take<double>(cnt);
-      if (periodic_ylines(P)) D.t = b.take<double>(cnt);
+      if (ylines_unswapped(c)) D.t = b.take<double>(cnt);
     } else {
       LevData<float> &F = c->d32[l];
       F.u[0] = b.take<float>(cnt);
       F.u[1] = b.take<float>(cnt);
       F.g = b.take<float>(cnt);
       F.r = b.take<float>(cnt);
-      if (periodic_ylines(P)) F.t = b.take<float>(cnt);
+      if (ylines_unswapped(c)) F.t = b.take<float>(cnt);
       if (c->kind == K_SEP) {
         F.sx = b.take<float>(n0);
         F.sy = b.take<float>(n0);

@@ -82,6 +82,7 @@ CASES = [
     (2, (65, 64), True, inputs.CELL, 4, "line_y", 0.7),
     (2, (129, 64), True, inputs.SEPARABLE, 5, "gsadi", 1.0),
     (3, (17, 16, 17), True, inputs.CONST, 3, "adi", 0.8),
+    (3, (17, 64, 17), True, inputs.SEPARABLE, 3, "gsadi", 1.0),
     # every grid fits the single-CTA coarse cycle (the whole F-cycle runs in one launch)
     (2, (33, 33), False, inputs.CONST, 4, "rbgs", 1.0),
     (2, (17, 33), False, inputs.CELL, 3, "zebra_y", 1.0),
