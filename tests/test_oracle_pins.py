@@ -877,3 +877,35 @@ def test_adi_is_robust_on_the_polar_map():
             cyc[(n, sm)] = c if st == orc.OK else 10 ** 6
     assert cyc[(65, "gsadi")] <= 7 and cyc[(129, "gsadi")] <= 7
     assert min(cyc[(n, s)] for n in (65, 129) for s in ("zebra_y", "rbgs")) > 5 * cyc[(129, "gsadi")]
+
+
+# --------------------------------------------------------------------------------------
+# qualitative claims of the paper
+# --------------------------------------------------------------------------------------
+
+def test_single_level_jacobi_rate_degrades_like_h_squared():
+    """One level, damped Jacobi as the whole iteration: the slowest error mode decays by
+    1 - omega (1 - cos(pi h)) per sweep, so 1 - rho falls by ~4 when h halves (the mesh
+    dependence that multigrid removes).  Measured from the residual decay of the oracle's
+    smoother on the lowest mode."""
+    gaps = []
+    for n in (17, 33, 65):
+        o = orc.Oracle(const_problem(n), levels=2, smoother="jacobi", omega=0.8)
+        x = np.linspace(0, 1, n)
+        u = np.outer(np.sin(math.pi * x), np.sin(math.pi * x))   # the slowest mode, zero right-hand side
+        g = o.zeros()
+        u1 = o.smooth(u, g, 1, l=2)
+        gaps.append(1.0 - np.linalg.norm(u1) / np.linalg.norm(u))
+    for a, b in zip(gaps, gaps[1:]):
+        assert 3.5 <= a / b <= 4.5
+
+
+def test_more_smoothing_steps_give_better_rates():
+    """Section "Smoothing": the F-cycle rate improves with nu1 = nu2 = 1, 2, 4 (RB-GS, 65^2)."""
+    rates = []
+    for nu in (1, 2, 4):
+        o = orc.Oracle(const_problem(65), levels=5, smoother="rbgs", nu1=nu, nu2=nu)
+        b = rand_field(o, np.random.default_rng(70))
+        x, st, cyc, rr, hist = o.solve(b, tol=1e-10)
+        rates.append((hist[-1] / hist[0]) ** (1.0 / cyc))
+    assert rates[0] > rates[1] > rates[2]
