@@ -86,6 +86,10 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        the energy norm of the error (Wallis 2008, section "Multigrid"):
                                        omega_l = (g - A u, P e) / (A P e, P e) on the iterate u before
                                        the correction; omega_corr is ignored */
+#define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
+                                       first single-precision TMA sweep is left out, so that the compute
+                                       warps' bounded waits run out (about a second) and the solve returns
+                                       MG_ETIMEOUT with the context still usable */
 
 typedef struct {
   int dim;                /* 2 or 3 */

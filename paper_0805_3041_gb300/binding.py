@@ -21,6 +21,7 @@ FP64, MIXED = 0, 1
 FLAG_NO_GRAPH, FLAG_TIMING, FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP, FLAG_NO_TMA = 1, 2, 4, 8, 16
 FLAG_FMG_START = 32
 FLAG_ADAPTIVE_CORR = 64
+FLAG_TEST_WAIT_TIMEOUT = 128
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5

@@ -130,7 +130,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
                                            const float *__restrict__ g, float *__restrict__ out, float omega,
                                            int first, const Lev<float> C, const float *__restrict__ ec,
                                            float omega_corr, int j0, int j1, int s0, float *ring, uint64_t *full,
-                                           uint64_t *empty, int *err) {
+                                           uint64_t *empty, int *err, int *inject) {
   constexpr int SLOT = 2 * SEGW + (MODE == 2 ? 2 * CSEGW : 0);   // floats per ring slot
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -221,6 +221,9 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
   // released the last rows, so that no copy is in flight when the CTA ends ----
   if (warp == NW) {
     if (lane != 0) return;
+    // test hook (MG_FLAG_TEST_WAIT_TIMEOUT): once per solve, one producer leaves its first valid
+    // row uncopied, so that the compute warps' bounded waits run out and the timeout path is taken
+    bool skip_pending = inject && blockIdx.x == 0 && atomicExch(inject, 0) != 0;
     int r = jfirst;   // rows jfirst .. r-1 have been issued
     bool ok = true;
     for (; r <= jlast; ++r) {
@@ -229,7 +232,8 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
         ok = false;
         break;
       }
-      issue(r);
+      if (skip_pending && valid(r)) skip_pending = false;   // this row's copy never comes
+      else issue(r);
     }
     for (int q = max(jfirst, jlast - RING + 1); q <= jlast && ok; ++q)
       ok = mbar_wait(&empty[(q - jfirst) & (RING - 1)], empty_parity(q), WAIT_CYCLES);
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
                                                       const float *__restrict__ g, float *__restrict__ out,
                                                       float omega, int first, Lev<float> C,
                                                       const float *__restrict__ ec, float omega_corr, int RC,
-                                                      int ngroups, int *err) {
+                                                      int ngroups, int *err, int *inject) {
   constexpr int SLOT = 2 * SEGW + (MODE == 2 ? 2 * CSEGW : 0);
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float *ring = reinterpret_cast<float *>(tma_smem);
@@ -417,9 +421,11 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
 
   const bool interior = L.per ? (j0 - 2 >= 0 && j1 + 1 <= L.n1 - 1) : (j0 - 2 >= 1 && j1 + 1 <= L.n1 - 2);
   if (interior)
-    band_sweep<KIND, MODE, true>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err);
+    band_sweep<KIND, MODE, true>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err,
+                                 inject);
   else
-    band_sweep<KIND, MODE, false>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err);
+    band_sweep<KIND, MODE, false>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err,
+                                  inject);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -729,7 +735,7 @@ thread_local TmaOcc tma_occ;
 
 bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const float *u, const float *g, float *out,
                      float omega, int first, int mode, const Lev<float> *C, const float *ec, float omega_corr,
-                     int *err, int rc) {
+                     int *err, int rc, int *inject) {
   if (L.dim != 2 || kind == K_CELL || kind == K_EDGE || L.pitch % 128 != 0 || L.n0 < 3 || !err) return false;
   if (mode == 2 && (!C || !ec || C->pitch % 128 != 0)) return false;
   // every copy starts on a 16-byte boundary: 16-byte aligned arrays, pitches of 128 floats
@@ -775,7 +781,8 @@ bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const floa
   const Lev<float> Cv = C ? *C : L;
   const float *e = ec ? ec : u;
 #define TMA_L(K, M)                                                                                          \
-  TMA_K(K, M)<<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr, RC, ngroups, err)
+  TMA_K(K, M)<<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr, RC, ngroups, err, \
+                                                       inject)
   if (kind == K_CONST) {
     if (mode == 0) TMA_L(K_CONST, 0); else if (mode == 1) TMA_L(K_CONST, 1); else TMA_L(K_CONST, 2);
   } else {

@@ -445,7 +445,8 @@ bool sweep_tma<float>(Sched &S, const Lev<float> &L, const float *u, const float
                       int mode, const Lev<float> *Cp, const float *ec, float oc) {
   mg_ctx *c = S.c;
   if (c->P.flags & MG_FLAG_NO_TMA) return false;
-  return launch_rb2d_tma(S.lc, L, c->kind, u, g, out, om, order, mode, Cp, ec, oc, c->st + 2, c->P.sweep_rows);
+  return launch_rb2d_tma(S.lc, L, c->kind, u, g, out, om, order, mode, Cp, ec, oc, c->st + 2, c->P.sweep_rows,
+                         (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) ? c->st + 5 : nullptr);
 }
 
 // The fused defect + restriction in FP32 through the TMA-fed kernel, where it applies.
@@ -1327,6 +1328,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     if ((lst = load_vec(c, lc, F64, x, c->mixed ? c->x64 : c->d64[L].u[0], host))) return lst;
     c->h_relres[3] = tol;
     CK(cudaMemcpyAsync(c->scal + 4, c->h_relres + 3, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
     CK(cudaGraphLaunch(c->lexec[transposed], c->stream));
     double *xin = c->mixed ? c->x64 : c->d64[L].u[0];
     std::vector<double> hbuf((size_t)c->P.max_cycles + 2);
@@ -1382,6 +1384,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
                                c->scal + 1);
   }
   launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+  if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
   if (use_graph) {
     mg_status st = build_graph(c, transposed);
     if (st) return st;

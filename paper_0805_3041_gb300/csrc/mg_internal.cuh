@@ -219,7 +219,8 @@ bool launch_rb2d_march(const Launch &lc, const Lev<T> &L, int kind, const T *u, 
 // Returns false (nothing launched) where it does not apply.
 bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const float *u, const float *g, float *out,
                      float omega, int first, int mode, const Lev<float> *C, const float *ec, float omega_corr,
-                     int *err, int rc);
+                     int *err, int rc,
+                     int *inject = nullptr);
 size_t rb2d_tma_smem(int mode);
 // the fused defect + full-weighting restriction (2-D, FP32, constant or separable
 // coefficients) streamed the same way; rc = coarse rows per CTA (0: from the occupancy)
