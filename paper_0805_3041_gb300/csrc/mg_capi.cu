@@ -592,6 +592,7 @@ struct ProgBuilder {
   const mg_ctx *c;
   std::vector<int4> ops;
   int cur[MAXLEV + 1] = {0};
+  explicit ProgBuilder(const mg_ctx *cc) : c(cc) {}
   void op(int code, int lev, int a, int b) { ops.push_back(make_int4(code, lev, a, b)); }
   // descriptor of `sweeps` red-black sweeps starting with colour `order` (CP_RB_HALF)
   static int rb_desc(int sweeps, int order, bool zero) { return order | (zero ? 2 : 0) | ((2 * sweeps - 1) << 2); }
@@ -1114,7 +1115,7 @@ static mg_status setup_levels(mg_ctx *c) {
     }
     std::vector<int4> all;
     for (int pid = 0; pid < 9; ++pid) {
-      ProgBuilder pb{c};
+      ProgBuilder pb(c);
       if (pid == PROG_FMG) {
         if (c->lcut < 2) continue;
         pb.fmg(c->lcut);
