@@ -6,10 +6,13 @@
 // place (colour = parity of the orthogonal index sum), which only reads lines
 // of the other colour.
 //
-// One thread per line: defect at the line's nodes, Thomas forward elimination
-// (modified coefficients kept in two scratch arrays of the level's layout),
-// back substitution.  y-lines are read fully coalesced (adjacent threads own
-// adjacent columns).
+// y-lines, by length (m unknowns a line; rows are read coalesced, adjacent
+// threads owning adjacent columns):
+// - 4 <= m <= 2048: k_yline_reg, segments in registers, the reduced system by
+//   parallel cyclic reduction in shared memory;
+// - m > 2048: k_yline_part, segments through three scratch arrays;
+// - m < 4 (and x-lines the dedicated x-line kernels do not take): k_line, one
+//   thread per line, Thomas with two scratch arrays of the level's layout.
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -147,6 +150,31 @@ __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, con
   }
 }
 
+// Node of row s (0-based unknown index) of the y-line through column i of plane offset pl.
+template <typename T>
+__device__ __forceinline__ long long yline_node(const Lev<T> &L, long long pl, int i, bool per, int s) {
+  return pl + (long long)(per ? s : s + 1) * L.pitch + i;
+}
+
+// Row s of the y-line through column i (m unknowns): a x_{s-1} + b x_s + c x_{s+1} = d, with d
+// the defect at the node and the couplings across a periodic y wrapping round.
+template <typename T, int DIM, int KIND>
+__device__ __forceinline__ void yline_row(const Lev<T> &L, long long pl, int i, bool per, int m, int s, const T *u,
+                                          const T *__restrict__ g, T &a, T &b, T &c, T &d) {
+  const int j = per ? s : s + 1;
+  const long long p = yline_node(L, pl, i, per, s);
+  long long dm, dp;
+  yoffs(L, j, dm, dp);
+  Weights<T, DIM, KIND> w;
+  w.load(L, i, p, dm);
+  d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
+  T D = (w.wW + w.wE) + (w.wS + w.wN);
+  if (DIM == 3) D += w.wB + w.wF;
+  b = KIND == K_CONST ? L.d : D;
+  a = (per || s > 0) ? -w.wS : T(0);
+  c = (per || s < m - 1) ? -w.wN : T(0);
+}
+
 // y-lines by the partition method.  A CTA takes 32 adjacent lines (one column each: rows are
 // read coalesced) and YSEG segments of each line, one thread per segment.  A thread eliminates
 // its segment down to two equations in the segment's end unknowns (forward elimination keeping
@@ -154,8 +182,7 @@ __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, con
 // coefficients in three scratch arrays; one thread per line then solves the 2 * YSEG reduced
 // equations (cyclic when y is periodic: Sherman-Morrison as in cyclic_yline), and every thread
 // recovers its interior unknowns.  Lines need >= 2 * YSEG unknowns.
-// YC = 32 columns x YSEG = 16 segments (a shape of 8 columns x 64 segments, for more CTAs on long
-// lines, measured no faster: its 128-equation reduced solves are sequential).
+// YC = 32 columns x YSEG = 16 segments; used for lines longer than k_yline_reg takes.
 template <typename T, int DIM, int KIND, int YC, int YSEG>
 __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, int colour, const T *u,
                                                           const T *__restrict__ g, T *out, T omega,
@@ -180,22 +207,8 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
   const int n = base_n + (ty < extra ? 1 : 0);
   const int s0 = ty * base_n + (ty < extra ? ty : extra);
   const long long plane = (long long)k * L.plane;
-  auto rowp = [&](int s) -> long long { return plane + (long long)(per ? s : s + 1) * L.pitch + i; };
-  // coefficients of row s of the line: a (to row s-1), b, c (to row s+1), d (the defect)
-  auto coef = [&](int s, T &a, T &b, T &c, T &d) {
-    const int j = per ? s : s + 1;
-    const long long p = rowp(s);
-    long long dm, dp;
-    yoffs(L, j, dm, dp);
-    Weights<T, DIM, KIND> w;
-    w.load(L, i, p, dm);
-    d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
-    T D = (w.wW + w.wE) + (w.wS + w.wN);
-    if (DIM == 3) D += w.wB + w.wF;
-    b = KIND == K_CONST ? L.d : D;
-    a = (per || s > 0) ? -w.wS : T(0);
-    c = (per || s < m - 1) ? -w.wN : T(0);
-  };
+  auto rowp = [&](int s) -> long long { return yline_node(L, plane, i, per, s); };
+  auto coef = [&](int s, T &a, T &b, T &c, T &d) { yline_row<T, DIM, KIND>(L, plane, i, per, m, s, u, g, a, b, c, d); };
   T ta = T(0), tb = T(1), tc = T(0), td = T(0), ba = T(0), bb = T(1), bc = T(0), bd = T(0);
   if (act) {
     T a0, b0, c0, d0;
@@ -307,10 +320,169 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
   }
 }
 
+// y-lines with every segment held in registers.  A CTA of blockDim = (YC, YSEG) threads takes YC
+// lines (adjacent columns of one colour) and cuts each into YSEG segments of at most NR rows.
+// A thread loads its segment's rows at once, eliminates them in registers to two equations in
+// the segment's end unknowns (as k_yline_part does), and the 2 * YSEG reduced equations of a line
+// are solved by parallel cyclic reduction in shared memory, two equations per thread.  The
+// reduction runs with wrap-around indices: that is the periodic line system itself, and with
+// its two corner couplings zero it is the Dirichlet one, so one code path serves both (2 * YSEG
+// is a power of two).  Equations are kept scaled to a unit diagonal.  After log2(2 * YSEG)
+// steps every equation couples only to its own unknown.  The interior unknowns then follow from
+// the end values.  No scratch arrays; every row is read once and written once.
+constexpr int kYlineThreads = 512;
+constexpr int kYlineSegMax = 256;
+constexpr int kYlineShared = 2 * kYlineThreads + 2 * kYlineSegMax;   // >= 2 YSEG (YC + 1)
+
+template <typename T, int DIM, int KIND, int NR>
+__global__ void __launch_bounds__(kYlineThreads, sizeof(T) == 4 ? 2 : 1)
+    k_yline_reg(Lev<T> L, int zebra, int colour, const T *u, const T *__restrict__ g, T *out, T omega) {
+  __shared__ T sa[kYlineShared], sc[kYlineShared], sd[kYlineShared];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int YC = (int)blockDim.x, YSEG = (int)blockDim.y, NE = 2 * YSEG, ld = YC + 1;
+  const int k = DIM == 3 ? 1 + (int)blockIdx.y : 0;
+  int i;
+  if (zebra) {
+    const int par = (((1 + k) & 1) == colour) ? 0 : 1;   // first column of this colour: 1 + par
+    i = 1 + par + 2 * ((int)blockIdx.x * YC + tx);
+  } else {
+    i = 1 + (int)blockIdx.x * YC + tx;
+  }
+  const bool act = i <= L.n0 - 2;
+  const bool per = L.per != 0;
+  const int m = per ? L.n1 : L.n1 - 2;
+  const int base_n = m / YSEG, extra = m % YSEG;
+  const int n = base_n + (ty < extra ? 1 : 0);   // 2 <= n <= NR
+  const int s0 = ty * base_n + (ty < extra ? ty : extra);
+  const long long plane = (long long)k * L.plane;
+  T ra[NR], rb[NR], rc[NR], rd[NR];
+  // the two reduced equations of the segment, scaled to a unit diagonal: a x_{e-1} + x_e + c x_{e+1} = d
+  T a0 = T(0), c0 = T(0), d0 = T(0), a1 = T(0), c1 = T(0), d1 = T(0);
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (q < n) yline_row<T, DIM, KIND>(L, plane, i, per, m, s0 + q, u, g, ra[q], rb[q], rc[q], rd[q]);
+    // forward elimination keeping the first unknown: ap x_first + x_q + cp x_{q+1} = dp (q >= 1)
+    T app = T(0), cpp = T(0), dpp = T(0);
+#pragma unroll
+    for (int q = 1; q < NR; ++q) {
+      if (q < n) {
+        T ap, cp, dv;
+        if (q == 1) {
+          const T r = T(1) / rb[1];
+          ap = ra[1] * r;
+          cp = rc[1] * r;
+          dv = rd[1] * r;
+        } else {
+          const T r = T(1) / (rb[q] - ra[q] * cpp);
+          ap = -r * ra[q] * app;
+          cp = r * rc[q];
+          dv = r * (rd[q] - ra[q] * dpp);
+        }
+        ra[q] = ap;
+        rc[q] = cp;
+        rd[q] = dv;
+        app = ap;
+        cpp = cp;
+        dpp = dv;
+      }
+    }
+    a1 = app;   // bottom: x_first, x_last and the next segment's first unknown
+    c1 = cpp;
+    d1 = dpp;
+    // backward elimination keeping both ends: x_q + ap x_first + cp x_last = dp (1 <= q <= n-2)
+    T an = app, cn = cpp, dn = dpp;
+#pragma unroll
+    for (int q = NR - 2; q >= 1; --q) {
+      if (q <= n - 2) {
+        if (q <= n - 3) {
+          rd[q] -= rc[q] * dn;
+          ra[q] -= rc[q] * an;
+          rc[q] = -rc[q] * cn;
+        }
+        an = ra[q];
+        cn = rc[q];
+        dn = rd[q];
+      }
+    }
+    // top: the previous segment's last unknown, x_first and x_last (row 1 eliminated)
+    T tb = rb[0], tc = rc[0], td = rd[0];
+    if (n > 2) {
+      tb = rb[0] - rc[0] * an;
+      tc = -rc[0] * cn;
+      td = rd[0] - rc[0] * dn;
+    }
+    const T r = T(1) / tb;
+    a0 = ra[0] * r;
+    c0 = tc * r;
+    d0 = td * r;
+  }
+  const int e0 = 2 * ty;
+  sa[e0 * ld + tx] = a0; sc[e0 * ld + tx] = c0; sd[e0 * ld + tx] = d0;
+  sa[(e0 + 1) * ld + tx] = a1; sc[(e0 + 1) * ld + tx] = c1; sd[(e0 + 1) * ld + tx] = d1;
+  if (act) {   // the centre values for the update, loaded while the reduced system is solved
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (q < n) rb[q] = u[yline_node(L, plane, i, per, s0 + q)];
+  }
+  // parallel cyclic reduction: equation e takes in e - s and e + s, then couples to e -+ 2s
+  for (int s = 1; s < NE; s <<= 1) {
+    __syncthreads();
+    const int m0 = ((e0 - s) & (NE - 1)) * ld + tx, p0 = ((e0 + s) & (NE - 1)) * ld + tx;
+    const int m1 = ((e0 + 1 - s) & (NE - 1)) * ld + tx, p1 = ((e0 + 1 + s) & (NE - 1)) * ld + tx;
+    const T r0 = T(1) / (T(1) - a0 * sc[m0] - c0 * sa[p0]);
+    const T r1 = T(1) / (T(1) - a1 * sc[m1] - c1 * sa[p1]);
+    const T na0 = -r0 * a0 * sa[m0], nc0 = -r0 * c0 * sc[p0], nd0 = r0 * (d0 - a0 * sd[m0] - c0 * sd[p0]);
+    const T na1 = -r1 * a1 * sa[m1], nc1 = -r1 * c1 * sc[p1], nd1 = r1 * (d1 - a1 * sd[m1] - c1 * sd[p1]);
+    __syncthreads();
+    a0 = na0; c0 = nc0; d0 = nd0;
+    a1 = na1; c1 = nc1; d1 = nd1;
+    sa[e0 * ld + tx] = a0; sc[e0 * ld + tx] = c0; sd[e0 * ld + tx] = d0;
+    sa[(e0 + 1) * ld + tx] = a1; sc[(e0 + 1) * ld + tx] = c1; sd[(e0 + 1) * ld + tx] = d1;
+  }
+  if (!act) return;
+  // both couplings now point at the equation's own unknown
+  const T x0 = d0 / (T(1) + a0 + c0), xl = d1 / (T(1) + a1 + c1);
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    if (q < n) {
+      const T x = q == 0 ? x0 : (q == n - 1 ? xl : rd[q] - ra[q] * x0 - rc[q] * xl);
+      out[yline_node(L, plane, i, per, s0 + q)] = fma(omega, x, rb[q]);
+    }
+  }
+}
+
+// Segments per line and lines per CTA for k_yline_reg with at most nr rows a segment: the fewest
+// segments (a power of two) that keep every segment within nr rows and at least two rows; 0 when
+// the line is too long for kYlineSegMax segments.
+static inline int yline_segments(int m, int nr) {
+  int seg = 1;
+  while (seg * nr < m) seg *= 2;
+  return (seg <= kYlineSegMax && 2 * seg <= m) ? seg : 0;
+}
+
 template <typename T>
 void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra, int colour, const T *u,
                  const T *g, T *out, T omega, T *s1, T *s2, T *s3) {
   const int mrows = L.per ? L.n1 : L.n1 - 2;
+  constexpr int NR = 8;
+  const int seg = dir == 1 && mrows >= 4 ? yline_segments(mrows, NR) : 0;
+  if (seg) {
+    const int nx = L.n0 - 2;
+    const int cols = zebra ? (nx + 1) / 2 : nx;
+    int yc = 1;
+    while (yc * seg < kYlineThreads && yc < cols) yc *= 2;
+    dim3 gr((unsigned)((cols + yc - 1) / yc), (unsigned)L.zrows()), bl((unsigned)yc, (unsigned)seg);
+#define YR(D, K) k_yline_reg<T, D, K, NR><<<gr, bl, 0, lc.s>>>(L, zebra, colour, u, g, out, omega)
+    if (L.dim == 2) {
+      if (kind == K_CONST) YR(2, K_CONST); else if (kind == K_SEP) YR(2, K_SEP); else if (kind == K_CELL) YR(2, K_CELL); else YR(2, K_EDGE);
+    } else {
+      if (kind == K_CONST) YR(3, K_CONST); else if (kind == K_SEP) YR(3, K_SEP); else if (kind == K_CELL) YR(3, K_CELL); else YR(3, K_EDGE);
+    }
+#undef YR
+    ++*lc.counter;
+    return;
+  }
   if (dir == 1 && s3 && mrows >= 32) {
     const int nx = L.n0 - 2;
     const int cols = zebra ? (nx + 1) / 2 : nx;

@@ -154,8 +154,6 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (p->dim != 2 && p->dim != 3) return MG_EINVAL;
   if (p->levels < 1 || p->levels > MAXLEV) return MG_EINVAL;
   if (p->smoother < MG_JACOBI || p->smoother > MG_GSADI) return MG_EINVAL;
-  // lines across the periodic direction are cyclic systems (solved by Sherman-Morrison); every
-  // smoothed level then has >= 4 rows
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return MG_EINVAL;
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_EINVAL;
   if (p->max_cycles < 0 || p->sweep_rows < 0 || p->tile_nodes < -1) return MG_EINVAL;
