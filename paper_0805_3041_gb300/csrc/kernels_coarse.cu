@@ -18,6 +18,7 @@ struct SLev {
   Lev<T> L;              // smem view: pitch = n0, k / ndinv / ex.. point into shared memory
   int off_u0, off_u1, off_g, off_r, off_k, off_dinv;   // element offsets into the smem pool
   int off_ex, off_ey, off_ez;                          // edge weights (-1: not held)
+  int off_z;                                           // line-step scratch (-1: not held)
   long long gpitch, gplane;                            // padded global layout of this level
   const T *gk, *gdinv;                                 // global cell data (loaded at start)
   const T *gex, *gey, *gez;                            // global edge weights (loaded at start)
@@ -61,6 +62,7 @@ __device__ __forceinline__ T *sarr(T *pool, int off) { return off >= 0 ? pool + 
   }
 
 static constexpr int CSK_STAGED_OPS = 1024;   // program steps staged in shared memory
+static constexpr int kCskThreads = 512;        // threads of the one CTA (up to 128 registers each)
 
 // bilinear / trilinear interpolation of the coarse array ec at fine node (i, j, k)
 template <typename T, int DIM>
@@ -76,11 +78,117 @@ __device__ __forceinline__ T interp_at(const Lev<T> &C, const T *ec, int i, int 
   return (s0 + s1) * T(0.125);
 }
 
+// Equations a thread holds in one line pass by cyclic reduction: lines x rows <= K * threads.  FP32
+// levels of the coarse kernel reach 5000 nodes, FP64 ones 1200 (and twice the registers a value).
+template <typename T>
+__host__ __device__ constexpr int line_pcr_k() { return sizeof(T) == 4 ? 8 : 4; }
+
+// One line pass (TRI along x or y; the zebra form takes the lines of one colour) on a level held
+// in shared memory, with every line solved at once by parallel cyclic reduction.  Row e of a line
+// is a x_{e-1} + x_e + c x_{e+1} = d after scaling by its diagonal: sa, sc and sd hold a, c and d
+// at the row's node.  At stride s each row takes in rows e - s and e + s and then couples to e -+ 2s.
+// A Dirichlet line ends after the stride passes m - 1, with no coupling left.  A periodic line
+// (m a power of two) wraps its indices and ends with both couplings on the row itself.
+// Thread t holds the equations q = t + u * nthr (u < K), q = row * NL + line over all NL
+// lines of the level (lines of the other colour idle).  The scaled values are held in registers
+// between the read and the write of a step.  x = d / (1 + a + c), dst = src + omega x.
+// dst may be sd (line Jacobi writes its scratch array); in the zebra form it is src.
+template <typename T, int DIM, int KIND>
+__device__ __forceinline__ void lines_pcr(const Lev<T> &L, int dir, int zebra, int colour, const T *src,
+                                          const T *__restrict__ g, T *dst, T omega, T *sa, T *sc, T *sd, int tid,
+                                          int nthr) {
+  constexpr int kLinePcrK = line_pcr_k<T>();
+  const bool cyc = dir == 1 && L.per;
+  const int nx = L.n0 - 2;
+  const int m = dir == 0 ? nx : L.yrows();
+  const int NL = dir == 0 ? (int)L.unk_rows() : nx * L.zrows();
+  const int stride = dir == 0 ? 1 : (int)L.pitch;
+  int pn[kLinePcrK], rw[kLinePcrK];   // node and row of each held equation (pn < 0: none)
+#pragma unroll
+  for (int u = 0; u < kLinePcrK; ++u) {
+    const int q = tid + u * nthr;
+    pn[u] = -1;
+    rw[u] = 0;
+    if (q >= NL * m) continue;
+    const int line = q % NL, row = q / NL;
+    int i, j, k;
+    if (dir == 0) {
+      row_jk(L, line, j, k);
+      i = 1 + row;
+      if (zebra && ((j + k) & 1) != colour) continue;
+    } else {
+      i = 1 + line % nx;
+      k = DIM == 3 ? 1 + line / nx : 0;
+      j = L.ylo() + row;
+      if (zebra && ((i + k) & 1) != colour) continue;
+    }
+    const int p = k * (int)L.plane + j * (int)L.pitch + i;
+    int dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, DIM, KIND> w;
+    w.load(L, i, p, dm);
+    const T d = residual_at<T, DIM, KIND>(L, w, src, p, dm, dp, g[p]);
+    T D = (w.wW + w.wE) + (w.wS + w.wN);
+    if (DIM == 3) D += w.wB + w.wF;
+    if (KIND == K_CONST) D = L.d;
+    const T lo = dir == 0 ? w.wW : w.wS, hi = dir == 0 ? w.wE : w.wN;
+    const T rD = T(1) / D;
+    sa[p] = (cyc || row > 0) ? -lo * rD : T(0);
+    sc[p] = (cyc || row < m - 1) ? -hi * rD : T(0);
+    sd[p] = d * rD;
+    pn[u] = p;
+    rw[u] = row;
+  }
+  for (int s = 1; s < m; s <<= 1) {
+    __syncthreads();
+    T na[kLinePcrK], nc[kLinePcrK], nd[kLinePcrK];
+#pragma unroll
+    for (int u = 0; u < kLinePcrK; ++u) {
+      if (pn[u] < 0) continue;
+      const int p = pn[u];
+      const T a = sa[p], c = sc[p], d = sd[p];
+      T am = T(0), cm = T(0), dmv = T(0), ap = T(0), cp = T(0), dpv = T(0);
+      // a row with no neighbour at distance s (Dirichlet) has a zero coupling there
+      if (rw[u] >= s || cyc) {
+        const int q = rw[u] >= s ? p - s * stride : p + (m - s) * stride;
+        am = sa[q];
+        cm = sc[q];
+        dmv = sd[q];
+      }
+      if (rw[u] + s < m || cyc) {
+        const int q = rw[u] + s < m ? p + s * stride : p - (m - s) * stride;
+        ap = sa[q];
+        cp = sc[q];
+        dpv = sd[q];
+      }
+      const T rr = T(1) / (T(1) - a * cm - c * ap);
+      na[u] = -rr * a * am;
+      nc[u] = -rr * c * cp;
+      nd[u] = rr * (d - a * dmv - c * dpv);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kLinePcrK; ++u) {
+      if (pn[u] < 0) continue;
+      sa[pn[u]] = na[u];
+      sc[pn[u]] = nc[u];
+      sd[pn[u]] = nd[u];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kLinePcrK; ++u) {
+    if (pn[u] < 0) continue;
+    const int p = pn[u];
+    const T x = sd[p] / (T(1) + sa[p] + sc[p]);
+    dst[p] = fma(omega, x, src[p]);
+  }
+}
+
 // FULL = false leaves out the line-smoother and adaptive-weight steps (programs of the point
 // smoothers with a fixed weight never hold them): a smaller kernel spends less of each step
 // fetching instructions.
 template <typename T, int DIM, int KIND, bool FULL>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
+__global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
                                                        int nops, int lc, const T *__restrict__ g_in,
                                                        const T *__restrict__ u_in, T *__restrict__ u_out,
                                                        const double *__restrict__ Ainv,
@@ -226,6 +334,20 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
         T *src = ub(o.w & 15), *dst = ub((o.w >> 4) & 15);
         T *cps = r, *dps = ub((o.w >> 8) & 15);
         int nlines = dir == 0 ? (int)L.unk_rows() : (L.n0 - 2) * L.zrows();
+        {   // every line at once by cyclic reduction where the level fits (r, z and the scratch array).
+          // In one SM its (lines x rows x log rows) work is issue-bound, a Thomas line a chain of rows:
+          // it pays where the chain is long (FP64 divisions, or the cyclic solve's extra passes) and
+          // few lines are active.  Measured on 65x65, 65x64 and 17x16x17 levels: FP32 Dirichlet
+          // lines and many short lines are faster with Thomas.
+          const int mrow = dir == 0 ? L.n0 - 2 : L.yrows();
+          const bool cyc = dir == 1 && L.per, pow2 = (mrow & (mrow - 1)) == 0;
+          const int active = zebra ? (nlines + 1) / 2 : nlines;
+          if (S.off_z >= 0 && (sizeof(T) == 8 || cyc) && active <= mrow && nlines * mrow <= line_pcr_k<T>() * nthr_ &&
+              (!cyc || pow2)) {
+            lines_pcr<T, DIM, KIND>(L, dir, zebra, colour, src, g, dst, omega, cps, pool + S.off_z, dps, tid_, nthr_);
+            break;
+          }
+        }
         for (int t = tid_; t < nlines; t += nthr_) {
           int m, a_fixed, kk;
           int base, stride;
@@ -242,6 +364,11 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const SLev<T> *__restrict
             int nx = L.n0 - 2;
             int ii = 1 + t % nx, k2 = (DIM == 3 ? 1 : 0) + t / nx;
             if (zebra && ((ii + k2) & 1) != colour) continue;
+            if (L.per) {   // every row an unknown: the cyclic system (third scratch array z)
+              cyclic_yline<T, DIM, KIND>(L, (long long)k2 * L.plane + ii, ii, src, g, dst, omega, cps, dps,
+                                         pool + S.off_z);
+              continue;
+            }
             m = L.n1 - 2;
             base = k2 * (int)L.plane + (int)L.pitch + ii;
             stride = (int)L.pitch;
@@ -428,7 +555,7 @@ void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, 
   do {                                                                                                       \
     auto fn = full ? k_coarse_cycle<T, D, K, true> : k_coarse_cycle<T, D, K, false>;                        \
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);                  \
-    fn<<<1, 512, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,       \
+    fn<<<1, kCskThreads, smem_bytes, lc.s>>>((const SLev<T> *)levs, prog, nops, lcut, g_in, u_in, u_out, Ainv,       \
                                       cidx_smem, nc, omega, omega_corr);                                     \
   } while (0)
   if (dim == 2) {
@@ -454,7 +581,7 @@ size_t coarse_slev_size() {
 // Fill the level descriptors (host): smem offsets in elements of T, returns the pool size in bytes.
 template <typename T>
 size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long long *gpitch, const long long *gplane,
-                          int kind) {
+                          int kind, bool zscratch) {
   static_assert(sizeof(SLev<T>) <= 512, "level table slot");
   SLev<T> *S = (SLev<T> *)out;
   int off = 0;
@@ -481,6 +608,7 @@ size_t coarse_fill_levels(void *out, int lcut, const Lev<T> *glev, const long lo
     s.off_g = take(cnt);
     s.off_r = take(cnt);
     s.off_k = s.off_dinv = s.off_ex = s.off_ey = s.off_ez = -1;
+    s.off_z = zscratch ? take(cnt) : -1;
     if (kind == K_CELL) {
       s.off_k = take(cnt);
       s.off_dinv = take(cnt);
@@ -505,7 +633,9 @@ template void launch_coarse_cycle<float>(const Launch &, int, int, const void *,
                                          size_t, bool);
 template size_t coarse_slev_size<double>();
 template size_t coarse_slev_size<float>();
-template size_t coarse_fill_levels<double>(void *, int, const Lev<double> *, const long long *, const long long *, int);
-template size_t coarse_fill_levels<float>(void *, int, const Lev<float> *, const long long *, const long long *, int);
+template size_t coarse_fill_levels<double>(void *, int, const Lev<double> *, const long long *, const long long *, int,
+                                           bool);
+template size_t coarse_fill_levels<float>(void *, int, const Lev<float> *, const long long *, const long long *, int,
+                                          bool);
 
 }  // namespace mg

@@ -17,71 +17,6 @@
 
 namespace mg {
 
-// y-line across a periodic direction (every row an unknown): a cyclic tridiagonal system, solved
-// by Sherman-Morrison.  With gamma = -D_0, A = T + u v^T where T drops the two corner couplings
-// (beta = -w_S of row 0, alpha = -w_N of row n1-1) and carries D_0 - gamma and
-// D_{n1-1} - alpha beta / gamma on its diagonal, u = (gamma, 0, .., 0, alpha),
-// v = (1, 0, .., 0, beta / gamma); x = y - (v.y / (1 + v.z)) z with T y = r and T z = u.
-// The two Thomas solves share the elimination; zps holds the second one's right-hand side.
-template <typename T, int DIM, int KIND>
-__device__ __forceinline__ void cyclic_yline(const Lev<T> &L, long long base, int i, const T *u, const T *g, T *out,
-                                             T omega, T *cps, T *dps, T *zps) {
-  const int m = L.n1;
-  const long long stride = L.pitch;
-  T beta = T(0), gamma = T(1), cprev = T(0), yprev = T(0), zprev = T(0);
-  for (int s = 0; s < m; ++s) {
-    long long p = base + s * stride;
-    long long dm, dp;
-    yoffs(L, s, dm, dp);
-    Weights<T, DIM, KIND> w;
-    w.load(L, i, p, dm);
-    T r = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
-    T D = (w.wW + w.wE) + (w.wS + w.wN);
-    if (DIM == 3) D += w.wB + w.wF;
-    if (KIND == K_CONST) D = L.d;
-    T lo = s > 0 ? -w.wS : T(0);
-    T up = s < m - 1 ? -w.wN : T(0);
-    T uz = T(0);
-    if (s == 0) {
-      beta = -w.wS;
-      gamma = -D;
-      D = D - gamma;
-      uz = gamma;
-    }
-    if (s == m - 1) {
-      const T alpha = -w.wN;
-      D = D - alpha * beta / gamma;
-      uz = alpha;
-    }
-    T den = D - lo * cprev;
-    T cp = up / den;
-    T yv = (r - lo * yprev) / den;
-    T zv = (uz - lo * zprev) / den;
-    cps[p] = cp;
-    dps[p] = yv;
-    zps[p] = zv;
-    cprev = cp;
-    yprev = yv;
-    zprev = zv;
-  }
-  T y = T(0), z = T(0), y0 = T(0), z0 = T(0), ylast = T(0), zlast = T(0);
-  for (int s = m - 1; s >= 0; --s) {
-    long long p = base + s * stride;
-    y = dps[p] - cps[p] * y;
-    z = zps[p] - cps[p] * z;
-    dps[p] = y;
-    zps[p] = z;
-    if (s == m - 1) { ylast = y; zlast = z; }
-    if (s == 0) { y0 = y; z0 = z; }
-  }
-  const T fac = (y0 + beta / gamma * ylast) / (T(1) + z0 + beta / gamma * zlast);
-  for (int s = 0; s < m; ++s) {
-    long long p = base + s * stride;
-    const T x = dps[p] - fac * zps[p];
-    out[p] = fma(omega, x, u[p]);
-  }
-}
-
 template <typename T, int DIM, int KIND>
 __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, const T *__restrict__ g, T *out, T omega,
                        T *__restrict__ cps, T *__restrict__ dps, T *__restrict__ zps) {

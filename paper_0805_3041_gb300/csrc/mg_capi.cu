@@ -142,11 +142,11 @@ static int coarsen_dims(const int nf[3], int dim, int per, int nc[3]) {
 
 static const long long kDenseCoarseMax = 4096;   // coarsest unknowns solved with a dense inverse
 
-// y-line smoothing across a periodic y: cyclic line systems (a third scratch array per level;
-// the single-CTA coarse kernel's line step does not take them)
-static bool periodic_ylines(const mg_params &P) {
-  return P.periodic_y && (P.smoother == MG_LINE_Y || P.smoother == MG_ZEBRA_Y || P.smoother == MG_ADI ||
-                          P.smoother == MG_GSADI);
+// line smoothers: the single-CTA coarse kernel keeps a third scratch array per level for their
+// line steps (cyclic reduction over all lines, or the cyclic Thomas solve)
+static bool line_smoother(const mg_params &P) {
+  return P.smoother == MG_LINE_X || P.smoother == MG_LINE_Y || P.smoother == MG_ZEBRA_X ||
+         P.smoother == MG_ZEBRA_Y || P.smoother == MG_ADI || P.smoother == MG_GSADI;
 }
 
 static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
@@ -282,9 +282,10 @@ static size_t layout(mg_ctx *c, char *ws) {
   }
   // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
   c->lcut = 0;
-  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode && !periodic_ylines(P)) {
+  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode) {
     size_t es = c->mixed ? 4 : 8, total = 0;
-    size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0);
+    size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0) +
+                    (line_smoother(P) ? 1 : 0);
     long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
     if (P.coarse_cut_nodes > 0) cap = P.coarse_cut_nodes;
     for (int l = 1; l <= c->L; ++l) {
@@ -1105,11 +1106,11 @@ static mg_status setup_levels(mg_ctx *c) {
     if (c->mixed) {
       std::vector<Lev<float>> lv(MAXLEV + 1);
       for (int l = 1; l <= c->lcut; ++l) lv[l] = lev32(c, l);
-      c->csk_smem = coarse_fill_levels<float>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind);
+      c->csk_smem = coarse_fill_levels<float>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind, line_smoother(P));
     } else {
       std::vector<Lev<double>> lv(MAXLEV + 1);
       for (int l = 1; l <= c->lcut; ++l) lv[l] = lev64(c, l);
-      c->csk_smem = coarse_fill_levels<double>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind);
+      c->csk_smem = coarse_fill_levels<double>(tab.data(), c->lcut, lv.data(), gp, gpl, c->kind, line_smoother(P));
     }
     std::vector<int4> all;
     for (int pid = 0; pid < 9; ++pid) {
