@@ -60,7 +60,8 @@ typedef enum {
                       "Coordinate systems"); the transposed cycle runs y then x               */
   MG_GSADI = 7     /* GSADI: a GSTRIx sweep then a GSTRIy sweep; transposed: y then x, each
                       with its colours reversed.  y-lines across a periodic y are cyclic
-                      tridiagonal systems (solved by Sherman-Morrison)                      */
+                      tridiagonal systems: solved by cyclic reduction with wrapped indices
+                      (lines of 4 to 2048 unknowns), else Thomas with Sherman-Morrison      */
 } mg_smoother;
 
 typedef enum { MG_COEF_CONST = 0, MG_COEF_SEPARABLE = 1, MG_COEF_CELL = 2, MG_COEF_EDGE = 3 } mg_coef_kind;
@@ -131,7 +132,7 @@ typedef struct {
      symmetric 5-/7-point operator in edge form, e.g. a grid refined in two directions or a
      mapped geometry whose weights vary in both directions (section "Anisotropies").  Coarse
      weights: harmonic mean of the two fine edges along a coarse edge, times 1/4.  y-line
-     smoothing uses the one-thread-per-line kernel (no axis swap). */
+     smoothing keeps its y-lines (no axis swap). */
   const double *ex, *ey, *ez;
 } mg_coeffs;
 

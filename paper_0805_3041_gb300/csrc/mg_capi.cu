@@ -524,7 +524,8 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, 1 - first);
     } else {
       // one line sweep in direction dir: line Jacobi out of place, or zebra (both colours) in place.
-      // x lines: one CTA per line (partition + PCR); y lines and very long lines: one thread per line
+      // x lines up to 4096 unknowns: the x-line kernels (one CTA or one warp a line, partition + PCR);
+      // y lines and longer x lines: launch_line (y-line kernels by length, else one thread a line)
       auto line_pass = [&](int dir, bool zebra) {
         bool fast = dir == 0 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && L.n0 - 2 <= 4096;
         if (zebra) {
