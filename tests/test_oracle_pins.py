@@ -863,6 +863,75 @@ def test_cyclic_thomas_matches_dense(m):
     assert np.allclose(orc.cyclic_thomas(lo, di, up, d), np.linalg.solve(A, d), rtol=0, atol=1e-13)
 
 
+def _thomas_ext(lo, di, up, d):
+    """Thomas in numpy's extended precision (the reference for the forward-error pin)."""
+    m = len(di)
+    cp, dp = np.zeros(m, lo.dtype), np.zeros(m, lo.dtype)
+    for s in range(m):
+        den = di[s] - (lo[s] * cp[s - 1] if s else 0)
+        cp[s] = up[s] / den
+        dp[s] = (d[s] - (lo[s] * dp[s - 1] if s else 0)) / den
+    x, xn = np.zeros(m, lo.dtype), lo.dtype.type(0)
+    for s in range(m - 1, -1, -1):
+        xn = dp[s] - cp[s] * xn
+        x[s] = xn
+    return x
+
+
+def _cyclic_ext(lo, di, up, d):
+    """The cyclic system in extended precision: the corner-free tridiagonal solve plus the rank-one
+    (Sherman-Morrison) correction, written out independently of the oracle."""
+    m = len(di)
+    gamma, beta, alpha = -di[0], lo[0], up[m - 1]
+    dd = di.copy()
+    dd[0] -= gamma
+    dd[m - 1] -= alpha * beta / gamma
+    l2, u2 = lo.copy(), up.copy()
+    l2[0] = 0
+    u2[m - 1] = 0
+    y = _thomas_ext(l2, dd, u2, d)
+    e = np.zeros(m, lo.dtype)
+    e[0], e[m - 1] = gamma, alpha
+    z = _thomas_ext(l2, dd, u2, e)
+    return y - (y[0] + beta / gamma * y[m - 1]) / (1 + z[0] + beta / gamma * z[m - 1]) * z
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps > 1e-18, reason="needs an extended-precision long double")
+@pytest.mark.parametrize("m,per", [(1025, False), (2047, False), (2048, True)])
+def test_line_solve_forward_error_on_anisotropic_lines(m, per):
+    """A y-line of a strongly anisotropic grid (9 x m nodes on the unit square: y-couplings ~1e6 against
+    an x margin ~1e2, Gershgorin condition bound kappa_G ~ 1e5).  The smoothed value u + C^{-1}(g - C u + s)
+    from the oracle's Thomas (cyclic for a periodic line) lies within kappa_G u (u = 2^-53) of the
+    same value in extended precision.  It also misses it by more than 1e-12 on the longest Dirichlet line.
+    That is the rounding that any FP64 solve of these lines carries, so two FP64 orders of operations
+    cannot agree to 1e-12 there."""
+    LD = np.longdouble
+    rng = np.random.default_rng(5 + m)
+    hy, hx = 1.0 / (m + 1), 1.0 / 8
+    wy = rng.uniform(0.5, 2, m + 1) / hy ** 2
+    wx = rng.uniform(0.5, 2, (m, 2)) / hx ** 2
+    lo, up = -wy[:-1].copy(), -wy[1:].copy()
+    if per:
+        lo[0] = up[-1] = -wy[0]
+    di = -(lo + up) + wx.sum(1)
+    if not per:
+        lo[0] = up[-1] = 0.0
+    u, g = rng.standard_normal(m), rng.standard_normal(m)
+    Cu = di * u + np.r_[0.0, lo[1:] * u[:-1]] + np.r_[up[:-1] * u[1:], 0.0]
+    if per:
+        Cu[0] += lo[0] * u[-1]
+        Cu[-1] += up[-1] * u[0]
+    d = g - Cu + wx.sum(1) * rng.standard_normal(m)   # a defect like a sweep's: off-line terms included
+    x = (orc.cyclic_thomas if per else orc.thomas)(lo, di, up, d)
+    xe = (_cyclic_ext if per else _thomas_ext)(*(a.astype(LD) for a in (lo, di, up, d)))
+    out, oute = u + x, u.astype(LD) + xe
+    err = float(np.abs(out - oute).max() / np.abs(oute).max())
+    kappa_g = 2.0 * di.max() / wx.sum(1).min()
+    assert err <= kappa_g * 2.0 ** -53
+    if m == 2047:
+        assert err > 1e-12
+
+
 def test_adi_is_robust_on_the_polar_map():
     """Section "Coordinate systems": on the annulus (r-weighted polar map, theta periodic) the
     alternating GSADI keeps its cycle count as the grid is refined, while point Gauss-Seidel and
