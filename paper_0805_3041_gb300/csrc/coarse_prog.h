@@ -14,7 +14,8 @@ enum CoarseOp {
   CP_RB_HALF = 6,   // red-black half sweeps on u_y[b], in place: a = first colour | zero << 1 |
                     // (count - 1) << 2, colours alternating, one barrier between them; zero: the
                     // first half sweep starts from a zero iterate and sets every unknown
-  CP_LINE = 7,      // a = dir | zebra << 1 | colour << 2,  b = src | dst << 4 | scratch << 8
+  CP_LINE = 7,      // a = dir | zebra << 1 | colour << 2,  b = src | dst << 4 | scratch << 8;
+                    // r, scratch and the level's z array hold the elimination
   CP_DEFECT = 8,    // r_y = g_y - A u_y[a]; b = 1: then g_{y-1} = R r_y in the same step
   CP_RESTRICT = 9,  // g_{y-1} = R r_y  (a = 1: R g_y, the right-hand side itself)
   CP_PROLONG = 10,  // u_y[a] += omega_l P u_{y-1}[b & 1]; b >> 1 = d + 1: then the red-black sweeps

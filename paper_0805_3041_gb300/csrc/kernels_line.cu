@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(kYlineThreads, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
-// Segments per line and lines per CTA for k_yline_reg with at most nr rows a segment: the fewest
-// segments (a power of two) that keep every segment within nr rows and at least two rows; 0 when
-// the line is too long for kYlineSegMax segments.
+// Segments per line for k_yline_reg with at most nr rows a segment: the fewest segments (a power
+// of two) that keep every segment within nr rows, provided each keeps at least two rows; 0 when the
+// line needs more than kYlineSegMax segments.  The launch then packs 512 / segments lines a CTA.
 static inline int yline_segments(int m, int nr) {
   int seg = 1;
   while (seg * nr < m) seg *= 2;
