@@ -30,6 +30,21 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef OR_THREADED
+#include <omp.h>
+#endif
+
+/* The timed CPU baseline builds this file a second time with -fopenmp -DOR_THREADED: the
+ * loops marked OR_PAR_ROWS then run their grid rows (and the line loops their lines) on all
+ * host cores.  Every node's arithmetic is the same in both builds, and each marked loop writes
+ * only its own nodes from values no other iteration of it writes (one colour of red-black
+ * Gauss-Seidel reads only the other colour; lines of one zebra colour are independent), so
+ * the two builds give identical results.  Sums over the grid (norms) stay serial. */
+#ifdef OR_THREADED
+#define OR_PAR_ROWS _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define OR_PAR_ROWS
+#endif
 
 typedef struct {
   int dim, n[3], per, kind;
@@ -137,9 +152,11 @@ static double diag_at(const lev_t *v, int i, int j, int k) {
 /* ------------------------------------------------------------------------- */
 
 static void lev_apply(const lev_t *v, const double *u, double *Au) {
+  OR_PAR_ROWS
   FOR_NODES(v) Au[nid(v, i, j, k)] = is_unk(v, i, j, k) ? apply_at(v, u, i, j, k) : 0.0;
 }
 static void lev_defect(const lev_t *v, const double *u, const double *g, double *r) {
+  OR_PAR_ROWS
   FOR_NODES(v) {
     size_t p = nid(v, i, j, k);
     r[p] = is_unk(v, i, j, k) ? g[p] - apply_at(v, u, i, j, k) : 0.0;
@@ -198,12 +215,14 @@ void or_cyclic_thomas(int m, const double *lo, const double *di, const double *u
 /* Jacobi, C = D: every unknown is corrected from the same old iterate */
 static void sweep_jacobi(const lev_t *v, double *u, const double *g, double omega, double *r) {
   lev_defect(v, u, g, r);
+  OR_PAR_ROWS
   FOR_NODES(v) if (is_unk(v, i, j, k)) u[nid(v, i, j, k)] += omega * r[nid(v, i, j, k)] / diag_at(v, i, j, k);
 }
 
 /* Gauss-Seidel in red-black order: red = (i+j+k) even.  One colour at a time,
  * each unknown corrected with the current iterate. */
 static void halfsweep_rb(const lev_t *v, double *u, const double *g, double omega, int colour) {
+  OR_PAR_ROWS
   FOR_NODES(v) {
     if (!is_unk(v, i, j, k) || ((i + j + k) & 1) != colour) continue;
     size_t p = nid(v, i, j, k);
@@ -253,31 +272,48 @@ static void line_update(const lev_t *v, double *u, const double *r, double omega
   }
 }
 
+/* every line of direction dir in planes kz0..kz1 whose colour matches (colour < 0: every line) */
+static void update_lines(const lev_t *v, double *u, const double *r, double omega, int dir, int colour, int kz0,
+                         int kz1) {
+#ifdef OR_THREADED
+#pragma omp parallel
+#endif
+  {
+    int len = v->n[dir];
+    double *lo = (double *)malloc(sizeof(double) * len), *di = (double *)malloc(sizeof(double) * len);
+    double *up = (double *)malloc(sizeof(double) * len), *rhs = (double *)malloc(sizeof(double) * len);
+    double *dx = (double *)malloc(sizeof(double) * len);
+    if (dir == 0) {
+      int j0 = v->per ? 0 : 1, j1 = v->per ? v->n[1] - 1 : v->n[1] - 2;
+#ifdef OR_THREADED
+#pragma omp for collapse(2) schedule(static)
+#endif
+      for (int k = kz0; k <= kz1; ++k)
+        for (int j = j0; j <= j1; ++j)
+          if (colour < 0 || ((j + k) & 1) == colour) line_update(v, u, r, omega, 0, j, k, lo, di, up, rhs, dx);
+    } else {
+#ifdef OR_THREADED
+#pragma omp for collapse(2) schedule(static)
+#endif
+      for (int k = kz0; k <= kz1; ++k)
+        for (int i = 1; i <= v->n[0] - 2; ++i)
+          if (colour < 0 || ((i + k) & 1) == colour) line_update(v, u, r, omega, 1, i, k, lo, di, up, rhs, dx);
+    }
+    free(lo); free(di); free(up); free(rhs); free(dx);
+  }
+}
+
 /* line smoothers: zebra = 0 -> line Jacobi (all lines from the old iterate);
  * zebra = 1 -> lines of one parity of the orthogonal index sum at a time */
 static void sweep_line(const lev_t *v, double *u, const double *g, double omega, int dir, int zebra, int first,
                        double *r) {
-  int len = v->n[dir] ;
-  double *lo = (double *)malloc(sizeof(double) * len), *di = (double *)malloc(sizeof(double) * len);
-  double *up = (double *)malloc(sizeof(double) * len), *rhs = (double *)malloc(sizeof(double) * len);
-  double *dx = (double *)malloc(sizeof(double) * len);
   int kz0 = (v->dim == 3) ? 1 : 0, kz1 = (v->dim == 3) ? v->n[2] - 2 : 0;
   int ncol = zebra ? 2 : 1;
   for (int pass = 0; pass < ncol; ++pass) {
     int colour = zebra ? ((first + pass) & 1) : -1;
     lev_defect(v, u, g, r);
-    if (dir == 0) {
-      int j0 = v->per ? 0 : 1, j1 = v->per ? v->n[1] - 1 : v->n[1] - 2;
-      for (int k = kz0; k <= kz1; ++k)
-        for (int j = j0; j <= j1; ++j)
-          if (colour < 0 || ((j + k) & 1) == colour) line_update(v, u, r, omega, 0, j, k, lo, di, up, rhs, dx);
-    } else {
-      for (int k = kz0; k <= kz1; ++k)
-        for (int i = 1; i <= v->n[0] - 2; ++i)
-          if (colour < 0 || ((i + k) & 1) == colour) line_update(v, u, r, omega, 1, i, k, lo, di, up, rhs, dx);
-    }
+    update_lines(v, u, r, omega, dir, colour, kz0, kz1);
   }
-  free(lo); free(di); free(up); free(rhs); free(dx);
 }
 
 /* `sweeps` smoothing steps; order OR_RED_FIRST: red (even) colour / even lines
@@ -320,6 +356,7 @@ static double w1(int a) { return a == 0 ? 0.5 : 0.25; }
 
 /* full weighting R: g_c(I) = sum_{a in {-1,0,1}^d} prod w1(a) r_f(2I + a) */
 static void lev_restrict(const lev_t *f, const lev_t *c, const double *rf, double *gc) {
+  OR_PAR_ROWS
   FOR_NODES(c) {
     size_t P = nid(c, i, j, k);
     gc[P] = 0.0;
@@ -339,6 +376,7 @@ static void lev_restrict(const lev_t *f, const lev_t *c, const double *rf, doubl
 /* bilinear / trilinear interpolation P = 2^d R^T, added with weight w:
  * u_f(i) += w * sum over coarse nodes I with |2I - i| <= 1 of prod 2 w1(2I - i) e_c(I) */
 static void lev_prolong_add(const lev_t *f, const lev_t *c, const double *ec, double *uf, double w) {
+  OR_PAR_ROWS
   FOR_NODES(f) {
     if (!is_unk(f, i, j, k)) continue;
     double s = 0.0;
@@ -820,6 +858,13 @@ void or_level_coeffs(const or_hier *H, int l, double *out) {
   memcpy(out, v->k, sizeof(double) * nk);
 }
 void or_apply(const or_hier *H, int l, const double *u, double *Au) { lev_apply(&H->lev[l], u, Au); }
+int or_threads(void) {
+#ifdef OR_THREADED
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 void or_diag(const or_hier *H, int l, double *D) {
   const lev_t *v = &H->lev[l];
   FOR_NODES(v) D[nid(v, i, j, k)] = is_unk(v, i, j, k) ? diag_at(v, i, j, k) : 0.0;

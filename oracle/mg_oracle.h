@@ -97,6 +97,8 @@ void or_thomas(int m, const double *lo, const double *di, const double *up,
 void or_cyclic_thomas(int m, const double *lo, const double *di, const double *up,
                       const double *d, double *x);
 void or_counts(const or_hier *H, long *smooth_sweeps, long *coarse_solves);
+/* threads the grid loops run on: 1, or the OpenMP thread count of the threaded build */
+int  or_threads(void);
 void or_reset_counts(or_hier *H);
 
 #ifdef __cplusplus

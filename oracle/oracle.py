@@ -36,18 +36,25 @@ SMOOTHERS = {"jacobi": JACOBI, "rbgs": RBGS, "line_x": LINE_X, "line_y": LINE_Y,
              "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y, "adi": ADI, "gsadi": GSADI}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FP contraction)."""
+_SO_MT = os.path.join(_BUILD, "liboracle_mt.so")
+
+
+def build(force: bool = False, threaded: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FP contraction).  threaded=True builds the
+    second library of the timed CPU baseline: the same source with -fopenmp -DOR_THREADED,
+    whose grid loops run on all host cores with identical results."""
     with _LOCK:
+        so = _SO_MT if threaded else _SO
         newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-        if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
-            return _SO
+        if not force and os.path.exists(so) and os.path.getmtime(so) >= newest:
+            return so
         os.makedirs(_BUILD, exist_ok=True)
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+        tmp = so + f".tmp{os.getpid()}"
+        extra = ["-fopenmp", "-DOR_THREADED"] if threaded else []
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", *extra,
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-        return _SO
+        os.replace(tmp, so)
+        return so
 
 
 class _Config(C.Structure):
@@ -60,13 +67,13 @@ class _Config(C.Structure):
                 ("adaptive_corr", C.c_int), ("ex", C.c_void_p), ("ey", C.c_void_p), ("ez", C.c_void_p)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(threaded: bool = False):
+    """The oracle library (plain, or the threaded build of the timed CPU baseline)."""
+    if threaded not in _libs:
+        L = C.CDLL(build(threaded=threaded))
         P = C.c_void_p
         L.or_create.argtypes = [C.POINTER(_Config), C.POINTER(P)]
         L.or_create.restype = C.c_int
@@ -101,8 +108,15 @@ def lib():
         L.or_cyclic_thomas.argtypes = [C.c_int, P, P, P, P, P]
         L.or_counts.argtypes = [P, P, C.POINTER(C.c_long)]
         L.or_reset_counts.argtypes = [P]
-        _lib = L
-    return _lib
+        L.or_threads.argtypes = []
+        L.or_threads.restype = C.c_int
+        _libs[threaded] = L
+    return _libs[threaded]
+
+
+def threads(threaded: bool = True) -> int:
+    """Threads the oracle's grid loops run on in that build."""
+    return int(lib(threaded).or_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -143,8 +157,9 @@ class Oracle:
 
     def __init__(self, prob: Problem, levels=2, smoother="rbgs", omega=1.0, nu1=2, nu2=2,
                  omega_corr=1.0, coarse_mode=COARSE_EXACT, coarse_sweeps=2, dense_max=1024,
-                 adaptive_corr=False):
+                 adaptive_corr=False, threaded=False):
         self.prob = prob
+        self._L = lib(threaded)
         cfg = _Config()
         cfg.dim = prob.dim
         cfg.n = (C.c_int * 3)(*prob.n)
@@ -168,7 +183,7 @@ class Oracle:
         cfg.dense_max = dense_max
         cfg.adaptive_corr = int(bool(adaptive_corr))
         h = C.c_void_p()
-        st = lib().or_create(C.byref(cfg), C.byref(h))
+        st = self._L.or_create(C.byref(cfg), C.byref(h))
         if st != OK:
             raise ValueError(f"oracle setup failed with status {st}")
         self._h = h
@@ -176,14 +191,14 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.or_destroy(h)
+        if h is not None and getattr(self, "_L", None) is not None:
+            self._L.or_destroy(h)
             self._h = None
 
     # -- level geometry ----------------------------------------------------------
     def dims(self, l):
         n = (C.c_int * 3)()
-        lib().or_level_dims(self._h, l, n)
+        self._L.or_level_dims(self._h, l, n)
         return tuple(n)
 
     def shape(self, l=None):
@@ -205,20 +220,20 @@ class Oracle:
         return m
 
     def unknowns(self, l=None):
-        return lib().or_level_unknowns(self._h, self.levels if l is None else l)
+        return self._L.or_level_unknowns(self._h, self.levels if l is None else l)
 
     # -- steps of the method -----------------------------------------------------
     def apply(self, u, l=None):
         l = self.levels if l is None else l
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = self.zeros(l)
-        lib().or_apply(self._h, l, _ptr(u), _ptr(out))
+        self._L.or_apply(self._h, l, _ptr(u), _ptr(out))
         return out
 
     def diag(self, l=None):
         l = self.levels if l is None else l
         out = self.zeros(l)
-        lib().or_diag(self._h, l, _ptr(out))
+        self._L.or_diag(self._h, l, _ptr(out))
         return out
 
     def defect(self, u, g, l=None):
@@ -226,45 +241,45 @@ class Oracle:
         u = np.ascontiguousarray(u, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
         out = self.zeros(l)
-        lib().or_defect(self._h, l, _ptr(u), _ptr(g), _ptr(out))
+        self._L.or_defect(self._h, l, _ptr(u), _ptr(g), _ptr(out))
         return out
 
     def norm(self, v, l=None):
         l = self.levels if l is None else l
-        return lib().or_norm2(self._h, l, _ptr(np.ascontiguousarray(v, dtype=np.float64)))
+        return self._L.or_norm2(self._h, l, _ptr(np.ascontiguousarray(v, dtype=np.float64)))
 
     def smooth(self, u, g, sweeps=1, order=RED_FIRST, l=None):
         l = self.levels if l is None else l
         u = np.array(u, dtype=np.float64, copy=True, order="C")
         g = np.ascontiguousarray(g, dtype=np.float64)
-        lib().or_smooth(self._h, l, _ptr(u), _ptr(g), sweeps, order)
+        self._L.or_smooth(self._h, l, _ptr(u), _ptr(g), sweeps, order)
         return u
 
     def restrict(self, rf, lf=None):
         lf = self.levels if lf is None else lf
         rf = np.ascontiguousarray(rf, dtype=np.float64)
         out = self.zeros(lf - 1)
-        lib().or_restrict(self._h, lf, _ptr(rf), _ptr(out))
+        self._L.or_restrict(self._h, lf, _ptr(rf), _ptr(out))
         return out
 
     def prolong_add(self, ec, uf, w=1.0, lf=None):
         lf = self.levels if lf is None else lf
         ec = np.ascontiguousarray(ec, dtype=np.float64)
         uf = np.array(uf, dtype=np.float64, copy=True, order="C")
-        lib().or_prolong_add(self._h, lf, _ptr(ec), _ptr(uf), w)
+        self._L.or_prolong_add(self._h, lf, _ptr(ec), _ptr(uf), w)
         return uf
 
     def coarse_solve(self, g):
         g = np.ascontiguousarray(g, dtype=np.float64)
         out = self.zeros(1)
-        lib().or_coarse_solve(self._h, _ptr(g), _ptr(out))
+        self._L.or_coarse_solve(self._h, _ptr(g), _ptr(out))
         return out
 
     def cycle(self, u, g, l=None, cycle=CYCLE_F, transposed=False):
         l = self.levels if l is None else l
         u = np.array(u, dtype=np.float64, copy=True, order="C")
         g = np.ascontiguousarray(g, dtype=np.float64)
-        lib().or_cycle(self._h, l, _ptr(u), _ptr(g), cycle, int(transposed))
+        self._L.or_cycle(self._h, l, _ptr(u), _ptr(g), cycle, int(transposed))
         return u
 
     def adaptive_omega(self, u, g, e, l=None):
@@ -272,13 +287,13 @@ class Oracle:
         coarse correction e (or_adaptive_omega)."""
         l = self.levels if l is None else l
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, g, e)]
-        return lib().or_adaptive_omega(self._h, l, *[_ptr(a) for a in arrs])
+        return self._L.or_adaptive_omega(self._h, l, *[_ptr(a) for a in arrs])
 
     def fmg_start(self, b, ncyc=1):
         """Nested-iteration start vector (or_fmg_start)."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = self.zeros()
-        lib().or_fmg_start(self._h, _ptr(b), _ptr(x), int(ncyc))
+        self._L.or_fmg_start(self._h, _ptr(b), _ptr(x), int(ncyc))
         return x
 
     def solve(self, b, x0=None, tol=1e-10, maxit=100, transposed=False, start="given"):
@@ -291,7 +306,7 @@ class Oracle:
         hist = np.zeros(maxit + 1, dtype=np.float64)
         cyc = C.c_int()
         rr = C.c_double()
-        st = lib().or_solve(self._h, _ptr(b), _ptr(x), tol, maxit, int(transposed), _ptr(hist), maxit + 1,
+        st = self._L.or_solve(self._h, _ptr(b), _ptr(x), tol, maxit, int(transposed), _ptr(hist), maxit + 1,
                             C.byref(cyc), C.byref(rr))
         return x, st, cyc.value, rr.value, hist[:cyc.value + 1].copy()
 
@@ -301,7 +316,7 @@ class Oracle:
         cy = p.n[1] if p.periodic_y else p.n[1] - 1
         shape = (cy, cx) if p.dim == 2 else (p.n[2] - 1, cy, cx)
         out = np.zeros(shape, dtype=np.float64)
-        lib().or_grad_k(self._h, _ptr(np.ascontiguousarray(u, dtype=np.float64)),
+        self._L.or_grad_k(self._h, _ptr(np.ascontiguousarray(u, dtype=np.float64)),
                         _ptr(np.ascontiguousarray(lam, dtype=np.float64)), _ptr(out))
         return out
 
@@ -317,17 +332,17 @@ class Oracle:
         else:
             cy = n[1] if p.periodic_y else n[1] - 1
             out = np.zeros((n[0] - 1) * cy * (n[2] - 1 if p.dim == 3 else 1))
-        lib().or_level_coeffs(self._h, l, _ptr(out))
+        self._L.or_level_coeffs(self._h, l, _ptr(out))
         return out
 
     def counts(self):
         sm = np.zeros(self.levels, dtype=np.int64)
         nc = C.c_long()
-        lib().or_counts(self._h, sm.ctypes.data_as(C.c_void_p), C.byref(nc))
+        self._L.or_counts(self._h, sm.ctypes.data_as(C.c_void_p), C.byref(nc))
         return sm, nc.value
 
     def reset_counts(self):
-        lib().or_reset_counts(self._h)
+        self._L.or_reset_counts(self._h)
 
 
 def thomas(lo, di, up, d):

@@ -978,3 +978,191 @@ def test_more_smoothing_steps_give_better_rates():
         x, st, cyc, rr, hist = o.solve(b, tol=1e-10)
         rates.append((hist[-1] / hist[0]) ** (1.0 / cyc))
     assert rates[0] > rates[1] > rates[2]
+
+
+# --------------------------------------------------------------------------------------
+# coarsening rules written out by hand, on data that varies in every direction
+# --------------------------------------------------------------------------------------
+
+def _hand_apply(u, wx, wy, wz, periodic_y):
+    """(A u)_p = sum over the edges e = (p, q) of w_e (u_p - u_q), at the unknowns only, from
+    per-node weights of the +x, +y (+z) edges; Dirichlet nodes read as 0.  Plain loops."""
+    dim = u.ndim
+    U = u if dim == 3 else u[None]
+    WX = wx if dim == 3 else wx[None]
+    WY = wy if dim == 3 else wy[None]
+    WZ = wz if dim == 3 else None
+    n2, n1, n0 = U.shape
+    out = np.zeros_like(U)
+
+    def unknown(i, j, k):
+        return 0 < i < n0 - 1 and (periodic_y or 0 < j < n1 - 1) and (dim == 2 or 0 < k < n2 - 1)
+
+    def val(i, j, k):
+        return U[k, j, i] if unknown(i, j, k) else 0.0
+
+    edges = []
+    for k in range(n2):
+        for j in range(n1):
+            for i in range(n0):
+                if i + 1 < n0:
+                    edges.append(((i, j, k), (i + 1, j, k), WX[k, j, i]))
+                if j + 1 < n1 or periodic_y:
+                    edges.append(((i, j, k), (i, (j + 1) % n1, k), WY[k, j, i]))
+                if dim == 3 and k + 1 < n2:
+                    edges.append(((i, j, k), (i, j, k + 1), WZ[k, j, i]))
+    for p, q, w in edges:
+        d = val(*p) - val(*q)
+        if unknown(*p):
+            out[p[2], p[1], p[0]] += w * d
+        if unknown(*q):
+            out[q[2], q[1], q[0]] -= w * d
+    return out if dim == 3 else out[0]
+
+
+def _cell_edges(k, h, dim, periodic_y, n):
+    """Edge weights of -div(k grad u) from a cell field: an edge weighs the mean of the 2 (2-D)
+    or 4 (3-D) cells that touch it, over h^2 of its direction.  Cells outside the grid do not
+    exist (they touch only edges between Dirichlet nodes, which carry no unknown)."""
+    n0, n1 = n[0], n[1]
+    n2 = n[2] if dim == 3 else 1
+    K = k if dim == 3 else k[None]
+    ncy = n1 if periodic_y else n1 - 1
+    ncz = n2 - 1 if dim == 3 else 1
+
+    def cell(i, j, kk):
+        if periodic_y:
+            j %= n1
+        if 0 <= i < n0 - 1 and 0 <= j < ncy and 0 <= kk < ncz:
+            return K[kk, j, i]
+        return None
+
+    wx, wy, wz = (np.zeros((n2, n1, n0)) for _ in range(3))
+    for kk in range(n2):
+        for j in range(n1):
+            for i in range(n0):
+                for arr, d, around in (
+                        (wx, 0, [(i, j - b, kk - c) for b in (0, 1) for c in ((0, 1) if dim == 3 else (0,))]),
+                        (wy, 1, [(i - a, j, kk - c) for a in (0, 1) for c in ((0, 1) if dim == 3 else (0,))]),
+                        (wz, 2, [(i - a, j - b, kk) for a in (0, 1) for b in (0, 1)] if dim == 3 else [])):
+                    cs = [cell(*t) for t in around]
+                    cs = [c for c in cs if c is not None]
+                    if cs:
+                        arr[kk, j, i] = sum(cs) / (len(around) * h[d] ** 2)
+    if dim == 2:
+        return wx[0], wy[0], None
+    return wx, wy, wz
+
+
+@pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False)])
+def test_cell_coarsening_by_hand_with_varying_k(dim, periodic_y):
+    """Coarse cell coefficient = mean of the 2^d child cells (coarse cell (I, J[, K]) covers
+    fine cells 2I..2I+1, 2J..2J+1[, 2K..2K+1]), edges formed from it with h doubled.  With k
+    varying from cell to cell a wrong child offset or a missing child changes the coarse
+    operator, which is compared on two coarser levels with one built here by hand."""
+    rng = np.random.default_rng(61 + dim + periodic_y)
+    n = (9, 8 if periodic_y else 9, 9 if dim == 3 else 1)
+    h = (1.0 / 8, 1.0 / n[1] if periodic_y else 1.0 / 8, 1.0 / 8)
+    ncy = n[1] if periodic_y else n[1] - 1
+    ks = (ncy, n[0] - 1) if dim == 2 else (n[2] - 1, ncy, n[0] - 1)
+    k = np.exp(rng.standard_normal(ks))
+    o = orc.Oracle(orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.CELL, h=h, k=k), levels=3)
+    kl, nl, hl = k, n, h
+    for l in (3, 2, 1):
+        if l < 3:
+            # children of coarse cell I: fine cells 2I and 2I + 1 in each direction
+            if dim == 2:
+                kl = 0.25 * (kl[0::2, 0::2] + kl[0::2, 1::2] + kl[1::2, 0::2] + kl[1::2, 1::2])
+            else:
+                kl = 0.125 * sum(kl[c::2, b::2, a::2] for a in (0, 1) for b in (0, 1) for c in (0, 1))
+            nl = ((nl[0] - 1) // 2 + 1, nl[1] // 2 if periodic_y else (nl[1] - 1) // 2 + 1,
+                  (nl[2] - 1) // 2 + 1 if dim == 3 else 1)
+            hl = tuple(2 * v for v in hl)
+        assert o.dims(l) == nl
+        wx, wy, wz = _cell_edges(kl, hl, dim, periodic_y, nl)
+        for _ in range(2):
+            u = rand_field(o, rng, l)
+            want = _hand_apply(u, wx, wy, wz, periodic_y)
+            assert np.abs(o.apply(u, l) - want).max() <= 1e-13 * np.abs(want).max(), l
+
+
+@pytest.mark.parametrize("dim,periodic_y", [(2, False), (2, True), (3, False), (3, True)])
+def test_edge_coarsening_by_hand_with_weights_varying_everywhere(dim, periodic_y):
+    """Coarse edge weight = 1/4 of the harmonic mean of the two fine edges that make up the
+    coarse edge (in series along it), taken on the fine line through the coarse edge's end
+    nodes (injection across: fine row 2J, plane 2K).  Weights drawn independently per edge, so
+    an across-edge index that is off (2J+1 for 2J, plane 0 for 2K) or a swapped direction
+    changes the result.  Coarse operators on two coarser levels against loops written here."""
+    rng = np.random.default_rng(71 + dim + 2 * periodic_y)
+    n = (17, 16 if periodic_y else 17, 9 if dim == 3 else 1)
+    shape = (n[1], n[0]) if dim == 2 else (n[2], n[1], n[0])
+    w = [np.exp(rng.standard_normal(shape)) for _ in range(3)]
+    p = orc.Problem(dim=dim, n=n, periodic_y=periodic_y, kind=orc.EDGE, h=(1, 1, 1), ex=w[0], ey=w[1],
+                    ez=w[2] if dim == 3 else None)
+    o = orc.Oracle(p, levels=3)
+
+    def H(a, b):
+        return 2 * a * b / (a + b)
+
+    ex, ey, ez = [a if dim == 3 else a[None] for a in w]
+    nl = n
+    for l in (3, 2, 1):
+        if l < 3:
+            nc = ((nl[0] - 1) // 2 + 1, nl[1] // 2 if periodic_y else (nl[1] - 1) // 2 + 1,
+                  (nl[2] - 1) // 2 + 1 if dim == 3 else 1)
+            cx, cy, cz = (np.zeros((nc[2], nc[1], nc[0])) for _ in range(3))
+            for K in range(nc[2]):
+                kk = 2 * K if dim == 3 else 0
+                for J in range(nc[1]):
+                    for I in range(nc[0]):
+                        if I + 1 < nc[0]:
+                            cx[K, J, I] = 0.25 * H(ex[kk, 2 * J, 2 * I], ex[kk, 2 * J, 2 * I + 1])
+                        if J + 1 < nc[1] or periodic_y:
+                            cy[K, J, I] = 0.25 * H(ey[kk, 2 * J, 2 * I], ey[kk, 2 * J + 1, 2 * I])
+                        if dim == 3 and K + 1 < nc[2]:
+                            cz[K, J, I] = 0.25 * H(ez[kk, 2 * J, 2 * I], ez[kk + 1, 2 * J, 2 * I])
+            ex, ey, ez, nl = cx, cy, cz, nc
+        assert o.dims(l) == nl
+        for _ in range(2):
+            u = rand_field(o, rng, l)
+            if dim == 2:
+                want = _hand_apply(u, ex[0], ey[0], None, periodic_y)
+            else:
+                want = _hand_apply(u, ex, ey, ez, periodic_y)
+            assert np.abs(o.apply(u, l) - want).max() <= 1e-13 * np.abs(want).max(), l
+
+
+# --------------------------------------------------------------------------------------
+# the threaded build of the timed CPU baseline
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("smoother,kind,periodic_y,dim", [("rbgs", orc.CONST, False, 2), ("jacobi", orc.SEPARABLE, True, 2),
+                                                         ("zebra_y", orc.CELL, False, 2), ("gsadi", orc.SEPARABLE, True, 2),
+                                                         ("zebra_x", orc.CONST, False, 3)])
+def test_threaded_oracle_is_bit_identical(smoother, kind, periodic_y, dim):
+    """The OpenMP build of the oracle (grid rows and lines spread over host cores) computes every
+    node exactly as the plain build: two cycles and a defect agree bit for bit."""
+    rng = np.random.default_rng(81)
+    n = (65, 64 if periodic_y else 65, 17 if dim == 3 else 1)
+    if dim == 3:
+        n = (33, 33, 17)
+    h = (1.0 / (n[0] - 1), 1.0 / n[1] if periodic_y else 1.0 / (n[1] - 1), 1.0 / max(n[2] - 1, 1))
+    kw = dict(dim=dim, n=n, periodic_y=periodic_y, kind=kind, h=h)
+    if kind == orc.CONST:
+        kw["c"] = (0.3 / h[0] ** 2, 1.0 / h[1] ** 2, 1.0 / h[2] ** 2)
+    elif kind == orc.SEPARABLE:
+        kw.update(sx=rng.uniform(0.5, 2, n[0] - 1), sy=rng.uniform(0.5, 2, n[0]), sz=rng.uniform(0.5, 2, n[0]))
+    else:
+        cy = n[1] if periodic_y else n[1] - 1
+        kw["k"] = np.exp(rng.standard_normal((cy, n[0] - 1) if dim == 2 else (n[2] - 1, cy, n[0] - 1)))
+    p = orc.Problem(**kw)
+    a = orc.Oracle(p, levels=3, smoother=smoother, omega=0.8 if smoother == "jacobi" else 1.0, dense_max=4096)
+    b = orc.Oracle(p, levels=3, smoother=smoother, omega=0.8 if smoother == "jacobi" else 1.0, dense_max=4096,
+                   threaded=True)
+    f = rng.uniform(-1, 1, a.shape()) * a.unknown_mask()
+    x, y = a.zeros(), b.zeros()
+    for _ in range(2):
+        x, y = a.cycle(x, f), b.cycle(y, f)
+    assert np.array_equal(x, y)
+    assert np.array_equal(a.defect(x, f), b.defect(y, f))
+    assert orc.threads(True) >= 1 and orc.threads(False) == 1
