@@ -69,10 +69,26 @@ def measured_peaks():
 FP64_TFLOPS_MEASURED = 1.197
 
 # DRAM bytes (read + write) per launch of the finest-level red-black sweep of the 4097^2
-# mixed solve, from one ncu capture of the current k_rb2d_tma: the mean of the cycle's four
-# launches (zero start 93.2 MB, plain 181.6 MB, correction folded in 205.5 MB, plain 181.7 MB).
-# It must be re-measured, or set to None, whenever that kernel changes.
-FINEST_SWEEP_TRAFFIC = 165.5e6
+# mixed solve, from one ncu capture of k_rb2d_tma: the mean of the cycle's four launches.  The
+# record names the SHA-256 of the kernel's source file at the time of the capture; when the
+# file has changed since, the counters no longer describe the kernel and traffic is reported
+# as null.
+FINEST_SWEEP_TRAFFIC = {"source": "paper_0805_3041_gb300/csrc/kernels_tma.cu",
+                        "sha256": "0000000000000000000000000000000000000000000000000000000000000000",
+                        "bytes": 165.5e6,
+                        "capture": "profiles/fcycle_mixed_rbgs_aniso4097.md"}
+
+
+def finest_sweep_traffic():
+    """The recorded DRAM traffic per launch, or None when the kernel's source has changed."""
+    import hashlib
+    rec = FINEST_SWEEP_TRAFFIC
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes"] if digest == rec["sha256"] else None
 
 
 class ClockSampler:
@@ -167,13 +183,37 @@ def oracle_cycles_to_tol(args, levels, omega):
     return cyc
 
 
-def oracle_cycle_time(args, levels, omega, sp=None, reps=1):
+def host_cpu():
+    """The host's CPU model (lscpu) and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count(), "arch": os.uname().machine}
+
+
+def oracle_threads():
+    """Threads of the oracle's threaded build (all host cores unless OMP_NUM_THREADS says
+    otherwise); None when that build is not available."""
+    from oracle import oracle as orc
+    try:
+        return orc.threads(True)
+    except Exception:
+        return None
+
+
+def oracle_cycle_time(args, levels, omega, sp=None, reps=1, threaded=False):
     """Seconds for one oracle F-cycle plus its residual check on the full grid."""
     from oracle import oracle as orc
     if sp is None:
         sp, _, _ = make_problem(args)
     o = orc.Oracle(orc.Problem(dim=2, n=sp.n, kind=orc.CONST, h=sp.h, c=sp.c), levels=levels,
-                   smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu)
+                   smoother=args.smoother, omega=omega, nu1=args.nu, nu2=args.nu, threaded=threaded)
     x = np.zeros_like(sp.b)
     ts = []
     for _ in range(reps):
@@ -190,21 +230,27 @@ def run_reference(args):
         return
     sp, levels, omega = make_problem(args)
     cyc = oracle_cycles_to_tol(args, levels, omega)
-    # one oracle cycle per step; the whole run is kept to about four minutes of oracle time
-    first = oracle_cycle_time(args, levels, omega, sp, reps=1)[0]
+    nthr = oracle_threads()
+    threaded = nthr is not None
+    # one oracle F-cycle per step on all host cores; the whole run is kept to about four
+    # minutes of oracle time
+    first = oracle_cycle_time(args, levels, omega, sp, reps=1, threaded=threaded)[0]
     budget = max(1, int(240.0 / max(first, 1e-3)) - 1)
     warm = min(args.warmup - 1, budget // 4) if args.warmup > 1 else 0
     timed = max(1, min(args.steps, budget - warm))
-    ts = oracle_cycle_time(args, levels, omega, sp, reps=warm + timed)[warm:]
+    ts = oracle_cycle_time(args, levels, omega, sp, reps=warm + timed, threaded=threaded)[warm:]
     per_cycle = float(np.mean(ts))
     value = per_cycle * cyc * 1e3
-    sample = (f"one oracle F-cycle + residual check on the full {args.n}^2 grid per step ({timed} timed), x{cyc} "
-              f"cycles (the oracle's cycle count to {args.tol:g} on 513^2, same eps/smoother)")
+    cores = nthr if threaded else 1
+    sample = (f"one oracle F-cycle + residual check on the full {args.n}^2 grid per step ({timed} timed) on "
+              f"{cores} host threads, x{cyc} cycles (the oracle's cycle count to {args.tol:g} on 513^2, same "
+              f"eps/smoother)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, levels, omega),
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -315,7 +361,7 @@ def run_ours(args):
         achieved = kern_bytes / (kern_ms * 1e-3) / 1e9 if kern_ms else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None,
-                "traffic": FINEST_SWEEP_TRAFFIC if args.n == 4097 and args.smoother == "rbgs" else None,
+                "traffic": finest_sweep_traffic() if args.n == 4097 and args.smoother == "rbgs" else None,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of the four "
                                   "finest-level sweeps of one refinement step (zero start, plain, correction "
                                   "folded in, plain)",
@@ -325,11 +371,20 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cyc = infos[-1]["cycles"]
-        ts = oracle_cycle_time(args, levels, omega, sp, reps=2)
-        per = float(np.min(ts))
-        cpu = {"value": per * cyc * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"2 oracle F-cycles (+ residual check) on the full {args.n}^2 grid, single thread; "
-                         f"fastest x {cyc} cycles (the GPU's count to tolerance)"}
+        one = float(oracle_cycle_time(args, levels, omega, sp, reps=1)[0])
+        nthr = oracle_threads()
+        if nthr is not None:
+            per = float(np.min(oracle_cycle_time(args, levels, omega, sp, reps=2, threaded=True)))
+            cores = nthr
+        else:
+            per, cores = one, 1
+        cpu = {"value": per * cyc * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+               "sample": f"2 oracle F-cycles (+ residual check) on the full {args.n}^2 grid on {cores} host "
+                         f"threads (rows and lines spread by OpenMP, results identical to the plain build); "
+                         f"fastest x {cyc} cycles (the GPU's count to tolerance)",
+               "single_thread_value": one * cyc * 1e3,
+               "single_thread_sample": f"1 oracle F-cycle (+ residual check), plain build, one thread, x {cyc}",
+               "host": host_cpu()}
 
     if rank == 0:
         last = infos[-1]
@@ -551,15 +606,19 @@ def run_config(args):
     if not args.no_cpu_baseline:   # one oracle F-cycle (+ residual) on the full grid, x the GPU's cycle count
         p = orc.Problem(dim=sp.dim, n=sp.n, periodic_y=sp.periodic_y, kind=sp.kind, h=sp.h, c=sp.c, sx=sp.sx,
                         sy=sp.sy, sz=sp.sz, k=sp.k)
-        o = orc.Oracle(p, levels=levels, smoother=smoother, omega=omega, nu1=args.nu, nu2=args.nu, dense_max=4096)
+        nthr = oracle_threads()
+        o = orc.Oracle(p, levels=levels, smoother=smoother, omega=omega, nu1=args.nu, nu2=args.nu, dense_max=4096,
+                       threaded=nthr is not None)
         t1 = time.perf_counter()
         xo = o.cycle(np.zeros_like(sp.b), sp.b)
         o.norm(o.defect(xo, sp.b))
         per = time.perf_counter() - t1
         mult = 2 if diff else 1   # the adjoint solve costs what the forward does
-        cpu = {"value": per * info["cycles"] * mult * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"1 oracle F-cycle (+ residual check) on the full grid, single thread, x {info['cycles']} "
-                         f"cycles" + (" x 2 (forward + adjoint)" if diff else "")}
+        cores = nthr or 1
+        cpu = {"value": per * info["cycles"] * mult * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+               "sample": f"1 oracle F-cycle (+ residual check) on the full grid on {cores} host threads, x "
+                         f"{info['cycles']} cycles" + (" x 2 (forward + adjoint)" if diff else ""),
+               "host": host_cpu()}
     line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",

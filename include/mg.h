@@ -7,8 +7,9 @@
  * smoothers x <- x - omega C^{-1}(A x - b) (section "Smoothers", choices of C
  * in "The choice of C") for the Poisson-type problems of sections
  * "Introduction / Motivation" and "Anisotropies": 5-point (2-D) / 7-point
- * (3-D) operators with constant, separable (mapped polar / cylindrical) or
- * per-cell coefficients, zero Dirichlet data, optionally periodic in y.
+ * (3-D) operators with constant, separable (mapped polar / cylindrical),
+ * per-cell (-div(k grad u)) or per-edge coefficients, zero Dirichlet data,
+ * optionally periodic in y.
  *
  * Conventions
  *   - Every array argument is a DEVICE pointer to a full node array (Dirichlet
@@ -17,12 +18,17 @@
  *     solutions are written as 0.  Cell arrays are (ncy, n0-1) / (n2-1, ncy, n0-1)
  *     with ncy = n1 if y is periodic else n1-1.
  *   - Level 1 is the coarsest grid and level L the finest, as in the paper.
- *   - Every call is stream-ordered on mg_params.stream (a cudaStream_t).  Calls
- *     that report convergence (mg_solve, mg_solve_adjoint) synchronise that
- *     stream once per cycle to read the residual norm.
+ *   - Every call is stream-ordered on mg_params.stream (a cudaStream_t).  A
+ *     solve (mg_solve, mg_solve_host, mg_solve_adjoint) is one CUDA graph
+ *     launch: the convergence test runs on the device after every cycle and
+ *     ends a device-side loop, and the host synchronises the stream once, when
+ *     the solve is over (MG_FLAG_NO_GRAPH: launched kernel by kernel, and the
+ *     host then reads the residual norm once per cycle).
  *   - Memory: the caller allocates the workspace (mg_workspace_bytes) and all
  *     argument arrays; the library allocates only the opaque context on the
  *     host and its CUDA graph.  The library never calls cudaMalloc.
+ *   - Sizes: at most 2^34 nodes, and at most 131,072 unknowns along x and
+ *     along y (the block partial sums of the reductions).
  *   - Errors: every call returns an mg_status; no exception crosses the ABI.
  *     MG_EINVAL is returned before any launch for bad arguments; CUDA failures
  *     give MG_ECUDA with the text in mg_last_error().
@@ -231,35 +237,56 @@ mg_status mg_residual_norm(mg_ctx *c, int level, const double *u, const double *
  *   u, b: device node arrays in the compact caller layout, read in place -- the
  *         Dirichlet entries of u must hold 0; out: device pointer to one double.
  * The per-block partial sums live in a file-scope __device__ array of 65,568 doubles
- * (~512 KB) that every GPU touched by the library holds until the process exits; at
- * most MG_NOALLOC_MAX_NODES nodes are accepted, larger grids return MG_EINVAL.  The
- * first call on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.  The call
- * is stream-ordered and asynchronous: *out is ready once p->stream has synchronised.
- * All calls share the one array, so calls that overlap on the GPU (other streams,
- * other host threads) race; each call writes every slot it later reads, nothing has
- * to be cleared between calls. */
+ * (~512 KB) that every GPU touched by the library holds until the process exits.  One
+ * partial sum covers at least 32 x-unknowns of a row, so a grid is accepted when it has at
+ * most MG_NOALLOC_MAX_NODES nodes AND at most MG_NOALLOC_MAX_XUNKNOWNS unknowns along x
+ * (n[0] - 2); any other grid returns MG_EINVAL before anything is launched.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  The call is
+ * stream-ordered and asynchronous: *out is ready once p->stream has synchronised.  All
+ * calls share the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; each call writes every slot it later reads, nothing has to be cleared
+ * between calls. */
 #define MG_NOALLOC_MAX_NODES 2147483647LL
+#define MG_NOALLOC_MAX_XUNKNOWNS (32LL * 65536)
 mg_status mg_residual_norm_noalloc(const mg_params *p, const mg_coeffs *k, const double *u, const double *b,
                                    double *out);
 
 /* Level geometry: nodes per direction of level l. */
 mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]);
 
-/* Single steps of the cycle, for testing; FP64 node arrays of the given level,
- * device pointers, out-of-place outputs.
+/* Single steps of the cycle, for testing.  Arguments are FP64 node arrays of the given
+ * level in the caller layout, device pointers, out-of-place outputs.  Each step runs the
+ * kernels the cycle runs on that level, in the context's precision: FP64 contexts compute
+ * in FP64; MG_MIXED contexts round the inputs to FP32, compute in FP32 (the coarsest solve
+ * excepted, which is FP64 in both) and widen the outputs to FP64.  MG_ETIMEOUT if a
+ * bounded device wait gave up.
  *   mg_step_smooth:   out = S^sweeps(u, g) with colour order 0 = red first, 1 = black first
  *   mg_step_defect:   r = g - A_l u
  *   mg_step_restrict: gc = R r            (level = fine level, >= 2)
  *   mg_step_prolong:  u_out = u + w P ec  (level = fine level, >= 2)
  *   mg_step_coarse:   u = A_1^{-1} g
- *   mg_step_cycle:    x_out = one F-cycle (transposed = 1: one transposed cycle) from x */
+ *   mg_step_cycle:    x_out = one F-cycle (transposed = 1: one transposed cycle) from x
+ *   mg_step_descend:  the first half of a visit of level l >= 2 in algorithm MG(l, u, g)
+ *                     (section "The Multigrid Technique"): u_out = S^nu1(u, g) (transposed:
+ *                     nu2 sweeps, colours reversed), then gc = R (g - A_l u_out) on level
+ *                     l-1.  u == NULL starts the sweeps from zero, as on the first visit
+ *                     of a coarse level.  The fused kernels the cycle uses here (sweeps with
+ *                     the defect and restriction, the streamed defect + restriction) run.
+ *   mg_step_ascend:   the second half: u_out = S^nu2(u + omega_l P ec, g) (transposed:
+ *                     nu1 sweeps, colours reversed), ec on level l-1, omega_l as the
+ *                     context's cycle takes it; the correction is folded into the first
+ *                     fused red-black sweep where the cycle folds it. */
 mg_status mg_step_smooth(mg_ctx *c, int level, const double *u, const double *g, double *out, int sweeps, int order);
 mg_status mg_step_defect(mg_ctx *c, int level, const double *u, const double *g, double *r);
 mg_status mg_step_restrict(mg_ctx *c, int level, const double *r, double *gc);
 mg_status mg_step_prolong(mg_ctx *c, int level, const double *ec, const double *u, double *u_out, double w);
 mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u);
 mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed);
+mg_status mg_step_descend(mg_ctx *c, int level, const double *u, const double *g, double *u_out, double *gc,
+                          int transposed);
+mg_status mg_step_ascend(mg_ctx *c, int level, const double *ec, const double *u, const double *g, double *u_out,
+                         int transposed);
 
 /* Mean duration (ms) of the finest-level smoothing launches recorded since the
  * last call (MG_FLAG_TIMING), their count, and the mean algorithmic bytes of one

@@ -28,7 +28,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
 
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
            "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
-           "mg_step_coarse", "mg_step_cycle", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
+           "mg_step_coarse", "mg_step_cycle", "mg_step_descend", "mg_step_ascend", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_solve", "mg_batch_destroy",
            "mg_solve_batched"]
 
@@ -103,6 +103,10 @@ def load(build_if_missing: bool = True):
     L.mg_step_coarse.restype = I
     L.mg_step_cycle.argtypes = [P, P, P, P, I]
     L.mg_step_cycle.restype = I
+    L.mg_step_descend.argtypes = [P, I, P, P, P, P, I]
+    L.mg_step_descend.restype = I
+    L.mg_step_ascend.argtypes = [P, I, P, P, P, P, I]
+    L.mg_step_ascend.restype = I
     L.mg_kernel_timing.argtypes = [P, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     L.mg_kernel_timing.restype = I
     L.mg_launch_count.argtypes = [P]
@@ -308,7 +312,7 @@ class Solver:
         self._check(self.lib.mg_apply(self.ctx, l, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr())))
         return out
 
-    # -- single steps (FP64 contexts) ---------------------------------------------------
+    # -- single steps (the context's precision; FP64 in and out) --------------------------
     def smooth(self, u, g, sweeps=1, order=0, l=None):
         l = self.levels if l is None else l
         u, g = self._dev(u), self._dev(g)
@@ -352,6 +356,26 @@ class Solver:
         self._check(self.lib.mg_step_cycle(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
                                            C.c_void_p(out.data_ptr()), int(transposed)))
         return out
+
+    def descend(self, u, g, l=None, transposed=False):
+        """mg_step_descend: (S^nu1(u, g), R(g - A S^nu1(u, g))); u=None starts from zero."""
+        l = self.levels if l is None else l
+        g = self._dev(g)
+        u = None if u is None else self._dev(u)
+        uo, gc = self.empty(l), self.empty(l - 1)
+        self._check(self.lib.mg_step_descend(self.ctx, l, None if u is None else C.c_void_p(u.data_ptr()),
+                                             C.c_void_p(g.data_ptr()), C.c_void_p(uo.data_ptr()),
+                                             C.c_void_p(gc.data_ptr()), int(transposed)))
+        return uo, gc
+
+    def ascend(self, ec, u, g, l=None, transposed=False):
+        """mg_step_ascend: S^nu2(u + omega_l P ec, g)."""
+        l = self.levels if l is None else l
+        ec, u, g = self._dev(ec), self._dev(u), self._dev(g)
+        uo = self.empty(l)
+        self._check(self.lib.mg_step_ascend(self.ctx, l, C.c_void_p(ec.data_ptr()), C.c_void_p(u.data_ptr()),
+                                            C.c_void_p(g.data_ptr()), C.c_void_p(uo.data_ptr()), int(transposed)))
+        return uo
 
     def kernel_timing(self):
         ms, n, by = C.c_double(), C.c_int(), C.c_double()

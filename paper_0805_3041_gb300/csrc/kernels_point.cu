@@ -452,14 +452,22 @@ void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
   ++*lc.counter;
 }
 
+// Rows per thread of a reduction over `rows` unknown rows of `xthreads` unknowns each, such that
+// its blocks (one partial sum each) number at most nparts and gridDim.y stays within 65535.
+// -1 when no R fits: the rows are wider than BX * nparts unknowns (norm_shape_ok is false).
 static inline int norm_R(long long rows, long long xthreads, int nparts) {
-  int R = rows_per_thread(rows);
-  while (true) {
-    dim3 gr = grid_for(xthreads, rows, R);
-    if ((long long)gr.x * gr.y <= nparts) return R;
-    R *= 2;
-  }
+  const long long gx = (xthreads + BX - 1) / BX;
+  if (gx < 1 || gx > nparts) return -1;
+  long long gy_max = nparts / gx;
+  if (gy_max > 65535) gy_max = 65535;
+  const long long per = (long long)BY * gy_max;               // rows covered per unit of R
+  long long R = (rows + per - 1) / per;
+  const long long R0 = rows_per_thread(rows);
+  if (R < R0) R = R0;
+  return (int)R;   // rows < 2^35 (set-up's node limit) and per >= 8: R < 2^32 / 2
 }
+
+bool norm_shape_ok(long long xunknowns, int nparts) { return (xunknowns + BX - 1) / BX <= nparts; }
 
 int norm_parts_count() { return 65536; }
 

@@ -165,6 +165,9 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   if (n[0] < 3 || n[1] < (p->periodic_y ? 2 : 3) || (p->dim == 3 && n[2] < 3)) return MG_EINVAL;
   if (p->periodic_y && (n[1] % 2)) return MG_EINVAL;
   if ((long long)n[0] * n[1] * n[2] > (1LL << 34)) return MG_EINVAL;
+  // the reductions keep one partial sum per block of 32 unknowns of a row (4096 partials for the
+  // adaptive weight's), on either axis (y-line smoothers may swap them)
+  if (!norm_shape_ok(n[0] - 2, 4096) || !norm_shape_ok(n[1] - 2, 4096)) return MG_EINVAL;
   for (int l = 1; l < p->levels; ++l) {
     int c[3];
     if (!coarsen_dims(n, p->dim, p->periodic_y, c)) return MG_EINVAL;
@@ -712,18 +715,16 @@ static void emit_adapt(Sched &S, int l, const T *g) {
   launch_scale_by<T>(S.lc, e, (long long)c->geo[l - 1].count, c->scal + 8);
 }
 
-// One cycle at level l on (u = current buffer of level l, g).  type 0 = F, 1 = V.
+// The descending half of a visit of level l >= 2: the pre-smoothing sweeps on (u = current
+// buffer of level l, g), then g_{l-1} = R (g - A u) into the coarse level's g.  Small 2-D
+// red-black grids run both sweeps, the defect and the restriction in one pass.
 template <typename T>
-static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool zero_start) {
+static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start) {
   mg_ctx *c = S.c;
-  if (l == 1) {
-    coarse_solve<T>(S, g);
-    return;
-  }
   LevData<T> &D = LevOf<T>::data(c, l);
   LevData<T> &Dc = LevOf<T>::data(c, l - 1);
   Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
-  int npre = transposed ? c->P.nu2 : c->P.nu1, npost = transposed ? c->P.nu1 : c->P.nu2;
+  int npre = transposed ? c->P.nu2 : c->P.nu1;
   int order = transposed ? 1 : 0;
   const long long tile_max = c->P.tile_nodes == 0 ? 1050625 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
   const bool fused2d = c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP);
@@ -743,6 +744,32 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
     launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
     launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
   }
+}
+
+// The ascending half of a visit of level l >= 2: the coarse correction (current buffer of
+// level l-1) added with omega_l (energy-optimal with MG_FLAG_ADAPTIVE_CORR), then the
+// post-smoothing sweeps; the correction is folded into the first fused red-black sweep.
+template <typename T>
+static void ascend(Sched &S, int l, const T *g, int transposed) {
+  mg_ctx *c = S.c;
+  LevData<T> &Dc = LevOf<T>::data(c, l - 1);
+  Lev<T> Lc = LevOf<T>::get(c, l - 1);
+  int npost = transposed ? c->P.nu1 : c->P.nu2;
+  int order = transposed ? 1 : 0;
+  if (adaptive_corr(c)) emit_adapt<T>(S, l, g);
+  smooth<T>(S, l, g, npost, order, false, &Lc, Dc.u[c->cur[l - 1]]);
+}
+
+// One cycle at level l on (u = current buffer of level l, g).  type 0 = F, 1 = V.
+template <typename T>
+static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool zero_start) {
+  mg_ctx *c = S.c;
+  if (l == 1) {
+    coarse_solve<T>(S, g);
+    return;
+  }
+  LevData<T> &Dc = LevOf<T>::data(c, l - 1);
+  descend<T>(S, l, g, transposed, zero_start);
   c->cur[l - 1] = 0;
   if (l - 1 == c->lcut) {
     // the whole coarse correction below level l in one single-CTA launch
@@ -754,8 +781,7 @@ static void cycle(Sched &S, int l, const T *g, int type, int transposed, bool ze
   } else {
     cycle<T>(S, l - 1, Dc.g, 1, transposed, true);
   }
-  if (adaptive_corr(c)) emit_adapt<T>(S, l, g);
-  smooth<T>(S, l, g, npost, order, false, &Lc, Dc.u[c->cur[l - 1]]);
+  ascend<T>(S, l, g, transposed);
 }
 
 // Ensure the finest level's current buffer is buffer 0 at the end of a cycle.
@@ -1152,6 +1178,147 @@ static mg_status setup_levels(mg_ctx *c) {
   if (st) return st;
   CK(cudaStreamSynchronize(c->stream));
   return MG_OK;
+}
+
+// ---- single steps ---------------------------------------------------------------------
+// Each runs the kernels the cycle runs, in the context's precision: FP64 contexts on the FP64
+// level arrays, MG_MIXED contexts on the FP32 ones (inputs rounded to FP32 on the way in,
+// results widened to FP64 on the way out).
+template <typename T>
+static void pack_lvl(mg_ctx *c, const Launch &lc, int l, const double *src, T *dst) {
+  Lev<T> L = LevOf<T>::get(c, l);
+  if (c->swap) launch_pack_swapped<T>(lc, L, src, dst, 1);
+  else launch_pack<T>(lc, L, src, dst, 1);
+}
+template <typename T>
+static void unpack_lvl(mg_ctx *c, const Launch &lc, int l, const T *src, double *dst) {
+  Lev<T> L = LevOf<T>::get(c, l);
+  if (c->swap) launch_unpack_swapped<T>(lc, L, src, dst, 1.0);
+  else launch_unpack<T>(lc, L, src, dst, 1.0);
+}
+
+// the end of a step: wait, then report a launch error or a bounded wait that gave up
+static mg_status step_end(mg_ctx *c) {
+  CK(cudaStreamSynchronize(c->stream));
+  mg_status st = last_launch(c);
+  if (st) return st;
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->st + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) {
+    CK(cudaMemsetAsync(c->st + 2, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->err = "a bounded device wait gave up";
+    return MG_ETIMEOUT;
+  }
+  return MG_OK;
+}
+
+template <typename T>
+static mg_status step_smooth_t(mg_ctx *c, int level, const double *u, const double *g, double *out, int sweeps,
+                               int order) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level);
+  pack_lvl<T>(c, lc, level, u, D.u[0]);
+  pack_lvl<T>(c, lc, level, g, D.g);
+  c->cur[level] = 0;
+  Sched S{c, lc, false};
+  smooth<T>(S, level, D.g, sweeps, order ? 1 : 0, false);
+  unpack_lvl<T>(c, lc, level, D.u[c->cur[level]], out);
+  c->cur[level] = 0;
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_defect_t(mg_ctx *c, int level, const double *u, const double *g, double *r) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level);
+  pack_lvl<T>(c, lc, level, u, D.u[0]);
+  pack_lvl<T>(c, lc, level, g, D.g);
+  launch_defect<T>(lc, LevOf<T>::get(c, level), c->kind, D.u[0], D.g, D.r);
+  unpack_lvl<T>(c, lc, level, D.r, r);
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_restrict_t(mg_ctx *c, int level, const double *r, double *gc) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level), &Dc = LevOf<T>::data(c, level - 1);
+  pack_lvl<T>(c, lc, level, r, D.r);
+  launch_restrict<T>(lc, LevOf<T>::get(c, level), LevOf<T>::get(c, level - 1), D.r, Dc.g);
+  unpack_lvl<T>(c, lc, level - 1, Dc.g, gc);
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_prolong_t(mg_ctx *c, int level, const double *ec, const double *u, double *u_out, double w) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level), &Dc = LevOf<T>::data(c, level - 1);
+  pack_lvl<T>(c, lc, level - 1, ec, Dc.u[0]);
+  pack_lvl<T>(c, lc, level, u, D.u[0]);
+  launch_prolong_add<T>(lc, LevOf<T>::get(c, level), LevOf<T>::get(c, level - 1), Dc.u[0], D.u[0], (T)w);
+  unpack_lvl<T>(c, lc, level, D.u[0], u_out);
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_descend_t(mg_ctx *c, int level, const double *u, const double *g, double *u_out,
+                                double *gc, int transposed) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level), &Dc = LevOf<T>::data(c, level - 1);
+  if (u) pack_lvl<T>(c, lc, level, u, D.u[0]);
+  else CK(cudaMemsetAsync(D.u[0], 0, sizeof(T) * (size_t)c->geo[level].count, c->stream));
+  pack_lvl<T>(c, lc, level, g, D.g);
+  c->cur[level] = 0;
+  Sched S{c, lc, false};
+  descend<T>(S, level, D.g, transposed ? 1 : 0, u == nullptr);
+  unpack_lvl<T>(c, lc, level, D.u[c->cur[level]], u_out);
+  unpack_lvl<T>(c, lc, level - 1, Dc.g, gc);
+  c->cur[level] = 0;
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_ascend_t(mg_ctx *c, int level, const double *ec, const double *u, const double *g,
+                               double *u_out, int transposed) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, level), &Dc = LevOf<T>::data(c, level - 1);
+  pack_lvl<T>(c, lc, level - 1, ec, Dc.u[0]);
+  pack_lvl<T>(c, lc, level, u, D.u[0]);
+  pack_lvl<T>(c, lc, level, g, D.g);
+  c->cur[level] = 0;
+  c->cur[level - 1] = 0;
+  Sched S{c, lc, false};
+  ascend<T>(S, level, D.g, transposed ? 1 : 0);
+  unpack_lvl<T>(c, lc, level, D.u[c->cur[level]], u_out);
+  c->cur[level] = 0;
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_coarse_t(mg_ctx *c, const double *g, double *u) {
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, 1);
+  pack_lvl<T>(c, lc, 1, g, D.g);
+  CK(cudaMemsetAsync(D.u[0], 0, sizeof(T) * (size_t)c->geo[1].count, c->stream));
+  coarse_solve_into<T>(c, lc, D.g, D.u[0]);
+  unpack_lvl<T>(c, lc, 1, D.u[0], u);
+  return step_end(c);
+}
+
+template <typename T>
+static mg_status step_cycle_t(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed) {
+  int L = c->L;
+  Launch lc{c->stream, &c->launches};
+  LevData<T> &D = LevOf<T>::data(c, L);
+  pack_lvl<T>(c, lc, L, b, D.g);
+  pack_lvl<T>(c, lc, L, x, D.u[0]);
+  Sched S{c, lc, false};
+  c->cur[L] = 0;
+  cycle<T>(S, L, D.g, 0, transposed ? 1 : 0, false);
+  unpack_lvl<T>(c, lc, L, D.u[c->cur[L]], x_out);
+  c->cur[L] = 0;
+  return step_end(c);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1682,90 +1849,51 @@ mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au) {
   return last_launch(c);
 }
 
-static mg_status need_fp64(mg_ctx *c) {
-  if (!c) return MG_EINVAL;
-  if (c->mixed) return MG_EINVAL;
-  return MG_OK;
-}
-
 mg_status mg_step_smooth(mg_ctx *c, int level, const double *u, const double *g, double *out, int sweeps, int order) {
-  if (need_fp64(c) || level < 1 || level > c->L || !u || !g || !out || sweeps < 0) return MG_EINVAL;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> Lv = lev64(c, level);
-  LevData<double> &D = c->d64[level];
-  pack_in(c, lc,Lv, u, D.u[0], 1);
-  pack_in(c, lc,Lv, g, D.g, 1);
-  c->cur[level] = 0;
-  Sched S{c, lc, false};
-  smooth<double>(S, level, D.g, sweeps, order ? 1 : 0, false);
-  unpack_out(c, lc,Lv, D.u[c->cur[level]], out, 1.0);
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || level < 1 || level > c->L || !u || !g || !out || sweeps < 0) return MG_EINVAL;
+  return c->mixed ? step_smooth_t<float>(c, level, u, g, out, sweeps, order)
+                  : step_smooth_t<double>(c, level, u, g, out, sweeps, order);
 }
 
 mg_status mg_step_defect(mg_ctx *c, int level, const double *u, const double *g, double *r) {
-  if (need_fp64(c) || level < 1 || level > c->L || !u || !g || !r) return MG_EINVAL;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> Lv = lev64(c, level);
-  LevData<double> &D = c->d64[level];
-  pack_in(c, lc,Lv, u, D.u[0], 1);
-  pack_in(c, lc,Lv, g, D.g, 1);
-  launch_defect<double>(lc, Lv, c->kind, D.u[0], D.g, D.r);
-  unpack_out(c, lc,Lv, D.r, r, 1.0);
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || level < 1 || level > c->L || !u || !g || !r) return MG_EINVAL;
+  return c->mixed ? step_defect_t<float>(c, level, u, g, r) : step_defect_t<double>(c, level, u, g, r);
 }
 
 mg_status mg_step_restrict(mg_ctx *c, int level, const double *r, double *gc) {
-  if (need_fp64(c) || level < 2 || level > c->L || !r || !gc) return MG_EINVAL;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
-  pack_in(c, lc,F, r, c->d64[level].r, 1);
-  launch_restrict<double>(lc, F, C, c->d64[level].r, c->d64[level - 1].g);
-  unpack_out(c, lc,C, c->d64[level - 1].g, gc, 1.0);
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || level < 2 || level > c->L || !r || !gc) return MG_EINVAL;
+  return c->mixed ? step_restrict_t<float>(c, level, r, gc) : step_restrict_t<double>(c, level, r, gc);
 }
 
 mg_status mg_step_prolong(mg_ctx *c, int level, const double *ec, const double *u, double *u_out, double w) {
-  if (need_fp64(c) || level < 2 || level > c->L || !ec || !u || !u_out) return MG_EINVAL;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> F = lev64(c, level), C = lev64(c, level - 1);
-  pack_in(c, lc,C, ec, c->d64[level - 1].u[0], 1);
-  pack_in(c, lc,F, u, c->d64[level].u[0], 1);
-  launch_prolong_add<double>(lc, F, C, c->d64[level - 1].u[0], c->d64[level].u[0], w);
-  unpack_out(c, lc,F, c->d64[level].u[0], u_out, 1.0);
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || level < 2 || level > c->L || !ec || !u || !u_out) return MG_EINVAL;
+  return c->mixed ? step_prolong_t<float>(c, level, ec, u, u_out, w)
+                  : step_prolong_t<double>(c, level, ec, u, u_out, w);
+}
+
+mg_status mg_step_descend(mg_ctx *c, int level, const double *u, const double *g, double *u_out, double *gc,
+                          int transposed) {
+  if (!c || level < 2 || level > c->L || !g || !u_out || !gc) return MG_EINVAL;
+  return c->mixed ? step_descend_t<float>(c, level, u, g, u_out, gc, transposed)
+                  : step_descend_t<double>(c, level, u, g, u_out, gc, transposed);
+}
+
+mg_status mg_step_ascend(mg_ctx *c, int level, const double *ec, const double *u, const double *g, double *u_out,
+                         int transposed) {
+  if (!c || level < 2 || level > c->L || !ec || !u || !g || !u_out) return MG_EINVAL;
+  return c->mixed ? step_ascend_t<float>(c, level, ec, u, g, u_out, transposed)
+                  : step_ascend_t<double>(c, level, ec, u, g, u_out, transposed);
 }
 
 mg_status mg_step_coarse(mg_ctx *c, const double *g, double *u) {
-  if (need_fp64(c) || !g || !u) return MG_EINVAL;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> C = lev64(c, 1);
-  pack_in(c, lc,C, g, c->d64[1].g, 1);
-  CK(cudaMemsetAsync(c->d64[1].u[0], 0, sizeof(double) * (size_t)c->geo[1].count, c->stream));
-  coarse_solve_into<double>(c, lc, c->d64[1].g, c->d64[1].u[0]);
-  unpack_out(c, lc,C, c->d64[1].u[0], u, 1.0);
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || !g || !u) return MG_EINVAL;
+  return c->mixed ? step_coarse_t<float>(c, g, u) : step_coarse_t<double>(c, g, u);
 }
 
 mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_out, int transposed) {
-  if (need_fp64(c) || !x || !b || !x_out) return MG_EINVAL;
-  int L = c->L;
-  Launch lc{c->stream, &c->launches};
-  Lev<double> F = lev64(c, L);
-  pack_in(c, lc,F, b, c->d64[L].g, 1);
-  pack_in(c, lc,F, x, c->d64[L].u[0], 1);
-  Sched S{c, lc, false};
-  c->cur[L] = 0;
-  if (transposed) cycle<double>(S, L, c->d64[L].g, 0, 1, false);
-  else cycle<double>(S, L, c->d64[L].g, 0, 0, false);
-  unpack_out(c, lc,F, c->d64[L].u[c->cur[L]], x_out, 1.0);
-  c->cur[L] = 0;
-  CK(cudaStreamSynchronize(c->stream));
-  return last_launch(c);
+  if (!c || !x || !b || !x_out) return MG_EINVAL;
+  return c->mixed ? step_cycle_t<float>(c, x, b, x_out, transposed)
+                  : step_cycle_t<double>(c, x, b, x_out, transposed);
 }
 
 mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *bytes_per_launch) {

@@ -247,6 +247,8 @@ void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra
                  T *s3);
 
 int norm_parts_count();
+// a reduction over rows of this many unknowns fits in nparts block partial sums
+bool norm_shape_ok(long long xunknowns, int nparts);
 void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq);
 
 // coarsest grid: u = A^{-1} g with a dense inverse (FP64), I/O in T

@@ -60,6 +60,8 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_params *p, const mg_coeff
   if (n0 < 3 || n1 < (p->periodic_y ? 2 : 3) || (p->dim == 3 && n2 < 3)) return MG_EINVAL;
   if (p->periodic_y && (n1 % 2)) return MG_EINVAL;
   if ((long long)n0 * n1 * n2 > MG_NOALLOC_MAX_NODES) return MG_EINVAL;
+  // one partial sum per block of 32 x-unknowns (at least) must fit in the array
+  if (!norm_shape_ok(n0 - 2, kNoallocParts)) return MG_EINVAL;
   double *scratch = nullptr;
   mg_status st = scratch_for_current_device(&scratch);
   if (st) return st;

@@ -102,3 +102,34 @@ def test_finite_differences_lognormal_1025(precision):
     scale = np.abs(g).max()
     print(f"{precision}: max |FD - adjoint| / max |grad| over 64 cells = {max(errs) / scale:.2e}")
     assert max(errs) <= 1e-5 * scale
+
+
+GRAD_CASES = [
+    # dim, n, periodic, smoother (zebra_y on a non-periodic cell problem runs axis-swapped)
+    (2, (129, 65), False, "rbgs"),
+    (2, (129, 64), True, "rbgs"),
+    (2, (65, 129), False, "zebra_y"),
+    (3, (33, 17, 33), False, "rbgs"),
+    (3, (17, 16, 17), True, "jacobi"),
+]
+
+
+@pytest.mark.parametrize("dim,n,per,sm", GRAD_CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gradient_kernel_matches_oracle_on_the_same_fields(dim, n, per, sm, precision):
+    """mg_grad_coeff and the oracle's gradient on the same u and lambda (no solve in between):
+    dL/dk_c = -sum over the cell's edges of (dw_e/dk_c)(u_p - u_q)(lambda_p - lambda_q), within
+    1e-12 of the array max.  The gradient is an FP64 kernel in both precisions."""
+    from paper_0805_3041_gb300.binding import Solver
+    from test_gpu_parity import spec_of, oracle_of
+    rng = np.random.default_rng(sum(n) + 5 * per + dim)
+    sp = spec_of(dim, n, per, inputs.CELL, rng)
+    o = oracle_of(sp, 2, sm, 1.0)
+    s = Solver(sp, levels=2, smoother=sm, omega=1.0, precision=precision, max_cycles=4)
+    for trial in range(2):
+        u = rng.standard_normal(o.shape()) * o.unknown_mask()
+        lam = rng.standard_normal(o.shape()) * o.unknown_mask()
+        got = s.grad_coeff(u, lam).cpu().numpy()
+        want = o.grad_k(u, lam)
+        assert got.shape == want.shape
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()

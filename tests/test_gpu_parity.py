@@ -134,6 +134,29 @@ def test_transfers(pair):
         assert rel(s.prolong_add(e, u, 0.9, lf), o.prolong_add(e, u, 0.9, lf)) <= TOL64
 
 
+@pytest.mark.parametrize("transposed", [False, True])
+def test_visit_halves(pair, transposed):
+    """The two halves of a level visit as the cycle runs them (fused sweep + defect +
+    restriction kernels included): pre-smoothing from u or from zero then R(g - A u);
+    correction u + P ec then post-smoothing."""
+    sp, o, s, rng = pair
+    nu_pre = 2   # nu1 = nu2 = 2 in every case
+    order = 1 if transposed else 0
+    for l in sorted({o.levels, 2}):
+        m = o.unknown_mask(l)
+        u = rng.standard_normal(o.shape(l)) * m
+        g = rng.standard_normal(o.shape(l))
+        for start in ("u", "zero"):
+            u0 = u if start == "u" else None
+            uo, gc = s.descend(u0, g, l, transposed=transposed)
+            ref = o.smooth(u if start == "u" else o.zeros(l), g, nu_pre, order, l)
+            assert rel(uo, ref) <= TOL64, (l, start)
+            assert rel(gc, o.restrict(o.defect(ref, g, l), l)) <= TOL64, (l, start)
+        ec = rng.standard_normal(o.shape(l - 1)) * o.unknown_mask(l - 1)
+        ref = o.smooth(o.prolong_add(ec, u, 1.0, l), g, nu_pre, order, l)
+        assert rel(s.ascend(ec, u, g, l, transposed=transposed), ref) <= TOL64, l
+
+
 def test_coarse_solve(pair):
     sp, o, s, rng = pair
     g = rng.standard_normal(o.shape(1)) * o.unknown_mask(1)
