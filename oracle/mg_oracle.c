@@ -51,6 +51,8 @@ typedef struct {
   double h[3], c[3];
   double *sx, *sy, *sz, *k;   /* owned copies of the coefficients of this level */
   double *ex, *ey, *ez;       /* OR_EDGE: per-node weights of the +x, +y, +z edges */
+  double *st9;                /* Galerkin coarse levels (2-D): the 9-point stencil of every node,
+                                 st9[9 p + 3 (b + 1) + (a + 1)] = A(p, p + (a, b)); NULL otherwise */
   double *u, *g, *r;          /* work vectors of this level (full node arrays) */
   long nsmooth;
 } lev_t;
@@ -61,6 +63,7 @@ struct or_hier {
   int smoother, nu1, nu2, coarse_mode, coarse_sweeps, dense_max;
   double omega, omega_corr;
   int adaptive_corr;
+  int galerkin;
   /* coarsest-grid direct solver */
   int nc;                     /* number of coarsest unknowns */
   size_t *cidx;               /* node index of each coarsest unknown */
@@ -122,8 +125,16 @@ static double wz_edge(const lev_t *v, int i, int j, int k) { /* (i,j,k)-(i,j,k+1
          (4.0 * v->h[2] * v->h[2]);
 }
 
-/* (A u)_p = sum over the edges at p of w_e (u_p - u_q) */
+/* (A u)_p = sum over the edges at p of w_e (u_p - u_q); on a Galerkin level the sum over the
+ * 9-point stencil, sum_{a,b} A(p, p + (a, b)) u_{p + (a, b)} */
 static double apply_at(const lev_t *v, const double *u, int i, int j, int k) {
+  if (v->st9) {
+    const double *a9 = v->st9 + 9 * nid(v, i, j, k);
+    double s9 = 0.0;
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) s9 += a9[3 * (b + 1) + (a + 1)] * val(v, u, i + a, j + b, k);
+    return s9;
+  }
   double up = u[nid(v, i, j, k)], s = 0.0;
   s += wx_edge(v, i - 1, j, k) * (up - val(v, u, i - 1, j, k));
   s += wx_edge(v, i, j, k) * (up - val(v, u, i + 1, j, k));
@@ -137,6 +148,7 @@ static double apply_at(const lev_t *v, const double *u, int i, int j, int k) {
 }
 /* D_p = sum of the weights of the edges at p (Dirichlet edges included) */
 static double diag_at(const lev_t *v, int i, int j, int k) {
+  if (v->st9) return v->st9[9 * nid(v, i, j, k) + 4];
   double s = wx_edge(v, i - 1, j, k) + wx_edge(v, i, j, k) + wy_edge(v, i, ywrap(v, j - 1), k) + wy_edge(v, i, j, k);
   if (v->dim == 3) s += wz_edge(v, i, j, k - 1) + wz_edge(v, i, j, k);
   return s;
@@ -225,6 +237,20 @@ static void halfsweep_rb(const lev_t *v, double *u, const double *g, double omeg
   OR_PAR_ROWS
   FOR_NODES(v) {
     if (!is_unk(v, i, j, k) || ((i + j + k) & 1) != colour) continue;
+    size_t p = nid(v, i, j, k);
+    u[p] += omega * (g[p] - apply_at(v, u, i, j, k)) / diag_at(v, i, j, k);
+  }
+}
+
+/* Gauss-Seidel on a Galerkin level (9-point stencil): nodes of one of the four colours
+ * (i mod 2, j mod 2) = (ci, cj) at a time, each corrected with the current iterate.  Nodes of one
+ * colour lie two apart and do not couple, and the two colours with i + j even (odd) together
+ * make up the red (black) nodes of the red-black order; on a 5-point level the four-colour
+ * order is the red-black one. */
+static void quartersweep(const lev_t *v, double *u, const double *g, double omega, int ci, int cj) {
+  OR_PAR_ROWS
+  FOR_NODES(v) {
+    if (!is_unk(v, i, j, k) || (i & 1) != ci || (j & 1) != cj) continue;
     size_t p = nid(v, i, j, k);
     u[p] += omega * (g[p] - apply_at(v, u, i, j, k)) / diag_at(v, i, j, k);
   }
@@ -324,6 +350,16 @@ static void lev_smooth(or_hier *H, lev_t *v, double *u, const double *g, int swe
     switch (H->smoother) {
       case OR_JACOBI: sweep_jacobi(v, u, g, H->omega, v->r); break;
       case OR_RBGS:
+        if (v->st9) {
+          /* red = colours (0,0), (1,1), black = (1,0), (0,1); the black-first order is the exact
+           * reverse of the red-first one, so the transposed cycle stays the adjoint */
+          static const int seq[4][2] = {{0, 0}, {1, 1}, {1, 0}, {0, 1}};
+          for (int q = 0; q < 4; ++q) {
+            const int *c = seq[first ? 3 - q : q];
+            quartersweep(v, u, g, H->omega, c[0], c[1]);
+          }
+          break;
+        }
         halfsweep_rb(v, u, g, H->omega, first);
         halfsweep_rb(v, u, g, H->omega, 1 - first);
         break;
@@ -475,6 +511,54 @@ static int coarsen(const lev_t *f, lev_t *c) {
           c->k[((size_t)K * cy + J) * cx + I] = s / (nz * 4.0);
         }
   }
+  return OR_OK;
+}
+
+/* A(p, p + (a, b)) of level v at unknown p = (i, j), 0 when p + (a, b) is not an unknown */
+static double a_entry(const lev_t *v, int i, int j, int a, int b) {
+  if (!is_unk(v, i + a, j + b, 0)) return 0.0;
+  if (v->st9) return v->st9[9 * nid(v, i, j, 0) + 3 * (b + 1) + (a + 1)];
+  if (a == 0 && b == 0) return diag_at(v, i, j, 0);
+  if (b == 0) return -(a > 0 ? wx_edge(v, i, j, 0) : wx_edge(v, i - 1, j, 0));
+  if (a == 0) return -(b > 0 ? wy_edge(v, i, j, 0) : wy_edge(v, i, j - 1, 0));
+  return 0.0;
+}
+
+/* Galerkin coarse operator A_c = R A P (2-D, y not periodic), R full weighting and P = 4 R^T
+ * bilinear interpolation over the unknowns: for every coarse unknown P and offset (al, be),
+ *   A_c(P, P + (al, be)) = sum_p R(P, p) sum_q A(p, q) P(q, P + (al, be)),
+ * p over the fine unknowns with |p - 2P| <= 1 (weights w1 x w1), q over the fine stencil of p,
+ * and P(q, Q) = (2 w1(q_x - 2 Q_x)) (2 w1(q_y - 2 Q_y)) when |q - 2Q| <= 1 in both directions
+ * (0 otherwise, and 0 when Q is not an unknown).  The coarse stencil reaches one coarse node
+ * in each direction: 9 points. */
+static int galerkin_coarse(const lev_t *f, lev_t *c) {
+  c->st9 = (double *)calloc(9 * nodes(c), sizeof(double));
+  if (!c->st9) return OR_ENOMEM;
+  for (int J = 1; J < c->n[1] - 1; ++J)
+    for (int I = 1; I < c->n[0] - 1; ++I) {
+      double *out = c->st9 + 9 * nid(c, I, J, 0);
+      for (int be = -1; be <= 1; ++be)
+        for (int al = -1; al <= 1; ++al) {
+          const int QI = I + al, QJ = J + be;
+          if (!is_unk(c, QI, QJ, 0)) continue;
+          double s = 0.0;
+          for (int pb = -1; pb <= 1; ++pb)
+            for (int pa = -1; pa <= 1; ++pa) {
+              const int pi = 2 * I + pa, pj = 2 * J + pb;
+              if (!is_unk(f, pi, pj, 0)) continue;
+              double t = 0.0;
+              for (int qb = -1; qb <= 1; ++qb)
+                for (int qa = -1; qa <= 1; ++qa) {
+                  const int qi = pi + qa, qj = pj + qb;
+                  const int dx = qi - 2 * QI, dy = qj - 2 * QJ;
+                  if (dx < -1 || dx > 1 || dy < -1 || dy > 1) continue;
+                  t += a_entry(f, pi, pj, qa, qb) * (2.0 * w1(dx)) * (2.0 * w1(dy));
+                }
+              s += w1(pa) * w1(pb) * t;
+            }
+          out[3 * (be + 1) + (al + 1)] = s;
+        }
+    }
   return OR_OK;
 }
 
@@ -737,7 +821,7 @@ void or_grad_k(const or_hier *H, const double *u, const double *lam, double *dk)
 
 static void free_level(lev_t *v) {
   free(v->sx); free(v->sy); free(v->sz); free(v->k);
-  free(v->ex); free(v->ey); free(v->ez);
+  free(v->ex); free(v->ey); free(v->ez); free(v->st9);
   free(v->u); free(v->g); free(v->r);
   memset(v, 0, sizeof(*v));
 }
@@ -769,6 +853,13 @@ int or_create(const or_config *cfg, or_hier **out) {
   H->nu2 = cfg->nu2;
   H->omega_corr = cfg->omega_corr;
   H->adaptive_corr = cfg->adaptive_corr ? 1 : 0;
+  H->galerkin = cfg->galerkin ? 1 : 0;
+  /* Galerkin coarse operators: 2-D, y not periodic, point smoothers (the 9-point stencils have
+   * no tridiagonal line part in the paper's sense) */
+  if (H->galerkin && (cfg->dim != 2 || cfg->periodic_y || (cfg->smoother != OR_JACOBI && cfg->smoother != OR_RBGS))) {
+    or_destroy(H);
+    return OR_EINVAL;
+  }
   H->coarse_mode = cfg->coarse_mode;
   H->coarse_sweeps = cfg->coarse_sweeps;
   H->dense_max = cfg->dense_max > 0 ? cfg->dense_max : 1024;
@@ -810,6 +901,7 @@ int or_create(const or_config *cfg, or_hier **out) {
   }
   for (int l = H->L - 1; l >= 1; --l) {
     int st = coarsen(&H->lev[l + 1], &H->lev[l]);
+    if (!st && H->galerkin) st = galerkin_coarse(&H->lev[l + 1], &H->lev[l]);
     if (st) { or_destroy(H); return st; }
   }
   for (int l = 1; l <= H->L; ++l) {
@@ -858,6 +950,12 @@ void or_level_coeffs(const or_hier *H, int l, double *out) {
   memcpy(out, v->k, sizeof(double) * nk);
 }
 void or_apply(const or_hier *H, int l, const double *u, double *Au) { lev_apply(&H->lev[l], u, Au); }
+int or_level_stencil(const or_hier *H, int l, double *out) {
+  const lev_t *v = &H->lev[l];
+  if (!v->st9) return OR_EINVAL;
+  memcpy(out, v->st9, sizeof(double) * 9 * nodes(v));
+  return OR_OK;
+}
 int or_threads(void) {
 #ifdef OR_THREADED
   return omp_get_max_threads();

@@ -60,6 +60,9 @@ typedef struct {
   const double *ex;   /* OR_EDGE: full node arrays, x fastest: ex[p] = weight of the edge from node */
   const double *ey;   /* p to its +x neighbour, ey[p] to +y (periodic: the last row's edge wraps to */
   const double *ez;   /* row 0), ez[p] to +z (3-D); entries with no such edge are ignored */
+  int galerkin;       /* 1: every coarse operator is the Galerkin product R A P of the next finer
+                         one (a 9-point stencil; 2-D, y not periodic, Jacobi or Gauss-Seidel, the
+                         latter in four colours (i mod 2, j mod 2) on those levels) */
 } or_config;
 
 typedef struct or_hier or_hier;
@@ -97,6 +100,9 @@ void or_thomas(int m, const double *lo, const double *di, const double *up,
 void or_cyclic_thomas(int m, const double *lo, const double *di, const double *up,
                       const double *d, double *x);
 void or_counts(const or_hier *H, long *smooth_sweeps, long *coarse_solves);
+/* Galerkin levels: the 9-point stencil of every node, out[9 p + 3 (b + 1) + (a + 1)] =
+ * A(p, p + (a, b)); OR_EINVAL on a level without one */
+int  or_level_stencil(const or_hier *H, int l, double *out);
 /* threads the grid loops run on: 1, or the OpenMP thread count of the threaded build */
 int  or_threads(void);
 void or_reset_counts(or_hier *H);

@@ -64,7 +64,8 @@ class _Config(C.Structure):
                 ("levels", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("omega_corr", C.c_double),
                 ("coarse_mode", C.c_int), ("coarse_sweeps", C.c_int), ("dense_max", C.c_int),
-                ("adaptive_corr", C.c_int), ("ex", C.c_void_p), ("ey", C.c_void_p), ("ez", C.c_void_p)]
+                ("adaptive_corr", C.c_int), ("ex", C.c_void_p), ("ey", C.c_void_p), ("ez", C.c_void_p),
+                ("galerkin", C.c_int)]
 
 
 _libs = {}
@@ -108,6 +109,8 @@ def lib(threaded: bool = False):
         L.or_cyclic_thomas.argtypes = [C.c_int, P, P, P, P, P]
         L.or_counts.argtypes = [P, P, C.POINTER(C.c_long)]
         L.or_reset_counts.argtypes = [P]
+        L.or_level_stencil.argtypes = [P, C.c_int, P]
+        L.or_level_stencil.restype = C.c_int
         L.or_threads.argtypes = []
         L.or_threads.restype = C.c_int
         _libs[threaded] = L
@@ -157,7 +160,7 @@ class Oracle:
 
     def __init__(self, prob: Problem, levels=2, smoother="rbgs", omega=1.0, nu1=2, nu2=2,
                  omega_corr=1.0, coarse_mode=COARSE_EXACT, coarse_sweeps=2, dense_max=1024,
-                 adaptive_corr=False, threaded=False):
+                 adaptive_corr=False, threaded=False, galerkin=False):
         self.prob = prob
         self._L = lib(threaded)
         cfg = _Config()
@@ -182,6 +185,7 @@ class Oracle:
         cfg.coarse_sweeps = coarse_sweeps
         cfg.dense_max = dense_max
         cfg.adaptive_corr = int(bool(adaptive_corr))
+        cfg.galerkin = int(bool(galerkin))
         h = C.c_void_p()
         st = self._L.or_create(C.byref(cfg), C.byref(h))
         if st != OK:
@@ -333,6 +337,14 @@ class Oracle:
             cy = n[1] if p.periodic_y else n[1] - 1
             out = np.zeros((n[0] - 1) * cy * (n[2] - 1 if p.dim == 3 else 1))
         self._L.or_level_coeffs(self._h, l, _ptr(out))
+        return out
+
+    def stencil(self, l):
+        """The 9-point stencil of a Galerkin level: array (..., 3, 3) over the node shape with
+        [.., b + 1, a + 1] = A(p, p + (a, b))."""
+        out = np.zeros(self.shape(l) + (3, 3))
+        if self._L.or_level_stencil(self._h, l, _ptr(out)) != OK:
+            raise ValueError(f"level {l} has no 9-point stencil")
         return out
 
     def counts(self):

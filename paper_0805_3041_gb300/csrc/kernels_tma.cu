@@ -37,6 +37,12 @@ constexpr int RING = 8;                // row slots (power of two)
 constexpr int RING_LOG = 3;
 constexpr int SEGW = 128 * NW + 8;     // floats per fine row segment: 4 + 512 + 4
 constexpr int CSEGW = 64 * NW + 8;     // floats per coarse row segment: 4 + 256 + 4
+// A ring slot of the sweep holds the row's g segment, after its u segment unless the iterate
+// starts at zero (mode 1, u is not read), then in mode 2 the two coarse rows of e.
+__host__ __device__ constexpr int slot_floats(int mode) {
+  return (mode == 1 ? SEGW : 2 * SEGW) + (mode == 2 ? 2 * CSEGW : 0);
+}
+__host__ __device__ constexpr int g_offset(int mode) { return mode == 1 ? 0 : SEGW; }
 // waits are bounded by the SM's cycle counter (a register read; 2^30 cycles is about 0.5 s)
 constexpr long long WAIT_CYCLES = 1ll << 30;    // give up a wait after this many cycles
 constexpr long long DRAIN_CYCLES = 1ll << 28;   // and drain each copy for at most this many
@@ -131,7 +137,8 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
                                            int first, const Lev<float> C, const float *__restrict__ ec,
                                            float omega_corr, int j0, int j1, int s0, float *ring, uint64_t *full,
                                            uint64_t *empty, int *err, int *inject) {
-  constexpr int SLOT = 2 * SEGW + (MODE == 2 ? 2 * CSEGW : 0);   // floats per ring slot
+  constexpr int SLOT = slot_floats(MODE);   // floats per ring slot
+  constexpr int GOFF = g_offset(MODE), EOFF = 2 * SEGW;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sw = s0 + 128 * warp;             // first column of the warp's strip
@@ -209,11 +216,11 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     mbar_expect_tx(bar, bytes);
     const long long ro = (long long)jw * L.pitch;
     if (MODE != 1) tma_load_1d(slot + doff, u + ro + cs, seg_bytes, bar);
-    tma_load_1d(slot + SEGW + doff, g + ro + cs, seg_bytes, bar);
+    tma_load_1d(slot + GOFF + doff, g + ro + cs, seg_bytes, bar);
     if (corr) {
-      tma_load_1d(slot + 2 * SEGW + cdoff, ec + (long long)J0 * C.pitch + ccs, cseg_bytes, bar);
+      tma_load_1d(slot + EOFF + cdoff, ec + (long long)J0 * C.pitch + ccs, cseg_bytes, bar);
       if (J1 != J0)
-        tma_load_1d(slot + 2 * SEGW + CSEGW + cdoff, ec + (long long)J1 * C.pitch + ccs, cseg_bytes, bar);
+        tma_load_1d(slot + EOFF + CSEGW + cdoff, ec + (long long)J1 * C.pitch + ccs, cseg_bytes, bar);
     }
   };
   // ---- producer warp (lane 0): every streamed row in order, each into its slot once all
@@ -279,7 +286,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
       // omega_l P e at the thread's columns: i >> 1 and (i + 1) >> 1 sit at coarse-segment
       // positions 4 + 64 warp + 2 lane + {0, 1, 2}
       const int jw = wrap(j);
-      const float *e0 = slot + 2 * SEGW, *e1 = ((jw & 1) ? e0 + CSEGW : e0);
+      const float *e0 = slot + EOFF, *e1 = ((jw & 1) ? e0 + CSEGW : e0);
       const int q = 4 + 64 * warp + 2 * lane;
       const float2 a0 = *reinterpret_cast<const float2 *>(e0 + q), a1 = *reinterpret_cast<const float2 *>(e1 + q);
       const float sq[3] = {a0.x + a1.x, a0.y + a1.y, e0[q + 2] + e1[q + 2]};
@@ -300,7 +307,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
   // first colour of row j relaxed from the old rows j-1, j, j+1 (row j lies in the grid)
   auto half_row = [&](HRow &H, const URow &Rm, const URow &R, const URow &Rp, int j) {
     const float *slot = slot_of(j);
-    const float4 g4 = *reinterpret_cast<const float4 *>(slot + SEGW + c0);
+    const float4 g4 = *reinterpret_cast<const float4 *>(slot + GOFF + c0);
     const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
     if (MODE == 1) {
       // zero iterate: the residual of a first-colour node is g, its new value omega/D g
@@ -309,7 +316,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
       const int p = (first + j) & 1;
 #pragma unroll
       for (int e = 0; e < 4; ++e) H.h[e] = (rowu && K.act[e] && (e & 1) == p) ? fmaf(K.O[e], gg[e], 0.f) : 0.f;
-      H.ho = (oact && rowu && (((io + j) & 1) == first)) ? fmaf(oO, slot[SEGW + co], 0.f) : 0.f;
+      H.ho = (oact && rowu && (((io + j) & 1) == first)) ? fmaf(oO, slot[GOFF + co], 0.f) : 0.f;
       return;
     }
     float left = __shfl_up_sync(FULL, R.u[3], 1), right = __shfl_down_sync(FULL, R.u[0], 1);
@@ -320,7 +327,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     else relax_colour<0>(H.h, R.u, left, right, Rm.u, Rp.u, gg, K, rowu);
     H.ho = R.out;
     if (oact && rowu && (((io + j) & 1) == first)) {
-      const float gout = slot[SEGW + co];
+      const float gout = slot[GOFF + co];
       const float w_ = lane == 0 ? R.out2 : R.u[3], e_ = lane == 0 ? R.u[0] : R.out2;
       float s = fmaf(-oD, R.out, gout);
       s = fmaf(oW, w_, s);
@@ -332,7 +339,7 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
   };
   // second colour of row j from the half-relaxed rows j-1, j, j+1; store the row
   auto out_row = [&](const HRow &Hm, const HRow &Hc, const HRow &Hp, int j) {
-    const float4 g4 = *reinterpret_cast<const float4 *>(slot_of(j) + SEGW + c0);
+    const float4 g4 = *reinterpret_cast<const float4 *>(slot_of(j) + GOFF + c0);
     const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
     float hl = __shfl_up_sync(FULL, Hc.h[3], 1), hr = __shfl_down_sync(FULL, Hc.h[0], 1);
     if (lane == 0) hl = Hc.ho;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
                                                       float omega, int first, Lev<float> C,
                                                       const float *__restrict__ ec, float omega_corr, int RC,
                                                       int ngroups, int *err, int *inject) {
-  constexpr int SLOT = 2 * SEGW + (MODE == 2 ? 2 * CSEGW : 0);
+  constexpr int SLOT = slot_floats(MODE);
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float *ring = reinterpret_cast<float *>(tma_smem);
   uint64_t *full = reinterpret_cast<uint64_t *>(ring + RING * SLOT);
@@ -721,7 +728,7 @@ bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev
 }
 
 size_t rb2d_tma_smem(int mode) {
-  const int slot = 2 * SEGW + (mode == 2 ? 2 * CSEGW : 0);
+  const int slot = slot_floats(mode);
   return (size_t)RING * slot * sizeof(float) + 2 * RING * sizeof(uint64_t);
 }
 

@@ -1166,3 +1166,172 @@ def test_threaded_oracle_is_bit_identical(smoother, kind, periodic_y, dim):
     assert np.array_equal(x, y)
     assert np.array_equal(a.defect(x, f), b.defect(y, f))
     assert orc.threads(True) >= 1 and orc.threads(False) == 1
+
+
+# --------------------------------------------------------------------------------------
+# Galerkin coarse operators A_c = R A P (2-D)
+# --------------------------------------------------------------------------------------
+
+def _interp_1d(nf):
+    """Linear interpolation between the unknowns of a coarse and a fine 1-D Dirichlet grid
+    (nf nodes -> (nf - 1) / 2 + 1): fine unknown 2I takes coarse I, 2I +- 1 half of it."""
+    nc = (nf - 1) // 2 + 1
+    P = np.zeros((nf - 2, nc - 2))
+    for I in range(1, nc - 1):
+        P[2 * I - 1, I - 1] = 1.0
+        P[2 * I - 2, I - 1] = 0.5
+        P[2 * I, I - 1] = 0.5
+    return P
+
+
+def _dense_op(o, l):
+    """The oracle's operator on level l as a dense matrix over the unknowns (x fastest)."""
+    m = o.unknown_mask(l)
+    idx = np.flatnonzero(m)
+    A = np.zeros((idx.size, idx.size))
+    for c, p in enumerate(idx):
+        e = np.zeros(m.size)
+        e[p] = 1.0
+        A[:, c] = o.apply(e.reshape(m.shape), l).ravel()[idx]
+    return A
+
+
+def _cell_problem(n, rng, jump=False):
+    h = (1.0 / (n[0] - 1), 1.0 / (n[1] - 1), 1.0)
+    k = np.exp(rng.standard_normal((n[1] - 1, n[0] - 1)))
+    if jump:
+        k[: (n[1] - 1) // 2, : (n[0] - 1) // 2] *= 1e3
+    return orc.Problem(dim=2, n=(n[0], n[1], 1), kind=orc.CELL, h=h, k=k)
+
+
+def test_galerkin_poisson_stencil_closed_form():
+    """For the 5-point Laplacian, full weighting and bilinear interpolation, R A P is the 9-point
+    stencil (1/H^2) [[-1/4, -1/2, -1/4], [-1/2, 3, -1/2], [-1/4, -1/2, -1/4]], H = 2h (a textbook
+    result), at every coarse node whose stencil stays off the boundary."""
+    n = 33
+    h = 1.0 / (n - 1)
+    o = orc.Oracle(orc.Problem(dim=2, n=(n, n, 1), kind=orc.CONST, h=(h, h, 1), c=(1 / h ** 2, 1 / h ** 2, 0)),
+                   levels=3, galerkin=True, dense_max=4096)
+    st = o.stencil(2)
+    want = np.array([[-0.25, -0.5, -0.25], [-0.5, 3.0, -0.5], [-0.25, -0.5, -0.25]]) / (2 * h) ** 2
+    nc = o.dims(2)[0]
+    for J in range(2, nc - 2):
+        for I in range(2, nc - 2):
+            assert np.abs(st[J, I] - want).max() <= 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n", [(17, 9), (17, 17), (33, 17)])
+def test_galerkin_equals_dense_rap(n):
+    """The oracle's coarse operators on two coarser levels equal R A P built densely here from the
+    fine operator, bilinear P (Kronecker product of 1-D linear interpolation) and R = P^T / 4, for
+    a cell coefficient that varies from cell to cell."""
+    rng = np.random.default_rng(sum(n))
+    p = _cell_problem(n, rng)
+    o = orc.Oracle(p, levels=3, galerkin=True, dense_max=4096)
+    A = _dense_op(o, 3)
+    dims = [o.dims(3)]
+    for l in (2, 1):
+        nf = dims[-1]
+        P = np.kron(_interp_1d(nf[1]), _interp_1d(nf[0]))
+        A = (P.T / 4.0) @ A @ P
+        got = _dense_op(o, l)
+        assert np.abs(got - A).max() <= 1e-13 * np.abs(A).max(), l
+        assert np.abs(got - got.T).max() <= 1e-13 * np.abs(A).max()
+        dims.append(o.dims(l))
+
+
+def test_galerkin_two_grid_cycle_is_the_textbook_two_grid_method():
+    """Two grids, exact coarse solve: one cycle is x <- S^nu2(y + P A_c^-1 R (b - A y)), y = S^nu1(x),
+    with A_c = R A P formed densely here."""
+    rng = np.random.default_rng(5)
+    n = (17, 17)
+    p = _cell_problem(n, rng)
+    for sm, om in (("jacobi", 0.8), ("rbgs", 1.0)):
+        o = orc.Oracle(p, levels=2, smoother=sm, omega=om, nu1=2, nu2=1, galerkin=True, dense_max=4096)
+        m = o.unknown_mask()
+        idx = np.flatnonzero(m)
+        A = _dense_op(o, 2)
+        P = np.kron(_interp_1d(n[1]), _interp_1d(n[0]))
+        Ac = (P.T / 4.0) @ A @ P
+        b = rng.uniform(-1, 1, m.shape) * m
+        x = rng.uniform(-1, 1, m.shape) * m
+        y = o.smooth(x, b, 2, 0)
+        r = (b - o.apply(y)).ravel()[idx]
+        e = P @ np.linalg.solve(Ac, (P.T / 4.0) @ r)
+        z = y.copy().ravel()
+        z[idx] += e
+        want = o.smooth(z.reshape(m.shape), b, 1, 0)
+        got = o.cycle(x, b)
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), sm
+
+
+def test_galerkin_four_colour_gauss_seidel_invariant():
+    """omega = 1: after a Gauss-Seidel sweep on a Galerkin (9-point) level the residual vanishes at
+    the colour updated last, (0, 1) in red-first order and (0, 0) in black-first order, and at no
+    other colour."""
+    rng = np.random.default_rng(6)
+    p = _cell_problem((33, 33), rng)
+    o = orc.Oracle(p, levels=3, smoother="rbgs", omega=1.0, galerkin=True, dense_max=4096)
+    l = 2
+    m = o.unknown_mask(l)
+    jj, ii = np.indices(m.shape)
+    u = rng.standard_normal(m.shape) * m
+    g = rng.standard_normal(m.shape) * m
+    for order, last in ((0, (0, 1)), (1, (0, 0))):
+        r = o.defect(o.smooth(u, g, 1, order, l), g, l)
+        sel = m & (ii % 2 == last[0]) & (jj % 2 == last[1])
+        assert np.abs(r[sel]).max() <= 1e-12 * np.abs(g).max()
+        assert np.abs(r[m & ~sel]).max() > 1e-3 * np.abs(g).max()
+
+
+def test_galerkin_transposed_cycle_is_the_adjoint():
+    """<M b, c> = <b, M^T c> for 1 and 2 cycles from zero: the four-colour order reversed in the
+    transposed cycle is the exact transpose of the forward sweeps."""
+    rng = np.random.default_rng(7)
+    p = _cell_problem((33, 17), rng)
+    o = orc.Oracle(p, levels=3, smoother="rbgs", omega=1.0, nu1=2, nu2=1, galerkin=True, dense_max=4096)
+    m = o.unknown_mask()
+    b = rng.standard_normal(m.shape) * m
+    c = rng.standard_normal(m.shape) * m
+    for ncyc in (1, 2):
+        x, y = o.zeros(), o.zeros()
+        for _ in range(ncyc):
+            x = o.cycle(x, b)
+            y = o.cycle(y, c, transposed=True)
+        lhs, rhs = np.vdot(x, c), np.vdot(b, y)
+        assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
+
+
+@pytest.mark.parametrize("sm,om", [("jacobi", 0.8), ("rbgs", 1.0)])
+def test_galerkin_cycles_converge_to_the_dense_solution(sm, om):
+    """F-cycles on four Galerkin levels converge to the dense solution of a problem with a
+    coefficient jump of 1e3, where Galerkin coarse operators keep the jump's effect."""
+    rng = np.random.default_rng(8)
+    p = _cell_problem((33, 33), rng, jump=True)
+    o = orc.Oracle(p, levels=4, smoother=sm, omega=om, galerkin=True, dense_max=4096)
+    m = o.unknown_mask()
+    b = rng.uniform(-1, 1, m.shape) * m
+    x, st, cyc, rr, hist = o.solve(b, tol=1e-12, maxit=100)
+    assert st == orc.OK
+    A = _dense_op(o, 4)
+    idx = np.flatnonzero(m)
+    xd = np.linalg.solve(A, b.ravel()[idx])
+    assert np.abs(x.ravel()[idx] - xd).max() <= 1e-10 * np.abs(xd).max()
+    # and faster than rediscretised coarse operators on this jump
+    o2 = orc.Oracle(p, levels=4, smoother=sm, omega=om, dense_max=4096)
+    cyc2 = o2.solve(b, tol=1e-12, maxit=200)[2]
+    print(f"{sm}: Galerkin {cyc} cycles, rediscretised {cyc2}")
+    assert cyc < cyc2
+
+
+def test_galerkin_rejects_what_it_does_not_cover():
+    h = 1.0 / 16
+    p3 = orc.Problem(dim=3, n=(17, 17, 17), kind=orc.CONST, h=(h, h, h), c=(1, 1, 1))
+    with pytest.raises(ValueError):
+        orc.Oracle(p3, levels=2, galerkin=True)
+    p2 = orc.Problem(dim=2, n=(17, 16, 1), periodic_y=True, kind=orc.CONST, h=(h, h, 1), c=(1, 1, 0))
+    with pytest.raises(ValueError):
+        orc.Oracle(p2, levels=2, galerkin=True)
+    p1 = orc.Problem(dim=2, n=(17, 17, 1), kind=orc.CONST, h=(h, h, 1), c=(1, 1, 0))
+    with pytest.raises(ValueError):
+        orc.Oracle(p1, levels=2, smoother="zebra_x", galerkin=True)
