@@ -93,6 +93,14 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        the energy norm of the error (Wallis 2008, section "Multigrid"):
                                        omega_l = (g - A u, P e) / (A P e, P e) on the iterate u before
                                        the correction; omega_corr is ignored */
+#define MG_FLAG_GALERKIN        256u /* coarse operators by the Galerkin product A_{l-1} = R A_l P (full
+                                       weighting R, bilinear P) instead of rediscretisation: 9-point
+                                       stencils below the finest grid.  2-D, y not periodic, MG_JACOBI
+                                       or MG_RBGS (on the 9-point levels Gauss-Seidel runs in four
+                                       colours (i mod 2, j mod 2): (0,0), (1,1), (1,0), (0,1), the
+                                       transposed cycle in the reverse order), coarsest grid of at
+                                       most 4096 unknowns, not with MG_FLAG_ADAPTIVE_CORR; otherwise
+                                       MG_EINVAL.  The single-CTA coarse cycle is not used */
 #define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
                                        first single-precision TMA sweep is left out, so that the compute
                                        warps' bounded waits run out (about a second) and the solve returns

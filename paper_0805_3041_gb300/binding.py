@@ -22,6 +22,7 @@ FLAG_NO_GRAPH, FLAG_TIMING, FLAG_NO_FUSED_COARSE, FLAG_NO_FUSED_SWEEP, FLAG_NO_T
 FLAG_FMG_START = 32
 FLAG_ADAPTIVE_CORR = 64
 FLAG_TEST_WAIT_TIMEOUT = 128
+FLAG_GALERKIN = 256
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5

@@ -95,6 +95,32 @@ __global__ void __launch_bounds__(BX *BY) k_rb_half(Lev<T> L, T *u, const T *__r
 }
 
 // ---------------------------------------------------------------------------------------
+// Gauss-Seidel on a 2-D Galerkin level (9-point stencil), in place on the nodes of one of the
+// four colours (i mod 2, j mod 2) = (ci, cj): nodes of one colour are two apart in both
+// directions and share no stencil, so the update is race free.  Thread t of colour row q
+// handles node i = 2 + 2t - ci... written below as i = (ci ? 1 : 2) + 2t, row j = (cj ? 1 : 2) + 2q.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BX *BY) k_gs9_colour(Lev<T> L, T *u, const T *__restrict__ g, T omega, int ci,
+                                                       int cj, int R) {
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int i = (ci ? 1 : 2) + 2 * t;
+  if (i > L.n0 - 2) return;
+  const int jlo = cj ? 1 : 2;
+  const int nr = (L.n1 - 2 - jlo) / 2 + 1;   // rows j = jlo, jlo + 2, ... <= n1 - 2
+  const int q0 = (blockIdx.y * BY + threadIdx.y) * R;
+  for (int q = q0; q < q0 + R && q < nr; ++q) {
+    const int j = jlo + 2 * q;
+    long long p = (long long)j * L.pitch + i, dm, dp;
+    yoffs(L, j, dm, dp);
+    Weights<T, 2, K_NINE> w;
+    w.load(L, i, p, dm);
+    T s = residual_at<T, 2, K_NINE>(L, w, u, p, dm, dp, g[p]);
+    u[p] = fma(omega * w.dinv, s, u[p]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // defect r = g - A u
 // ---------------------------------------------------------------------------------------
 template <typename T, int DIM, int KIND>
@@ -416,12 +442,19 @@ __global__ void __launch_bounds__(BX *BY) k_grad_k(Lev<double> L, const double *
     }                                                                          \
   } while (0)
 
+// the same, with the 2-D Galerkin (9-point) levels: for the kernels that run on every kind of level
+#define DISPATCH_DK9(DIMV, KINDV, KERNEL, ...)                                 \
+  do {                                                                         \
+    if ((DIMV) == 2 && (KINDV) == K_NINE) KERNEL<T, 2, K_NINE> __VA_ARGS__;    \
+    else DISPATCH_DK(DIMV, KINDV, KERNEL, __VA_ARGS__);                        \
+  } while (0)
+
 template <typename T>
 void launch_jacobi(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega) {
   long long rows = L.unk_rows();
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  DISPATCH_DK(L.dim, kind, k_jacobi, <<<gr, bl, 0, lc.s>>>(L, u, g, out, omega, R));
+  DISPATCH_DK9(L.dim, kind, k_jacobi, <<<gr, bl, 0, lc.s>>>(L, u, g, out, omega, R));
   ++*lc.counter;
 }
 
@@ -430,7 +463,7 @@ void launch_jacobi_zero(const Lev<T> &L, int kind, const Launch &lc, const T *g,
   long long rows = L.unk_rows();
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  DISPATCH_DK(L.dim, kind, k_jacobi_zero, <<<gr, bl, 0, lc.s>>>(L, g, out, omega, R));
+  DISPATCH_DK9(L.dim, kind, k_jacobi_zero, <<<gr, bl, 0, lc.s>>>(L, g, out, omega, R));
   ++*lc.counter;
 }
 
@@ -444,11 +477,23 @@ void launch_rb_half(const Launch &lc, const Lev<T> &L, int kind, T *u, const T *
 }
 
 template <typename T>
+void launch_gs9_colour(const Launch &lc, const Lev<T> &L, T *u, const T *g, T omega, int ci, int cj) {
+  const int jlo = cj ? 1 : 2;
+  const long long rows = L.n1 - 2 >= jlo ? (L.n1 - 2 - jlo) / 2 + 1 : 0;
+  const long long xs = L.n0 - 2 >= (ci ? 1 : 2) ? (L.n0 - 2 - (ci ? 1 : 2)) / 2 + 1 : 0;
+  if (rows <= 0 || xs <= 0) return;
+  int R = rows_per_thread(rows);
+  dim3 gr = grid_for(xs, rows, R), bl(BX, BY);
+  k_gs9_colour<T><<<gr, bl, 0, lc.s>>>(L, u, g, omega, ci, cj, R);
+  ++*lc.counter;
+}
+
+template <typename T>
 void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *r) {
   long long rows = L.unk_rows();
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  DISPATCH_DK(L.dim, kind, k_defect, <<<gr, bl, 0, lc.s>>>(L, u, g, r, R));
+  DISPATCH_DK9(L.dim, kind, k_defect, <<<gr, bl, 0, lc.s>>>(L, u, g, r, R));
   ++*lc.counter;
 }
 
@@ -477,7 +522,7 @@ void launch_defect_norm(const Launch &lc, const Lev<T> &L, int kind, const T *u,
   long long rows = L.unk_rows();
   int R = norm_R(rows, L.xunk(), nparts);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
-  DISPATCH_DK(L.dim, kind, k_defect_norm, <<<gr, bl, 0, lc.s>>>(L, u, g, partials, R));
+  DISPATCH_DK9(L.dim, kind, k_defect_norm, <<<gr, bl, 0, lc.s>>>(L, u, g, partials, R));
   ++*lc.counter;
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
@@ -612,6 +657,7 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
   template void launch_jacobi<T>(const Launch &, const Lev<T> &, int, const T *, const T *, T *, T);         \
   template void launch_jacobi_zero<T>(const Lev<T> &, int, const Launch &, const T *, T *, T);              \
   template void launch_rb_half<T>(const Launch &, const Lev<T> &, int, T *, const T *, T, int);             \
+  template void launch_gs9_colour<T>(const Launch &, const Lev<T> &, T *, const T *, T, int, int);          \
   template void launch_defect<T>(const Launch &, const Lev<T> &, int, const T *, const T *, T *);           \
   template void launch_defect_norm<T>(const Launch &, const Lev<T> &, int, const T *, const T *, double *, int, \
                                       double *);                                                              \

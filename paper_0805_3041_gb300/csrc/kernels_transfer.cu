@@ -185,6 +185,17 @@ __global__ void k_assemble_dense(Lev<T> L, const long long *__restrict__ cidx, c
   Weights<T, DIM, KIND> w;
   w.load(L, i, p, dm);
   double *row = A + (long long)r * nc;
+  if (KIND == K_NINE) {   // 2-D Galerkin level: the 9-point stencil
+    row[r] += (double)w.dd;
+    const long long nb9[8] = {p - 1, p + 1, p + dm, p + dp, p + dm - 1, p + dm + 1, p + dp - 1, p + dp + 1};
+    const double w9[8] = {(double)w.wW, (double)w.wE, (double)w.wS, (double)w.wN,
+                          (double)w.wSW, (double)w.wSE, (double)w.wNW, (double)w.wNE};
+    for (int e = 0; e < 8; ++e) {
+      int c = cmap[nb9[e]];
+      if (c >= 0) row[c] -= w9[e];
+    }
+    return;
+  }
   double D = (double)w.wW + (double)w.wE + (double)w.wS + (double)w.wN;
   if (DIM == 3) D += (double)w.wB + (double)w.wF;
   row[r] += D;
@@ -201,7 +212,8 @@ void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const lo
                            int nc, double *A) {
   int th = 128, bl = (nc + th - 1) / th;
   if (L.dim == 2) {
-    if (kind == K_CONST) k_assemble_dense<T, 2, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    if (kind == K_NINE) k_assemble_dense<T, 2, K_NINE><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
+    else if (kind == K_CONST) k_assemble_dense<T, 2, K_CONST><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else if (kind == K_SEP) k_assemble_dense<T, 2, K_SEP><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else if (kind == K_CELL) k_assemble_dense<T, 2, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else k_assemble_dense<T, 2, K_EDGE><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
@@ -333,6 +345,87 @@ void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Galerkin coarse operator A_c = R A P (2-D, y not periodic): R full weighting, P = 4 R^T
+// bilinear interpolation, both over the unknowns.  For coarse unknown P and offset (al, be):
+//   A_c(P, P + (al, be)) = sum_p R(P, p) sum_q A(p, q) P(q, P + (al, be)),
+// p over the fine unknowns within one node of 2P (weights w(pa) w(pb), w(0) = 1/2, w(+-1) = 1/4),
+// q over the stencil of p, P(q, Q) = (2 w(dx)) (2 w(dy)) with (dx, dy) = q - 2Q within one node.
+// One thread per coarse node writes D, the +x, +y, +x+y, -x+y weights (w = -A) and 1/D;
+// nodes that are not unknowns, and couplings to them, get 0.
+
+// A(p, p + (a, b)) of fine level F at unknown p = (i, j); 0 if p + (a, b) is not an unknown
+template <int KIND>
+__device__ __forceinline__ double stencil_entry(const Lev<double> &F, int i, int j, int a, int b) {
+  const int qi = i + a, qj = j + b;
+  if (qi < 1 || qi > F.n0 - 2 || qj < 1 || qj > F.n1 - 2) return 0.0;
+  const long long p = (long long)j * F.pitch + i, dm = -F.pitch;
+  Weights<double, 2, KIND> w;
+  w.load(F, i, p, dm);
+  if (KIND == K_NINE) {
+    if (a == 0 && b == 0) return w.dd;
+    if (b == 0) return a > 0 ? -w.wE : -w.wW;
+    if (a == 0) return b > 0 ? -w.wN : -w.wS;
+    if (b > 0) return a > 0 ? -w.wNE : -w.wNW;
+    return a > 0 ? -w.wSE : -w.wSW;
+  }
+  if (a == 0 && b == 0) return KIND == K_CONST ? F.d : (w.wW + w.wE) + (w.wS + w.wN);
+  if (b == 0) return a > 0 ? -w.wE : -w.wW;
+  if (a == 0) return b > 0 ? -w.wN : -w.wS;
+  return 0.0;
+}
+
+__device__ __forceinline__ double fw1(int a) { return a == 0 ? 0.5 : 0.25; }
+
+template <int KIND>
+__global__ void k_rap(Lev<double> F, Lev<double> C, double *__restrict__ dg, double *__restrict__ ex,
+                      double *__restrict__ ey, double *__restrict__ ene, double *__restrict__ enw,
+                      double *__restrict__ dinv) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
+  if (I >= C.n0 || J >= C.n1) return;
+  const long long pc = (long long)J * C.pitch + I;
+  const bool unk = I >= 1 && I <= C.n0 - 2 && J >= 1 && J <= C.n1 - 2;
+  double a9[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if (unk) {
+    for (int be = -1; be <= 1; ++be)
+      for (int al = -1; al <= 1; ++al) {
+        const int QI = I + al, QJ = J + be;
+        if (QI < 1 || QI > C.n0 - 2 || QJ < 1 || QJ > C.n1 - 2) continue;
+        double s = 0.0;
+        for (int pb = -1; pb <= 1; ++pb)
+          for (int pa = -1; pa <= 1; ++pa) {
+            const int pi = 2 * I + pa, pj = 2 * J + pb;
+            if (pi < 1 || pi > F.n0 - 2 || pj < 1 || pj > F.n1 - 2) continue;
+            double t = 0.0;
+            for (int qb = -1; qb <= 1; ++qb)
+              for (int qa = -1; qa <= 1; ++qa) {
+                const int dx = pi + qa - 2 * QI, dy = pj + qb - 2 * QJ;
+                if (dx < -1 || dx > 1 || dy < -1 || dy > 1) continue;
+                t += stencil_entry<KIND>(F, pi, pj, qa, qb) * (2.0 * fw1(dx)) * (2.0 * fw1(dy));
+              }
+            s += fw1(pa) * fw1(pb) * t;
+          }
+        a9[be + 1][al + 1] = s;
+      }
+  }
+  dg[pc] = a9[1][1];
+  ex[pc] = -a9[1][2];
+  ey[pc] = -a9[2][1];
+  ene[pc] = -a9[2][2];
+  enw[pc] = -a9[2][0];
+  dinv[pc] = unk ? 1.0 / a9[1][1] : 0.0;
+}
+
+void launch_rap(const Launch &lc, const Lev<double> &F, int fkind, const Lev<double> &C, double *dg, double *ex,
+                double *ey, double *ene, double *enw, double *dinv) {
+  dim3 gr((C.n0 + 127) / 128, C.n1, 1);
+  if (fkind == K_CONST) k_rap<K_CONST><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
+  else if (fkind == K_SEP) k_rap<K_SEP><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
+  else if (fkind == K_CELL) k_rap<K_CELL><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
+  else if (fkind == K_EDGE) k_rap<K_EDGE><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
+  else k_rap<K_NINE><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
+  ++*lc.counter;
+}
+
 // edge coefficients: coarse weights edge by edge, and 1/D
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ double harm0(double a, double b) { return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0; }

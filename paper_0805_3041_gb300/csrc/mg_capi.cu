@@ -48,6 +48,7 @@ struct LevData {
   T *k = nullptr, *ndinv = nullptr;
   T *ex = nullptr, *ey = nullptr, *ez = nullptr;
   T *t = nullptr;   // third line-solve scratch array (y-lines across a periodic y)
+  T *dg = nullptr, *enw = nullptr;   // Galerkin levels: diagonal and -x+y weights (ex, ey, ez: +x, +y, +x+y)
 };
 
 struct LevGeom {
@@ -62,6 +63,7 @@ struct mg_ctx {
   mg_coeffs K;
   int L;
   int kind;
+  bool galerkin = false;   // MG_FLAG_GALERKIN: levels below the finest hold R A P (K_NINE)
   LevGeom geo[MAXLEV + 1];
   LevData<double> d64[MAXLEV + 1];
   LevData<float> d32[MAXLEV + 1];
@@ -117,6 +119,9 @@ struct mg_ctx {
   std::vector<double> ev_bytes;   // algorithmic bytes of the launch opened by each pool event
   std::string err;
 };
+
+// the operator form of level l: the context's coefficient kind, or K_NINE on Galerkin coarse levels
+static int lev_kind(const mg_ctx *c, int l) { return (c->galerkin && l < c->L) ? K_NINE : c->kind; }
 
 // rows padded to 128 elements: the marching kernels read 128-column strips with vector loads
 static size_t padded_pitch(int n0) { return (size_t)((n0 + 127) / 128) * 128; }
@@ -176,6 +181,12 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
   // coarsest grid: a dense inverse up to kDenseCoarseMax unknowns, conjugate gradients above
   long long nc = (long long)(n[0] - 2) * (p->periodic_y ? n[1] : n[1] - 2) * (p->dim == 3 ? n[2] - 2 : 1);
   if (nc > (1LL << 26)) return MG_EINVAL;
+  // Galerkin coarse operators: 2-D, y not periodic, point smoothers, the dense coarsest solve,
+  // the fixed correction weight
+  if ((p->flags & MG_FLAG_GALERKIN) &&
+      (p->dim != 2 || p->periodic_y || (p->smoother != MG_JACOBI && p->smoother != MG_RBGS) ||
+       nc > kDenseCoarseMax || (p->flags & MG_FLAG_ADAPTIVE_CORR)))
+    return MG_EINVAL;
   return MG_OK;
 }
 
@@ -225,6 +236,14 @@ static size_t layout(mg_ctx *c, char *ws) {
       if (P.dim == 3) D.ez = b.take<double>(cnt);
       D.ndinv = b.take<double>(cnt);
     }
+    if (lev_kind(c, l) == K_NINE) {
+      D.dg = b.take<double>(cnt);
+      D.ex = b.take<double>(cnt);
+      D.ey = b.take<double>(cnt);
+      D.ez = b.take<double>(cnt);
+      D.enw = b.take<double>(cnt);
+      D.ndinv = b.take<double>(cnt);
+    }
     if (!c->mixed) {
       D.u[0] = b.take<double>(cnt);
       D.u[1] = b.take<double>(cnt);
@@ -250,6 +269,14 @@ static size_t layout(mg_ctx *c, char *ws) {
         F.ex = b.take<float>(cnt);
         F.ey = b.take<float>(cnt);
         if (P.dim == 3) F.ez = b.take<float>(cnt);
+        F.ndinv = b.take<float>(cnt);
+      }
+      if (lev_kind(c, l) == K_NINE) {
+        F.dg = b.take<float>(cnt);
+        F.ex = b.take<float>(cnt);
+        F.ey = b.take<float>(cnt);
+        F.ez = b.take<float>(cnt);
+        F.enw = b.take<float>(cnt);
         F.ndinv = b.take<float>(cnt);
       }
     }
@@ -285,7 +312,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   }
   // single-CTA coarse kernel: deepest level whose grids (and all coarser) fit in shared memory
   c->lcut = 0;
-  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode) {
+  if (!(P.flags & MG_FLAG_NO_FUSED_COARSE) && !c->cg_mode && !c->galerkin) {
     size_t es = c->mixed ? 4 : 8, total = 0;
     size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0) +
                     (line_smoother(P) ? 1 : 0);
@@ -333,6 +360,7 @@ static Lev<double> lev64(const mg_ctx *c, int l) {
   L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
   L.k = D.k; L.ndinv = D.ndinv;
   L.ex = D.ex; L.ey = D.ey; L.ez = D.ez;
+  L.dg = D.dg; L.enw = D.enw;
   return L;
 }
 // Line smoothers along y on constant or cell coefficients are run along x on the
@@ -372,6 +400,7 @@ static Lev<float> lev32(const mg_ctx *c, int l) {
   L.sx = D.sx; L.sy = D.sy; L.sz = D.sz; L.sdinv = D.sdinv;
   L.k = D.k; L.ndinv = D.ndinv;
   L.ex = D.ex; L.ey = D.ey; L.ez = D.ez;
+  L.dg = D.dg; L.enw = D.enw;
   return L;
 }
 template <typename T> struct LevOf;
@@ -477,7 +506,8 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
   int &cur = c->cur[l];
   bool jac = c->P.smoother == MG_JACOBI;
   bool line = c->P.smoother >= MG_LINE_X;
-  bool rb2d = c->P.smoother == MG_RBGS && c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP);
+  const int kind = lev_kind(c, l);
+  bool rb2d = c->P.smoother == MG_RBGS && c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && kind != K_NINE;
   if (ec && !(rb2d && sweeps > 0)) {
     launch_prolong_add<T>(S.lc, L, *Cp, ec, D.u[cur], oc);
     ec = nullptr;
@@ -501,8 +531,8 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
       odd_guard = 1;
     }
     if (jac) {
-      if (zero_start && s == 0) launch_jacobi_zero<T>(L, c->kind, S.lc, g, D.u[1 - cur], om);
-      else launch_jacobi<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om);
+      if (zero_start && s == 0) launch_jacobi_zero<T>(L, kind, S.lc, g, D.u[1 - cur], om);
+      else launch_jacobi<T>(S.lc, L, kind, D.u[cur], g, D.u[1 - cur], om);
       cur = 1 - cur;
     } else if (rb2d) {
       int mode = (zero_start && s == 0) ? 1 : (ec && s == 0) ? 2 : 0;
@@ -521,10 +551,18 @@ static void smooth(Sched &S, int l, const T *g, int sweeps, int order, bool zero
                                           oc)))
         launch_rb2d<T>(S.lc, L, c->kind, D.u[cur], g, D.u[1 - cur], om, order, mode, Cp, ec, oc);
       cur = 1 - cur;
+    } else if (!line && kind == K_NINE) {
+      // Gauss-Seidel on a Galerkin level: four colours, red (0,0), (1,1) then black (1,0), (0,1);
+      // order 1 runs the exact reverse
+      static const int seq[4][2] = {{0, 0}, {1, 1}, {1, 0}, {0, 1}};
+      for (int q = 0; q < 4; ++q) {
+        const int *cc = seq[order ? 3 - q : q];
+        launch_gs9_colour<T>(S.lc, L, D.u[cur], g, om, cc[0], cc[1]);
+      }
     } else if (!line) {
       int first = order;
-      launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, first);
-      launch_rb_half<T>(S.lc, L, c->kind, D.u[cur], g, om, 1 - first);
+      launch_rb_half<T>(S.lc, L, kind, D.u[cur], g, om, first);
+      launch_rb_half<T>(S.lc, L, kind, D.u[cur], g, om, 1 - first);
     } else {
       // one line sweep in direction dir: line Jacobi out of place, or zebra (both colours) in place.
       // x lines up to 4096 unknowns: the x-line kernels (one CTA or one warp a line, partition + PCR);
@@ -727,7 +765,7 @@ static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start
   int npre = transposed ? c->P.nu2 : c->P.nu1;
   int order = transposed ? 1 : 0;
   const long long tile_max = c->P.tile_nodes == 0 ? 1050625 : c->P.tile_nodes < 0 ? -1 : c->P.tile_nodes;
-  const bool fused2d = c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP);
+  const bool fused2d = c->P.dim == 2 && !(c->P.flags & MG_FLAG_NO_FUSED_SWEEP) && lev_kind(c, l) != K_NINE;
   if (fused2d && c->P.smoother == MG_RBGS && npre == 2 && tile_max >= 0 && (long long)L.n0 * L.n1 <= tile_max &&
       !(S.timing && l == c->L)) {
     // small grid: both pre-smoothing sweeps, the defect and the restriction in one pass
@@ -741,7 +779,7 @@ static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start
       launch_defect_restrict2d<T>(S.lc, L, Lc, c->kind, D.u[c->cur[l]], g, Dc.g);
   } else {
     smooth<T>(S, l, g, npre, order, zero_start);
-    launch_defect<T>(S.lc, L, c->kind, D.u[c->cur[l]], g, D.r);
+    launch_defect<T>(S.lc, L, lev_kind(c, l), D.u[c->cur[l]], g, D.r);
     launch_restrict<T>(S.lc, L, Lc, D.r, Dc.g);
   }
 }
@@ -1063,6 +1101,12 @@ static mg_status setup_levels(mg_ctx *c) {
     }
     for (int l = L; l >= 1; --l) launch_edge_dinv(lc, lev64(c, l), c->d64[l].ndinv);
   }
+  // Galerkin: every coarser operator is R A P of the next finer one (9-point stencils)
+  if (c->galerkin)
+    for (int l = L - 1; l >= 1; --l) {
+      LevData<double> &Cd = c->d64[l];
+      launch_rap(lc, lev64(c, l + 1), lev_kind(c, l + 1), lev64(c, l), Cd.dg, Cd.ex, Cd.ey, Cd.ez, Cd.enw, Cd.ndinv);
+    }
   // work vectors start at zero (Dirichlet nodes stay zero for good)
   for (int l = L; l >= 1; --l) {
     size_t cnt = (size_t)c->geo[l].count;
@@ -1086,6 +1130,14 @@ static mg_status setup_levels(mg_ctx *c) {
         launch_to_float(lc, c->d64[l].ey, D.ey, (long long)cnt);
         if (P.dim == 3) launch_to_float(lc, c->d64[l].ez, D.ez, (long long)cnt);
         launch_to_float(lc, c->d64[l].ndinv, D.ndinv, (long long)cnt);
+      }
+      if (lev_kind(c, l) == K_NINE) {
+        const LevData<double> &S = c->d64[l];
+        for (int q = 0; q < 6; ++q) {
+          const double *src[6] = {S.dg, S.ex, S.ey, S.ez, S.enw, S.ndinv};
+          float *dst[6] = {D.dg, D.ex, D.ey, D.ez, D.enw, D.ndinv};
+          launch_to_float(lc, src[q], dst[q], (long long)cnt);
+        }
       }
     }
   }
@@ -1116,7 +1168,7 @@ static mg_status setup_levels(mg_ctx *c) {
         CK(cudaMemsetAsync(c->cgw, 0, sizeof(double) * 4 * (size_t)c->geo[1].count, c->stream));
       } else {
         CK(cudaMemsetAsync(c->Ainv, 0, sizeof(double) * (size_t)c->nc * c->nc, c->stream));
-        launch_assemble_dense<double>(lc, lev64(c, 1), c->kind, c->cidx, c->cmap, c->nc, c->Ainv);
+        launch_assemble_dense<double>(lc, lev64(c, 1), lev_kind(c, 1), c->cidx, c->cmap, c->nc, c->Ainv);
         for (int k = 0; k < c->nc; ++k) launch_gj_step(lc, c->Ainv, c->gjcol, c->nc, k);
       }
     }
@@ -1235,7 +1287,7 @@ static mg_status step_defect_t(mg_ctx *c, int level, const double *u, const doub
   LevData<T> &D = LevOf<T>::data(c, level);
   pack_lvl<T>(c, lc, level, u, D.u[0]);
   pack_lvl<T>(c, lc, level, g, D.g);
-  launch_defect<T>(lc, LevOf<T>::get(c, level), c->kind, D.u[0], D.g, D.r);
+  launch_defect<T>(lc, LevOf<T>::get(c, level), lev_kind(c, level), D.u[0], D.g, D.r);
   unpack_lvl<T>(c, lc, level, D.r, r);
   return step_end(c);
 }
@@ -1334,6 +1386,7 @@ size_t mg_workspace_bytes(const mg_params *p, const mg_coeffs *k) {
   c->K = *k;
   c->L = p->levels;
   c->kind = k->kind;
+  c->galerkin = (p->flags & MG_FLAG_GALERKIN) != 0;
   c->mixed = p->precision == MG_MIXED;
   apply_swap(c);
   size_t s = layout(c, nullptr);
@@ -1354,6 +1407,7 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
   c->K = *k;
   c->L = p->levels;
   c->kind = k->kind;
+  c->galerkin = (p->flags & MG_FLAG_GALERKIN) != 0;
   c->mixed = p->precision == MG_MIXED;
   c->stream = (cudaStream_t)p->stream;
   apply_swap(c);
@@ -1828,7 +1882,7 @@ mg_status mg_residual_norm(mg_ctx *c, int level, const double *u, const double *
   LevData<double> &D = c->d64[level];
   pack_in(c, lc, Lv, u, D.u[0], 1);
   pack_in(c, lc, Lv, b, D.g, 1);
-  launch_defect_norm<double>(lc, Lv, c->kind, D.u[0], D.g, c->partials, norm_parts_count(), c->scal + 3);
+  launch_defect_norm<double>(lc, Lv, lev_kind(c, level), D.u[0], D.g, c->partials, norm_parts_count(), c->scal + 3);
   launch_sqrt(lc, c->scal + 3, out);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);
@@ -1843,7 +1897,7 @@ mg_status mg_apply(mg_ctx *c, int level, const double *u, double *Au) {
   double *ub = c->mixed ? D.u[0] : D.u[1];
   pack_in(c, lc,Lv, u, ub, 1);
   CK(cudaMemsetAsync(D.g, 0, sizeof(double) * (size_t)c->geo[level].count, c->stream));
-  launch_defect<double>(lc, Lv, c->kind, ub, D.g, D.r);   // r = 0 - A u
+  launch_defect<double>(lc, Lv, lev_kind(c, level), ub, D.g, D.r);   // r = 0 - A u
   unpack_out(c, lc,Lv, D.r, Au, -1.0);
   CK(cudaStreamSynchronize(c->stream));
   return last_launch(c);

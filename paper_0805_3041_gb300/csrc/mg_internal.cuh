@@ -13,7 +13,11 @@
 
 namespace mg {
 
-enum Kind { K_CONST = 0, K_SEP = 1, K_CELL = 2, K_EDGE = 3 };
+// K_NINE: a Galerkin coarse level (2-D): a 9-point stencil per node, stored by symmetry as
+// its diagonal D (dg), the weights w = -A(p, q) of the couplings to the +x (ex), +y (ey),
+// +x+y (ez) and -x+y (enw) neighbours, and 1/D (ndinv); the other four couplings of a node
+// are those of its neighbours.
+enum Kind { K_CONST = 0, K_SEP = 1, K_CELL = 2, K_EDGE = 3, K_NINE = 4 };
 
 // Everything a kernel needs to know about one level.  Passed by value.
 template <typename T>
@@ -29,6 +33,8 @@ struct Lev {
   T ax, ay, az;
   // edge coefficients: per node, the weights of the edges to the +x, +y, +z neighbours (1/D in ndinv)
   const T *ex, *ey, *ez;
+  // Galerkin levels (K_NINE): diagonal, and the -x+y coupling (ez holds the +x+y one)
+  const T *dg, *enw;
 
   __host__ __device__ int ylo() const { return per ? 0 : 1; }
   __host__ __device__ int yrows() const { return per ? n1 : n1 - 2; }
@@ -68,9 +74,25 @@ __device__ __forceinline__ void row_jk(const Lev<T> &L, long long r, int &j, int
 template <typename T, int DIM, int KIND>
 struct Weights {
   T wW, wE, wS, wN, wB, wF, dinv;
+  T wSW, wSE, wNW, wNE, dd;   // K_NINE only: corner couplings and the diagonal
   template <typename IT>
   __device__ __forceinline__ void load(const Lev<T> &L, int i, IT p, IT dm) {
-    if (KIND == K_CONST) {
+    if (KIND == K_NINE) {
+      // 2-D Galerkin level: the node's own +x, +y, +x+y, -x+y couplings, the rest from the
+      // neighbours that own them
+      const IT pt = (IT)L.pitch;
+      wE = L.ex[p];
+      wW = L.ex[p - 1];
+      wN = L.ey[p];
+      wS = L.ey[p - pt];
+      wNE = L.ez[p];
+      wSW = L.ez[p - pt - 1];
+      wNW = L.enw[p];
+      wSE = L.enw[p - pt + 1];
+      wB = wF = T(0);
+      dd = L.dg[p];
+      dinv = L.ndinv[p];
+    } else if (KIND == K_CONST) {
       wW = wE = L.cx;
       wS = wN = L.cy;
       wB = wF = L.cz;
@@ -126,6 +148,18 @@ __device__ __forceinline__ T residual_at(const Lev<T> &L, const Weights<T, DIM, 
                                          IT p, IT dm, IT dp, T gp) {
   T up = u[p];
   T s;
+  if (KIND == K_NINE) {
+    s = fma(-w.dd, up, gp);
+    s = fma(w.wW, u[p - 1], s);
+    s = fma(w.wE, u[p + 1], s);
+    s = fma(w.wS, u[p + dm], s);
+    s = fma(w.wN, u[p + dp], s);
+    s = fma(w.wSW, u[p + dm - 1], s);
+    s = fma(w.wSE, u[p + dm + 1], s);
+    s = fma(w.wNW, u[p + dp - 1], s);
+    s = fma(w.wNE, u[p + dp + 1], s);
+    return s;
+  }
   if (KIND == K_CONST) {
     s = fma(-L.d, up, gp);
   } else {
@@ -226,6 +260,9 @@ template <typename T>
 void launch_jacobi_zero(const Lev<T> &L, int kind, const Launch &lc, const T *g, T *out, T omega);
 template <typename T>
 void launch_rb_half(const Launch &lc, const Lev<T> &L, int kind, T *u, const T *g, T omega, int colour);
+// Gauss-Seidel on a 2-D Galerkin level: the nodes of colour (i mod 2, j mod 2) = (ci, cj), in place
+template <typename T>
+void launch_gs9_colour(const Launch &lc, const Lev<T> &L, T *u, const T *g, T omega, int ci, int cj);
 template <typename T>
 void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *r);
 // sum of squares over the unknowns -> *out_sq (deterministic: per-block partials, fixed-order finish)
@@ -326,6 +363,10 @@ void launch_coarse_cg(const Launch &lc, const Lev<double> &L, int kind, const T 
 void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<double> &C, const double *fx,
                          const double *fy, const double *fz, double *cx, double *cy, double *cz);
 void launch_edge_dinv(const Launch &lc, const Lev<double> &L, double *dinv);
+// Galerkin coarse operator R A P of fine level F (kind fkind, 2-D, y not periodic) on coarse level C:
+// diagonal, +x / +y / +x+y / -x+y weights (w = -A) and 1/D per coarse node
+void launch_rap(const Launch &lc, const Lev<double> &F, int fkind, const Lev<double> &C, double *dg, double *ex,
+                double *ey, double *ene, double *enw, double *dinv);
 void launch_to_float(const Launch &lc, const double *src, float *dst, long long n);
 void launch_cell_pack(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst);
 void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact);
