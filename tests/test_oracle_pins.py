@@ -1172,7 +1172,7 @@ def test_threaded_oracle_is_bit_identical(smoother, kind, periodic_y, dim):
 # Galerkin coarse operators A_c = R A P (2-D)
 # --------------------------------------------------------------------------------------
 
-def _interp_1d(nf):
+def _lin_interp_1d(nf):
     """Linear interpolation between the unknowns of a coarse and a fine 1-D Dirichlet grid
     (nf nodes -> (nf - 1) / 2 + 1): fine unknown 2I takes coarse I, 2I +- 1 half of it."""
     nc = (nf - 1) // 2 + 1
@@ -1232,7 +1232,7 @@ def test_galerkin_equals_dense_rap(n):
     dims = [o.dims(3)]
     for l in (2, 1):
         nf = dims[-1]
-        P = np.kron(_interp_1d(nf[1]), _interp_1d(nf[0]))
+        P = np.kron(_lin_interp_1d(nf[1]), _lin_interp_1d(nf[0]))
         A = (P.T / 4.0) @ A @ P
         got = _dense_op(o, l)
         assert np.abs(got - A).max() <= 1e-13 * np.abs(A).max(), l
@@ -1251,7 +1251,7 @@ def test_galerkin_two_grid_cycle_is_the_textbook_two_grid_method():
         m = o.unknown_mask()
         idx = np.flatnonzero(m)
         A = _dense_op(o, 2)
-        P = np.kron(_interp_1d(n[1]), _interp_1d(n[0]))
+        P = np.kron(_lin_interp_1d(n[1]), _lin_interp_1d(n[0]))
         Ac = (P.T / 4.0) @ A @ P
         b = rng.uniform(-1, 1, m.shape) * m
         x = rng.uniform(-1, 1, m.shape) * m
