@@ -43,10 +43,13 @@ def parse():
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso", choices=["aniso", "batched", "small", "annulus", "cylinder", "diff"],
+    ap.add_argument("--workload", default="aniso",
+                    choices=["aniso", "batched", "small", "annulus", "cylinder", "diff", "steps"],
                     help="aniso: the 4097^2 anisotropic solve (default); batched: 256 uneven instances in one "
-                         "graph; small: 129^2 Poisson, Jacobi, FP64; annulus: 2049x2048 polar map; cylinder: "
-                         "257x256x257 cylindrical map; diff: 1025^2 -div(k grad u) loss and gradient")
+                         "launch; small: 129^2 Poisson, Jacobi, FP64; annulus: 2049x2048 polar map; cylinder: "
+                         "257x256x257 cylindrical map; diff: 1025^2 -div(k grad u) loss and gradient; steps: the "
+                         "finest-level kernels of the aniso solve one step at a time (per-kernel timing, and a "
+                         "short fixed launch sequence for profilers)")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--levels", type=int, default=0,
                     help="grids of the hierarchy (0: as many as the grid allows); coarsest grids above 4096 "
@@ -409,7 +412,7 @@ def run_batched(args):
     import torch
     from paper_0805_3041_gb300 import inputs
     from paper_0805_3041_gb300.autotune import Autotuner
-    from paper_0805_3041_gb300.binding import Solver, Batch
+    from paper_0805_3041_gb300.binding import Solver, Batch, BATCH_GRAPH
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
@@ -423,7 +426,8 @@ def run_batched(args):
                for sp, cfg in zip(specs, cfgs)]
     bs = [torch.from_numpy(sp.b).to(dev) for sp in specs]
     xs = [torch.zeros_like(b) for b in bs]
-    batch = Batch(solvers, bs, xs)
+    batch = Batch(solvers, bs, xs)   # the persistent kernel when every instance qualifies
+    persistent, ctas, teams = batch.info()
     torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -464,6 +468,16 @@ def run_batched(args):
             out.append(s.solve_into(b, x, tol=args.tol))
         return out
 
+    # the same batch as one CUDA graph with a branch per instance, for comparison
+    gbatch = Batch(solvers, bs, xs, mode=BATCH_GRAPH)
+
+    def graph_solve():
+        for x in xs:
+            x.zero_()
+        return gbatch.solve(tol=args.tol)
+
+    graph_ms, ginfos = timed(graph_solve, max(2, args.steps // 2), 1)
+    gbatch.close()
     seq_ms, seq = timed(lambda: sequential(solvers), max(1, args.steps // 4), 1)
     fp64 = [Solver(sp, levels=inputs.max_levels(sp.n), precision="fp64", max_cycles=100, device=dev, **cfg)
             for sp, cfg in zip(specs, cfgs)]
@@ -494,11 +508,14 @@ def run_batched(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{args.count} independent 2-D anisotropic Poisson instances, N uniform over "
                                    f"{{65,129,257,513,1025}}, eps log-uniform [1e-3,1], f~U[-1,1] seed 4, x0=0, "
-                                   f"mixed precision to {args.tol:g}, one CUDA graph launch per batch, "
-                                   f"autotuned schedule per class",
+                                   f"mixed precision to {args.tol:g}, "
+                                   + (f"one persistent cooperative launch per batch ({ctas} CTAs, {teams} teams)"
+                                      if persistent else "one CUDA graph launch per batch")
+                                   + ", autotuned schedule per class",
                        "instances": args.count, "nodes": int(nodes), "schedules": classes,
                        "l2": "L2 flushed between steps"},
             "cycles_max": max(i["cycles"] for i in infos), "relres_max": max(i["relres"] for i in infos),
+            "form": "persistent" if persistent else "graph", "graph_form_ms": graph_ms,
             "sequential_mixed_ms": seq_ms, "sequential_fp64_ms": f64_ms,
             "fp64_relres_max": max(i["relres"] for i in f64),
             "setup_s": setup_s, "tune_s": tune_s, "roofline": None,
@@ -633,6 +650,45 @@ def run_config(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------------------
+# the finest-level kernels of the solve, one step at a time
+# --------------------------------------------------------------------------------------
+def run_steps(args):
+    """Each timed iteration runs, on the finest grid of the mixed context: one sweep (mode 0),
+    the descending half of a visit from zero (mode 1, mode 0, defect + restriction), the ascending
+    half (mode 2, mode 0) and the refinement loop's outer defect -- the single-step entry points,
+    which also pack and unpack their FP64 arguments.  The step groups are timed with CUDA events;
+    under a profiler each iteration is the same fixed sequence of kernels."""
+    import torch
+    from paper_0805_3041_gb300.binding import Solver
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    sp, levels, omega = make_problem(args)
+    s = Solver(sp, levels=levels, smoother="rbgs", omega=omega, nu1=2, nu2=2, precision="mixed", max_cycles=4,
+               flags=args.flags, device=dev)
+    rng = np.random.default_rng(0)
+    u = torch.tensor(rng.standard_normal(sp.shape) * 1e-3, device=dev)
+    g = torch.tensor(sp.b, device=dev)
+    ec = torch.tensor(rng.standard_normal(s.level_shape(levels - 1)) * 1e-3, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    groups = {"sweep": lambda: s.smooth(u, g, 1, 0), "descend": lambda: s.descend(None, g),
+              "ascend": lambda: s.ascend(ec, u, g), "outer_defect": lambda: s.outer_defect(u, g)}
+    ms = {k: [] for k in groups}
+    for it in range(args.warmup + args.steps):
+        for k, fn in groups.items():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if it >= args.warmup:
+                ms[k].append(e0.elapsed_time(e1))
+    line = {"workload": "steps", "n": args.n, "levels": levels, "steps": args.steps, "warmup": args.warmup,
+            "ms_median": {k: float(np.median(v)) for k, v in ms.items()},
+            "note": "each group includes the pack / unpack kernels of its FP64 arguments"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -641,6 +697,8 @@ def main():
         run_batched(args)
     elif args.workload in ("small", "annulus", "cylinder", "diff"):
         run_config(args)
+    elif args.workload == "steps":
+        run_steps(args)
     else:
         run_ours(args)
 

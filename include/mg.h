@@ -101,6 +101,13 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        transposed cycle in the reverse order), coarsest grid of at
                                        most 4096 unknowns, not with MG_FLAG_ADAPTIVE_CORR; otherwise
                                        MG_EINVAL.  The single-CTA coarse cycle is not used */
+#define MG_FLAG_FP64_DEFECT     512u /* MG_MIXED: keep the refinement loop's defect r = b - A x in FP64.
+                                       By default, in 2-D with constant or separable coefficients, that
+                                       defect is evaluated in float-float arithmetic (each FP64 operand
+                                       split into two floats, error-free FP32 sums and products; about
+                                       2^-46 of |A||x| in error instead of 2^-53), the loop stops when
+                                       that residual is below half the tolerance, and the reported
+                                       relative residual is the FP64 one of the result */
 #define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
                                        first single-precision TMA sweep is left out, so that the compute
                                        warps' bounded waits run out (about a second) and the solve returns
@@ -193,28 +200,53 @@ mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double to
  * The paper solves one problem at a time; solving many independent problems together
  * is an addition of this library.  Each instance has its own context (its own sizes,
  * coefficients, smoother, precision and max_cycles) and its own b / x (device
- * pointers, layout as for mg_solve).  The whole batch runs as ONE CUDA graph launch on
- * the first context's stream: every instance is an independent branch (copy b and
- * x in, initial check, a device-side loop of cycles or refinement steps that stops on
- * that instance's own test, copy x out), so instances of very different sizes proceed
- * concurrently and the host synchronises once.
+ * pointers, layout as for mg_solve).  A batch runs in one of two forms, on the first
+ * context's stream, with one host synchronisation per solve:
+ *   - persistent (MG_BATCH_PERSISTENT): ONE cooperative kernel launch solves every
+ *     instance.  Each instance is owned by a team of CTAs (sized in proportion to its
+ *     grid; instances beyond the resident CTA count are dealt to teams in turn) that runs
+ *     the instance's whole mixed-precision solve -- copy in, FP32 F-cycles, FP64 defect
+ *     and update, the convergence test, copy out -- from a step program, with a team
+ *     barrier between steps (grids up to 129^2 run on the team's first CTA alone).
+ *     Every barrier wait is bounded (about a second): a team whose wait runs out stops,
+ *     and its instances report MG_ETIMEOUT.  Covers contexts that are 2-D, y not
+ *     periodic, constant or separable coefficients, MG_MIXED with inner_cycles = 1,
+ *     MG_JACOBI / MG_RBGS / MG_LINE_X / MG_ZEBRA_X (and MG_LINE_Y / MG_ZEBRA_Y with
+ *     constant coefficients, which run as x-lines of the axis-swapped problem), without
+ *     MG_FLAG_GALERKIN, MG_FLAG_FMG_START or MG_FLAG_ADAPTIVE_CORR, with a coarsest grid
+ *     of at most 4096 unknowns.  Its tables live in the contexts' workspaces.
+ *   - graph (MG_BATCH_GRAPH): ONE CUDA graph launch with an independent branch per
+ *     instance (copy in, initial check, a device-side loop to that instance's own test,
+ *     copy out), for any contexts.
+ *   MG_BATCH_AUTO takes the persistent form when every context qualifies, else the graph.
  *
- * mg_batch_create: builds and instantiates the graph for count contexts and their
+ * mg_batch_create / mg_batch_create_ex: builds the batch for count contexts and their
  *   b[i] / x[i] (host arrays of device pointers; the pointer values are kept).  The
  *   contexts, b[i] and x[i] must stay valid until mg_batch_destroy.  MG_EINVAL for a
- *   NULL argument, count < 1, a context used twice, contexts on different devices or
- *   a context made with MG_FLAG_NO_GRAPH or MG_FLAG_TIMING.  The batch uses no device
- *   memory of its own (each instance works in its context's workspace); it owns a
- *   small pinned host buffer for the tolerance and the per-instance reports.
+ *   NULL argument, count < 1, a context used twice, contexts on different devices, a
+ *   context made with MG_FLAG_NO_GRAPH or MG_FLAG_TIMING, or MG_BATCH_PERSISTENT for
+ *   contexts it does not cover.  The batch uses no device memory of its own (each
+ *   instance works in its context's workspace); it owns a small pinned host buffer for
+ *   the tolerance and the per-instance reports.  A context in a persistent batch may
+ *   still be solved on its own.
  * mg_batch_solve: solves every instance to ||b_i - A_i x_i|| / ||b_i|| <= tol from
  *   the start vectors in x[i]; reps (NULL, or count reports) receives each instance's
  *   report.  Returns MG_OK when every instance converged, else the status of the
  *   first instance (in index order) that did not (MG_ENOCONV, MG_EDIVERGED,
- *   MG_ETIMEOUT); the x[i] hold each instance's last iterate either way.
- * mg_solve_batched: create, solve and destroy in one call (the graph is built on
- *   every call; keep a batch to solve the same set repeatedly). */
+ *   MG_ETIMEOUT); the x[i] hold each instance's last iterate either way (not for an
+ *   instance that reports MG_ETIMEOUT).
+ * mg_batch_info: the form a batch runs in, and for the persistent form its CTA and team
+ *   counts.
+ * mg_solve_batched: create (MG_BATCH_AUTO), solve and destroy in one call (the batch is
+ *   built on every call; keep a batch to solve the same set repeatedly). */
 typedef struct mg_batch mg_batch;
+#define MG_BATCH_AUTO 0
+#define MG_BATCH_GRAPH 1
+#define MG_BATCH_PERSISTENT 2
 mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, mg_batch **out);
+mg_status mg_batch_create_ex(mg_ctx *const *cs, int count, const double *const *b, double *const *x, int mode,
+                             mg_batch **out);
+mg_status mg_batch_info(const mg_batch *bt, int *persistent, int *ctas, int *teams);
 mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps);
 void mg_batch_destroy(mg_batch *bt);
 mg_status mg_solve_batched(mg_ctx *const *cs, int count, const double *const *b, double *const *x, double tol,
@@ -295,6 +327,10 @@ mg_status mg_step_descend(mg_ctx *c, int level, const double *u, const double *g
                           int transposed);
 mg_status mg_step_ascend(mg_ctx *c, int level, const double *ec, const double *u, const double *g, double *u_out,
                          int transposed);
+/* MG_MIXED contexts: the refinement loop's defect r = (float)(b - A x) of the finest grid, as the
+ * solve computes it (float-float or FP64, see MG_FLAG_FP64_DEFECT), widened to FP64 into r (caller
+ * layout); *sq (host, may be NULL) receives the sum of its squares.  MG_EINVAL for FP64 contexts. */
+mg_status mg_step_outer_defect(mg_ctx *c, const double *x, const double *b, double *r, double *sq);
 
 /* Mean duration (ms) of the finest-level smoothing launches recorded since the
  * last call (MG_FLAG_TIMING), their count, and the mean algorithmic bytes of one

@@ -23,15 +23,17 @@ FLAG_FMG_START = 32
 FLAG_ADAPTIVE_CORR = 64
 FLAG_TEST_WAIT_TIMEOUT = 128
 FLAG_GALERKIN = 256
+FLAG_FP64_DEFECT = 512
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED = 0, 1, 2, 3, 4, 5
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6
 
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
            "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
-           "mg_step_coarse", "mg_step_cycle", "mg_step_descend", "mg_step_ascend", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
-           "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_solve", "mg_batch_destroy",
-           "mg_solve_batched"]
+           "mg_step_coarse", "mg_step_cycle", "mg_step_descend", "mg_step_ascend", "mg_step_outer_defect", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
+           "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_create_ex", "mg_batch_info",
+           "mg_batch_solve", "mg_batch_destroy", "mg_solve_batched"]
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
 class Params(C.Structure):
@@ -108,6 +110,8 @@ def load(build_if_missing: bool = True):
     L.mg_step_descend.restype = I
     L.mg_step_ascend.argtypes = [P, I, P, P, P, P, I]
     L.mg_step_ascend.restype = I
+    L.mg_step_outer_defect.argtypes = [P, P, P, P, C.POINTER(D)]
+    L.mg_step_outer_defect.restype = I
     L.mg_kernel_timing.argtypes = [P, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     L.mg_kernel_timing.restype = I
     L.mg_launch_count.argtypes = [P]
@@ -119,6 +123,10 @@ def load(build_if_missing: bool = True):
     L.mg_last_error.restype = C.c_char_p
     L.mg_batch_create.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), C.POINTER(P)]
     L.mg_batch_create.restype = I
+    L.mg_batch_create_ex.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, C.POINTER(P)]
+    L.mg_batch_create_ex.restype = I
+    L.mg_batch_info.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]
+    L.mg_batch_info.restype = I
     L.mg_batch_solve.argtypes = [P, D, C.POINTER(Report)]
     L.mg_batch_solve.restype = I
     L.mg_batch_destroy.argtypes = [P]
@@ -378,6 +386,16 @@ class Solver:
                                             C.c_void_p(g.data_ptr()), C.c_void_p(uo.data_ptr()), int(transposed)))
         return uo
 
+    def outer_defect(self, x, b):
+        """mg_step_outer_defect (MG_MIXED): the refinement loop's defect (float-float or FP64) widened
+        to FP64, and the sum of its squares."""
+        x, b = self._dev(x), self._dev(b)
+        r = self.empty()
+        sq = C.c_double()
+        self._check(self.lib.mg_step_outer_defect(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
+                                                  C.c_void_p(r.data_ptr()), C.byref(sq)))
+        return r, sq.value
+
     def kernel_timing(self):
         ms, n, by = C.c_double(), C.c_int(), C.c_double()
         self._check(self.lib.mg_kernel_timing(self.ctx, C.byref(ms), C.byref(n), C.byref(by)))
@@ -418,26 +436,36 @@ def _batch_infos(reps, hists):
 
 
 class Batch:
-    """Several independent solves as one CUDA graph (mg_batch_create / mg_batch_solve):
+    """Several independent solves in one launch (mg_batch_create_ex / mg_batch_solve):
     solvers[i] solves its problem with right-hand side bs[i] and start vector / solution
     xs[i] (contiguous float64 CUDA tensors of the solver's shape, kept by reference).
-    The graph is built once; solve() launches it and returns one info dict per instance."""
+    mode: BATCH_AUTO (the persistent kernel when every solver qualifies, else one CUDA
+    graph), BATCH_GRAPH or BATCH_PERSISTENT.  Built once; solve() launches it and returns
+    one info dict per instance."""
 
-    def __init__(self, solvers, bs, xs):
+    def __init__(self, solvers, bs, xs, mode=BATCH_AUTO):
         self.lib = load()
         self.solvers, self.bs, self.xs = list(solvers), list(bs), list(xs)
         n, cs, bp, xp = _batch_args(self.solvers, self.bs, self.xs)
         self.n = n
         h = C.c_void_p()
-        st = self.lib.mg_batch_create(cs, n, bp, xp, C.byref(h))
+        st = self.lib.mg_batch_create_ex(cs, n, bp, xp, int(mode), C.byref(h))
         if st != OK:
             raise MGError(st, self.lib.mg_last_error(self.solvers[0].ctx).decode())
         self.handle = h.value
 
+    def info(self):
+        """(persistent, ctas, teams) of the batch (mg_batch_info)."""
+        per, ctas, teams = C.c_int(), C.c_int(), C.c_int()
+        self.lib.mg_batch_info(self.handle, C.byref(per), C.byref(ctas), C.byref(teams))
+        return bool(per.value), ctas.value, teams.value
+
     def solve(self, tol=1e-10):
+        """Solve every instance; one info dict per instance, whose status says how that instance
+        ended (an instance whose bounded device wait ran out reports MG_ETIMEOUT)."""
         reps, hists = _batch_reports(self.solvers, self.n)
         st = self.lib.mg_batch_solve(self.handle, float(tol), reps)
-        if st not in (OK, ENOCONV, EDIVERGED):
+        if st not in (OK, ENOCONV, EDIVERGED, ETIMEOUT):
             raise MGError(st, self.lib.mg_last_error(self.solvers[0].ctx).decode())
         return _batch_infos(reps, hists)
 

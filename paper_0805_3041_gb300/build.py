@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmg_gb300.so")
 SOURCES = ["mg_capi.cu", "kernels_point.cu", "kernels_transfer.cu", "kernels_line.cu", "kernels_coarse.cu",
            "kernels_fast.cu", "kernels_xline.cu", "kernels_march.cu", "kernels_tma.cu", "noalloc.cu",
-           "kernels_cg.cu"]
-HEADERS = ["mg_internal.cuh", "coarse_prog.h"]
+           "kernels_cg.cu", "kernels_batch.cu", "kernels_ff.cu"]
+HEADERS = ["mg_internal.cuh", "coarse_prog.h", "batch_prog.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,216 @@
+// kernels_ff.cu -- the outer defect of the mixed-precision refinement in float-float arithmetic.
+//
+// The refinement loop (row a11: r = b - A x in FP64 drives an FP32 F-cycle) needs the defect of
+// the FP64 iterate to far more than FP32 accuracy: near convergence its 5-point sums cancel
+// terms some 1e7 times larger than the result.  In FP64 that is five FMAs per unknown on a
+// GPU whose FP64 pipe runs at ~1/50 of its FP32 rate, which bounds the kernel well below the
+// memory rate.  Here every FP64 operand is split into a pair of floats (hi + lo, 47 significant
+// bits) by integer operations on its bit pattern, and the stencil is evaluated with error-free
+// FP32 transformations (TwoSum; a product and its exact rounding error by FMA), so the kernel
+// runs on the FP32 and integer pipes.  The defect leaves rounded to FP32 (the FP32 cycle's
+// right-hand side), with the sum of its squares for the stopping test.
+//
+// Accuracy: the pair keeps |d - (hi + lo)| <= 2^-46 |d| of each operand; the stencil terms are
+// then summed almost exactly, so the defect's error is about 2^-46 times the largest term,
+// |A||x|, instead of FP64's 2^-53 (a numpy emulation of the 4097^2 benchmark put it at 5e-2
+// of ||r|| at a relative residual of 2e-11, 1e-2 at 1e-10).  The solver therefore stops the
+// loop on this defect with a margin (half the tolerance) and reports the relative residual of
+// a final FP64 defect.
+//
+// One warp covers 32 columns and marches down a band of rows, holding the split rows j-1, j,
+// j+1 in registers; x-neighbours come by shuffles (the strip's edge lanes split the column
+// beside the strip themselves).  2-D, constant or separable coefficients.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+namespace {
+constexpr int FX = 32, FY = 8;   // block: 8 warps, each one strip of 32 columns
+
+struct FF {
+  float h, l;
+};
+
+// d = h + l with h its leading 24 significant bits (truncated) and l the next 23 (truncated),
+// from the bit pattern alone.  |d| below 2^-80 splits to l = 0 (below 2^-126: h = 0 as well);
+// an error of at most 2^-80 |d|... i.e. nothing that matters next to the stencil's other terms.
+__device__ __forceinline__ FF split(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const int ef = e - 896;   // float biased exponent of h: e - 1023 + 127
+  FF r;
+  if (ef < 1) {
+    r.h = 0.f;
+    r.l = 0.f;
+    return r;
+  }
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  r.h = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
+  // next 23 mantissa bits as an integer m: lo = m * 2^(e - 1023 - 46); 2^23 + m has the float
+  // bit pattern 0x4b000000 | m, so that float minus 2^23 is m exactly
+  const unsigned m = (lw >> 6) & 0x7fffffu;
+  const int es = e - 942;   // biased exponent of 2^(e - 1069)
+  const float fm = __uint_as_float(0x4b000000u | m) - 8388608.0f;
+  const float v = es >= 1 ? fm * __uint_as_float((unsigned)es << 23) : 0.f;
+  r.l = __uint_as_float(__float_as_uint(v) | sign);
+  return r;
+}
+
+// s + t = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) with hi + lo ~ c * x: the product of the leading parts exactly (FMA), plus the
+// cross terms; c's and x's low parts product is below 2^-92 of the result and is dropped
+__device__ __forceinline__ void prod(const FF &c, const FF &x, float &p, float &e) {
+  p = c.h * x.h;
+  e = fmaf(c.h, x.h, -p);
+  e = fmaf(c.h, x.l, e);
+  e = fmaf(c.l, x.h, e);
+}
+
+// a + b for two pairs (the sum of the leading parts exactly, the low parts added)
+__device__ __forceinline__ FF add(const FF &a, const FF &b) {
+  float s, t;
+  two_sum(a.h, b.h, s, t);
+  FF r;
+  r.h = s;
+  r.l = t + (a.l + b.l);
+  return r;
+}
+
+__device__ __forceinline__ float block_sum_ff(float v) {
+  __shared__ float red[FX * FY / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int t = threadIdx.y * FX + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (t == 0)
+    for (int w = 0; w < FX * FY / 32; ++w) s += red[w];
+  return s;
+}
+
+// r32 = (float)(b - A x) at the unknowns of rows [band * R, band * R + R), and one partial sum
+// of r32^2 per block
+template <int KIND>
+__global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const double *__restrict__ x,
+                                                      const double *__restrict__ b, float *__restrict__ r32,
+                                                      double *__restrict__ partials, int R) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int i = 1 + (blockIdx.x * FY + threadIdx.y) * FX + lane;   // this thread's column
+  const int nx = L.n0 - 2;
+  const int rows = L.per ? L.n1 : L.n1 - 2, ylo = L.per ? 0 : 1;
+  const int r0 = blockIdx.y * R, r1 = min(rows, r0 + R);
+  const bool act = i <= nx;
+  const int ic = act ? i : 1;
+  const bool edge = lane == 0 || lane == 31;
+  const int io = lane == 0 ? i - 1 : i + 1;   // the column beside the strip (edge lanes)
+  const bool oin = io >= 1 && io <= nx;        // an unknown column (else it reads as 0)
+  // coefficients of the column (FP64, split once)
+  FF cW, cE, cY, cD;
+  if (KIND == K_CONST) {
+    cW = cE = split(L.cx);
+    cY = split(L.cy);
+    cD = split(L.d);
+  } else {
+    const double w = L.sx[ic - 1], e = L.sx[ic], y = L.sy[ic];
+    cW = split(w);
+    cE = split(e);
+    cY = split(y);
+    cD = split((w + e) + (y + y));
+  }
+  auto row_of = [&](int r) -> long long {   // node offset of unknown row r (wrapped when periodic)
+    int j = ylo + r;
+    if (L.per) j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
+    return (long long)j * L.pitch;
+  };
+  auto load = [&](int r) -> FF {   // x at (i, row r); rows outside the unknowns (Dirichlet) read 0
+    FF z;
+    z.h = 0.f;
+    z.l = 0.f;
+    if (!act) return z;
+    if (!L.per && (r < 0 || r >= rows)) return z;
+    return split(x[row_of(r) + i]);
+  };
+  float acc = 0.f;
+  if (r0 < r1) {
+    FF xm = load(r0 - 1), xc = load(r0), xp;
+    for (int r = r0; r < r1; ++r) {
+      xp = load(r + 1);
+      const long long p = row_of(r) + i;
+      // x-neighbours: the adjacent lanes' values, the edge lanes' from the column beside
+      FF xw, xe;
+      xw.h = __shfl_up_sync(FULL, xc.h, 1);
+      xw.l = __shfl_up_sync(FULL, xc.l, 1);
+      xe.h = __shfl_down_sync(FULL, xc.h, 1);
+      xe.l = __shfl_down_sync(FULL, xc.l, 1);
+      if (edge) {
+        FF xo;
+        xo.h = 0.f;
+        xo.l = 0.f;
+        if (oin) xo = split(x[p - i + io]);
+        if (lane == 0) xw = xo;
+        else xe = xo;
+      }
+      if (act) {
+        const FF bb = split(b[p]);
+        float p1, e1, p2, e2, p3, e3, p4, e4;
+        prod(cD, xc, p1, e1);
+        if (KIND == K_CONST) {
+          const FF sx = add(xw, xe);
+          prod(cW, sx, p2, e2);
+          p4 = 0.f;
+          e4 = 0.f;
+        } else {
+          prod(cW, xw, p2, e2);
+          prod(cE, xe, p4, e4);
+        }
+        const FF sy = add(xm, xp);
+        prod(cY, sy, p3, e3);
+        // b - D x_p + W x_w + E x_e + Y (x_s + x_n): the leading parts by TwoSum, the rest added
+        float s, t1, t2, t3, t4;
+        two_sum(bb.h, -p1, s, t1);
+        two_sum(s, p2, s, t2);
+        two_sum(s, p3, s, t3);
+        two_sum(s, p4, s, t4);
+        const float lo = (((bb.l - e1) + (e2 + e3)) + e4) + ((t1 + t2) + (t3 + t4));
+        const float res = s + lo;
+        r32[p] = res;
+        acc = fmaf(res, res, acc);
+      }
+      xm = xc;
+      xc = xp;
+    }
+  }
+  const float bs = block_sum_ff(acc);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (double)bs;
+}
+}  // namespace
+
+bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
+                      double *partials, int nparts, double *out_sq) {
+  if (L.dim != 2 || (kind != K_CONST && kind != K_SEP)) return false;
+  const int nx = L.n0 - 2, rows = L.per ? L.n1 : L.n1 - 2;
+  if (nx < 1 || rows < 1) return false;
+  const int gx = (nx + FX * FY - 1) / (FX * FY);
+  if (gx > nparts) return false;
+  // rows per block: 32, more when the blocks would outnumber the partial sums or gridDim.y
+  long long R = 32;
+  const long long gy_max = std::min<long long>(65535, nparts / gx);
+  if ((rows + R - 1) / R > gy_max) R = (rows + gy_max - 1) / gy_max;
+  const dim3 gr((unsigned)gx, (unsigned)((rows + R - 1) / R)), bl(FX, FY);
+  if (kind == K_CONST) k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, (int)R);
+  else k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, (int)R);
+  ++*lc.counter;
+  launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
+  return true;
+}
+
+}  // namespace mg

@@ -567,7 +567,7 @@ void launch_norm_finish(const Launch &lc, const double *partials, int nparts, do
 // check before the first cycle.  ||b|| = 0 stops at once (x = 0); a non-finite ||b||
 // gives a non-finite relative residual.
 __global__ void k_step_end(cudaGraphConditionalHandle h, const double *sq, const double *bsq, double *hist, int *st,
-                           const double *tol, int maxit, int init) {
+                           const double *tol, int maxit, int init, double tol_scale) {
   double b = bsq[0];
   double rel = b == 0.0 ? 0.0 : sqrt(sq[0]) / sqrt(b);
   int it = init ? 0 : st[0] + 1;
@@ -580,7 +580,7 @@ __global__ void k_step_end(cudaGraphConditionalHandle h, const double *sq, const
   } else if (!(rel == rel) || rel > 1.7976931348623157e308) {
     go = 0;
     status = 5;
-  } else if (rel <= tol[0] || b == 0.0) {
+  } else if (rel <= tol[0] * tol_scale || b == 0.0) {
     go = 0;
   } else if (it >= maxit) {
     go = 0;
@@ -590,8 +590,23 @@ __global__ void k_step_end(cudaGraphConditionalHandle h, const double *sq, const
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
-                     double *hist, int *st, const double *tol, int maxit, int init) {
-  k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init);
+                     double *hist, int *st, const double *tol, int maxit, int init, double tol_scale) {
+  k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init, tol_scale);
+  ++*lc.counter;
+}
+
+// After a loop that stopped on the float-float defect: the FP64 relative residual replaces
+// the last entry of the history; a loop that stopped as converged but is not (beyond tol in
+// FP64) gets status 8, which the host resolves by continuing the iteration.
+__global__ void k_final_check(const double *sq, const double *bsq, double *hist, int *st, const double *tol) {
+  const double b = bsq[0];
+  const double rel = b == 0.0 ? 0.0 : sqrt(sq[0]) / sqrt(b);
+  if (hist) hist[st[0]] = rel;
+  if (st[1] == 0 && b != 0.0 && !(rel <= tol[0])) st[1] = 8;
+}
+void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
+                        const double *tol) {
+  k_final_check<<<1, 1, 0, lc.s>>>(sq, bsq, hist, st, tol);
   ++*lc.counter;
 }
 

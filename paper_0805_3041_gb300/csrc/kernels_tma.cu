@@ -38,10 +38,14 @@ constexpr int RING_LOG = 3;
 constexpr int SEGW = 128 * NW + 8;     // floats per fine row segment: 4 + 512 + 4
 constexpr int CSEGW = 64 * NW + 8;     // floats per coarse row segment: 4 + 256 + 4
 // A ring slot of the sweep holds the row's g segment, after its u segment unless the iterate
-// starts at zero (mode 1, u is not read), then in mode 2 the two coarse rows of e.
+// starts at zero (mode 1, u is not read), then in mode 2 one coarse row of e: slot j holds
+// coarse row (j + 1) >> 1, so that fine row j interpolates from its own slot's coarse row and,
+// for odd j, the previous slot's -- each coarse row is copied twice, not three times.  The
+// first streamed row's previous coarse row has a segment of its own after the ring.
 __host__ __device__ constexpr int slot_floats(int mode) {
-  return (mode == 1 ? SEGW : 2 * SEGW) + (mode == 2 ? 2 * CSEGW : 0);
+  return (mode == 1 ? SEGW : 2 * SEGW) + (mode == 2 ? CSEGW : 0);
 }
+__host__ __device__ constexpr int pre_floats(int mode) { return mode == 2 ? CSEGW : 0; }
 __host__ __device__ constexpr int g_offset(int mode) { return mode == 1 ? 0 : SEGW; }
 // waits are bounded by the SM's cycle counter (a register read; 2^30 cycles is about 0.5 s)
 constexpr long long WAIT_CYCLES = 1ll << 30;    // give up a wait after this many cycles
@@ -135,8 +139,8 @@ template <int KIND, int MODE, bool IN>
 __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__restrict__ u,
                                            const float *__restrict__ g, float *__restrict__ out, float omega,
                                            int first, const Lev<float> C, const float *__restrict__ ec,
-                                           float omega_corr, int j0, int j1, int s0, float *ring, uint64_t *full,
-                                           uint64_t *empty, int *err, int *inject) {
+                                           float omega_corr, int j0, int j1, int s0, float *ring, float *pre,
+                                           uint64_t *full, uint64_t *empty, int *err, int *inject) {
   constexpr int SLOT = slot_floats(MODE);   // floats per ring slot
   constexpr int GOFF = g_offset(MODE), EOFF = 2 * SEGW;
   const unsigned FULL = 0xffffffffu;
@@ -208,19 +212,18 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     float *slot = ring + (k & (RING - 1)) * SLOT;
     uint64_t *bar = &full[k & (RING - 1)];
     const int jw = wrap(j);
-    const bool corr = MODE == 2 && unk(j);
-    int J0 = jw >> 1, J1 = (jw + 1) >> 1;
-    if (J1 >= C.n1) J1 -= C.n1;
-    const uint32_t bytes =
-        (MODE == 1 ? 1u : 2u) * seg_bytes + (corr ? (J1 != J0 ? 2u : 1u) * cseg_bytes : 0u);
+    // mode 2: every streamed row carries coarse row (jw + 1) >> 1; the first also jw >> 1
+    int Jc = (jw + 1) >> 1;
+    if (Jc >= C.n1) Jc -= C.n1;
+    const bool pre_row = MODE == 2 && j == jfirst;
+    const uint32_t bytes = (MODE == 1 ? 1u : 2u) * seg_bytes + (MODE == 2 ? (pre_row ? 2u : 1u) * cseg_bytes : 0u);
     mbar_expect_tx(bar, bytes);
     const long long ro = (long long)jw * L.pitch;
     if (MODE != 1) tma_load_1d(slot + doff, u + ro + cs, seg_bytes, bar);
     tma_load_1d(slot + GOFF + doff, g + ro + cs, seg_bytes, bar);
-    if (corr) {
-      tma_load_1d(slot + EOFF + cdoff, ec + (long long)J0 * C.pitch + ccs, cseg_bytes, bar);
-      if (J1 != J0)
-        tma_load_1d(slot + EOFF + CSEGW + cdoff, ec + (long long)J1 * C.pitch + ccs, cseg_bytes, bar);
+    if (MODE == 2) {
+      tma_load_1d(slot + EOFF + cdoff, ec + (long long)Jc * C.pitch + ccs, cseg_bytes, bar);
+      if (pre_row) tma_load_1d(pre + cdoff, ec + (long long)(jw >> 1) * C.pitch + ccs, cseg_bytes, bar);
     }
   };
   // ---- producer warp (lane 0): every streamed row in order, each into its slot once all
@@ -286,7 +289,10 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
       // omega_l P e at the thread's columns: i >> 1 and (i + 1) >> 1 sit at coarse-segment
       // positions 4 + 64 warp + 2 lane + {0, 1, 2}
       const int jw = wrap(j);
-      const float *e0 = slot + EOFF, *e1 = ((jw & 1) ? e0 + CSEGW : e0);
+      // coarse rows jw >> 1 (e0) and (jw + 1) >> 1 (e1): this slot's, and for odd jw the previous
+      // row's slot (the segment after the ring for the first streamed row)
+      const float *e1 = slot + EOFF;
+      const float *e0 = (jw & 1) ? (j == jfirst ? pre : slot_of(j - 1) + EOFF) : e1;
       const int q = 4 + 64 * warp + 2 * lane;
       const float2 a0 = *reinterpret_cast<const float2 *>(e0 + q), a1 = *reinterpret_cast<const float2 *>(e1 + q);
       const float sq[3] = {a0.x + a1.x, a0.y + a1.y, e0[q + 2] + e1[q + 2]};
@@ -396,10 +402,11 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
                                                       float omega, int first, Lev<float> C,
                                                       const float *__restrict__ ec, float omega_corr, int RC,
                                                       int ngroups, int *err, int *inject) {
-  constexpr int SLOT = slot_floats(MODE);
+  constexpr int SLOT = slot_floats(MODE), PRE = pre_floats(MODE);
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float *ring = reinterpret_cast<float *>(tma_smem);
-  uint64_t *full = reinterpret_cast<uint64_t *>(ring + RING * SLOT);
+  float *pre = ring + RING * SLOT;
+  uint64_t *full = reinterpret_cast<uint64_t *>(pre + PRE);
   uint64_t *empty = full + RING;
 
   const int grp = blockIdx.x % ngroups, band = blockIdx.x / ngroups;
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
 
   // Segment positions that no copy writes (outside the array: the grid's left and right
   // margins) stay zero.
-  for (int t = threadIdx.x; t < RING * SLOT; t += 32 * (NW + 1)) ring[t] = 0.f;
+  for (int t = threadIdx.x; t < RING * SLOT + PRE; t += 32 * (NW + 1)) ring[t] = 0.f;
   if (threadIdx.x == 0) {
     for (int s = 0; s < RING; ++s) {
       mbar_init(&full[s], 1);
@@ -428,11 +435,11 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
 
   const bool interior = L.per ? (j0 - 2 >= 0 && j1 + 1 <= L.n1 - 1) : (j0 - 2 >= 1 && j1 + 1 <= L.n1 - 2);
   if (interior)
-    band_sweep<KIND, MODE, true>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err,
-                                 inject);
+    band_sweep<KIND, MODE, true>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, pre, full, empty,
+                                 err, inject);
   else
-    band_sweep<KIND, MODE, false>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, full, empty, err,
-                                  inject);
+    band_sweep<KIND, MODE, false>(L, u, g, out, omega, first, C, ec, omega_corr, j0, j1, s0, ring, pre, full, empty,
+                                  err, inject);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -729,7 +736,7 @@ bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev
 
 size_t rb2d_tma_smem(int mode) {
   const int slot = slot_floats(mode);
-  return (size_t)RING * slot * sizeof(float) + 2 * RING * sizeof(uint64_t);
+  return ((size_t)RING * slot + pre_floats(mode)) * sizeof(float) + 2 * RING * sizeof(uint64_t);
 }
 
 namespace {

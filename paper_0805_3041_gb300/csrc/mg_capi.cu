@@ -19,6 +19,7 @@
 
 #include "../../include/mg.h"
 #include "coarse_prog.h"
+#include "batch_prog.h"
 #include "mg_internal.cuh"
 
 using namespace mg;
@@ -64,6 +65,7 @@ struct mg_ctx {
   int L;
   int kind;
   bool galerkin = false;   // MG_FLAG_GALERKIN: levels below the finest hold R A P (K_NINE)
+  bool ff = false;         // MG_MIXED: the refinement loop's defect in float-float (kernels_ff.cu)
   LevGeom geo[MAXLEV + 1];
   LevData<double> d64[MAXLEV + 1];
   LevData<float> d32[MAXLEV + 1];
@@ -89,6 +91,7 @@ struct mg_ctx {
   void *slev = nullptr;            // device table of shared-memory level views
   int4 *prog = nullptr;            // device programs
   int prog_off[9] = {0}, prog_len[9] = {0};
+  int prog_used = 0;               // int4 entries of prog taken by the coarse programs
   long long *cidx_s = nullptr;     // coarsest unknowns in the compact shared-memory layout
   size_t csk_smem = 0;
   // y-line smoothers run as x-line smoothers on the axis-swapped problem: internal node
@@ -119,6 +122,11 @@ struct mg_ctx {
   std::vector<double> ev_bytes;   // algorithmic bytes of the launch opened by each pool event
   std::string err;
 };
+
+// A refinement loop driven by the float-float defect stops when that defect's relative residual
+// is below this fraction of the tolerance (its error is ~1e-2 of ||r|| there); the FP64 residual
+// computed afterwards is the one reported.
+static const double kFFStop = 0.5;
 
 // the operator form of level l: the context's coefficient kind, or K_NINE on Galerkin coarse levels
 static int lev_kind(const mg_ctx *c, int l) { return (c->galerkin && l < c->L) ? K_NINE : c->kind; }
@@ -909,10 +917,12 @@ static void emit_mixed_step(Sched &S, int transposed) {
     finest_to_zero<float>(S);
   }
   launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
-  launch_defect64_to32(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
-                       c->scal + 1);
+  if (!(c->ff && launch_defect_ff(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials,
+                                  norm_parts_count(), c->scal + 1)))
+    launch_defect64_to32(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                         c->scal + 1);
   if (S.loop) launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4,
-                              c->P.max_cycles, 0);
+                              c->P.max_cycles, 0, c->ff ? kFFStop : 1.0);
   else launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
 }
 
@@ -981,6 +991,16 @@ static cudaError_t capture_loop(mg_ctx *c, cudaStream_t s, int transposed, long 
       cudaGraph_t bout = cp.conditional.phGraph_out[0];
       e = cudaStreamEndCapture(c->cap2, &bout);
     }
+  }
+  if (e == cudaSuccess && c->mixed && c->ff) {
+    // the loop stopped on the float-float defect: the FP64 residual of the result, reported
+    long long f0 = c->launches;
+    Launch lc{s, &c->launches};
+    launch_defect_norm<double>(lc, lev64(c, c->L), c->kind, c->x64, c->b64, c->partials, norm_parts_count(),
+                               c->scal + 1);
+    launch_final_check(lc, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4);
+    e = cudaGetLastError();
+    *init_k += c->launches - f0;
   }
   c->launches = before;
   return e;
@@ -1208,6 +1228,7 @@ static mg_status setup_levels(mg_ctx *c) {
       c->prog_len[pid] = (int)pb.ops.size();
       all.insert(all.end(), pb.ops.begin(), pb.ops.end());
     }
+    c->prog_used = (int)all.size();
     if (all.size() > 32768) {
       c->err = "coarse program too long";
       return MG_EINVAL;
@@ -1387,6 +1408,8 @@ size_t mg_workspace_bytes(const mg_params *p, const mg_coeffs *k) {
   c->L = p->levels;
   c->kind = k->kind;
   c->galerkin = (p->flags & MG_FLAG_GALERKIN) != 0;
+  c->ff = p->precision == MG_MIXED && p->dim == 2 && (k->kind == MG_COEF_CONST || k->kind == MG_COEF_SEPARABLE) &&
+          !(p->flags & MG_FLAG_FP64_DEFECT);
   c->mixed = p->precision == MG_MIXED;
   apply_swap(c);
   size_t s = layout(c, nullptr);
@@ -1408,6 +1431,8 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
   c->L = p->levels;
   c->kind = k->kind;
   c->galerkin = (p->flags & MG_FLAG_GALERKIN) != 0;
+  c->ff = p->precision == MG_MIXED && p->dim == 2 && (k->kind == MG_COEF_CONST || k->kind == MG_COEF_SEPARABLE) &&
+          !(p->flags & MG_FLAG_FP64_DEFECT);
   c->mixed = p->precision == MG_MIXED;
   c->stream = (cudaStream_t)p->stream;
   apply_swap(c);
@@ -1551,17 +1576,26 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     c->h_relres[3] = tol;
     CK(cudaMemcpyAsync(c->scal + 4, c->h_relres + 3, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
-    CK(cudaGraphLaunch(c->lexec[transposed], c->stream));
     double *xin = c->mixed ? c->x64 : c->d64[L].u[0];
-    std::vector<double> hbuf((size_t)c->P.max_cycles + 2);
+    std::vector<double> hbuf((size_t)c->P.max_cycles + 2), hall;
     int sth[3] = {0, 0, 0};
-    CK(cudaMemcpyAsync(sth, c->st, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(hbuf.data(), c->hist, sizeof(double) * hbuf.size(), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if ((st = last_launch(c))) return st;
-    int cycles = sth[0];
-    c->launches += c->loop_init_kernels[transposed] + (long long)cycles * c->loop_body_kernels[transposed];
+    int cycles = 0;
+    // A loop that stopped on the float-float defect as converged whose FP64 residual is still
+    // above tol (status 8; not expected at these error levels) continues from its iterate.
+    for (int round = 0; round < 4; ++round) {
+      CK(cudaGraphLaunch(c->lexec[transposed], c->stream));
+      CK(cudaMemcpyAsync(sth, c->st, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(hbuf.data(), c->hist, sizeof(double) * hbuf.size(), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if ((st = last_launch(c))) return st;
+      c->launches += c->loop_init_kernels[transposed] + (long long)sth[0] * c->loop_body_kernels[transposed];
+      for (int t = hall.empty() ? 0 : 1; t <= sth[0]; ++t) hall.push_back(hbuf[t]);
+      cycles += sth[0];
+      if (sth[1] != 8 || cycles >= c->P.max_cycles) break;
+    }
+    if (sth[1] == 8) sth[1] = 4;
+    hbuf = hall;
     if (c->h_relres[0] == 0.0) {   // b = 0: x = 0
       CK(cudaMemsetAsync(xin, 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
     }
@@ -1633,9 +1667,22 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
       result = MG_OK;
       break;
     }
+    // after a refinement step the float-float defect's residual is a stopping signal only: below
+    // the loop's margin the FP64 residual is computed, decides and is reported
+    bool exact = true;
+    if (c->mixed && c->ff && it > 0 && std::isfinite(rr)) {
+      exact = rr <= tol * kFFStop;
+      if (exact) {
+        launch_defect_norm<double>(lc, F64, c->kind, c->x64, c->b64, c->partials, norm_parts_count(), c->scal + 1);
+        launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
+        CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        rr = c->h_relres[2];
+      }
+    }
     hist.push_back(rr);
     if (!std::isfinite(rr)) { result = MG_EDIVERGED; break; }
-    if (rr <= tol) { result = MG_OK; break; }
+    if (exact && rr <= tol) { result = MG_OK; break; }
     if (it >= c->P.max_cycles) { result = MG_ENOCONV; break; }
     if (use_graph) {
       CK(cudaGraphLaunch(c->gexec[transposed], c->stream));
@@ -1702,6 +1749,14 @@ struct mg_batch {
   double *host = nullptr;        // pinned: [0] tolerance, then one report row per instance
   int stride = 0;                // doubles per report row: loop state (2), ||b||^2 (1), history
   std::vector<long long> loop_init, loop_body, extra;   // kernel counts per instance
+  // persistent form: one cooperative launch over all instances
+  bool persistent = false;
+  int grid = 0, nteams = 0;
+  BatchTeam *d_teams = nullptr;   // device tables (in the first context's workspace)
+  BatchInst *d_insts = nullptr;
+  int *d_order = nullptr;
+  unsigned *d_bar = nullptr;
+  int epoch = 0;                  // solves launched: a finished instance's report row carries it
 };
 
 static void batch_free(mg_batch *bt) {
@@ -1711,7 +1766,279 @@ static void batch_free(mg_batch *bt) {
   delete bt;
 }
 
-mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, mg_batch **out) {
+// ---- the persistent batched solve --------------------------------------------------------
+// Can this context's solve run inside the persistent batch kernel?  2-D, y not periodic,
+// constant or separable coefficients, the mixed form with one FP32 cycle per refinement step,
+// point Jacobi / red-black Gauss-Seidel or x-line smoothers (y-lines of the constant kind are
+// x-lines after the axis swap), rediscretised coarse operators, the dense coarsest solve, the
+// fixed correction weight and the caller's start vector.
+static bool batch_persistent_ok(const mg_ctx *c) {
+  const mg_params &P = c->P;
+  if (P.dim != 2 || P.periodic_y || !c->mixed || c->galerkin || c->cg_mode) return false;
+  if (c->kind != K_CONST && c->kind != K_SEP) return false;
+  if (P.smoother != MG_JACOBI && P.smoother != MG_RBGS && P.smoother != MG_LINE_X && P.smoother != MG_ZEBRA_X)
+    return false;
+  if (P.flags & (MG_FLAG_FMG_START | MG_FLAG_ADAPTIVE_CORR)) return false;
+  if (P.inner_cycles != 1) return false;
+  return true;
+}
+
+// Step program of one instance (see batch_prog.h); levels with at most kSoloNodes nodes run on
+// the team's first CTA alone.
+struct BatchProg {
+  const mg_ctx *c;
+  std::vector<int4> ops;
+  int cur[MAXLEV + 1];
+  long long solo_nodes;
+  explicit BatchProg(const mg_ctx *cc, long long solo) : c(cc), solo_nodes(solo) {
+    for (int l = 0; l <= MAXLEV; ++l) cur[l] = 0;
+  }
+  bool small(int l) const { return (long long)c->geo[l].n[0] * c->geo[l].n[1] <= solo_nodes; }
+  void op(int code, int l, int a, int b) {
+    const bool solo = l >= 1 && small(l);
+    ops.push_back(make_int4(code | (solo ? BP_SOLO : 0), l, a, b));
+  }
+  void smooth(int l, int sweeps, int order, bool zero) {
+    if (sweeps <= 0) return;
+    if (zero) op(BP_ZERO, l, cur[l], 0);
+    for (int s = 0; s < sweeps; ++s) {
+      switch (c->P.smoother) {
+        case MG_JACOBI:
+          op(BP_JAC, l, 0, cur[l] | (1 - cur[l]) << 4);
+          cur[l] = 1 - cur[l];
+          break;
+        case MG_RBGS:
+          op(BP_RB, l, order, cur[l]);
+          op(BP_RB, l, 1 - order, cur[l]);
+          break;
+        case MG_ZEBRA_X:
+          op(BP_XLINE, l, 1 | order << 1, cur[l] | cur[l] << 4);
+          op(BP_XLINE, l, 1 | (1 - order) << 1, cur[l] | cur[l] << 4);
+          break;
+        default:   // MG_LINE_X
+          op(BP_XLINE, l, 0, cur[l] | (1 - cur[l]) << 4);
+          cur[l] = 1 - cur[l];
+          break;
+      }
+    }
+  }
+  // the F-cycle (type 0) or V-cycle (1) at level l, as cycle() runs it
+  void cycle(int l, int type, bool zero) {
+    if (l == 1) {
+      op(BP_COARSE, 1, cur[1], 0);
+      return;
+    }
+    smooth(l, c->P.nu1, 0, zero);
+    op(BP_DEFECT, l, cur[l], 0);
+    op(BP_RESTRICT, l, 0, 0);
+    cur[l - 1] = 0;
+    if (type == 0) {
+      cycle(l - 1, 0, true);
+      if (l - 1 > 1) cycle(l - 1, 1, false);
+    } else {
+      cycle(l - 1, 1, true);
+    }
+    op(BP_PROLONG, l, cur[l], cur[l - 1]);
+    smooth(l, c->P.nu2, 0, false);
+  }
+  void build() {
+    const int L = c->L;
+    ops.push_back(make_int4(BP_PACK, 0, 0, 0));
+    ops.push_back(make_int4(BP_NORM_B, 0, 0, 0));
+    ops.push_back(make_int4(BP_DEFECT64, 0, 0, 0));
+    const int check0 = (int)ops.size();
+    ops.push_back(make_int4(BP_CHECK, 0, 1, 0));   // w: the unpack step, filled in below
+    const int loop = (int)ops.size();
+    cur[L] = 0;
+    cycle(L, 0, true);
+    ops.push_back(make_int4(BP_UPDATE, 0, cur[L], 0));
+    ops.push_back(make_int4(BP_DEFECT64, 0, 0, 0));
+    const int check1 = (int)ops.size();
+    ops.push_back(make_int4(BP_CHECK, loop, 0, 0));
+    const int unpack = (int)ops.size();
+    ops.push_back(make_int4(BP_UNPACK, 0, 0, 0));
+    ops.push_back(make_int4(BP_END, 0, 0, 0));
+    ops[check0].w = unpack;
+    ops[check1].w = unpack;
+  }
+};
+
+static const long long kBatchSoloNodes = 17000;   // grids up to 129^2 on one CTA
+
+// Lay out the persistent form of a batch: programs and level tables in each instance's
+// workspace (after its coarse programs), the instance, team, order and barrier tables in the
+// first instance's.  Returns false (nothing launched, nothing changed on the device) when an
+// instance does not qualify or the tables do not fit.
+static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
+  const int count = (int)bt->cs.size();
+  for (mg_ctx *c : bt->cs)
+    if (!batch_persistent_ok(c)) return false;
+  mg_ctx *c0 = bt->cs[0];
+  int sms = 0, coop = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c0->dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return false;
+  }
+  const int per_sm = batch_ctas_per_sm();
+  if (per_sm < 1) return false;
+  const int G = sms * per_sm;
+  // team sizes in proportion to the finest grid's nodes, at least one CTA each
+  std::vector<long long> nodes(count);
+  for (int i = 0; i < count; ++i) nodes[i] = (long long)bt->cs[i]->geo[bt->cs[i]->L].count;
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nodes[a] > nodes[b]; });
+  std::vector<BatchTeam> teams;
+  if (count <= G) {
+    // largest alpha with sum_i max(1, min(32, floor(alpha n_i))) <= G
+    auto total = [&](double a) {
+      long long t = 0;
+      for (int i = 0; i < count; ++i) t += std::max<long long>(1, std::min<long long>(32, (long long)(a * nodes[i])));
+      return t;
+    };
+    double lo = 0.0, hi = 1.0;
+    while (total(hi) <= G && hi < 1e9) hi *= 2;
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      (total(mid) <= G ? lo : hi) = mid;
+    }
+    int cta = 0;
+    for (int q = 0; q < count; ++q) {
+      const int i = order[q];
+      const int sz = (int)std::max<long long>(1, std::min<long long>(32, (long long)(lo * nodes[i])));
+      teams.push_back(BatchTeam{cta, sz, q, 1, nullptr, nullptr});
+      cta += sz;
+    }
+  } else {
+    // more instances than resident CTAs: single-CTA teams, instances dealt largest first to
+    // the least-loaded team
+    std::vector<long long> load(G, 0);
+    std::vector<std::vector<int>> lists(G);
+    for (int q = 0; q < count; ++q) {
+      const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lists[t].push_back(order[q]);
+      load[t] += nodes[order[q]];
+    }
+    std::vector<int> ord2;
+    for (int t = 0; t < G; ++t) {
+      teams.push_back(BatchTeam{t, 1, (int)ord2.size(), (int)lists[t].size(), nullptr, nullptr});
+      ord2.insert(ord2.end(), lists[t].begin(), lists[t].end());
+    }
+    order = ord2;
+  }
+  int grid = 0;
+  for (const BatchTeam &t : teams) grid += t.size;
+  // host rows of the reports: the kernel writes them through the mapped pinned buffer
+  double *hdev = nullptr;
+  if (cudaHostGetDevicePointer((void **)&hdev, bt->host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  // per-instance programs and level tables
+  std::vector<BatchInst> insts(count);
+  struct Up { void *dst; std::vector<char> bytes; };
+  std::vector<Up> uploads;
+  for (int i = 0; i < count; ++i) {
+    mg_ctx *c = bt->cs[i];
+    BatchProg pb(c, kBatchSoloNodes);
+    pb.build();
+    std::vector<BatchLev> lv(c->L);
+    for (int l = 1; l <= c->L; ++l) {
+      BatchLev &v = lv[l - 1];
+      v.L = lev32(c, l);
+      v.u[0] = c->d32[l].u[0];
+      v.u[1] = c->d32[l].u[1];
+      v.g = c->d32[l].g;
+      v.r = c->d32[l].r;
+    }
+    const size_t off = ((size_t)c->prog_used + 15) / 16 * 16;   // int4 units
+    const size_t lev_i4 = (sizeof(BatchLev) * lv.size() + 15) / 16;
+    if (off + lev_i4 + pb.ops.size() > 32768) return false;
+    BatchLev *dlev = reinterpret_cast<BatchLev *>(c->prog + off);
+    int4 *dprog = c->prog + off + lev_i4;
+    uploads.push_back(Up{dlev, std::vector<char>((char *)lv.data(), (char *)lv.data() + sizeof(BatchLev) * lv.size())});
+    uploads.push_back(Up{dprog, std::vector<char>((char *)pb.ops.data(), (char *)(pb.ops.data() + pb.ops.size()))});
+    BatchInst &I = insts[i];
+    memset(&I, 0, sizeof(I));
+    I.L = c->L;
+    I.lev = dlev;
+    I.prog = dprog;
+    I.plen = (int)pb.ops.size();
+    I.F64 = lev64(c, c->L);
+    I.kind = c->kind;
+    I.x64 = c->x64;
+    I.b64 = c->b64;
+    I.bcall = bt->b[i];
+    I.xcall = bt->x[i];
+    I.swap = c->swap ? 1 : 0;
+    I.n0c = c->swap ? c->geo[c->L].n[1] : c->geo[c->L].n[0];
+    I.n1c = c->swap ? c->geo[c->L].n[0] : c->geo[c->L].n[1];
+    I.Ainv = c->Ainv;
+    I.cidx = c->cidx;
+    I.nc = c->nc;
+    I.scal = c->scal;
+    I.hrow = hdev + 1 + (size_t)i * bt->stride;   // the report row
+    I.st = c->st;
+    I.tol = tol_dev;
+    I.maxit = c->P.max_cycles;
+    I.omega = (float)c->P.omega;
+    I.omega_corr = (float)c->P.omega_corr;
+    I.fail_arrival = (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
+  }
+  // batch-wide tables after the first instance's own
+  size_t off0 = 0;
+  {
+    mg_ctx *c = c0;
+    const size_t off = ((size_t)c->prog_used + 15) / 16 * 16;
+    BatchProg pb(c, kBatchSoloNodes);
+    pb.build();
+    off0 = off + (sizeof(BatchLev) * c->L + 15) / 16 + pb.ops.size();
+    off0 = (off0 + 15) / 16 * 16;
+  }
+  const size_t nt = teams.size();
+  const size_t need = (sizeof(BatchInst) * count + 15) / 16 + (sizeof(BatchTeam) * nt + 15) / 16 +
+                      (sizeof(int) * count + 15) / 16 + (sizeof(unsigned) * nt + 15) / 16 +
+                      (sizeof(double) * 2 * (size_t)grid + 15) / 16;
+  if (off0 + need > 32768) return false;
+  char *base = reinterpret_cast<char *>(c0->prog + off0);
+  BatchInst *d_insts = reinterpret_cast<BatchInst *>(base);
+  base += (sizeof(BatchInst) * count + 15) / 16 * 16;
+  BatchTeam *d_teams = reinterpret_cast<BatchTeam *>(base);
+  base += (sizeof(BatchTeam) * nt + 15) / 16 * 16;
+  int *d_order = reinterpret_cast<int *>(base);
+  base += (sizeof(int) * count + 15) / 16 * 16;
+  unsigned *d_bar = reinterpret_cast<unsigned *>(base);
+  base += (sizeof(unsigned) * nt + 15) / 16 * 16;
+  double *d_part = reinterpret_cast<double *>(base);
+  for (size_t t = 0; t < nt; ++t) {
+    teams[t].bar = d_bar + t;
+    teams[t].part = d_part + 2 * (size_t)teams[t].cta0;
+  }
+  uploads.push_back(Up{d_insts, std::vector<char>((char *)insts.data(), (char *)(insts.data() + count))});
+  uploads.push_back(Up{d_teams, std::vector<char>((char *)teams.data(), (char *)(teams.data() + nt))});
+  uploads.push_back(Up{d_order, std::vector<char>((char *)order.data(), (char *)(order.data() + count))});
+  for (const Up &u : uploads)
+    if (cudaMemcpyAsync(u.dst, u.bytes.data(), u.bytes.size(), cudaMemcpyHostToDevice, c0->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  if (cudaStreamSynchronize(c0->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  bt->persistent = true;
+  bt->grid = grid;
+  bt->nteams = (int)nt;
+  bt->d_teams = d_teams;
+  bt->d_insts = d_insts;
+  bt->d_order = d_order;
+  bt->d_bar = d_bar;
+  return true;
+}
+
+static mg_status batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, int mode,
+                              mg_batch **out) {
   if (!out) return MG_EINVAL;
   *out = nullptr;
   if (!cs || !b || !x || count < 1) return MG_EINVAL;
@@ -1741,6 +2068,21 @@ mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, 
     cudaGetLastError();
     batch_free(bt);
     return MG_ECUDA;
+  }
+  std::memset(bt->host, 0, sizeof(double) * (1 + (size_t)count * bt->stride));
+  if (mode != MG_BATCH_GRAPH) {
+    double *hdev = nullptr;
+    bool ok = cudaHostGetDevicePointer((void **)&hdev, bt->host, 0) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    if (ok && batch_build_persistent(bt, hdev)) {
+      *out = bt;
+      return MG_OK;
+    }
+    if (mode == MG_BATCH_PERSISTENT) {
+      c0->err = "the persistent batched solve does not cover these instances";
+      batch_free(bt);
+      return MG_EINVAL;
+    }
   }
   // capture: fork one branch per instance from the root stream, join them at the end
   cudaStream_t root = nullptr;
@@ -1797,8 +2139,68 @@ mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, 
   return MG_OK;
 }
 
+mg_status mg_batch_create(mg_ctx *const *cs, int count, const double *const *b, double *const *x, mg_batch **out) {
+  return batch_create(cs, count, b, x, MG_BATCH_AUTO, out);
+}
+
+mg_status mg_batch_create_ex(mg_ctx *const *cs, int count, const double *const *b, double *const *x, int mode,
+                             mg_batch **out) {
+  if (mode != MG_BATCH_AUTO && mode != MG_BATCH_GRAPH && mode != MG_BATCH_PERSISTENT) return MG_EINVAL;
+  return batch_create(cs, count, b, x, mode, out);
+}
+
+mg_status mg_batch_info(const mg_batch *bt, int *persistent, int *ctas, int *teams) {
+  if (!bt) return MG_EINVAL;
+  if (persistent) *persistent = bt->persistent ? 1 : 0;
+  if (ctas) *ctas = bt->grid;
+  if (teams) *teams = bt->nteams;
+  return MG_OK;
+}
+
+// The persistent form: one cooperative launch; every finished instance's report row carries
+// this launch's epoch, a row without it belongs to an instance whose team gave up a wait.
+static mg_status batch_solve_persistent(mg_batch *bt, double tol, mg_report *reps) {
+  auto t0 = std::chrono::steady_clock::now();
+  mg_ctx *c = bt->cs[0];
+  const int count = (int)bt->cs.size();
+  bt->host[0] = tol;
+  const int epoch = ++bt->epoch;
+  CK(cudaMemsetAsync(bt->d_bar, 0, sizeof(unsigned) * (size_t)bt->nteams, c->stream));
+  CK(launch_batch(c->stream, bt->grid, bt->d_teams, bt->nteams, bt->d_insts, bt->d_order, epoch, &c->launches));
+  CK(cudaStreamSynchronize(c->stream));
+  mg_status result = MG_OK;
+  for (int i = 0; i < count; ++i) {
+    mg_ctx *ci = bt->cs[i];
+    const double *row = bt->host + 1 + (size_t)i * bt->stride;
+    int st4[4];
+    std::memcpy(st4, row, sizeof(st4));
+    const bool done = st4[3] == epoch;
+    const int cycles = done ? st4[0] : 0;
+    mg_status si = st4[1] == 4 ? MG_ENOCONV : st4[1] == 5 ? MG_EDIVERGED : MG_OK;
+    if (!done) {   // a bounded wait gave up in this instance's team: clear the flag, report it
+      CK(cudaMemsetAsync(ci->st + 2, 0, sizeof(int), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      si = MG_ETIMEOUT;
+    }
+    if (si != MG_OK && result == MG_OK) result = si;
+    if (reps) {
+      mg_report &r = reps[i];
+      const double *hist = row + 3;
+      r.cycles = cycles;
+      r.relres = done ? hist[cycles] : 0.0;
+      r.rate = (done && cycles > 0 && hist[0] > 0.0) ? std::pow(hist[cycles] / hist[0], 1.0 / cycles) : 0.0;
+      r.status = si;
+      if (r.history)
+        for (int t = 0; t <= cycles && t < r.history_cap; ++t) r.history[t] = done ? hist[t] : 0.0;
+      r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+  return result;
+}
+
 mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps) {
   if (!bt || !(tol >= 0.0)) return MG_EINVAL;
+  if (bt->persistent) return batch_solve_persistent(bt, tol, reps);
   auto t0 = std::chrono::steady_clock::now();
   mg_ctx *c = bt->cs[0];
   const int count = (int)bt->cs.size();
@@ -1816,7 +2218,7 @@ mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps) {
     const double bsq = row[2];
     const double *hist = row + 3;
     ci->launches += bt->extra[i] + bt->loop_init[i] + (long long)cycles * bt->loop_body[i];
-    mg_status si = st3[1] == 4 ? MG_ENOCONV : st3[1] == 5 ? MG_EDIVERGED : MG_OK;
+    mg_status si = (st3[1] == 4 || st3[1] == 8) ? MG_ENOCONV : st3[1] == 5 ? MG_EDIVERGED : MG_OK;
     if (st3[2] || st3[1] == 6) {   // a bounded device wait gave up: clear the flag, report it
       CK(cudaMemsetAsync(ci->st + 2, 0, sizeof(int), c->stream));
       fixups = true;
@@ -1948,6 +2350,21 @@ mg_status mg_step_cycle(mg_ctx *c, const double *x, const double *b, double *x_o
   if (!c || !x || !b || !x_out) return MG_EINVAL;
   return c->mixed ? step_cycle_t<float>(c, x, b, x_out, transposed)
                   : step_cycle_t<double>(c, x, b, x_out, transposed);
+}
+
+mg_status mg_step_outer_defect(mg_ctx *c, const double *x, const double *b, double *r, double *sq) {
+  if (!c || !x || !b || !r || !c->mixed) return MG_EINVAL;
+  const int L = c->L;
+  Launch lc{c->stream, &c->launches};
+  Lev<double> F64 = lev64(c, L);
+  pack_in(c, lc, F64, x, c->x64, 1);
+  pack_in(c, lc, F64, b, c->b64, 1);
+  if (!(c->ff && launch_defect_ff(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                                  c->scal + 1)))
+    launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
+  unpack_lvl<float>(c, lc, L, c->d32[L].g, r);
+  if (sq) CK(cudaMemcpyAsync(sq, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return step_end(c);
 }
 
 mg_status mg_kernel_timing(mg_ctx *c, double *mean_ms, int *launches, double *bytes_per_launch) {

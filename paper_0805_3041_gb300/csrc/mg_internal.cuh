@@ -396,6 +396,14 @@ bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int co
 void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
                           float *r32, double *partials, int nparts, double *out_sq);
 void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c);
+// the same outer defect in float-float arithmetic on the FP32 and integer pipes (2-D, constant or
+// separable coefficients; false, and nothing launched, otherwise)
+bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
+                      double *partials, int nparts, double *out_sq);
+// after a loop stopped on the float-float defect: its FP64 relative residual into hist[st[0]], status 8
+// when it stopped as converged but the FP64 residual is above tol
+void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
+                        const double *tol);
 // adaptive correction weight: omega = (g - A u, pe) / (A pe, pe) over the unknowns of L
 // (pe = P e, zero off the unknowns), written to *omega; partials: nparts doubles of scratch;
 // count: a device counter that is zero between launches (the kernel re-arms it)
@@ -418,6 +426,6 @@ void launch_relres(const Launch &lc, const double *sq, const double *bsq, double
 void launch_sqrt(const Launch &lc, const double *src, double *dst);
 // end of a cycle of a device-side solve loop: history, cycle count, status, WHILE condition
 void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
-                     double *hist, int *st, const double *tol, int maxit, int init);
+                     double *hist, int *st, const double *tol, int maxit, int init, double tol_scale = 1.0);
 
 }  // namespace mg

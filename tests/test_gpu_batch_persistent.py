@@ -1,0 +1,157 @@
+"""The persistent batched solve: many instances in one cooperative kernel launch.
+
+Each instance is solved by a team of CTAs from its own step program (FP32 F-cycles, FP64
+defect, update and test).  Its arithmetic is its own (point loops, one thread per x-line),
+so results are checked against the oracle: every instance reaches 1e-10 in the oracle's FP64
+residual, at the mean contraction per step of its own mg_solve (within 0.05) and within one step
+plus 10 % of its count, and its report matches the residual.
+Also: a batch with more instances than resident CTAs (teams take several in turn), a zero
+right-hand side, repeated launches, the forms a batch can take, and a team barrier whose
+wait runs out (test hook: one CTA leaves without arriving) -- MG_ETIMEOUT, the device stays
+usable and later solves are correct.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_0805_3041_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_0805_3041_gb300.binding import (Solver, Batch, MGError, EINVAL, BATCH_PERSISTENT,  # noqa: E402
+                                           BATCH_AUTO, BATCH_GRAPH, FLAG_TEST_WAIT_TIMEOUT)
+
+
+def oracle_relres(sp, x):
+    p = orc.Problem(dim=2, n=sp.n, periodic_y=False, kind=sp.kind, h=sp.h, c=sp.c, sx=sp.sx, sy=sp.sy, sz=sp.sz)
+    o = orc.Oracle(p, levels=1, smoother="rbgs", dense_max=0)
+    return o.norm(o.defect(x, sp.b)) / o.norm(sp.b)
+
+
+# smoothers that converge for the anisotropy: point smoothers for eps > 0.3, y-lines below
+POINT = [("rbgs", 1.0, 2), ("jacobi", 0.8, 2)]
+LINES = [("zebra_y", 1.0, 1), ("line_y", 0.7, 2)]
+
+
+def mixed_set(count, sizes, seed):
+    specs = inputs.batched(count=count, sizes=sizes, eps_range=(1e-3, 1.0), seed=seed)
+    out = []
+    for q, sp in enumerate(specs):
+        eps = sp.c[0] * sp.h[0] ** 2
+        if q % 5 == 4:   # separable coefficients: a stretched grid of the same size (point smoothers)
+            sp = inputs.stretched_x(n=sp.n[0], beta=2.0, seed=seed + q)
+            eps = 1.0
+        sm, om, nu = (POINT if eps > 0.3 else LINES)[(q // 2) % 2]
+        s = Solver(sp, levels=inputs.max_levels(sp.n), smoother=sm, omega=om, nu1=nu, nu2=nu, precision="mixed",
+                   max_cycles=80)
+        out.append((sp, s))
+    return out
+
+
+def tensors(sp):
+    b = torch.from_numpy(sp.b).cuda()
+    return b, torch.zeros_like(b)
+
+
+def test_persistent_batch_reaches_the_fp64_residual():
+    inst = mixed_set(24, (65, 129, 257, 513), seed=51)
+    bs, xs = zip(*[tensors(sp) for sp, _ in inst])
+    batch = Batch([s for _, s in inst], bs, xs, mode=BATCH_PERSISTENT)
+    per, ctas, teams = batch.info()
+    assert per and teams == len(inst) and ctas >= teams
+    infos = batch.solve(tol=1e-10)
+    for (sp, s), b, x, info in zip(inst, bs, xs, infos):
+        rr = oracle_relres(sp, x.cpu().numpy())
+        ref = s.solve_into(b, torch.zeros_like(b), tol=1e-10)
+        print(f"{sp.n[0]}x{sp.n[1]} {s.params.smoother}: persistent {info['cycles']} steps relres {info['relres']:.2e} "
+              f"(oracle {rr:.2e}); own solve {ref['cycles']}")
+        assert info["status"] == "MG_OK" and rr <= 1e-10, (sp.name, info, rr)
+        assert abs(rr - info["relres"]) <= 1e-2 * rr + 1e-15
+        # its own arithmetic (point loops for the fused tile kernels): the mean contraction per step
+        # agrees, and the step at which the residual crosses the tolerance may move by one, or by
+        # 10 % on slowly converging instances (a rate near 1 makes the crossing sensitive)
+        assert abs(info["rate"] - ref["rate"]) <= 0.05
+        assert abs(info["cycles"] - ref["cycles"]) <= 1 + 0.1 * ref["cycles"]
+        assert len(info["history"]) == info["cycles"] + 1 and info["history"][-1] == info["relres"]
+    # launched again from the same start vectors: the same iterates
+    first = [x.clone() for x in xs]
+    for x in xs:
+        x.zero_()
+    again = batch.solve(tol=1e-10)
+    for a, c, x0, x1 in zip(infos, again, first, xs):
+        assert a["cycles"] == c["cycles"] and torch.equal(x0, x1)
+    batch.close()
+
+
+def test_more_instances_than_resident_ctas():
+    inst = []
+    rng = np.random.default_rng(52)
+    for q in range(700):
+        n = (17, 33)[q % 2]
+        sp = inputs.anisotropic(n=n, eps=float(10 ** rng.uniform(-1, 0)), seed_f=1000 + q)
+        inst.append((sp, Solver(sp, levels=inputs.max_levels(sp.n), smoother="rbgs", precision="mixed",
+                                max_cycles=40)))
+    bs, xs = zip(*[tensors(sp) for sp, _ in inst])
+    batch = Batch([s for _, s in inst], bs, xs, mode=BATCH_PERSISTENT)
+    per, ctas, teams = batch.info()
+    assert per and teams < len(inst)
+    infos = batch.solve(tol=1e-10)
+    for (sp, s), x, info in list(zip(inst, xs, infos))[::37]:
+        assert info["status"] == "MG_OK" and oracle_relres(sp, x.cpu().numpy()) <= 1e-10
+    assert all(i["status"] == "MG_OK" for i in infos)
+    batch.close()
+
+
+def test_zero_rhs_and_forms():
+    inst = mixed_set(4, (65, 129), seed=53)
+    bs, xs = zip(*[tensors(sp) for sp, _ in inst])
+    bs[2].zero_()
+    xs[2].fill_(1.0)
+    batch = Batch([s for _, s in inst], bs, xs)      # AUTO: every instance qualifies
+    assert batch.info()[0]
+    infos = batch.solve(tol=1e-10)
+    assert infos[2]["status"] == "MG_OK" and infos[2]["cycles"] == 0 and torch.count_nonzero(xs[2]) == 0
+    batch.close()
+    # an instance the persistent form does not cover: AUTO takes the graph, PERSISTENT refuses
+    sp3 = inputs.poisson_3d(n=17, seed=5)
+    s3 = Solver(sp3, levels=3, smoother="rbgs", precision="mixed")
+    b3, x3 = tensors(sp3)
+    solvers = [s for _, s in inst] + [s3]
+    auto = Batch(solvers, list(bs) + [b3], list(xs) + [x3], mode=BATCH_AUTO)
+    assert not auto.info()[0]
+    auto.close()
+    with pytest.raises(MGError) as e:
+        Batch(solvers, list(bs) + [b3], list(xs) + [x3], mode=BATCH_PERSISTENT)
+    assert e.value.status == EINVAL
+    assert not Batch([s for _, s in inst], bs, xs, mode=BATCH_GRAPH).info()[0]
+
+
+def test_barrier_wait_that_runs_out_reports_timeout():
+    """The big instance's team has several CTAs; with the test hook its last CTA leaves at the
+    first team barrier without arriving, the others' bounded waits run out (about a second), and
+    the instance reports MG_ETIMEOUT.  The small instance (its own team) is solved.  Afterwards the
+    device is usable: a new batch of the same problem without the hook is correct."""
+    sp_big = inputs.anisotropic(n=513, eps=0.5, seed_f=7)
+    sp_small = inputs.anisotropic(n=65, eps=0.5, seed_f=8)
+    bad = Solver(sp_big, levels=inputs.max_levels(sp_big.n), smoother="rbgs", precision="mixed",
+                 flags=FLAG_TEST_WAIT_TIMEOUT)
+    small = Solver(sp_small, levels=inputs.max_levels(sp_small.n), smoother="rbgs", precision="mixed")
+    (b0, x0), (b1, x1) = tensors(sp_big), tensors(sp_small)
+    batch = Batch([bad, small], [b0, b1], [x0, x1], mode=BATCH_PERSISTENT)
+    per, ctas, teams = batch.info()
+    assert per and ctas > teams   # the big instance's team has more than one CTA
+    infos = batch.solve(tol=1e-10)
+    assert infos[0]["status"] == "MG_ETIMEOUT"
+    assert infos[1]["status"] == "MG_OK" and oracle_relres(sp_small, x1.cpu().numpy()) <= 1e-10
+    batch.close()
+    good = Solver(sp_big, levels=inputs.max_levels(sp_big.n), smoother="rbgs", precision="mixed")
+    x0.zero_()
+    b2 = Batch([good, small], [b0, b1], [x0, x1], mode=BATCH_PERSISTENT)
+    infos = b2.solve(tol=1e-10)
+    assert all(i["status"] == "MG_OK" for i in infos)
+    assert oracle_relres(sp_big, x0.cpu().numpy()) <= 1e-10
+    b2.close()

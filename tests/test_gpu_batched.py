@@ -1,8 +1,8 @@
 """Batched solves (mg_batch_create / mg_batch_solve / mg_solve_batched) through the C ABI.
 
-Each instance of a batch runs exactly the kernels its own mg_solve runs (the same
-device-side loop, as one branch of one graph), so the batch must reproduce the
-individual solves bit for bit, with the same cycle counts; a few instances are also
+In the graph form each instance of a batch runs exactly the kernels its own mg_solve
+runs (the same device-side loop, as one branch of one graph), so the batch must
+reproduce the individual solves bit for bit, with the same cycle counts; a few instances are also
 checked against the oracle's FP64 residual.  Instances: uneven sizes, anisotropies
 eps in [1e-3, 1] with the smoother chosen for each, mixed and FP64 precision.
 """
@@ -19,7 +19,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_0805_3041_gb300.binding import (Solver, Batch, solve_batched, MGError, FLAG_NO_GRAPH,  # noqa: E402
-                                           EINVAL)
+                                           EINVAL, BATCH_GRAPH)
 
 
 def instances(count=10, seed=41):
@@ -44,7 +44,8 @@ def test_batch_matches_individual_solves():
     inst = instances()
     bs, xs = zip(*[tensors(sp) for sp, _ in inst])
     solvers = [s for _, s in inst]
-    batch = Batch(solvers, bs, xs)
+    batch = Batch(solvers, bs, xs, mode=BATCH_GRAPH)
+    assert not batch.info()[0]
     infos = batch.solve(tol=1e-10)
     for (sp, s), b, x, info in zip(inst, bs, xs, infos):
         xr = torch.zeros_like(b)
