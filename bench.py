@@ -426,7 +426,7 @@ def run_batched(args):
                for sp, cfg in zip(specs, cfgs)]
     bs = [torch.from_numpy(sp.b).to(dev) for sp in specs]
     xs = [torch.zeros_like(b) for b in bs]
-    batch = Batch(solvers, bs, xs)   # the persistent kernel when every instance qualifies
+    batch = Batch(solvers, bs, xs)   # small instances in the persistent kernel, the rest as a graph
     persistent, ctas, teams = batch.info()
     torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t0
@@ -509,13 +509,15 @@ def run_batched(args):
             "config": {"workload": f"{args.count} independent 2-D anisotropic Poisson instances, N uniform over "
                                    f"{{65,129,257,513,1025}}, eps log-uniform [1e-3,1], f~U[-1,1] seed 4, x0=0, "
                                    f"mixed precision to {args.tol:g}, "
-                                   + (f"one persistent cooperative launch per batch ({ctas} CTAs, {teams} teams)"
-                                      if persistent else "one CUDA graph launch per batch")
+                                   + (f"{persistent} instances up to 257^2 in one persistent cooperative launch "
+                                      f"({ctas} CTAs, {teams} teams), the other {args.count - persistent} in one "
+                                      f"CUDA graph launch" if persistent else "one CUDA graph launch per batch")
                                    + ", autotuned schedule per class",
                        "instances": args.count, "nodes": int(nodes), "schedules": classes,
                        "l2": "L2 flushed between steps"},
             "cycles_max": max(i["cycles"] for i in infos), "relres_max": max(i["relres"] for i in infos),
-            "form": "persistent" if persistent else "graph", "graph_form_ms": graph_ms,
+            "form": ("persistent + graph" if persistent < args.count else "persistent") if persistent else "graph",
+            "graph_form_ms": graph_ms,
             "sequential_mixed_ms": seq_ms, "sequential_fp64_ms": f64_ms,
             "fp64_relres_max": max(i["relres"] for i in f64),
             "setup_s": setup_s, "tune_s": tune_s, "roofline": None,

@@ -218,7 +218,10 @@ mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double to
  *   - graph (MG_BATCH_GRAPH): ONE CUDA graph launch with an independent branch per
  *     instance (copy in, initial check, a device-side loop to that instance's own test,
  *     copy out), for any contexts.
- *   MG_BATCH_AUTO takes the persistent form when every context qualifies, else the graph.
+ *   MG_BATCH_AUTO: the qualifying instances whose finest grid has at most 100,000 nodes (up to
+ *     257^2) in one persistent launch, then the others in one graph launch (an instance with a
+ *     large grid solves faster as graph branches spread over the whole GPU than as a team of
+ *     a few CTAs).
  *
  * mg_batch_create / mg_batch_create_ex: builds the batch for count contexts and their
  *   b[i] / x[i] (host arrays of device pointers; the pointer values are kept).  The
@@ -235,8 +238,8 @@ mg_status mg_solve_adjoint(mg_ctx *c, const double *g, double *lambda, double to
  *   first instance (in index order) that did not (MG_ENOCONV, MG_EDIVERGED,
  *   MG_ETIMEOUT); the x[i] hold each instance's last iterate either way (not for an
  *   instance that reports MG_ETIMEOUT).
- * mg_batch_info: the form a batch runs in, and for the persistent form its CTA and team
- *   counts.
+ * mg_batch_info: *persistent = the number of instances the persistent launch solves (0: the
+ *   graph alone), with its CTA and team counts.
  * mg_solve_batched: create (MG_BATCH_AUTO), solve and destroy in one call (the batch is
  *   built on every call; keep a batch to solve the same set repeatedly). */
 typedef struct mg_batch mg_batch;

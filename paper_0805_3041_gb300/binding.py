@@ -439,8 +439,8 @@ class Batch:
     """Several independent solves in one launch (mg_batch_create_ex / mg_batch_solve):
     solvers[i] solves its problem with right-hand side bs[i] and start vector / solution
     xs[i] (contiguous float64 CUDA tensors of the solver's shape, kept by reference).
-    mode: BATCH_AUTO (the persistent kernel when every solver qualifies, else one CUDA
-    graph), BATCH_GRAPH or BATCH_PERSISTENT.  Built once; solve() launches it and returns
+    mode: BATCH_AUTO (qualifying instances of up to 257^2 in the persistent kernel, the rest
+    in one CUDA graph), BATCH_GRAPH or BATCH_PERSISTENT.  Built once; solve() launches it and returns
     one info dict per instance."""
 
     def __init__(self, solvers, bs, xs, mode=BATCH_AUTO):
@@ -455,10 +455,10 @@ class Batch:
         self.handle = h.value
 
     def info(self):
-        """(persistent, ctas, teams) of the batch (mg_batch_info)."""
+        """(instances in the persistent launch, its CTAs, its teams) of the batch (mg_batch_info)."""
         per, ctas, teams = C.c_int(), C.c_int(), C.c_int()
         self.lib.mg_batch_info(self.handle, C.byref(per), C.byref(ctas), C.byref(teams))
-        return bool(per.value), ctas.value, teams.value
+        return per.value, ctas.value, teams.value
 
     def solve(self, tol=1e-10):
         """Solve every instance; one info dict per instance, whose status says how that instance

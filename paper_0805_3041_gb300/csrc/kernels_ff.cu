@@ -18,8 +18,9 @@
 // a final FP64 defect.
 //
 // One warp covers 32 columns and marches down a band of rows, holding the split rows j-1, j,
-// j+1 in registers; x-neighbours come by shuffles (the strip's edge lanes split the column
-// beside the strip themselves).  2-D, constant or separable coefficients.
+// j+1 in registers and the loads of the next rows in flight; x-neighbours come by shuffles (the
+// strip's edge lanes split the column beside the strip themselves).  2-D, constant or separable
+// coefficients.
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -32,8 +33,8 @@ struct FF {
 };
 
 // d = h + l with h its leading 24 significant bits (truncated) and l the next 23 (truncated),
-// from the bit pattern alone.  |d| below 2^-80 splits to l = 0 (below 2^-126: h = 0 as well);
-// an error of at most 2^-80 |d|... i.e. nothing that matters next to the stencil's other terms.
+// from the bit pattern alone.  |d| below 2^-80 splits with l = 0 (an absolute error below
+// 2^-103), below 2^-126 to h = l = 0: far below every other term of the stencil.
 __device__ __forceinline__ FF split(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
@@ -131,19 +132,21 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
     if (L.per) j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
     return (long long)j * L.pitch;
   };
-  auto load = [&](int r) -> FF {   // x at (i, row r); rows outside the unknowns (Dirichlet) read 0
-    FF z;
-    z.h = 0.f;
-    z.l = 0.f;
-    if (!act) return z;
-    if (!L.per && (r < 0 || r >= rows)) return z;
-    return split(x[row_of(r) + i]);
+  auto raw = [&](int r) -> double {   // x at (i, row r); rows outside the unknowns (Dirichlet) read 0
+    if (!act || (!L.per && (r < 0 || r >= rows))) return 0.0;
+    return x[row_of(r) + i];
   };
   float acc = 0.f;
   if (r0 < r1) {
-    FF xm = load(r0 - 1), xc = load(r0), xp;
+    FF xm = split(raw(r0 - 1)), xc = split(raw(r0)), xp;
+    // one row of lookahead: the loads of row r + 2 (x) and r + 1 (b) are in flight while row r
+    // is computed
+    double xnext = raw(r0 + 1);
+    double bcur = act ? b[row_of(r0) + i] : 0.0;
     for (int r = r0; r < r1; ++r) {
-      xp = load(r + 1);
+      const double xafter = raw(r + 2);
+      const double bnext = (act && r + 1 < r1) ? b[row_of(r + 1) + i] : 0.0;
+      xp = split(xnext);
       const long long p = row_of(r) + i;
       // x-neighbours: the adjacent lanes' values, the edge lanes' from the column beside
       FF xw, xe;
@@ -160,33 +163,38 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         else xe = xo;
       }
       if (act) {
-        const FF bb = split(b[p]);
-        float p1, e1, p2, e2, p3, e3, p4, e4;
+        const FF bb = split(bcur);
+        float p1, e1, p2, e2, p3, e3;
         prod(cD, xc, p1, e1);
-        if (KIND == K_CONST) {
-          const FF sx = add(xw, xe);
-          prod(cW, sx, p2, e2);
-          p4 = 0.f;
-          e4 = 0.f;
-        } else {
-          prod(cW, xw, p2, e2);
-          prod(cE, xe, p4, e4);
-        }
         const FF sy = add(xm, xp);
         prod(cY, sy, p3, e3);
         // b - D x_p + W x_w + E x_e + Y (x_s + x_n): the leading parts by TwoSum, the rest added
-        float s, t1, t2, t3, t4;
+        float s, t1, t2, t3;
         two_sum(bb.h, -p1, s, t1);
-        two_sum(s, p2, s, t2);
-        two_sum(s, p3, s, t3);
-        two_sum(s, p4, s, t4);
-        const float lo = (((bb.l - e1) + (e2 + e3)) + e4) + ((t1 + t2) + (t3 + t4));
+        float lo;
+        if (KIND == K_CONST) {
+          const FF sx = add(xw, xe);
+          prod(cW, sx, p2, e2);
+          two_sum(s, p2, s, t2);
+          two_sum(s, p3, s, t3);
+          lo = ((bb.l - e1) + (e2 + e3)) + ((t1 + t2) + t3);
+        } else {
+          float p4, e4, t4;
+          prod(cW, xw, p2, e2);
+          prod(cE, xe, p4, e4);
+          two_sum(s, p2, s, t2);
+          two_sum(s, p3, s, t3);
+          two_sum(s, p4, s, t4);
+          lo = (((bb.l - e1) + (e2 + e3)) + e4) + ((t1 + t2) + (t3 + t4));
+        }
         const float res = s + lo;
         r32[p] = res;
         acc = fmaf(res, res, acc);
       }
       xm = xc;
       xc = xp;
+      xnext = xafter;
+      bcur = bnext;
     }
   }
   const float bs = block_sum_ff(acc);

@@ -996,8 +996,8 @@ static cudaError_t capture_loop(mg_ctx *c, cudaStream_t s, int transposed, long 
     // the loop stopped on the float-float defect: the FP64 residual of the result, reported
     long long f0 = c->launches;
     Launch lc{s, &c->launches};
-    launch_defect_norm<double>(lc, lev64(c, c->L), c->kind, c->x64, c->b64, c->partials, norm_parts_count(),
-                               c->scal + 1);
+    launch_defect64_to32(lc, lev64(c, c->L), c->kind, c->x64, c->b64, c->d32[c->L].g, c->partials,
+                         norm_parts_count(), c->scal + 1);
     launch_final_check(lc, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4);
     e = cudaGetLastError();
     *init_k += c->launches - f0;
@@ -1673,7 +1673,8 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     if (c->mixed && c->ff && it > 0 && std::isfinite(rr)) {
       exact = rr <= tol * kFFStop;
       if (exact) {
-        launch_defect_norm<double>(lc, F64, c->kind, c->x64, c->b64, c->partials, norm_parts_count(), c->scal + 1);
+        launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
+                             c->scal + 1);
         launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
         CK(cudaMemcpyAsync(c->h_relres, c->scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -1749,8 +1750,13 @@ struct mg_batch {
   double *host = nullptr;        // pinned: [0] tolerance, then one report row per instance
   int stride = 0;                // doubles per report row: loop state (2), ||b||^2 (1), history
   std::vector<long long> loop_init, loop_body, extra;   // kernel counts per instance
-  // persistent form: one cooperative launch over all instances
+  // persistent form: one cooperative launch over the instances marked in pers (all of them, or in
+  // the automatic form those with small grids; the rest run as the graph's branches)
   bool persistent = false;
+  std::vector<char> pers;
+  std::vector<mg_status> pstat;   // status of each persistent instance in the last solve
+  int npers = 0;
+  bool has_graph = false;
   int grid = 0, nteams = 0;
   BatchTeam *d_teams = nullptr;   // device tables (in the first context's workspace)
   BatchInst *d_insts = nullptr;
@@ -1864,16 +1870,22 @@ struct BatchProg {
 };
 
 static const long long kBatchSoloNodes = 17000;   // grids up to 129^2 on one CTA
+// MG_BATCH_AUTO: instances whose finest grid holds at most this many nodes (padded; 257^2 grids)
+// go to the persistent kernel, larger ones to the graph (measured: the persistent kernel solves
+// 145 instances of 65^2..257^2 in 40 ms against the graph's 49 ms, but 60 of 1025^2 in 171 ms
+// against 68 ms, each such instance getting a few CTAs instead of the whole GPU)
+static const long long kBatchAutoMaxNodes = 100000;
 
 // Lay out the persistent form of a batch: programs and level tables in each instance's
 // workspace (after its coarse programs), the instance, team, order and barrier tables in the
 // first instance's.  Returns false (nothing launched, nothing changed on the device) when an
 // instance does not qualify or the tables do not fit.
-static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
-  const int count = (int)bt->cs.size();
-  for (mg_ctx *c : bt->cs)
-    if (!batch_persistent_ok(c)) return false;
-  mg_ctx *c0 = bt->cs[0];
+static bool batch_build_persistent(mg_batch *bt, const double *tol_dev, const std::vector<int> &sel) {
+  const int count = (int)sel.size();
+  if (count < 1) return false;
+  for (int i : sel)
+    if (!batch_persistent_ok(bt->cs[i])) return false;
+  mg_ctx *c0 = bt->cs[sel[0]];
   int sms = 0, coop = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c0->dev) != cudaSuccess || !coop) {
@@ -1885,7 +1897,7 @@ static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
   const int G = sms * per_sm;
   // team sizes in proportion to the finest grid's nodes, at least one CTA each
   std::vector<long long> nodes(count);
-  for (int i = 0; i < count; ++i) nodes[i] = (long long)bt->cs[i]->geo[bt->cs[i]->L].count;
+  for (int i = 0; i < count; ++i) nodes[i] = (long long)bt->cs[sel[i]]->geo[bt->cs[sel[i]]->L].count;
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nodes[a] > nodes[b]; });
@@ -1940,7 +1952,7 @@ static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
   struct Up { void *dst; std::vector<char> bytes; };
   std::vector<Up> uploads;
   for (int i = 0; i < count; ++i) {
-    mg_ctx *c = bt->cs[i];
+    mg_ctx *c = bt->cs[sel[i]];
     BatchProg pb(c, kBatchSoloNodes);
     pb.build();
     std::vector<BatchLev> lv(c->L);
@@ -1969,8 +1981,8 @@ static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
     I.kind = c->kind;
     I.x64 = c->x64;
     I.b64 = c->b64;
-    I.bcall = bt->b[i];
-    I.xcall = bt->x[i];
+    I.bcall = bt->b[sel[i]];
+    I.xcall = bt->x[sel[i]];
     I.swap = c->swap ? 1 : 0;
     I.n0c = c->swap ? c->geo[c->L].n[1] : c->geo[c->L].n[0];
     I.n1c = c->swap ? c->geo[c->L].n[0] : c->geo[c->L].n[1];
@@ -1978,7 +1990,7 @@ static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
     I.cidx = c->cidx;
     I.nc = c->nc;
     I.scal = c->scal;
-    I.hrow = hdev + 1 + (size_t)i * bt->stride;   // the report row
+    I.hrow = hdev + 1 + (size_t)sel[i] * bt->stride;   // the instance's report row
     I.st = c->st;
     I.tol = tol_dev;
     I.maxit = c->P.max_cycles;
@@ -2028,6 +2040,10 @@ static bool batch_build_persistent(mg_batch *bt, const double *tol_dev) {
     return false;
   }
   bt->persistent = true;
+  bt->pers.assign(bt->cs.size(), 0);
+  bt->pstat.assign(bt->cs.size(), MG_OK);
+  for (int i : sel) bt->pers[i] = 1;
+  bt->npers = count;
   bt->grid = grid;
   bt->nteams = (int)nt;
   bt->d_teams = d_teams;
@@ -2070,20 +2086,30 @@ static mg_status batch_create(mg_ctx *const *cs, int count, const double *const 
     return MG_ECUDA;
   }
   std::memset(bt->host, 0, sizeof(double) * (1 + (size_t)count * bt->stride));
+  bt->pers.assign(count, 0);
   if (mode != MG_BATCH_GRAPH) {
+    // persistent: every instance (MG_BATCH_PERSISTENT), or the qualifying ones with small finest
+    // grids (MG_BATCH_AUTO; larger ones solve faster as graph branches over the whole GPU)
+    std::vector<int> sel;
+    for (int i = 0; i < count; ++i)
+      if (mode == MG_BATCH_PERSISTENT ||
+          (batch_persistent_ok(cs[i]) && (long long)cs[i]->geo[cs[i]->L].count <= kBatchAutoMaxNodes))
+        sel.push_back(i);
     double *hdev = nullptr;
-    bool ok = cudaHostGetDevicePointer((void **)&hdev, bt->host, 0) == cudaSuccess;
+    bool ok = !sel.empty() && cudaHostGetDevicePointer((void **)&hdev, bt->host, 0) == cudaSuccess;
     if (!ok) cudaGetLastError();
-    if (ok && batch_build_persistent(bt, hdev)) {
-      *out = bt;
-      return MG_OK;
-    }
-    if (mode == MG_BATCH_PERSISTENT) {
+    ok = ok && batch_build_persistent(bt, hdev, sel);
+    if (mode == MG_BATCH_PERSISTENT && !ok) {
       c0->err = "the persistent batched solve does not cover these instances";
       batch_free(bt);
       return MG_EINVAL;
     }
+    if (ok && bt->npers == count) {
+      *out = bt;
+      return MG_OK;
+    }
   }
+  bt->has_graph = true;
   // capture: fork one branch per instance from the root stream, join them at the end
   cudaStream_t root = nullptr;
   std::vector<cudaEvent_t> evs(count + 1, nullptr);
@@ -2094,6 +2120,7 @@ static mg_status batch_create(mg_ctx *const *cs, int count, const double *const 
   bool capturing = e == cudaSuccess;
   if (e == cudaSuccess) e = cudaEventRecord(evs[count], root);
   for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    if (bt->pers[i]) continue;   // solved by the persistent kernel
     mg_ctx *c = cs[i];
     cudaStream_t s = c->cap;
     Launch lc{s, &c->launches};
@@ -2151,7 +2178,7 @@ mg_status mg_batch_create_ex(mg_ctx *const *cs, int count, const double *const *
 
 mg_status mg_batch_info(const mg_batch *bt, int *persistent, int *ctas, int *teams) {
   if (!bt) return MG_EINVAL;
-  if (persistent) *persistent = bt->persistent ? 1 : 0;
+  if (persistent) *persistent = bt->persistent ? bt->npers : 0;
   if (ctas) *ctas = bt->grid;
   if (teams) *teams = bt->nteams;
   return MG_OK;
@@ -2170,6 +2197,7 @@ static mg_status batch_solve_persistent(mg_batch *bt, double tol, mg_report *rep
   CK(cudaStreamSynchronize(c->stream));
   mg_status result = MG_OK;
   for (int i = 0; i < count; ++i) {
+    if (!bt->pers[i]) continue;
     mg_ctx *ci = bt->cs[i];
     const double *row = bt->host + 1 + (size_t)i * bt->stride;
     int st4[4];
@@ -2183,6 +2211,7 @@ static mg_status batch_solve_persistent(mg_batch *bt, double tol, mg_report *rep
       si = MG_ETIMEOUT;
     }
     if (si != MG_OK && result == MG_OK) result = si;
+    bt->pstat[i] = si;
     if (reps) {
       mg_report &r = reps[i];
       const double *hist = row + 3;
@@ -2200,7 +2229,12 @@ static mg_status batch_solve_persistent(mg_batch *bt, double tol, mg_report *rep
 
 mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps) {
   if (!bt || !(tol >= 0.0)) return MG_EINVAL;
-  if (bt->persistent) return batch_solve_persistent(bt, tol, reps);
+  if (bt->persistent && !bt->has_graph) return batch_solve_persistent(bt, tol, reps);
+  mg_status pres = MG_OK;
+  if (bt->persistent) {   // the small instances first, in one cooperative launch; then the graph
+    pres = batch_solve_persistent(bt, tol, reps);
+    if (pres != MG_OK && pres != MG_ENOCONV && pres != MG_EDIVERGED && pres != MG_ETIMEOUT) return pres;
+  }
   auto t0 = std::chrono::steady_clock::now();
   mg_ctx *c = bt->cs[0];
   const int count = (int)bt->cs.size();
@@ -2210,6 +2244,10 @@ mg_status mg_batch_solve(mg_batch *bt, double tol, mg_report *reps) {
   mg_status result = MG_OK;
   bool fixups = false;
   for (int i = 0; i < count; ++i) {
+    if (bt->persistent && bt->pers[i]) {   // reported by the persistent launch above
+      if (bt->pstat[i] != MG_OK && result == MG_OK) result = bt->pstat[i];
+      continue;
+    }
     mg_ctx *ci = bt->cs[i];
     const double *row = bt->host + 1 + (size_t)i * bt->stride;
     int st3[3];

@@ -62,7 +62,7 @@ def test_persistent_batch_reaches_the_fp64_residual():
     bs, xs = zip(*[tensors(sp) for sp, _ in inst])
     batch = Batch([s for _, s in inst], bs, xs, mode=BATCH_PERSISTENT)
     per, ctas, teams = batch.info()
-    assert per and teams == len(inst) and ctas >= teams
+    assert per == len(inst) and teams == len(inst) and ctas >= teams
     infos = batch.solve(tol=1e-10)
     for (sp, s), b, x, info in zip(inst, bs, xs, infos):
         rr = oracle_relres(sp, x.cpu().numpy())
@@ -98,7 +98,7 @@ def test_more_instances_than_resident_ctas():
     bs, xs = zip(*[tensors(sp) for sp, _ in inst])
     batch = Batch([s for _, s in inst], bs, xs, mode=BATCH_PERSISTENT)
     per, ctas, teams = batch.info()
-    assert per and teams < len(inst)
+    assert per == len(inst) and teams < len(inst)
     infos = batch.solve(tol=1e-10)
     for (sp, s), x, info in list(zip(inst, xs, infos))[::37]:
         assert info["status"] == "MG_OK" and oracle_relres(sp, x.cpu().numpy()) <= 1e-10
@@ -111,23 +111,36 @@ def test_zero_rhs_and_forms():
     bs, xs = zip(*[tensors(sp) for sp, _ in inst])
     bs[2].zero_()
     xs[2].fill_(1.0)
-    batch = Batch([s for _, s in inst], bs, xs)      # AUTO: every instance qualifies
-    assert batch.info()[0]
+    batch = Batch([s for _, s in inst], bs, xs)      # AUTO: every instance qualifies and is small
+    assert batch.info()[0] == len(inst)
     infos = batch.solve(tol=1e-10)
     assert infos[2]["status"] == "MG_OK" and infos[2]["cycles"] == 0 and torch.count_nonzero(xs[2]) == 0
     batch.close()
-    # an instance the persistent form does not cover: AUTO takes the graph, PERSISTENT refuses
+    # an instance the persistent form does not cover (3-D) and one too large for it under AUTO:
+    # AUTO solves the small 2-D ones in the persistent launch and the two others as graph
+    # branches; PERSISTENT refuses the set
     sp3 = inputs.poisson_3d(n=17, seed=5)
     s3 = Solver(sp3, levels=3, smoother="rbgs", precision="mixed")
     b3, x3 = tensors(sp3)
-    solvers = [s for _, s in inst] + [s3]
-    auto = Batch(solvers, list(bs) + [b3], list(xs) + [x3], mode=BATCH_AUTO)
-    assert not auto.info()[0]
+    sp4 = inputs.anisotropic(n=513, eps=0.7, seed_f=9)
+    s4 = Solver(sp4, levels=inputs.max_levels(sp4.n), smoother="rbgs", precision="mixed")
+    b4, x4 = tensors(sp4)
+    solvers = [s for _, s in inst] + [s3, s4]
+    for x in xs:
+        x.zero_()
+    auto = Batch(solvers, list(bs) + [b3, b4], list(xs) + [x3, x4], mode=BATCH_AUTO)
+    assert auto.info()[0] == len(inst)
+    infos = auto.solve(tol=1e-10)
+    assert all(i["status"] == "MG_OK" for i in infos)
+    for sp, x in ((sp4, x4), (inst[0][0], xs[0])):
+        assert oracle_relres(sp, x.cpu().numpy()) <= 1e-10
+    o3 = orc.Oracle(orc.Problem(dim=3, n=sp3.n, kind=sp3.kind, h=sp3.h, c=sp3.c), levels=1, dense_max=0)
+    assert o3.norm(o3.defect(x3.cpu().numpy(), sp3.b)) <= 1e-10 * o3.norm(sp3.b)
     auto.close()
     with pytest.raises(MGError) as e:
-        Batch(solvers, list(bs) + [b3], list(xs) + [x3], mode=BATCH_PERSISTENT)
+        Batch([s for _, s in inst] + [s3], list(bs) + [b3], list(xs) + [x3], mode=BATCH_PERSISTENT)
     assert e.value.status == EINVAL
-    assert not Batch([s for _, s in inst], bs, xs, mode=BATCH_GRAPH).info()[0]
+    assert Batch([s for _, s in inst], bs, xs, mode=BATCH_GRAPH).info()[0] == 0
 
 
 def test_barrier_wait_that_runs_out_reports_timeout():
@@ -143,7 +156,7 @@ def test_barrier_wait_that_runs_out_reports_timeout():
     (b0, x0), (b1, x1) = tensors(sp_big), tensors(sp_small)
     batch = Batch([bad, small], [b0, b1], [x0, x1], mode=BATCH_PERSISTENT)
     per, ctas, teams = batch.info()
-    assert per and ctas > teams   # the big instance's team has more than one CTA
+    assert per == 2 and ctas > teams   # the big instance's team has more than one CTA
     infos = batch.solve(tol=1e-10)
     assert infos[0]["status"] == "MG_ETIMEOUT"
     assert infos[1]["status"] == "MG_OK" and oracle_relres(sp_small, x1.cpu().numpy()) <= 1e-10

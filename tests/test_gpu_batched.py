@@ -45,7 +45,7 @@ def test_batch_matches_individual_solves():
     bs, xs = zip(*[tensors(sp) for sp, _ in inst])
     solvers = [s for _, s in inst]
     batch = Batch(solvers, bs, xs, mode=BATCH_GRAPH)
-    assert not batch.info()[0]
+    assert batch.info()[0] == 0
     infos = batch.solve(tol=1e-10)
     for (sp, s), b, x, info in zip(inst, bs, xs, infos):
         xr = torch.zeros_like(b)
