@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mg.h"
 #include "coarse_prog.h"
 #include "batch_prog.h"
@@ -127,6 +129,22 @@ struct mg_ctx {
 // is below this fraction of the tolerance (its error is ~1e-2 of ||r|| there); the FP64 residual
 // computed afterwards is the one reported.
 static const double kFFStop = 0.5;
+
+// NVTX ranges name the phases of the cycle (solve, refinement step, each level's descending
+// and ascending half, the coarse cycle in one CTA, the coarsest solve) for profilers.  They are
+// pushed on the host around the launches: kernel by kernel (MG_FLAG_NO_GRAPH) they bracket
+// the phase's kernels on a timeline; in the graph form they bracket the capture.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  NvtxRange(const char *what, int level) {
+    char buf[64];
+    snprintf(buf, sizeof buf, "level %d: %s", level, what);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // the operator form of level l: the context's coefficient kind, or K_NINE on Galerkin coarse levels
 static int lev_kind(const mg_ctx *c, int l) { return (c->galerkin && l < c->L) ? K_NINE : c->kind; }
@@ -616,6 +634,7 @@ static void coarse_solve_into(mg_ctx *c, const Launch &lc, const T *g, T *u) {
 }
 template <typename T>
 static void coarse_solve(Sched &S, const T *g) {
+  NvtxRange nr("coarsest solve");
   mg_ctx *c = S.c;
   LevData<T> &D = LevOf<T>::data(c, 1);
   coarse_solve_into<T>(c, S.lc, g, D.u[c->cur[1]]);
@@ -629,6 +648,7 @@ static const int PROG_FMG = 8;   // nested iteration on levels 1..lcut
 
 template <typename T>
 static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out) {
+  NvtxRange nr("coarse grids in one CTA");
   mg_ctx *c = S.c;
   launch_coarse_cycle<T>(S.lc, c->P.dim, c->kind, c->slev, c->prog + c->prog_off[pid], c->prog_len[pid], c->lcut,
                          g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)corr_weight(c),
@@ -766,6 +786,7 @@ static void emit_adapt(Sched &S, int l, const T *g) {
 // red-black grids run both sweeps, the defect and the restriction in one pass.
 template <typename T>
 static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start) {
+  NvtxRange nr("pre-smoothing, defect, restriction", l);
   mg_ctx *c = S.c;
   LevData<T> &D = LevOf<T>::data(c, l);
   LevData<T> &Dc = LevOf<T>::data(c, l - 1);
@@ -797,6 +818,7 @@ static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start
 // post-smoothing sweeps; the correction is folded into the first fused red-black sweep.
 template <typename T>
 static void ascend(Sched &S, int l, const T *g, int transposed) {
+  NvtxRange nr("correction, post-smoothing", l);
   mg_ctx *c = S.c;
   LevData<T> &Dc = LevOf<T>::data(c, l - 1);
   Lev<T> Lc = LevOf<T>::get(c, l - 1);
@@ -891,6 +913,7 @@ static void emit_fmg_start(Sched &S) {
 
 // FP64 form: one F-cycle on the finest level followed by the residual check.
 static void emit_fp64_cycle(Sched &S, int transposed) {
+  NvtxRange nr("F-cycle");
   mg_ctx *c = S.c;
   int L = c->L;
   c->cur[L] = 0;
@@ -906,6 +929,7 @@ static void emit_fp64_cycle(Sched &S, int transposed) {
 
 // Mixed form: FP32 inner F-cycles on r32 from zero, FP64 update, FP64 defect and check.
 static void emit_mixed_step(Sched &S, int transposed) {
+  NvtxRange nr("refinement step: FP32 F-cycle, update, outer defect");
   mg_ctx *c = S.c;
   int L = c->L;
   for (int q = 0; q < c->P.inner_cycles; ++q) {
@@ -1559,6 +1583,7 @@ static mg_status store_vec(mg_ctx *c, const Launch &lc, const Lev<double> &F, co
 // Shared driver of mg_solve / mg_solve_host / mg_solve_adjoint.
 static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg_report *rep, int transposed,
                            bool host = false) {
+  NvtxRange nr(transposed ? "adjoint solve" : "solve");
   auto t0 = std::chrono::steady_clock::now();
   int L = c->L;
   Launch lc{c->stream, &c->launches};
