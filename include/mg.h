@@ -105,9 +105,17 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        By default, in 2-D with constant or separable coefficients, that
                                        defect is evaluated in float-float arithmetic (each FP64 operand
                                        split into two floats, error-free FP32 sums and products; about
-                                       2^-46 of |A||x| in error instead of 2^-53), the loop stops when
-                                       that residual is below half the tolerance, and the reported
-                                       relative residual is the FP64 one of the result */
+                                       2^-46 of |b| + |A||x| in error instead of 2^-53).  The kernel
+                                       also sums (|b| + |A||x|)^2; the loop stops on that residual only
+                                       when it is below the tolerance by the error estimate E = 2^-46
+                                       times the root of that sum, moves to FP64 defects when E is half
+                                       the tolerance or more, when the residual is within 10 E of the
+                                       tolerance or when a step cuts it by less than half, and the
+                                       reported relative residual is the FP64 one of the result */
+#define MG_FLAG_NO_PDL          1024u /* graphs keep ordinary dependencies between kernels (by default the
+                                       kernel-to-kernel edges of the solve's graphs are programmatic: a
+                                       kernel's launch overlaps its predecessor's end and waits for its
+                                       completion before reading) -- results do not depend on it */
 #define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
                                        first single-precision TMA sweep is left out, so that the compute
                                        warps' bounded waits run out (about a second) and the solve returns
@@ -331,8 +339,9 @@ mg_status mg_step_descend(mg_ctx *c, int level, const double *u, const double *g
 mg_status mg_step_ascend(mg_ctx *c, int level, const double *ec, const double *u, const double *g, double *u_out,
                          int transposed);
 /* MG_MIXED contexts: the refinement loop's defect r = (float)(b - A x) of the finest grid, as the
- * solve computes it (float-float or FP64, see MG_FLAG_FP64_DEFECT), widened to FP64 into r (caller
- * layout); *sq (host, may be NULL) receives the sum of its squares.  MG_EINVAL for FP64 contexts. */
+ * solve's loop first computes it (float-float or FP64, see MG_FLAG_FP64_DEFECT), widened to FP64
+ * into r (caller layout); *sq (host, may be NULL) receives the sum of its squares.  MG_EINVAL for
+ * FP64 contexts. */
 mg_status mg_step_outer_defect(mg_ctx *c, const double *x, const double *b, double *r, double *sq);
 
 /* Mean duration (ms) of the finest-level smoothing launches recorded since the

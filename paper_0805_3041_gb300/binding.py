@@ -24,6 +24,7 @@ FLAG_ADAPTIVE_CORR = 64
 FLAG_TEST_WAIT_TIMEOUT = 128
 FLAG_GALERKIN = 256
 FLAG_FP64_DEFECT = 512
+FLAG_NO_PDL = 1024
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6

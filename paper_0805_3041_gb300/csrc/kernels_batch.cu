@@ -486,6 +486,7 @@ __device__ bool run_instance(const BatchInst &I, TeamState &t, int epoch) {
 
 __global__ void __launch_bounds__(BT) k_batch(const BatchTeam *teams, int nteams, const BatchInst *insts,
                                               const int *order, int epoch) {
+  MG_PDL_WAIT();
   // this CTA's team
   int lo = 0, hi = nteams - 1;
   while (lo < hi) {

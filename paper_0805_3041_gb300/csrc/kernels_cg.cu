@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(Lev<double> L, const T
                                                            double *__restrict__ p, double *__restrict__ ap,
                                                            double *__restrict__ part, int max_it, double rtol2,
                                                            int *__restrict__ iters) {
+  MG_PDL_WAIT();
   cgx::grid_group grid = cgx::this_grid();
   __shared__ double red[33];
   const int nx = L.n0 - 2;

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__r
                                                        const double *__restrict__ Ainv,
                                                        const long long *__restrict__ cidx_smem, int nc, T omega,
                                                        T omega_corr) {
+  MG_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *pool = reinterpret_cast<T *>(smem_raw);
   // stage the level table and the program in shared memory (each step reads them)

@@ -81,6 +81,7 @@ template <typename T, int KIND, int MODE>
 __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                               T *__restrict__ out, T omega, int first, Lev<T> C,
                                               const T *__restrict__ ec, T omega_corr) {
+  MG_PDL_WAIT();
   __shared__ T su[(TY + 4) * SX];        // u rows j0-2 .. j0+TY+1, columns i0-2 .. i0+TX+1 at c = 0 .. TX+3
   __shared__ T sg[(TY + 2) * SX];        // g rows j0-1 .. j0+TY, columns i0-1 .. i0+TX at c = 1 .. TX+2
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -166,6 +167,7 @@ template <typename T, int KIND, int MODE, int NS>
 __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                  T *__restrict__ out, T omega, int first, Lev<T> C,
                                                  const T *__restrict__ ec, T omega_corr) {
+  MG_PDL_WAIT();
   constexpr int H = 2 * NS;                 // halo of the u tile
   constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
   constexpr int SXN = TX + 2 * H + 1;       // smem row stride
@@ -241,6 +243,7 @@ template <typename T, int KIND, int MODE, int NS>
 __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T *__restrict__ u,
                                                     const T *__restrict__ g, T *__restrict__ out, T omega, int first,
                                                     T *__restrict__ gc) {
+  MG_PDL_WAIT();
   constexpr int H = 2 * NS + 2;             // halo of the u tile
   constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
   constexpr int SXN = TX + 2 * H + 1;       // smem row stride
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, const T *__restrict__ u,
                                                            const T *__restrict__ g, T *__restrict__ gc) {
+  MG_PDL_WAIT();
   constexpr int CY = CYOf<T>::v;
   constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;   // fine defect region
   constexpr int US = RX + 3;                        // smem stride

@@ -11,11 +11,16 @@
 // right-hand side), with the sum of its squares for the stopping test.
 //
 // Accuracy: the pair keeps |d - (hi + lo)| <= 2^-46 |d| of each operand; the stencil terms are
-// then summed almost exactly, so the defect's error is about 2^-46 times the largest term,
-// |A||x|, instead of FP64's 2^-53 (a numpy emulation of the 4097^2 benchmark put it at 5e-2
-// of ||r|| at a relative residual of 2e-11, 1e-2 at 1e-10).  The solver therefore stops the
-// loop on this defect with a margin (half the tolerance) and reports the relative residual of
-// a final FP64 defect.
+// then summed almost exactly, so the defect's error at a node is a few 2^-46 times its largest
+// terms, |b| + |A||x|, instead of FP64's 2^-53.  How much of that shows in ||r|| depends on the
+// problem: on the 4097^2 isotropic benchmark near convergence the error is ~1e-12 ||b||
+// (0.04 of 2^-46 ||(|b| + |A||x|)||); on strongly anisotropic lines (eps = 1e3) it is 0.19 of
+// that norm, 7e-11 ||b||, too large for a 1e-10 stopping test.  The kernel therefore also
+// returns the sum of squares of |b| + |A||x| (from the leading parts), the solver estimates
+// the error as a fraction of its root, stops on this defect only when the residual is below
+// the tolerance by that margin, and switches the loop to FP64 defects (use64, which this
+// kernel reads) once the residual is within the margin of the tolerance.  The relative
+// residual reported is that of a final FP64 defect.
 //
 // One warp covers 32 columns and marches down a band of rows, holding the split rows j-1, j,
 // j+1 in registers and the loads of the next rows in flight; x-neighbours come by shuffles (the
@@ -85,24 +90,39 @@ __device__ __forceinline__ FF add(const FF &a, const FF &b) {
   return r;
 }
 
-__device__ __forceinline__ float block_sum_ff(float v) {
-  __shared__ float red[FX * FY / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// block sums of two values; thread 0 gets both
+__device__ __forceinline__ void block_sum2_ff(float &v, float &w) {
+  __shared__ float red[2][FX * FY / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, o);
+    w += __shfl_down_sync(0xffffffffu, w, o);
+  }
   const int t = threadIdx.y * FX + threadIdx.x;
-  if ((t & 31) == 0) red[t >> 5] = v;
+  if ((t & 31) == 0) {
+    red[0][t >> 5] = v;
+    red[1][t >> 5] = w;
+  }
   __syncthreads();
-  float s = 0.f;
-  if (t == 0)
-    for (int w = 0; w < FX * FY / 32; ++w) s += red[w];
-  return s;
+  if (t == 0) {
+    v = w = 0.f;
+    for (int k = 0; k < FX * FY / 32; ++k) {
+      v += red[0][k];
+      w += red[1][k];
+    }
+  }
 }
 
-// r32 = (float)(b - A x) at the unknowns of rows [band * R, band * R + R), and one partial sum
-// of r32^2 per block
+// r32 = (float)(b - A x) at the unknowns of rows [band * R, band * R + R), one partial sum of
+// r32^2 per block, and one of (|b| + |A||x|)^2 per block (partials + half).  With *use64 set
+// the same marching evaluates the defect in FP64, in the FP64 defect kernel's order, and the
+// second sum is 0.
 template <int KIND>
 __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const double *__restrict__ x,
                                                       const double *__restrict__ b, float *__restrict__ r32,
-                                                      double *__restrict__ partials, int R) {
+                                                      double *__restrict__ partials, int half, int R,
+                                                      const int *__restrict__ use64) {
+  MG_PDL_WAIT();
+  const bool f64 = use64 != nullptr && *use64 != 0;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const int i = 1 + (blockIdx.x * FY + threadIdx.y) * FX + lane;   // this thread's column
@@ -136,8 +156,49 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
     if (!act || (!L.per && (r < 0 || r >= rows))) return 0.0;
     return x[row_of(r) + i];
   };
-  float acc = 0.f;
-  if (r0 < r1) {
+  float acc = 0.f, acc2 = 0.f;
+  if (f64 && r0 < r1) {
+    double wW, wE, wY, dD;
+    if (KIND == K_CONST) {
+      wW = wE = L.cx;
+      wY = L.cy;
+      dD = L.d;
+    } else {
+      wW = L.sx[ic - 1];
+      wE = L.sx[ic];
+      wY = L.sy[ic];
+      dD = (wW + wE) + (wY + wY);
+    }
+    double xm = raw(r0 - 1), xc = raw(r0), xnext = raw(r0 + 1);
+    double bcur = act ? b[row_of(r0) + i] : 0.0;
+    for (int r = r0; r < r1; ++r) {
+      const double xafter = raw(r + 2);
+      const double bnext = (act && r + 1 < r1) ? b[row_of(r + 1) + i] : 0.0;
+      const double xp = xnext;
+      const long long p = row_of(r) + i;
+      double xw = __shfl_up_sync(FULL, xc, 1), xe = __shfl_down_sync(FULL, xc, 1);
+      if (edge) {
+        const double xo = oin ? x[p - i + io] : 0.0;
+        if (lane == 0) xw = xo;
+        else xe = xo;
+      }
+      if (act) {
+        double s = fma(-dD, xc, bcur);
+        s = fma(wW, xw, s);
+        s = fma(wE, xe, s);
+        s = fma(wY, xm, s);
+        s = fma(wY, xp, s);
+        const float res = (float)s;
+        r32[p] = res;
+        acc = fmaf(res, res, acc);
+      }
+      xm = xc;
+      xc = xp;
+      xnext = xafter;
+      bcur = bnext;
+    }
+  } else if (r0 < r1) {
+    const float aW = fabsf(cW.h), aE = fabsf(cE.h), aY = fabsf(cY.h), aD = fabsf(cD.h);
     FF xm = split(raw(r0 - 1)), xc = split(raw(r0)), xp;
     // one row of lookahead: the loads of row r + 2 (x) and r + 1 (b) are in flight while row r
     // is computed
@@ -190,6 +251,11 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         const float res = s + lo;
         r32[p] = res;
         acc = fmaf(res, res, acc);
+        // |b| + |A||x| from the leading parts: the scale of this node's float-float error
+        const float tt = fmaf(aD, fabsf(xc.h),
+                              fmaf(aW, fabsf(xw.h), fmaf(aE, fabsf(xe.h), fmaf(aY, fabsf(xm.h) + fabsf(xp.h),
+                                                                                fabsf(bb.h)))));
+        acc2 = fmaf(tt, tt, acc2);
       }
       xm = xc;
       xc = xp;
@@ -197,27 +263,52 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
       bcur = bnext;
     }
   }
-  const float bs = block_sum_ff(acc);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (double)bs;
+  block_sum2_ff(acc, acc2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int q = blockIdx.y * gridDim.x + blockIdx.x;
+    partials[q] = (double)acc;
+    partials[half + q] = (double)acc2;
+  }
+}
+
+// block 0: out_sq = sum of partials[0, n); block 1: out_t = sum of partials[half, half + n)
+// (fixed order, as the norm finish)
+__global__ void __launch_bounds__(1024) k_ff_finish(const double *__restrict__ partials, int n, int half,
+                                                    double *out_sq, double *out_t) {
+  MG_PDL_WAIT();
+  const double *src = partials + (blockIdx.x ? half : 0);
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) acc += src[t];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) (blockIdx.x ? out_t : out_sq)[0] = s;
+  }
 }
 }  // namespace
 
 bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
-                      double *partials, int nparts, double *out_sq) {
+                      double *partials, int nparts, double *out_sq, double *out_t, const int *use64) {
   if (L.dim != 2 || (kind != K_CONST && kind != K_SEP)) return false;
   const int nx = L.n0 - 2, rows = L.per ? L.n1 : L.n1 - 2;
   if (nx < 1 || rows < 1) return false;
+  const int half = nparts / 2;   // the two sums' partials side by side
   const int gx = (nx + FX * FY - 1) / (FX * FY);
-  if (gx > nparts) return false;
+  if (gx > half) return false;
   // rows per block: 32, more when the blocks would outnumber the partial sums or gridDim.y
   long long R = 32;
-  const long long gy_max = std::min<long long>(65535, nparts / gx);
+  const long long gy_max = std::min<long long>(65535, half / gx);
   if ((rows + R - 1) / R > gy_max) R = (rows + gy_max - 1) / gy_max;
   const dim3 gr((unsigned)gx, (unsigned)((rows + R - 1) / R)), bl(FX, FY);
-  if (kind == K_CONST) k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, (int)R);
-  else k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, (int)R);
+  if (kind == K_CONST) k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
+  else k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
   ++*lc.counter;
-  launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
+  k_ff_finish<<<2, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), half, out_sq, out_t);
+  ++*lc.counter;
   return true;
 }
 

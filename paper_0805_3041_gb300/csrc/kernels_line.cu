@@ -20,6 +20,7 @@ namespace mg {
 template <typename T, int DIM, int KIND>
 __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, const T *__restrict__ g, T *out, T omega,
                        T *__restrict__ cps, T *__restrict__ dps, T *__restrict__ zps) {
+  MG_PDL_WAIT();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int m;
   long long base, stride;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
                                                           const T *__restrict__ g, T *out, T omega,
                                                           T *__restrict__ sap, T *__restrict__ scp,
                                                           T *__restrict__ sdp) {
+  MG_PDL_WAIT();
   constexpr int NE = 2 * YSEG;
   __shared__ T ra[NE][YC + 1], rb[NE][YC + 1], rc[NE][YC + 1], rd[NE][YC + 1], rz[NE][YC + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -272,6 +274,7 @@ constexpr int kYlineShared = 2 * kYlineThreads + 2 * kYlineSegMax;   // >= 2 YSE
 template <typename T, int DIM, int KIND, int NR>
 __global__ void __launch_bounds__(kYlineThreads, sizeof(T) == 4 ? 2 : 1)
     k_yline_reg(Lev<T> L, int zebra, int colour, const T *u, const T *__restrict__ g, T *out, T omega) {
+  MG_PDL_WAIT();
   __shared__ T sa[kYlineShared], sc[kYlineShared], sd[kYlineShared];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int YC = (int)blockDim.x, YSEG = (int)blockDim.y, NE = 2 * YSEG, ld = YC + 1;

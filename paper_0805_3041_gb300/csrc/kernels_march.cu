@@ -55,6 +55,7 @@ template <typename T, int KIND, int MODE>
 __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                     T *__restrict__ out, T omega, int first, Lev<T> C,
                                                     const T *__restrict__ ec, T omega_corr, int RC) {
+  MG_PDL_WAIT();
   constexpr int NV = Vec<T>::N;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;

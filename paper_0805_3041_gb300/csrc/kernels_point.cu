@@ -28,6 +28,7 @@ static inline dim3 grid_for(long long xthreads, long long rows, int R) {
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_jacobi(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                    T *__restrict__ out, T omega, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi(Lev<T> L, const T *__restrict
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_jacobi_zero(Lev<T> L, const T *__restrict__ g, T *__restrict__ out,
                                                         T omega, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi_zero(Lev<T> L, const T *__res
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_rb_half(Lev<T> L, T *u, const T *__restrict__ g, T omega, int colour,
                                                     int R) {
+  MG_PDL_WAIT();
   int t = blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
@@ -103,6 +106,7 @@ __global__ void __launch_bounds__(BX *BY) k_rb_half(Lev<T> L, T *u, const T *__r
 template <typename T>
 __global__ void __launch_bounds__(BX *BY) k_gs9_colour(Lev<T> L, T *u, const T *__restrict__ g, T omega, int ci,
                                                        int cj, int R) {
+  MG_PDL_WAIT();
   const int t = blockIdx.x * BX + threadIdx.x;
   const int i = (ci ? 1 : 2) + 2 * t;
   if (i > L.n0 - 2) return;
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(BX *BY) k_gs9_colour(Lev<T> L, T *u, const T *
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_defect(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                    T *__restrict__ r_out, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -179,6 +184,7 @@ __device__ __forceinline__ float block_sum_f(float v) {
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_defect_norm(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                         double *__restrict__ partials, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
@@ -204,6 +210,7 @@ __global__ void __launch_bounds__(BX *BY) k_defect_norm(Lev<T> L, const T *__res
 template <typename T>
 __global__ void __launch_bounds__(BX *BY) k_norm_parts(Lev<T> L, const T *__restrict__ v, double *__restrict__ partials,
                                                        int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
@@ -224,6 +231,7 @@ __global__ void __launch_bounds__(BX *BY) k_norm_parts(Lev<T> L, const T *__rest
 
 // single block: out[0] = sum of partials in a fixed order
 __global__ void __launch_bounds__(1024) k_norm_finish(const double *__restrict__ partials, int n, double *out) {
+  MG_PDL_WAIT();
   double acc = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) acc += partials[t];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -258,6 +266,7 @@ template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                       const T *__restrict__ pe, double *__restrict__ partials,
                                                       unsigned *__restrict__ count, double *__restrict__ omega, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
   long long nr = L.unk_rows();
@@ -311,6 +320,7 @@ __global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restr
 // e *= omega over a whole node array
 template <typename T>
 __global__ void k_scale_by(T *__restrict__ e, long long n, const double *__restrict__ w) {
+  MG_PDL_WAIT();
   const T f = (T)w[0];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     e[t] *= f;
@@ -318,6 +328,7 @@ __global__ void k_scale_by(T *__restrict__ e, long long n, const double *__restr
 
 // relres = sqrt(sq) / sqrt(bsq), recorded in the device history
 __global__ void k_relres(const double *sq, const double *bsq, double *hist, int it, double *out) {
+  MG_PDL_WAIT();
   double rel = sqrt(sq[0]) / sqrt(bsq[0]);
   out[0] = rel;
   if (hist) hist[it] = rel;
@@ -337,6 +348,7 @@ __global__ void __launch_bounds__(BX *BY) k_defect64_to32(Lev<double> L, const d
                                                           const double *__restrict__ b, float *__restrict__ r32,
                                                           long long pitch32, long long plane32,
                                                           double *__restrict__ partials, int Rrt) {
+  MG_PDL_WAIT();
   const int R = RT > 0 ? RT : Rrt;
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -367,6 +379,7 @@ __global__ void __launch_bounds__(BX *BY) k_defect64_to32(Lev<double> L, const d
 template <int RT>
 __global__ void __launch_bounds__(BX *BY) k_ir_update(Lev<double> L, double *__restrict__ x, const float *__restrict__ c,
                                                       long long pitch32, long long plane32, int Rrt) {
+  MG_PDL_WAIT();
   const int R = RT > 0 ? RT : Rrt;
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > L.n0 - 2) return;
@@ -391,6 +404,7 @@ __global__ void __launch_bounds__(BX *BY) k_ir_update(Lev<double> L, double *__r
 template <int DIM>
 __global__ void __launch_bounds__(BX *BY) k_grad_k(Lev<double> L, const double *__restrict__ u,
                                                    const double *__restrict__ lam, double *__restrict__ dk, int R) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * BX + threadIdx.x;   // cell x index 0 .. n0-2
   if (i > L.n0 - 2) return;
   int ncy = L.per ? L.n1 : L.n1 - 1, ncz = DIM == 3 ? L.n2 - 1 : 1;
@@ -563,35 +577,50 @@ void launch_norm_finish(const Launch &lc, const double *partials, int nparts, do
 // End of a cycle inside a device-side solve loop (a CUDA-graph WHILE node): record the
 // relative residual, count the cycle and set the loop condition.  st[0] = cycles done,
 // st[1] = status (0 running / converged, 4 no convergence, 5 non-finite, 6 a bounded
-// device wait gave up), st[2] = set by a kernel whose wait gave up.  init = 1 for the
-// check before the first cycle.  ||b|| = 0 stops at once (x = 0); a non-finite ||b||
-// gives a non-finite relative residual.
+// device wait gave up), st[2] = set by a kernel whose wait gave up, st[6] = the loop's outer
+// defect runs in FP64 (set here, see below).  init = 1 for the check before the first cycle.
+// ||b|| = 0 stops at once (x = 0); a non-finite ||b|| gives a non-finite relative residual.
+// tsq (float-float outer defect, st[6] clear): the defect's error is estimated as
+// E = ff_err * sqrt(tsq) / ||b|| relative to ||b||; the loop stops when the residual plus E is
+// within tol, and sets st[6] (FP64 defects from the next step on) when E is half of tol or more
+// (the float-float residual could never decide), when the residual is within ff_switch * E of
+// tol, or when it fell by less than half in the step: near the defect's error the FP32 cycle
+// is driven by that error, whose smooth part it amplifies, and the loop stalls.
 __global__ void k_step_end(cudaGraphConditionalHandle h, const double *sq, const double *bsq, double *hist, int *st,
-                           const double *tol, int maxit, int init, double tol_scale) {
+                           const double *tol, int maxit, int init, const double *tsq, double ff_err,
+                           double ff_switch) {
+  MG_PDL_WAIT();
   double b = bsq[0];
   double rel = b == 0.0 ? 0.0 : sqrt(sq[0]) / sqrt(b);
   int it = init ? 0 : st[0] + 1;
   st[0] = it;
   if (hist) hist[it] = rel;
   int go = 1, status = 0;
+  const double err = (tsq && !st[6] && b != 0.0) ? ff_err * sqrt(tsq[0]) / sqrt(b) : 0.0;
   if (st[2]) {
     go = 0;
     status = 6;
   } else if (!(rel == rel) || rel > 1.7976931348623157e308) {
     go = 0;
     status = 5;
-  } else if (rel <= tol[0] * tol_scale || b == 0.0) {
+  } else if (rel + err <= tol[0] || b == 0.0) {
     go = 0;
-  } else if (it >= maxit) {
-    go = 0;
-    status = 4;
+  } else {
+    if (err > 0.0 && (err >= 0.5 * tol[0] || rel <= tol[0] + ff_switch * err ||
+                      (it >= 2 && hist && rel > 0.5 * hist[it - 1])))
+      st[6] = 1;
+    if (it >= maxit) {
+      go = 0;
+      status = 4;
+    }
   }
   st[1] = status;
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
-                     double *hist, int *st, const double *tol, int maxit, int init, double tol_scale) {
-  k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init, tol_scale);
+                     double *hist, int *st, const double *tol, int maxit, int init, const double *tsq,
+                     double ff_err, double ff_switch) {
+  k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init, tsq, ff_err, ff_switch);
   ++*lc.counter;
 }
 
@@ -599,6 +628,7 @@ void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const doubl
 // the last entry of the history; a loop that stopped as converged but is not (beyond tol in
 // FP64) gets status 8, which the host resolves by continuing the iteration.
 __global__ void k_final_check(const double *sq, const double *bsq, double *hist, int *st, const double *tol) {
+  MG_PDL_WAIT();
   const double b = bsq[0];
   const double rel = b == 0.0 ? 0.0 : sqrt(sq[0]) / sqrt(b);
   if (hist) hist[st[0]] = rel;
@@ -610,7 +640,10 @@ void launch_final_check(const Launch &lc, const double *sq, const double *bsq, d
   ++*lc.counter;
 }
 
-__global__ void k_sqrt(const double *src, double *dst) { dst[0] = sqrt(src[0]); }
+__global__ void k_sqrt(const double *src, double *dst) {
+  MG_PDL_WAIT();
+  dst[0] = sqrt(src[0]);
+}
 void launch_sqrt(const Launch &lc, const double *src, double *dst) {
   k_sqrt<<<1, 1, 0, lc.s>>>(src, dst);
   ++*lc.counter;

@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_rb2d_tma(Lev<float> L, const 
                                                       float omega, int first, Lev<float> C,
                                                       const float *__restrict__ ec, float omega_corr, int RC,
                                                       int ngroups, int *err, int *inject) {
+  MG_PDL_WAIT();
   constexpr int SLOT = slot_floats(MODE), PRE = pre_floats(MODE);
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float *ring = reinterpret_cast<float *>(tma_smem);
@@ -661,6 +662,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_defect_restrict_tma(Lev<float
                                                                        const float *__restrict__ g,
                                                                        float *__restrict__ gc, int RCc, int ngroups,
                                                                        int *err) {
+  MG_PDL_WAIT();
   constexpr int SLOT = 2 * SEGW;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float *ring = reinterpret_cast<float *>(tma_smem);

@@ -24,6 +24,7 @@ static inline int rpt(long long rows) { return rows >= 2048 ? 4 : 1; }
 template <typename T, int DIM>
 __global__ void __launch_bounds__(BX *BY) k_restrict(Lev<T> F, Lev<T> C, const T *__restrict__ rf, T *__restrict__ gc,
                                                      int R) {
+  MG_PDL_WAIT();
   int I = 1 + blockIdx.x * BX + threadIdx.x;
   if (I > C.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(BX *BY) k_restrict(Lev<T> F, Lev<T> C, const T
 template <typename T, int DIM>
 __global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, const T *__restrict__ ec,
                                                         T *__restrict__ uf, T w, int R) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * BX + threadIdx.x;
   if (i > F.n0 - 2) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, cons
 template <typename T, int DIM>
 __global__ void __launch_bounds__(BX *BY) k_interp(Lev<T> F, Lev<T> C, const T *__restrict__ ec,
                                                    T *__restrict__ out, int R) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * BX + threadIdx.x;
   if (i >= F.n0) return;
   long long r0 = ((long long)blockIdx.y * BY + threadIdx.y) * R;
@@ -153,6 +156,7 @@ void launch_prolong_add(const Launch &lc, const Lev<T> &F, const Lev<T> &C, cons
 template <typename T>
 __global__ void k_coarse_apply(const double *__restrict__ Ainv, const long long *__restrict__ cidx, int nc,
                                const T *__restrict__ g, T *__restrict__ u) {
+  MG_PDL_WAIT();
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nc) return;
   const double *row = Ainv + (long long)warp * nc;
@@ -174,6 +178,7 @@ void launch_coarse_apply(const Launch &lc, const double *Ainv, const long long *
 template <typename T, int DIM, int KIND>
 __global__ void k_assemble_dense(Lev<T> L, const long long *__restrict__ cidx, const int *__restrict__ cmap, int nc,
                                  double *__restrict__ A) {
+  MG_PDL_WAIT();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nc) return;
   long long p = cidx[r];
@@ -230,6 +235,7 @@ void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const lo
 //   (a) save column k, divide row k by the pivot, set A[k][k] = 1/pivot;
 //   (b) A[i][j] -= col[i] * A[k][j] for i != k, with A[i][k] := -col[i] / pivot.
 __global__ void k_gj_a(double *A, double *col, int n, int k) {
+  MG_PDL_WAIT();
   for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(long long)i * n + k];
   __syncthreads();
   double piv = col[k];
@@ -237,6 +243,7 @@ __global__ void k_gj_a(double *A, double *col, int n, int k) {
     A[(long long)k * n + j] = (j == k ? 1.0 : A[(long long)k * n + j]) / piv;
 }
 __global__ void k_gj_b(double *A, const double *__restrict__ col, int n, int k) {
+  MG_PDL_WAIT();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n * n) return;
   int i = (int)(t / n), j = (int)(t % n);
@@ -258,6 +265,7 @@ void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep) 
 // separable weights: W_x(I) = 1/4 H(w_x(2I), w_x(2I+1)), W_y(I) = 1/4 w_y(2I), W_z(I) = 1/4 w_z(2I)
 __global__ void k_coarsen_sep(const double *fsx, const double *fsy, const double *fsz, int nf0, double *csx,
                               double *csy, double *csz, int nc0) {
+  MG_PDL_WAIT();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nc0) return;
   if (I < nc0 - 1) {
@@ -276,6 +284,7 @@ void launch_coarsen_sep(const Launch &lc, const double *fsx, const double *fsy, 
 }
 
 __global__ void k_sep_dinv(const double *sx, const double *sy, const double *sz, int n0, int dim, double *dinv) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n0) return;
   if (i < 1 || i > n0 - 2) { dinv[i] = 0.0; return; }
@@ -291,6 +300,7 @@ void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const
 
 // coarse cell coefficient = mean of the 2^d child cells
 __global__ void k_coarsen_cell(Lev<double> F, Lev<double> C, const double *__restrict__ kf, double *__restrict__ kc) {
+  MG_PDL_WAIT();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y, K = blockIdx.z;
   int ncx = C.n0 - 1, ncy = C.per ? C.n1 : C.n1 - 1;
@@ -312,6 +322,7 @@ void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<doubl
 
 template <int DIM>
 __global__ void k_cell_dinv(Lev<double> L, double *__restrict__ dinv) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r = blockIdx.y + (long long)blockIdx.z * gridDim.y;
@@ -380,6 +391,7 @@ template <int KIND>
 __global__ void k_rap(Lev<double> F, Lev<double> C, double *__restrict__ dg, double *__restrict__ ex,
                       double *__restrict__ ey, double *__restrict__ ene, double *__restrict__ enw,
                       double *__restrict__ dinv) {
+  MG_PDL_WAIT();
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
   if (I >= C.n0 || J >= C.n1) return;
   const long long pc = (long long)J * C.pitch + I;
@@ -436,6 +448,7 @@ __device__ __forceinline__ double harm0(double a, double b) { return a + b > 0.0
 __global__ void k_coarsen_edge(Lev<double> F, Lev<double> C, const double *__restrict__ fx,
                                const double *__restrict__ fy, const double *__restrict__ fz, double *__restrict__ cx,
                                double *__restrict__ cy, double *__restrict__ cz) {
+  MG_PDL_WAIT();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y, K = blockIdx.z;
   if (I >= C.n0) return;
@@ -455,6 +468,7 @@ void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<doubl
 // 1/D at the unknowns, D = the sum of the weights of the edges at the node
 template <int DIM>
 __global__ void k_edge_dinv(Lev<double> L, double *__restrict__ dinv) {
+  MG_PDL_WAIT();
   int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   if (i > L.n0 - 2) return;
   long long r = blockIdx.y + (long long)blockIdx.z * gridDim.y;
@@ -479,6 +493,7 @@ void launch_edge_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
 }
 
 __global__ void k_to_float(const double *__restrict__ s, float *__restrict__ d, long long n) {
+  MG_PDL_WAIT();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long st = (long long)gridDim.x * blockDim.x;
   for (; t < n; t += st) d[t] = (float)s[t];
@@ -496,6 +511,7 @@ void launch_to_float(const Launch &lc, const double *src, float *dst, long long 
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_pack(Lev<T> L, const double *__restrict__ src, T *__restrict__ dst, int zero_boundary) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, k = blockIdx.z;
   if (i >= L.n0) return;
@@ -507,6 +523,7 @@ __global__ void k_pack(Lev<T> L, const double *__restrict__ src, T *__restrict__
 }
 template <typename T>
 __global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict__ dst, double scale) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, k = blockIdx.z;
   if (i >= L.n0) return;
@@ -514,6 +531,7 @@ __global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict
 }
 template <typename T>
 __global__ void k_zero_boundary(Lev<T> L, T *__restrict__ dst) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, k = blockIdx.z;
   if (i >= L.n0) return;
@@ -529,6 +547,7 @@ void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst) {
 }
 template <typename T>
 __global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
+  MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.pitch) return;
   dst[(long long)blockIdx.z * L.plane + (long long)blockIdx.y * L.pitch + i] = T(0);
@@ -561,6 +580,7 @@ void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst) {
 template <typename T, typename U>
 __global__ void k_transpose_copy(const U *__restrict__ src, T *__restrict__ dst, int rows_i, int cols_i,
                                  long long pitch_i, long long plane_i, int to_internal, double scale) {
+  MG_PDL_WAIT();
   __shared__ double tile[32][33];
   int k = blockIdx.z;
   int bx = blockIdx.x * 32, by = blockIdx.y * 32;   // internal column / row origin
@@ -621,6 +641,7 @@ template void launch_unpack_swapped<float>(const Launch &, const Lev<float> &, c
 
 // cell arrays: compact (ncz, ncy, n0-1) <-> node layout of the level
 __global__ void k_cell_pack(Lev<double> L, const double *__restrict__ src, double *__restrict__ dst, int dir) {
+  MG_PDL_WAIT();
   int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1;
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   if (i >= ncx || j >= ncy) return;

@@ -33,6 +33,7 @@ __device__ __forceinline__ int skew(int i) { return i + (i >> 4); }
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(NT) k_xline(Lev<T> L, const T *u, const T *__restrict__ g, T *out, T omega,
                                               int zebra, int colour) {
+  MG_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char xl_raw[];
   T *sd = reinterpret_cast<T *>(xl_raw);                     // rhs, later the solution
   T *sa = sd + XL_SZ, *sb = sa + XL_SZ, *sc = sb + XL_SZ;    // coefficients (variable kinds)
@@ -204,6 +205,7 @@ constexpr int WBUF = 32 * WSMAX + 32 * WSMAX / 16 + 8;
 template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(32 * WL) k_xline_warp(Lev<T> L, const T *u, const T *__restrict__ g, T *out,
                                                          T omega, int zebra, int colour) {
+  MG_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char xw_raw[];
   constexpr int NB = KIND == K_CONST ? 1 : 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

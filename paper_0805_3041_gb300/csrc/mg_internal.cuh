@@ -13,6 +13,12 @@
 
 namespace mg {
 
+// First statement of every kernel of the library: when the kernel is the downstream end of a
+// programmatic dependency in a CUDA graph (its launch may begin while the upstream kernel drains),
+// it waits here until the upstream kernel has completed and its writes are visible.  For an
+// ordinary launch it returns at once.
+#define MG_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
 // K_NINE: a Galerkin coarse level (2-D): a 9-point stencil per node, stored by symmetry as
 // its diagonal D (dg), the weights w = -A(p, q) of the couplings to the +x (ex), +y (ey),
 // +x+y (ez) and -x+y (enw) neighbours, and 1/D (ndinv); the other four couplings of a node
@@ -397,9 +403,11 @@ void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, cons
                           float *r32, double *partials, int nparts, double *out_sq);
 void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const float *c);
 // the same outer defect in float-float arithmetic on the FP32 and integer pipes (2-D, constant or
-// separable coefficients; false, and nothing launched, otherwise)
+// separable coefficients; false, and nothing launched, otherwise).  out_t: the sum of squares of
+// |b| + |A||x| over the unknowns, the scale of the float-float error (0 in FP64 mode); use64:
+// device flag (null: never set) that makes the kernel evaluate the defect in FP64 instead
 bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
-                      double *partials, int nparts, double *out_sq);
+                      double *partials, int nparts, double *out_sq, double *out_t, const int *use64);
 // after a loop stopped on the float-float defect: its FP64 relative residual into hist[st[0]], status 8
 // when it stopped as converged but the FP64 residual is above tol
 void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
@@ -424,8 +432,13 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out);
 // dst[0] = sqrt(src[0])
 void launch_sqrt(const Launch &lc, const double *src, double *dst);
-// end of a cycle of a device-side solve loop: history, cycle count, status, WHILE condition
+// end of a cycle of a device-side solve loop: history, cycle count, status, WHILE condition.
+// After a float-float defect (tsq: its sum of squares of |b| + |A||x|; null otherwise) the loop
+// stops only when the residual is below tol by the estimated error E = ff_err * sqrt(tsq), and
+// sets st[6] (FP64 defects from the next step on) when E >= tol / 2, when the residual is within
+// ff_switch * E of tol, or when it fell by less than half in the step
 void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const double *sq, const double *bsq,
-                     double *hist, int *st, const double *tol, int maxit, int init, double tol_scale = 1.0);
+                     double *hist, int *st, const double *tol, int maxit, int init, const double *tsq = nullptr,
+                     double ff_err = 0.0, double ff_switch = 0.0);
 
 }  // namespace mg

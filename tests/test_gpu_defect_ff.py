@@ -7,10 +7,12 @@ defect by its own FP32 rounding, 2^-24 |r|, plus the pair arithmetic's error, a 
 the largest stencil term, (|b| + |A||x|)_p; the test allows 2^-24 |r| + 16 * 2^-46 (|b| + |A||x|)_p
 and prints what it finds.  At an iterate near convergence (relative residual ~2e-11 at 4097^2,
 where the 5-point sums cancel terms ~1e7 times the result) the error of the whole defect is
-printed relative to ||r|| and bounded relative to ||b||: the loop stops when the float-float
-relative residual is below half the tolerance, 5e-11, so an error below 5e-11 ||b|| keeps the
-FP64 relative residual under 1e-10 there; the test asks for half of that, 2.5e-11 ||b||.  MG_FLAG_FP64_DEFECT keeps the FP64 kernel: within its FP32 rounding of
-the oracle's defect.  The mixed solve with the float-float loop reports its FP64 residual.
+printed relative to ||r|| and bounded relative to ||b||: there the error must stay below the
+solver's own estimate, 2^-46 ||(|b| + |A||x|)||, by which the loop stops short of the
+tolerance.  MG_FLAG_FP64_DEFECT keeps the FP64 kernel: within its FP32 rounding of the oracle's
+defect.  The mixed solve with the float-float loop reports its FP64 residual; on lines so
+strongly coupled that the float-float error is near the tolerance (eps = 1e3, error ~7e-11
+||b||) the loop moves to FP64 defects and still meets 1e-10 in the oracle's residual.
 """
 import numpy as np
 import pytest
@@ -77,8 +79,11 @@ def test_float_float_defect_within_its_bound(name, make, L):
     sm = "zebra_y" if name == "const-eps1e-3" else "rbgs"
     s64 = Solver(sp, levels=L, smoother=sm, precision="mixed", max_cycles=40, flags=FLAG_FP64_DEFECT)
     x, info = s64.solve(sp.b, tol=1e-10)
-    relb = check(o, s, x.cpu().numpy(), sp.b, f"{name} converged x (relres {info['relres']:.1e})")
-    assert relb <= 2.5e-11
+    xn = x.cpu().numpy()
+    relb = check(o, s, xn, sp.b, f"{name} converged x (relres {info['relres']:.1e})")
+    estimate = U46 * np.linalg.norm(abs_terms(o, xn, sp.b)) / np.linalg.norm(sp.b * m)
+    print(f"   error / ||b|| {relb:.2e}, the solver's estimate {estimate:.2e}")
+    assert relb <= estimate
 
 
 def test_fp64_flag_keeps_the_fp64_defect():
@@ -97,7 +102,7 @@ def test_fp64_flag_keeps_the_fp64_defect():
 
 @pytest.mark.parametrize("flags", [0, FLAG_FP64_DEFECT])
 def test_mixed_solve_reports_the_fp64_residual(flags):
-    """The loop stops on the float-float residual (below half the tolerance) and reports the FP64
+    """The loop stops on the float-float residual (below the tolerance by its error estimate) and reports the FP64
     one: 1e-10 in the oracle's residual, the same report to 1e-3, graph and kernel by kernel."""
     from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH
     sp = inputs.anisotropic(n=2049, eps=0.3, seed_f=4)
@@ -109,3 +114,23 @@ def test_mixed_solve_reports_the_fp64_residual(flags):
         print(f"flags {flags | extra}: {info['cycles']} steps, report {info['relres']:.4e}, oracle {rr:.4e}")
         assert info["status"] == "MG_OK" and rr <= 1e-10
         assert abs(rr - info["relres"]) <= 1e-3 * rr
+
+
+def test_strongly_coupled_lines_move_the_loop_to_fp64_defects():
+    """x-lines with eps = 1e3 (n = 2049 x 17): the float-float defect's error (~7e-11 ||b|| near
+    the solution) is close to the tolerance, so the loop has to finish on FP64 defects; it then
+    takes at most one refinement step more than a loop on FP64 defects throughout."""
+    from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH
+    sp = spec_of(2, (2049, 17), False, inputs.CONST, np.random.default_rng(5), eps=1e3)
+    p = orc.Problem(dim=2, n=sp.n, periodic_y=False, kind=sp.kind, h=sp.h, c=sp.c)
+    o = orc.Oracle(p, levels=4, smoother="zebra_x", dense_max=4096)
+    ref = Solver(sp, levels=4, smoother="zebra_x", precision="mixed", max_cycles=40, flags=FLAG_FP64_DEFECT)
+    _, iref = ref.solve(sp.b, tol=1e-10)
+    for extra in (0, FLAG_NO_GRAPH):
+        s = Solver(sp, levels=4, smoother="zebra_x", precision="mixed", max_cycles=40, flags=extra)
+        x, info = s.solve(sp.b, tol=1e-10)
+        rr = o.norm(o.defect(x.cpu().numpy(), sp.b)) / o.norm(sp.b)
+        print(f"flags {extra}: {info['cycles']} steps (FP64 defects: {iref['cycles']}), report {info['relres']:.3e}, "
+              f"oracle {rr:.3e}")
+        assert info["status"] == "MG_OK" and rr <= 1e-10
+        assert info["cycles"] <= iref["cycles"] + 1
