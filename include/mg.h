@@ -51,7 +51,9 @@ typedef enum {
   MG_ENOCONV = 4,    /* max_cycles reached before the tolerance; x holds the last iterate */
   MG_EDIVERGED = 5,  /* the residual norm became non-finite */
   MG_ETIMEOUT = 6,   /* a bounded device wait gave up; the output is not the solution */
-  MG_EBOUNDS = 7     /* a device-side check found an out-of-range index (reserved) */
+  MG_EBOUNDS = 7     /* the checking build (-DMG_DEBUG, see mg_debug_build): a device-side check
+                        found an out-of-range node index; the access was skipped (no fault), the
+                        site is in mg_last_error, and the result of the call is not valid */
 } mg_status;
 
 /* Choice of C in x <- x + omega C^{-1} (b - A x) (section "The choice of C"). */
@@ -116,6 +118,11 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        kernel-to-kernel edges of the solve's graphs are programmatic: a
                                        kernel's launch overlaps its predecessor's end and waits for its
                                        completion before reading) -- results do not depend on it */
+#define MG_FLAG_TEST_BOUNDS     2048u /* test hook of the checking build (mg_debug_build() == 1): each
+                                       solve starts with one device-side bounds check of the index one
+                                       past the finest grid's last node (nothing is accessed there), so
+                                       that it returns MG_EBOUNDS with the context still usable; the
+                                       normal build returns MG_EINVAL for this flag */
 #define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
                                        first single-precision TMA sweep is left out, so that the compute
                                        warps' bounded waits run out (about a second) and the solve returns
@@ -357,6 +364,12 @@ long long mg_launch_count(const mg_ctx *c);
 void mg_destroy(mg_ctx *c);
 const char *mg_status_str(mg_status s);
 const char *mg_last_error(const mg_ctx *c);
+
+/* 1 for the checking build of this library (compiled with -DMG_DEBUG: every kernel checks the
+ * node indices of its global accesses against the level's arrays, skips an access out of range
+ * and records its site; each call that synchronises then returns MG_EBOUNDS), 0 for the normal
+ * build, whose kernels carry no checks. */
+int mg_debug_build(void);
 
 #ifdef __cplusplus
 }

@@ -25,15 +25,16 @@ FLAG_TEST_WAIT_TIMEOUT = 128
 FLAG_GALERKIN = 256
 FLAG_FP64_DEFECT = 512
 FLAG_NO_PDL = 1024
+FLAG_TEST_BOUNDS = 2048
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED, ETIMEOUT, EBOUNDS = 0, 1, 2, 3, 4, 5, 6, 7
 
 EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_solve_adjoint", "mg_grad_coeff", "mg_apply",
            "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_step_descend", "mg_step_ascend", "mg_step_outer_defect", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_create_ex", "mg_batch_info",
-           "mg_batch_solve", "mg_batch_destroy", "mg_solve_batched"]
+           "mg_batch_solve", "mg_batch_destroy", "mg_solve_batched", "mg_debug_build"]
 BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
@@ -56,21 +57,21 @@ class Report(C.Structure):
                 ("history", C.c_void_p), ("history_cap", C.c_int), ("seconds", C.c_double)]
 
 
-_lib = None
+_libs = {}
 
 
-def library_path() -> str:
-    return _build.LIB
+def library_path(debug: bool = False) -> str:
+    return _build.LIB_DEBUG if debug else _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load (building if needed) the shared library and declare its signatures."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        path = _build.build()
+def load(build_if_missing: bool = True, debug: bool = False):
+    """Load (building if needed) the shared library and declare its signatures.  debug=True: the
+    checking build (device-side bounds checks, MG_EBOUNDS), a separate library file."""
+    if debug in _libs:
+        return _libs[debug]
+    path = library_path(debug)
+    if build_if_missing and not _build.up_to_date(debug):
+        path = _build.build(debug=debug)
     if not os.path.exists(path):
         raise RuntimeError(f"solver library missing: {path} (run __graft_entry__.build())")
     L = C.CDLL(path)
@@ -133,7 +134,9 @@ def load(build_if_missing: bool = True):
     L.mg_batch_destroy.argtypes = [P]
     L.mg_solve_batched.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), D, C.POINTER(Report)]
     L.mg_solve_batched.restype = I
-    _lib = L
+    L.mg_debug_build.argtypes = []
+    L.mg_debug_build.restype = I
+    _libs[debug] = L
     return L
 
 
@@ -158,11 +161,11 @@ class Solver:
 
     def __init__(self, spec, levels, smoother="rbgs", omega=1.0, nu1=2, nu2=2, omega_corr=1.0,
                  precision="fp64", max_cycles=100, inner_cycles=1, flags=0, device="cuda", stream=None,
-                 coarse_cut_nodes=0, sweep_rows=0, tile_nodes=0):
+                 coarse_cut_nodes=0, sweep_rows=0, tile_nodes=0, debug=False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the multigrid solver needs a CUDA GPU; no CPU path exists")
-        self.lib = load()
+        self.lib = load(debug=debug)
         self.device = torch.device(device)
         self.spec = spec
         self.dim = spec.dim
@@ -445,7 +448,7 @@ class Batch:
     one info dict per instance."""
 
     def __init__(self, solvers, bs, xs, mode=BATCH_AUTO):
-        self.lib = load()
+        self.lib = list(solvers)[0].lib   # the contexts' library (normal or checking build)
         self.solvers, self.bs, self.xs = list(solvers), list(bs), list(xs)
         n, cs, bp, xp = _batch_args(self.solvers, self.bs, self.xs)
         self.n = n
@@ -484,7 +487,7 @@ class Batch:
 
 def solve_batched(solvers, bs, xs, tol=1e-10):
     """mg_solve_batched: build, launch and free the batch graph in one call."""
-    lib = load()
+    lib = list(solvers)[0].lib
     n, cs, bp, xp = _batch_args(solvers, bs, xs)
     reps, hists = _batch_reports(solvers, n)
     st = lib.mg_solve_batched(cs, n, bp, xp, float(tol), reps)

@@ -14,6 +14,7 @@
 //
 // A wait that runs out (about a second) sets the instance's wait flag and the team stops;
 // the host reports MG_ETIMEOUT for it and for the instances the team had not reached.
+#define MG_FILE_ID 11   // bounds-check sites (-DMG_DEBUG)
 #include "batch_prog.h"
 #include "coarse_prog.h"
 
@@ -131,6 +132,7 @@ struct W5 {
 template <typename T, int KIND>
 __device__ __forceinline__ T resid5(const Lev<T> &L, const W5<T, KIND> &c, const T *u, long long p, T gp) {
   const long long pt = L.pitch;
+  if (!MG_CK(L, p - pt) || !MG_CK(L, p + pt)) return gp;   // debug build (p -+ 1 lie between)
   T s = fma(-c.d, u[p], gp);
   s = fma(c.w, u[p - 1], s);
   s = fma(c.e, u[p + 1], s);
@@ -150,6 +152,7 @@ __device__ void st_rb(const BatchLev &V, float *u, int colour, float omega, int 
     const int j = 1 + jr, i = 1 + 2 * ti + ((colour + j + 1) & 1);
     if (i > nx) continue;
     const long long p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     W5<float, KIND> c;
     c.load(L, i);
     u[p] = fmaf(omega * c.dinv, resid5<float, KIND>(L, c, u, p, V.g[p]), u[p]);
@@ -164,6 +167,7 @@ __device__ void st_jac(const BatchLev &V, const float *u, float *out, float omeg
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
     const long long p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     W5<float, KIND> c;
     c.load(L, i);
     out[p] = fmaf(omega * c.dinv, resid5<float, KIND>(L, c, u, p, V.g[p]), u[p]);
@@ -178,6 +182,7 @@ __device__ void st_defect(const BatchLev &V, const float *u, int gt, int nt) {
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
     const long long p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     W5<float, KIND> c;
     c.load(L, i);
     V.r[p] = resid5<float, KIND>(L, c, u, p, V.g[p]);
@@ -197,6 +202,7 @@ __device__ void st_xline(const BatchLev &V, const float *u, float *out, float *s
     const int j = 1 + jr;
     if (zebra && (j & 1) != colour) continue;
     const long long row = (long long)j * L.pitch;
+    if (!MG_CK(L, row + 1 - L.pitch) || !MG_CK(L, row + nx + L.pitch)) continue;   // debug build
     float cprev = 0.f, dprev = 0.f;
     for (int i = 1; i <= nx; ++i) {
       const long long p = row + i;
@@ -229,6 +235,7 @@ __device__ void st_restrict(const BatchLev &F, const BatchLev &C, int gt, int nt
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), I = 1 + (int)(t - (long long)jr * nx), J = 1 + jr;
     const long long pf = (long long)(2 * J) * F.L.pitch + 2 * I, pt = F.L.pitch;
+    if (!MG_CK(F.L, pf - pt - 1) || !MG_CK(F.L, pf + pt + 1) || !MG_CK(C.L, (long long)J * C.L.pitch + I)) continue;
     const float *r = F.r;
     const float rowm = (r[pf - pt - 1] + r[pf - pt + 1]) + 2.f * r[pf - pt];
     const float row0 = (r[pf - 1] + r[pf + 1]) + 2.f * r[pf];
@@ -244,8 +251,9 @@ __device__ void st_prolong(const BatchLev &F, const BatchLev &C, float *u, const
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
     const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
     const long long a0 = (long long)J0 * C.L.pitch, a1 = (long long)J1 * C.L.pitch;
-    const float corr = ((e[a0 + I0] + e[a0 + I1]) + (e[a1 + I0] + e[a1 + I1])) * 0.25f;
     const long long p = (long long)j * F.L.pitch + i;
+    if (!MG_CK(F.L, p) || !MG_CK(C.L, a0 + I0) || !MG_CK(C.L, a1 + I1)) continue;   // debug build
+    const float corr = ((e[a0 + I0] + e[a0 + I1]) + (e[a1 + I0] + e[a1 + I1])) * 0.25f;
     u[p] = fmaf(w, corr, u[p]);
   }
 }
@@ -277,6 +285,7 @@ __device__ double st_defect64(const BatchInst &I, const BatchLev &V, int gt, int
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
     const long long p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     W5<double, KIND> c;
     c.load(L, i);
     const float s = (float)resid5<double, KIND>(L, c, I.x64, p, I.b64[p]);
@@ -293,6 +302,7 @@ __device__ double st_norm_b(const BatchInst &I, int gt, int nt) {
   double acc = 0.0;
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
+    if (!MG_CK(L, (long long)j * L.pitch + i)) continue;   // debug build
     const double v = I.b64[(long long)j * L.pitch + i];
     acc = fma(v, v, acc);
   }
@@ -306,6 +316,7 @@ __device__ void st_update(const BatchInst &I, const float *c, int gt, int nt) {
   for (long long t = gt; t < total; t += nt) {
     const int jr = (int)(t / nx), i = 1 + (int)(t - (long long)jr * nx), j = 1 + jr;
     const long long p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     I.x64[p] += (double)c[p];
   }
 }
@@ -321,6 +332,7 @@ __device__ void st_pack(const BatchInst &I, int gt, int nt) {
     const int j = (int)(t / L.n0), i = (int)(t - (long long)j * L.n0);
     const bool unk = i >= 1 && i <= L.n0 - 2 && j >= 1 && j <= L.n1 - 2;
     const long long q = caller_index(I, i, j), p = (long long)j * L.pitch + i;
+    if (!MG_CK(L, p)) continue;   // debug build
     I.x64[p] = unk ? I.xcall[q] : 0.0;
     I.b64[p] = unk ? I.bcall[q] : 0.0;
   }
@@ -330,6 +342,7 @@ __device__ void st_unpack(const BatchInst &I, bool zero, int gt, int nt) {
   const long long total = (long long)L.n0 * L.n1;
   for (long long t = gt; t < total; t += nt) {
     const int j = (int)(t / L.n0), i = (int)(t - (long long)j * L.n0);
+    if (!MG_CK(L, (long long)j * L.pitch + i)) continue;   // debug build
     I.xcall[caller_index(I, i, j)] = zero ? 0.0 : I.x64[(long long)j * L.pitch + i];
   }
 }

@@ -9,6 +9,7 @@
 // partials, so all blocks take identical decisions and the result does not depend on timing.
 #include <cooperative_groups.h>
 
+#define MG_FILE_ID 10   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(Lev<double> L, const T
   for (long long t = t0; t < nunk; t += nt) {
     int i, j, k;
     const long long q = node(t, i, j, k);
+    if (!MG_CK(L, q)) continue;   // debug build
     const double v = (double)g[q];
     x[q] = 0.0;
     r[q] = v;
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(Lev<double> L, const T
     for (long long t = t0; t < nunk; t += nt) {
       int i, j, k;
       const long long q = node(t, i, j, k);
+      if (!MG_CK(L, q)) continue;   // debug build
       long long dm, dp;
       yoffs(L, j, dm, dp);
       Weights<double, DIM, KIND> w;
@@ -108,6 +111,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(Lev<double> L, const T
     for (long long t = t0; t < nunk; t += nt) {
       int i, j, k;
       const long long q = node(t, i, j, k);
+      if (!MG_CK(L, q)) continue;   // debug build
       x[q] = fma(alpha, p[q], x[q]);
       const double rv = fma(-alpha, ap[q], r[q]);
       r[q] = rv;
@@ -119,12 +123,14 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(Lev<double> L, const T
     for (long long t = t0; t < nunk; t += nt) {
       int i, j, k;
       const long long q = node(t, i, j, k);
+      if (!MG_CK(L, q)) continue;   // debug build
       p[q] = fma(beta, p[q], r[q]);
     }
   }
   for (long long t = t0; t < nunk; t += nt) {
     int i, j, k;
     const long long q = node(t, i, j, k);
+    if (!MG_CK(L, q)) continue;   // debug build
     u[q] = (T)x[q];
   }
   if (t0 == 0) iters[0] = it;

@@ -8,6 +8,7 @@
 // program of steps built on the host, with one __syncthreads() between steps.
 // This turns the ~L^2/2 coarse level visits of an F-cycle, each a handful of
 // latency-bound kernels, into a single launch per visit of level lc + 1.
+#define MG_FILE_ID 4   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 #include "coarse_prog.h"
 
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__r
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         int i = t % S.L.n0, rr = t / S.L.n0, j = rr % S.L.n1, k = rr / S.L.n1;
         long long gp = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+        if (!MG_CKN(S.L, gp, S.gplane * S.L.n2)) continue;   // debug build
         kk[t] = S.gk[gp];
         dv[t] = S.gdinv[gp];
       }
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__r
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         int i = t % S.L.n0, rr = t / S.L.n0, j = rr % S.L.n1, k = rr / S.L.n1;
         long long gp = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+        if (!MG_CKN(S.L, gp, S.gplane * S.L.n2)) continue;   // debug build
         wx[t] = S.gex[gp];
         wy[t] = S.gey[gp];
         if (DIM == 3) pool[S.off_ez + t] = S.gez[gp];
@@ -287,7 +290,12 @@ __global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__r
             const int i = 1 + t % nx, rr = t / nx;
             const int j = L.ylo() + (DIM == 3 ? rr % ny : rr), k = DIM == 3 ? 1 + rr / ny : 0;
             pp[q] = k * (int)L.plane + j * (int)L.pitch + i;
-            v[q] = src[(long long)k * S.gplane + (long long)j * S.gpitch + i];
+            const long long gq = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+            if (!MG_CKN(L, gq, S.gplane * L.n2)) {   // debug build
+              pp[q] = -1;
+              continue;
+            }
+            v[q] = src[gq];
           }
         }
 #pragma unroll
@@ -307,7 +315,10 @@ __global__ void __launch_bounds__(kCskThreads) k_coarse_cycle(const SLev<T> *__r
         load_unk(ub(o.z), u_in);
         break;
       case CP_STORE_U:
-        FOR_UNK(L, { u_out[(long long)k * S.gplane + (long long)j * S.gpitch + i] = ub(o.z)[p]; });
+        FOR_UNK(L, {
+          const long long gq = (long long)k * S.gplane + (long long)j * S.gpitch + i;
+          if (MG_CKN(L, gq, S.gplane * L.n2)) u_out[gq] = ub(o.z)[p];
+        });
         break;
       case CP_ZERO_U:
         FOR_UNK(L, { ub(o.z)[p] = T(0); });

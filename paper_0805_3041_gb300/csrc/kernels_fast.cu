@@ -16,6 +16,7 @@
 // All loops are row-per-warp (8 warps, lanes along x): no integer division per
 // element, one bounds / periodic-wrap decision per row, 128-byte aligned
 // main-body accesses with the halo columns loaded by a few lanes.
+#define MG_FILE_ID 5   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -36,6 +37,7 @@ __device__ __forceinline__ const T *row_ptr(const T *a, const Lev<T> &L, int j) 
   } else if (j < 0 || j >= L.n1) {
     return nullptr;
   }
+  if (!MG_CKN(L, j, L.n1)) return nullptr;
   return a + (long long)j * L.pitch;
 }
 template <typename T>
@@ -58,9 +60,10 @@ __device__ __forceinline__ bool owned_row(const Lev<T> &L, int j) {
 template <typename T, int KIND, int S>
 __device__ __forceinline__ T relax_at(const Lev<T> &L, const T *s, int r, int c, T gp, int i, long long p,
                                       long long dm, T omega) {
+  T uc = s[r * S + c];
+  if (!MG_CK(L, p) || !MG_CK(L, p + dm)) return uc;   // the weights' reads (cell / edge kinds)
   Weights<T, 2, KIND> w;
   w.load(L, i, p, dm);
-  T uc = s[r * S + c];
   T sum;
   if (KIND == K_CONST) {
     sum = fma(-L.d, uc, gp);
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u,
       int i = i0 - 2 + c;
       bool inx = xin || (i >= 0 && i < L.n0);
       T v = (rp && inx) ? rp[i] : T(0);
-      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2) {
+      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2 && MG_CKN(C, J0, C.n1) && MG_CKN(C, J1, C.n1) &&
+          MG_CKN(C, (i + 1) >> 1, C.n0)) {
         int I0 = i >> 1, I1 = (i + 1) >> 1;
         T s = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
         v = fma(omega_corr, s, v);
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u,
     T *op = out + (long long)j * L.pitch;
     for (int c = lane; c < TX; c += 32) {
       int i = i0 + c;
-      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + 2) * SX + c + 2];
+      if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + 2) * SX + c + 2];
     }
   }
 }
@@ -189,7 +193,8 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
       int i = i0 - H + c;
       bool inx = i >= 0 && i < L.n0;
       T v = (rp && inx) ? rp[i] : T(0);
-      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2) {
+      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2 && MG_CKN(C, J0, C.n1) && MG_CKN(C, J1, C.n1) &&
+          MG_CKN(C, (i + 1) >> 1, C.n0)) {
         int I0 = i >> 1, I1 = (i + 1) >> 1;
         T s = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
         v = fma(omega_corr, s, v);
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
     T *op = out + (long long)j * L.pitch;
     for (int c = lane; c < TX; c += 32) {
       int i = i0 + c;
-      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + H) * SXN + c + H];
+      if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + H) * SXN + c + H];
     }
   }
 }
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     for (int cc = lane; cc < TX + 2; cc += 32) {
       int i = i0 - 1 + cc;
       T d = T(0);
-      if (rowok && i >= 1 && i <= L.n0 - 2) {
+      if (rowok && i >= 1 && i <= L.n0 - 2 && MG_CK(L, rowoff + i) && MG_CK(L, rowoff + i + dm)) {
         long long p = rowoff + i;
         Weights<T, 2, KIND> wt;
         wt.load(L, i, p, dm);
@@ -327,11 +332,12 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     T *op = out + (long long)j * L.pitch;
     for (int c = lane; c < TX; c += 32) {
       int i = i0 + c;
-      if (i >= 1 && i <= L.n0 - 2) op[i] = su[(rr + H) * SXN + c + H];
+      if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + H) * SXN + c + H];
     }
   }
   int I = (i0 >> 1) + lane, J = (j0 >> 1) + warp;
-  if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
+  if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
+      MG_CK(C, (long long)J * C.pitch + I)) {
     const T *sp = sr + (2 * warp + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
     auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
     gc[(long long)J * C.pitch + I] = ((row3(sp - DS) + row3(sp + DS)) + T(2) * row3(sp)) * T(0.0625);
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, c
     for (int c = lane; c < RX; c += 32) {
       int i = fi0 + c;
       T d = T(0);
-      if (rowok && i >= 1 && i <= F.n0 - 2) {
+      if (rowok && i >= 1 && i <= F.n0 - 2 && MG_CK(F, rowoff + i) && MG_CK(F, rowoff + i + dm)) {
         long long p = rowoff + i;
         Weights<T, 2, KIND> w;
         w.load(F, i, p, dm);
@@ -397,7 +403,8 @@ __global__ void __launch_bounds__(256) k_defect_restrict2d(Lev<T> F, Lev<T> C, c
   __syncthreads();
   for (int cy = warp; cy < CY; cy += 8) {
     int I = I0 + lane, J = J0 + cy;
-    if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2))) {
+    if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
+        MG_CK(C, (long long)J * C.pitch + I)) {
       const T *s = sr + (2 * cy + 1) * US + (2 * lane + 1);   // centre of the stencil in sr
       auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
       T v = ((row3(s - US) + row3(s + US)) + T(2) * row3(s)) * T(0.0625);

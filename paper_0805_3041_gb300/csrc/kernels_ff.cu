@@ -26,6 +26,7 @@
 // j+1 in registers and the loads of the next rows in flight; x-neighbours come by shuffles (the
 // strip's edge lanes split the column beside the strip themselves).  2-D, constant or separable
 // coefficients.
+#define MG_FILE_ID 12   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -154,7 +155,12 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
   };
   auto raw = [&](int r) -> double {   // x at (i, row r); rows outside the unknowns (Dirichlet) read 0
     if (!act || (!L.per && (r < 0 || r >= rows))) return 0.0;
-    return x[row_of(r) + i];
+    const long long q = row_of(r) + i;
+    return MG_CK(L, q) ? x[q] : 0.0;   // (the check: debug build only)
+  };
+  auto bval = [&](int r) -> double {   // b at (i, row r) of an unknown row
+    const long long q = row_of(r) + i;
+    return MG_CK(L, q) ? b[q] : 0.0;
   };
   float acc = 0.f, acc2 = 0.f;
   if (f64 && r0 < r1) {
@@ -170,15 +176,15 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
       dD = (wW + wE) + (wY + wY);
     }
     double xm = raw(r0 - 1), xc = raw(r0), xnext = raw(r0 + 1);
-    double bcur = act ? b[row_of(r0) + i] : 0.0;
+    double bcur = act ? bval(r0) : 0.0;
     for (int r = r0; r < r1; ++r) {
       const double xafter = raw(r + 2);
-      const double bnext = (act && r + 1 < r1) ? b[row_of(r + 1) + i] : 0.0;
+      const double bnext = (act && r + 1 < r1) ? bval(r + 1) : 0.0;
       const double xp = xnext;
       const long long p = row_of(r) + i;
       double xw = __shfl_up_sync(FULL, xc, 1), xe = __shfl_down_sync(FULL, xc, 1);
       if (edge) {
-        const double xo = oin ? x[p - i + io] : 0.0;
+        const double xo = (oin && MG_CK(L, p - i + io)) ? x[p - i + io] : 0.0;
         if (lane == 0) xw = xo;
         else xe = xo;
       }
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         s = fma(wY, xm, s);
         s = fma(wY, xp, s);
         const float res = (float)s;
-        r32[p] = res;
+        if (MG_CK(L, p)) r32[p] = res;
         acc = fmaf(res, res, acc);
       }
       xm = xc;
@@ -203,10 +209,10 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
     // one row of lookahead: the loads of row r + 2 (x) and r + 1 (b) are in flight while row r
     // is computed
     double xnext = raw(r0 + 1);
-    double bcur = act ? b[row_of(r0) + i] : 0.0;
+    double bcur = act ? bval(r0) : 0.0;
     for (int r = r0; r < r1; ++r) {
       const double xafter = raw(r + 2);
-      const double bnext = (act && r + 1 < r1) ? b[row_of(r + 1) + i] : 0.0;
+      const double bnext = (act && r + 1 < r1) ? bval(r + 1) : 0.0;
       xp = split(xnext);
       const long long p = row_of(r) + i;
       // x-neighbours: the adjacent lanes' values, the edge lanes' from the column beside
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         FF xo;
         xo.h = 0.f;
         xo.l = 0.f;
-        if (oin) xo = split(x[p - i + io]);
+        if (oin && MG_CK(L, p - i + io)) xo = split(x[p - i + io]);
         if (lane == 0) xw = xo;
         else xe = xo;
       }
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
           lo = (((bb.l - e1) + (e2 + e3)) + e4) + ((t1 + t2) + (t3 + t4));
         }
         const float res = s + lo;
-        r32[p] = res;
+        if (MG_CK(L, p)) r32[p] = res;
         acc = fmaf(res, res, acc);
         // |b| + |A||x| from the leading parts: the scale of this node's float-float error
         const float tt = fmaf(aD, fabsf(xc.h),

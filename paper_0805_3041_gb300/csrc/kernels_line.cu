@@ -13,6 +13,7 @@
 // - m > 2048: k_yline_part, segments through three scratch arrays;
 // - m < 4 (and x-lines the dedicated x-line kernels do not take): k_line, one
 //   thread per line, Thomas with two scratch arrays of the level's layout.
+#define MG_FILE_ID 3   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -61,6 +62,7 @@ __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, con
     int j = dir == 0 ? a_fixed : 1 + s;
     long long dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p) || !MG_CK(L, p + dm)) return;   // debug build: the line leaves the array
     Weights<T, DIM, KIND> w;
     w.load(L, i, p, dm);
     T r = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -81,6 +83,7 @@ __global__ void k_line(Lev<T> L, int dir, int zebra, int colour, const T *u, con
   T x = T(0);
   for (int s = m - 1; s >= 0; --s) {
     long long p = base + s * stride;
+    if (!MG_CK(L, p)) return;   // debug build
     x = dps[p] - cps[p] * x;
     out[p] = fma(omega, x, u[p]);
   }
@@ -101,6 +104,11 @@ __device__ __forceinline__ void yline_row(const Lev<T> &L, long long pl, int i, 
   const long long p = yline_node(L, pl, i, per, s);
   long long dm, dp;
   yoffs(L, j, dm, dp);
+  if (!MG_CK(L, p) || !MG_CK(L, p + dm)) {   // debug build: a neutral row instead of the access
+    a = c = d = T(0);
+    b = T(1);
+    return;
+  }
   Weights<T, DIM, KIND> w;
   w.load(L, i, p, dm);
   d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -167,6 +175,7 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
         dv = r * (d - a * dpp);
       }
       const long long p = rowp(s0 + q);
+      if (!MG_CK(L, p)) continue;   // debug build
       sap[p] = ap;
       scp[p] = cp;
       sdp[p] = dv;
@@ -181,6 +190,7 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
     T an = app, cn = cpp, dn = dpp;   // row q+1, starting at q+1 = n-1
     for (int q = n - 2; q >= 1; --q) {
       const long long p = rowp(s0 + q);
+      if (!MG_CK(L, p)) continue;   // debug build
       T aq = sap[p], cq = scp[p], dq = sdp[p];
       if (q <= n - 3) {
         dq = dq - cq * dn;
@@ -252,6 +262,7 @@ __global__ void __launch_bounds__(YC * YSEG) k_yline_part(Lev<T> L, int zebra, i
   const T x0 = rd[2 * ty][tx], xl = rd[2 * ty + 1][tx];
   for (int q = 0; q < n; ++q) {
     const long long p = rowp(s0 + q);
+    if (!MG_CK(L, p)) continue;   // debug build
     const T x = q == 0 ? x0 : (q == n - 1 ? xl : sdp[p] - sap[p] * x0 - scp[p] * xl);
     out[p] = fma(omega, x, u[p]);
   }
@@ -361,7 +372,7 @@ __global__ void __launch_bounds__(kYlineThreads, sizeof(T) == 4 ? 2 : 1)
   if (act) {   // the centre values for the update, loaded while the reduced system is solved
 #pragma unroll
     for (int q = 0; q < NR; ++q)
-      if (q < n) rb[q] = u[yline_node(L, plane, i, per, s0 + q)];
+      if (q < n && MG_CK(L, yline_node(L, plane, i, per, s0 + q))) rb[q] = u[yline_node(L, plane, i, per, s0 + q)];
   }
   // parallel cyclic reduction: equation e takes in e - s and e + s, then couples to e -+ 2s
   for (int s = 1; s < NE; s <<= 1) {
@@ -383,7 +394,7 @@ __global__ void __launch_bounds__(kYlineThreads, sizeof(T) == 4 ? 2 : 1)
   const T x0 = d0 / (T(1) + a0 + c0), xl = d1 / (T(1) + a1 + c1);
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    if (q < n) {
+    if (q < n && MG_CK(L, yline_node(L, plane, i, per, s0 + q))) {
       const T x = q == 0 ? x0 : (q == n - 1 ? xl : rd[q] - ra[q] * x0 - rc[q] * xl);
       out[yline_node(L, plane, i, per, s0 + q)] = fma(omega, x, rb[q]);
     }

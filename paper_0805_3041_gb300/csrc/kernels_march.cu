@@ -12,6 +12,7 @@
 // come from warp shuffles; the edge lanes recompute the outside first-colour value
 // from their prefetched scalars.  Each node is read once and written once:
 // 12 B / unknown in FP32, 24 B in FP64.
+#define MG_FILE_ID 7   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
   auto load_row = [&](RowW<T> &R, int j) {
     bool ok = row_ok(j);
     int jw = wrap(j);
+    if (ok && (!MG_CKN(L, jw, L.n1) || !MG_CKN(L, i0 + NV - 1, L.pitch))) ok = false;   // debug build
     const T *up = u + (long long)jw * L.pitch, *gp = g + (long long)jw * L.pitch;
     if (ok) {
       if (MODE != 1) vload<T>(R.u, up + i0);
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
       }
       if (io >= 0 && io < L.pitch) R.gout = gp[io];
     }
-    if (MODE == 2 && unk_row(j)) {
+    if (MODE == 2 && unk_row(j) && MG_CKN(C, (jw + 1) >> 1 >= C.n1 ? 0 : (jw + 1) >> 1, C.n1) &&
+        MG_CKN(C, jw >> 1, C.n1)) {
       // coarse values of the thread's columns: coarse columns c0 .. c0 + NV/2 of rows J0, J1
       int J0 = jw >> 1, J1 = (jw + 1) >> 1;
       if (J1 >= C.n1) J1 -= C.n1;
@@ -234,7 +237,8 @@ __global__ void __launch_bounds__(128) k_rb2d_march(Lev<T> L, const T *__restric
     // second colour on row j; its own values are still the old ones in hc
     T O[NV];
     relax_sel(O, hc, hl, hr, hm, hp, w0.g, 1 - ((first + j) & 1), true);
-    vstore<T>(out + (long long)j * L.pitch + i0, O);   // rows j0 .. j1-1 are real unknown rows
+    if (MG_CK(L, (long long)j * L.pitch + i0 + NV - 1))
+      vstore<T>(out + (long long)j * L.pitch + i0, O);   // rows j0 .. j1-1 are real unknown rows
   };
   for (int j = j0; j < j1; j += 12) {
     step(W0, W1, W2, W3, Hm, hom, Hc, hoc, Hp, hop, j);

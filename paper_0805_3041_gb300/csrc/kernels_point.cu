@@ -9,6 +9,7 @@
 // Launch shape: blocks of 32 x 8 threads.  threadIdx.x runs along x (coalesced
 // rows), each thread handles R consecutive unknown rows (j, k).  Every thread
 // writes only unknown nodes of its own rows.
+#define MG_FILE_ID 1   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi(Lev<T> L, const T *__restrict
     row_jk(L, r, j, k);
     long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p)) continue;
     Weights<T, DIM, KIND> w;
     w.load(L, i, p, dm);
     T s = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -63,6 +65,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi_zero(Lev<T> L, const T *__res
     row_jk(L, r, j, k);
     long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p)) continue;
     Weights<T, DIM, KIND> w;
     w.load(L, i, p, dm);
     out[p] = omega * w.dinv * g[p];
@@ -90,6 +93,7 @@ __global__ void __launch_bounds__(BX *BY) k_rb_half(Lev<T> L, T *u, const T *__r
     if (i > L.n0 - 2) continue;
     long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p)) continue;
     Weights<T, DIM, KIND> w;
     w.load(L, i, p, dm);
     T s = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(BX *BY) k_gs9_colour(Lev<T> L, T *u, const T *
     const int j = jlo + 2 * q;
     long long p = (long long)j * L.pitch + i, dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p)) continue;
     Weights<T, 2, K_NINE> w;
     w.load(L, i, p, dm);
     T s = residual_at<T, 2, K_NINE>(L, w, u, p, dm, dp, g[p]);
@@ -142,6 +147,7 @@ __global__ void __launch_bounds__(BX *BY) k_defect(Lev<T> L, const T *__restrict
     row_jk(L, r, j, k);
     long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
     yoffs(L, j, dm, dp);
+    if (!MG_CK(L, p)) continue;
     Weights<T, DIM, KIND> w;
     w.load(L, i, p, dm);
     r_out[p] = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -197,6 +203,7 @@ __global__ void __launch_bounds__(BX *BY) k_defect_norm(Lev<T> L, const T *__res
       row_jk(L, r, j, k);
       long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
       yoffs(L, j, dm, dp);
+      if (!MG_CK(L, p)) continue;
       Weights<T, DIM, KIND> w;
       w.load(L, i, p, dm);
       double s = (double)residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -221,7 +228,9 @@ __global__ void __launch_bounds__(BX *BY) k_norm_parts(Lev<T> L, const T *__rest
       if (r >= nr) break;
       int j, k;
       row_jk(L, r, j, k);
-      double s = (double)v[(long long)k * L.plane + (long long)j * L.pitch + i];
+      const long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
+      if (!MG_CK(L, p)) continue;
+      double s = (double)v[p];
       acc = fma(s, s, acc);
     }
   }
@@ -279,6 +288,7 @@ __global__ void __launch_bounds__(BX *BY) k_corr_dots(Lev<T> L, const T *__restr
       row_jk(L, r, j, k);
       long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
       yoffs(L, j, dm, dp);
+      if (!MG_CK(L, p)) continue;
       Weights<T, DIM, KIND> w;
       w.load(L, i, p, dm);
       T d = residual_at<T, DIM, KIND>(L, w, u, p, dm, dp, g[p]);
@@ -363,11 +373,14 @@ __global__ void __launch_bounds__(BX *BY) k_defect64_to32(Lev<double> L, const d
         row_jk(L, r, j, k);
         long long p = (long long)k * L.plane + (long long)j * L.pitch + i, dm, dp;
         yoffs(L, j, dm, dp);
+        if (!MG_CK(L, p)) continue;
         Weights<double, DIM, KIND> w;
         w.load(L, i, p, dm);
         double s = residual_at<double, DIM, KIND>(L, w, x, p, dm, dp, b[p]);
         float s32 = (float)s;
-        r32[(long long)k * plane32 + (long long)j * pitch32 + i] = s32;
+        const long long p32 = (long long)k * plane32 + (long long)j * pitch32 + i;
+        if (!MG_CKN(L, p32, plane32 * (L.dim == 3 ? L.n2 : 1))) continue;
+        r32[p32] = s32;
         acc = fmaf(s32, s32, acc);
       }
     }
@@ -392,7 +405,9 @@ __global__ void __launch_bounds__(BX *BY) k_ir_update(Lev<double> L, double *__r
       int j, k;
       row_jk(L, r, j, k);
       long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
-      x[p] += (double)c[(long long)k * plane32 + (long long)j * pitch32 + i];
+      const long long p32 = (long long)k * plane32 + (long long)j * pitch32 + i;
+      if (!MG_CK(L, p) || !MG_CKN(L, p32, plane32 * (L.dim == 3 ? L.n2 : 1))) continue;
+      x[p] += (double)c[p32];
     }
   }
 }
@@ -416,6 +431,8 @@ __global__ void __launch_bounds__(BX *BY) k_grad_k(Lev<double> L, const double *
     int j = (int)(r % ncy), k = (int)(r / ncy);
     long long p = (long long)k * L.plane + (long long)j * L.pitch + i;
     long long up = (L.per && j == L.n1 - 1) ? -(long long)(L.n1 - 1) * L.pitch : L.pitch;
+    // the cell's far corner (and, for the periodic wrap, the row it wraps to)
+    if (!MG_CK(L, p) || !MG_CK(L, p + up + 1 + (DIM == 3 ? L.plane : 0))) continue;
     if (DIM == 2) {
       double u00 = u[p], u10 = u[p + 1], u01 = u[p + up], u11 = u[p + up + 1];
       double l00 = lam[p], l10 = lam[p + 1], l01 = lam[p + up], l11 = lam[p + up + 1];
@@ -637,6 +654,17 @@ __global__ void k_final_check(const double *sq, const double *bsq, double *hist,
 void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
                         const double *tol) {
   k_final_check<<<1, 1, 0, lc.s>>>(sq, bsq, hist, st, tol);
+  ++*lc.counter;
+}
+
+// Test hook of the -DMG_DEBUG build (MG_FLAG_TEST_BOUNDS): one bounds check of the index one past
+// the level's last node, which fails and is recorded; nothing is read or written there.
+__global__ void k_bounds_probe(Lev<double> L) {
+  MG_PDL_WAIT();
+  if (!MG_CK(L, L.plane * (L.dim == 3 ? L.n2 : 1))) return;
+}
+void launch_bounds_probe(const Launch &lc, const Lev<double> &L) {
+  k_bounds_probe<<<1, 1, 0, lc.s>>>(L);
   ++*lc.counter;
 }
 

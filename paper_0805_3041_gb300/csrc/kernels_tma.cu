@@ -27,6 +27,7 @@
 
 #include <algorithm>
 
+#define MG_FILE_ID 8   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -216,6 +217,11 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     int Jc = (jw + 1) >> 1;
     if (Jc >= C.n1) Jc -= C.n1;
     const bool pre_row = MODE == 2 && j == jfirst;
+    // debug build: the copies' rows and spans lie inside u, g and ec; else nothing is issued and
+    // the compute warps' bounded waits run out
+    if (!MG_CKN(L, jw, L.n1) || !MG_CKN(L, ce - 1, L.pitch) ||
+        (MODE == 2 && (!MG_CKN(C, Jc, C.n1) || !MG_CKN(C, jw >> 1, C.n1) || !MG_CKN(C, cce - 1, C.pitch))))
+      return;
     const uint32_t bytes = (MODE == 1 ? 1u : 2u) * seg_bytes + (MODE == 2 ? (pre_row ? 2u : 1u) * cseg_bytes : 0u);
     mbar_expect_tx(bar, bytes);
     const long long ro = (long long)jw * L.pitch;
@@ -353,7 +359,8 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
     float o[4];
     if ((first + j) & 1) relax_colour<0>(o, Hc.h, hl, hr, Hm.h, Hp.h, gg, K, true);
     else relax_colour<1>(o, Hc.h, hl, hr, Hm.h, Hp.h, gg, K, true);
-    *reinterpret_cast<float4 *>(out + (long long)j * L.pitch + i0) = make_float4(o[0], o[1], o[2], o[3]);
+    if (MG_CK(L, (long long)j * L.pitch + i0 + 3))
+      *reinterpret_cast<float4 *>(out + (long long)j * L.pitch + i0) = make_float4(o[0], o[1], o[2], o[3]);
   };
 
   bool ok = true;
@@ -515,6 +522,7 @@ __device__ __forceinline__ void band_dr(const Lev<float> L, const Lev<float> C, 
     float *slot = ring + (k & (RING - 1)) * SLOT;
     uint64_t *bar = &full[k & (RING - 1)];
     const long long ro = (long long)wrap(j) * L.pitch;
+    if (!MG_CKN(L, wrap(j), L.n1) || !MG_CKN(L, ce - 1, L.pitch)) return;   // debug build, as in the sweep
     mbar_expect_tx(bar, 2u * seg_bytes);
     tma_load_1d(slot + doff, u + ro + cs, seg_bytes, bar);
     tma_load_1d(slot + SEGW + doff, g + ro + cs, seg_bytes, bar);
@@ -605,6 +613,7 @@ __device__ __forceinline__ void band_dr(const Lev<float> L, const Lev<float> C, 
     if (!Jok) return;
     const int I = (sw >> 1) + 2 * lane;
     float *rowp = gc + (long long)J * C.pitch;
+    if (!MG_CK(C, (long long)J * C.pitch + I + 1)) return;
     if (I >= 1 && I <= C.n0 - 2) rowp[I] = va;
     if (I + 1 >= 1 && I + 1 <= C.n0 - 2) rowp[I + 1] = vb;
   };

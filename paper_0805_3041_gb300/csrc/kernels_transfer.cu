@@ -6,6 +6,7 @@
 //
 // Wallis (2008), section "The Multigrid Technique": g_{l-1} = R d_l,
 // u + omega_l P u_{l-1}, and A_1^{-1} g on the coarsest grid.
+#define MG_FILE_ID 2   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -37,6 +38,13 @@ __global__ void __launch_bounds__(BX *BY) k_restrict(Lev<T> F, Lev<T> C, const T
     long long dm, dp;
     yoffs(F, 2 * J, dm, dp);
     long long pf = (long long)(2 * K) * F.plane + (long long)(2 * J) * F.pitch + 2 * I;
+    const long long pc = (long long)K * C.plane + (long long)J * C.pitch + I;
+    {
+      const long long zl = DIM == 3 ? F.plane : 0;   // the 3 x 3 (x 3) fine stencil's corners
+      if (!MG_CK(C, pc) || !MG_CK(F, pf - zl + dm - 1) || !MG_CK(F, pf - zl + dp + 1) || !MG_CK(F, pf + zl + dm - 1) ||
+          !MG_CK(F, pf + zl + dp + 1))
+        continue;
+    }
     auto row3 = [&](long long c) -> T { return (rf[c - 1] + rf[c + 1]) + T(2) * rf[c]; };
     auto plane3 = [&](long long c) -> T { return (row3(c + dm) + row3(c + dp)) + T(2) * row3(c); };
     T s;
@@ -45,7 +53,7 @@ __global__ void __launch_bounds__(BX *BY) k_restrict(Lev<T> F, Lev<T> C, const T
     } else {
       s = ((plane3(pf - F.plane) + plane3(pf + F.plane)) + T(2) * plane3(pf)) * T(0.015625);
     }
-    gc[(long long)K * C.plane + (long long)J * C.pitch + I] = s;
+    gc[pc] = s;
   }
 }
 
@@ -69,6 +77,14 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, cons
     int J0 = j >> 1, J1 = (j + 1) >> 1;
     if (J1 >= C.n1) J1 -= C.n1;   // periodic wrap (only reachable when y is periodic)
     long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+    long long p = (long long)k * F.plane + (long long)j * F.pitch + i;
+    {
+      const long long zhi = DIM == 3 ? (long long)((k + 1) >> 1) * C.plane : 0;
+      const long long zlo = DIM == 3 ? (long long)(k >> 1) * C.plane : 0;
+      if (!MG_CK(F, p) || !MG_CK(C, zlo + a0 + I0) || !MG_CK(C, zhi + a1 + I1) || !MG_CK(C, zlo + a1 + I0) ||
+          !MG_CK(C, zhi + a0 + I1))
+        continue;
+    }
     T s;
     if (DIM == 2) {
       s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
@@ -78,7 +94,6 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(Lev<T> F, Lev<T> C, cons
       T s1 = (ec[z1 + a0 + I0] + ec[z1 + a0 + I1]) + (ec[z1 + a1 + I0] + ec[z1 + a1 + I1]);
       s = (s0 + s1) * T(0.125);
     }
-    long long p = (long long)k * F.plane + (long long)j * F.pitch + i;
     uf[p] = fma(w, s, uf[p]);
   }
 }
@@ -101,10 +116,16 @@ __global__ void __launch_bounds__(BX *BY) k_interp(Lev<T> F, Lev<T> C, const T *
     const int j = DIM == 3 ? (int)r % F.n1 : (int)r, k = DIM == 3 ? (int)r / F.n1 : 0;
     const bool unk = xin && (F.per || (j >= 1 && j <= F.n1 - 2)) && (DIM == 2 || (k >= 1 && k <= F.n2 - 2));
     T s = T(0);
+    const long long po = (long long)k * F.plane + (long long)j * F.pitch + i;
+    if (!MG_CK(F, po)) continue;
     if (unk) {
       int J0 = j >> 1, J1 = (j + 1) >> 1;
       if (J1 >= C.n1) J1 -= C.n1;   // periodic wrap
       long long a0 = (long long)J0 * C.pitch, a1 = (long long)J1 * C.pitch;
+      const long long zhi = DIM == 3 ? (long long)((k + 1) >> 1) * C.plane : 0;
+      const long long zlo = DIM == 3 ? (long long)(k >> 1) * C.plane : 0;
+      if (!MG_CK(C, zlo + a0 + I0) || !MG_CK(C, zhi + a1 + I1) || !MG_CK(C, zlo + a1 + I0) || !MG_CK(C, zhi + a0 + I1))
+        continue;
       if (DIM == 2) {
         s = ((ec[a0 + I0] + ec[a0 + I1]) + (ec[a1 + I0] + ec[a1 + I1])) * T(0.25);
       } else {
@@ -114,7 +135,7 @@ __global__ void __launch_bounds__(BX *BY) k_interp(Lev<T> F, Lev<T> C, const T *
         s = (s0 + s1) * T(0.125);
       }
     }
-    out[(long long)k * F.plane + (long long)j * F.pitch + i] = s;
+    out[po] = s;
   }
 }
 
@@ -306,6 +327,9 @@ __global__ void k_coarsen_cell(Lev<double> F, Lev<double> C, const double *__res
   int ncx = C.n0 - 1, ncy = C.per ? C.n1 : C.n1 - 1;
   if (I >= ncx || J >= ncy) return;
   int nz = C.dim == 3 ? 2 : 1;
+  if (!MG_CK(C, (long long)K * C.plane + (long long)J * C.pitch + I) ||
+      !MG_CK(F, (long long)(2 * K + nz - 1) * F.plane + (long long)(2 * J + 1) * F.pitch + 2 * I + 1))
+    return;
   double s = 0.0;
   for (int z = 0; z < nz; ++z)
     for (int b = 0; b < 2; ++b)
@@ -517,6 +541,7 @@ __global__ void k_pack(Lev<T> L, const double *__restrict__ src, T *__restrict__
   if (i >= L.n0) return;
   long long s = ((long long)k * L.n1 + j) * L.n0 + i;
   long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  if (!MG_CK(L, d)) return;
   bool bnd = (i == 0 || i == L.n0 - 1) || (!L.per && (j == 0 || j == L.n1 - 1)) ||
              (L.dim == 3 && (k == 0 || k == L.n2 - 1));
   dst[d] = (zero_boundary && bnd) ? T(0) : (T)src[s];
@@ -527,7 +552,9 @@ __global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, k = blockIdx.z;
   if (i >= L.n0) return;
-  dst[((long long)k * L.n1 + j) * L.n0 + i] = scale * (double)src[(long long)k * L.plane + (long long)j * L.pitch + i];
+  const long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  if (!MG_CK(L, d)) return;
+  dst[((long long)k * L.n1 + j) * L.n0 + i] = scale * (double)src[d];
 }
 template <typename T>
 __global__ void k_zero_boundary(Lev<T> L, T *__restrict__ dst) {
@@ -537,7 +564,8 @@ __global__ void k_zero_boundary(Lev<T> L, T *__restrict__ dst) {
   if (i >= L.n0) return;
   bool bnd = (i == 0 || i == L.n0 - 1) || (!L.per && (j == 0 || j == L.n1 - 1)) ||
              (L.dim == 3 && (k == 0 || k == L.n2 - 1));
-  if (bnd) dst[(long long)k * L.plane + (long long)j * L.pitch + i] = T(0);
+  const long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  if (bnd && MG_CK(L, d)) dst[d] = T(0);
 }
 template <typename T>
 void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst) {
@@ -550,7 +578,8 @@ __global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
   MG_PDL_WAIT();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.pitch) return;
-  dst[(long long)blockIdx.z * L.plane + (long long)blockIdx.y * L.pitch + i] = T(0);
+  const long long d = (long long)blockIdx.z * L.plane + (long long)blockIdx.y * L.pitch + i;
+  if (MG_CK(L, d)) dst[d] = T(0);
 }
 
 template <typename T>
@@ -647,6 +676,7 @@ __global__ void k_cell_pack(Lev<double> L, const double *__restrict__ src, doubl
   if (i >= ncx || j >= ncy) return;
   long long c = ((long long)k * ncy + j) * ncx + i;
   long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
+  if (!MG_CK(L, d)) return;
   if (dir == 0) dst[d] = src[c];
   else dst[c] = src[d];
 }

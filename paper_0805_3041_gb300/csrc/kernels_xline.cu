@@ -18,6 +18,7 @@
 //  4. every thread recovers its interior unknowns from the two solved ends and
 //     the result is written back coalesced.
 // Reads the off-line neighbours and b once, writes the line once.
+#define MG_FILE_ID 6   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -50,6 +51,10 @@ __global__ void __launch_bounds__(NT) k_xline(Lev<T> L, const T *u, const T *__r
   const long long row = (long long)k * L.plane + (long long)j * L.pitch;
   long long dm, dp;
   yoffs(L, j, dm, dp);
+  {   // debug build: the line and its neighbour lines lie inside the arrays (uniform per CTA)
+    const long long zp = DIM == 3 ? L.plane : 0;
+    if (!MG_CK(L, row + 1 + (dm < dp ? dm : dp) - zp) || !MG_CK(L, row + m + (dm < dp ? dp : dm) + zp)) return;
+  }
   // 1. right-hand side of the line system and its coefficients
   for (int q = tid; q < m; q += NT) {
     int i = q + 1;
@@ -220,6 +225,10 @@ __global__ void __launch_bounds__(32 * WL) k_xline_warp(Lev<T> L, const T *u, co
   const long long row = (long long)k * L.plane + (long long)j * L.pitch;
   long long dm, dp;
   yoffs(L, j, dm, dp);
+  {   // debug build: the line and its neighbour lines lie inside the arrays (uniform per warp)
+    const long long zp = DIM == 3 ? L.plane : 0;
+    if (!MG_CK(L, row + 1 + (dm < dp ? dm : dp) - zp) || !MG_CK(L, row + m + (dm < dp ? dp : dm) + zp)) return;
+  }
   // 1. right-hand side (g + off-line couplings) and the line's coefficients, coalesced
   for (int q = lane; q < m; q += 32) {
     int i = q + 1;

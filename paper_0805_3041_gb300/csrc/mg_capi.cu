@@ -22,6 +22,7 @@
 #include "../../include/mg.h"
 #include "coarse_prog.h"
 #include "batch_prog.h"
+#define MG_FILE_ID 13   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 using namespace mg;
@@ -109,6 +110,7 @@ struct mg_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // forward / transposed cycle + check
   cudaGraphExec_t lexec[2] = {nullptr, nullptr};   // whole solve: device-side WHILE loop
   long long loop_init_kernels[2] = {0, 0}, loop_body_kernels[2] = {0, 0};
+  unsigned *oob = nullptr;                         // device bounds word (-DMG_DEBUG build's checks)
   int *st = nullptr;                               // device loop state: [0] cycles done, [1] status, [2] a wait
                                                    // gave up, [4] CG, [5] test hook, [6] FP64 outer defects
   unsigned *cnt = nullptr;                         // device: block counter of last-block reductions (zero at rest)
@@ -223,6 +225,9 @@ static mg_status check_params(const mg_params *p, const mg_coeffs *k) {
       (p->dim != 2 || p->periodic_y || (p->smoother != MG_JACOBI && p->smoother != MG_RBGS) ||
        nc > kDenseCoarseMax || (p->flags & MG_FLAG_ADAPTIVE_CORR)))
     return MG_EINVAL;
+#ifndef MG_DEBUG
+  if (p->flags & MG_FLAG_TEST_BOUNDS) return MG_EINVAL;   // the probe needs the checking build
+#endif
   return MG_OK;
 }
 
@@ -331,6 +336,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   c->scal = b.take<double>(16);
   c->hist = b.take<double>((size_t)P.max_cycles + 2);
   c->st = b.take<int>(8);
+  c->oob = b.take<unsigned>(4);
   c->cnt = b.take<unsigned>(8);
   // coarsest grid
   const LevGeom &g1 = c->geo[1];
@@ -388,6 +394,7 @@ static Lev<T> make_lev(const mg_ctx *c, int l) {
   L.ax = (T)g.ax;
   L.ay = (T)g.ay;
   L.az = (T)g.az;
+  L.oob = c->oob;
   return L;
 }
 static Lev<double> lev64(const mg_ctx *c, int l) {
@@ -458,12 +465,37 @@ template <> struct LevOf<float> {
     }                                                                    \
   } while (0)
 
+// Source file of a bounds-check site id (the MG_FILE_ID of each translation unit).
+static const char *site_file(unsigned id) {
+  static const char *names[] = {"?", "kernels_point.cu", "kernels_transfer.cu", "kernels_line.cu",
+                                "kernels_coarse.cu", "kernels_fast.cu", "kernels_xline.cu", "kernels_march.cu",
+                                "kernels_tma.cu", "noalloc.cu", "kernels_cg.cu", "kernels_batch.cu",
+                                "kernels_ff.cu", "mg_capi.cu", "?", "mg_internal.cuh"};
+  return id < 16 ? names[id] : "?";
+}
+
+// After the context's stream has been synchronised: a failed launch, and in the -DMG_DEBUG
+// build a device-side bounds check that failed since the last call (the word is cleared).
 static mg_status last_launch(mg_ctx *c) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     c->err = std::string("kernel launch: ") + cudaGetErrorString(e);
     return MG_ECUDA;
   }
+#ifdef MG_DEBUG
+  unsigned site = 0;
+  e = cudaMemcpy(&site, c->oob, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && site) e = cudaMemset(c->oob, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    c->err = std::string("bounds word: ") + cudaGetErrorString(e);
+    return MG_ECUDA;
+  }
+  if (site) {
+    c->err = std::string("device bounds check failed at ") + site_file(site >> 16) + ":" +
+             std::to_string(site & 0xffffu) + " (access skipped)";
+    return MG_EBOUNDS;
+  }
+#endif
   return MG_OK;
 }
 
@@ -1143,6 +1175,7 @@ static mg_status setup_levels(mg_ctx *c) {
   const mg_params &P = c->P;
   int L = c->L;
   CK(cudaMemsetAsync(c->st, 0, sizeof(int) * 8, c->stream));   // loop state and the device-wait flag
+  CK(cudaMemsetAsync(c->oob, 0, sizeof(unsigned) * 4, c->stream));
   CK(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned) * 8, c->stream));
   // geometry constants per level
   for (int l = L; l >= 1; --l) {
@@ -1572,6 +1605,14 @@ const char *mg_status_str(mg_status s) {
 
 const char *mg_last_error(const mg_ctx *c) { return c ? c->err.c_str() : "no context"; }
 
+int mg_debug_build(void) {
+#ifdef MG_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 long long mg_launch_count(const mg_ctx *c) { return c ? c->launches : 0; }
 
 mg_status mg_level_dims(const mg_ctx *c, int level, int n[3]) {
@@ -1657,6 +1698,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     c->h_relres[3] = tol;
     CK(cudaMemcpyAsync(c->scal + 4, c->h_relres + 3, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
+    if (c->P.flags & MG_FLAG_TEST_BOUNDS) launch_bounds_probe(lc, F64);
     CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int), c->stream));   // float-float outer defects first
     double *xin = c->mixed ? c->x64 : c->d64[L].u[0];
     std::vector<double> hbuf((size_t)c->P.max_cycles + 2), hall;
@@ -1725,6 +1767,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   }
   launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
   if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
+  if (c->P.flags & MG_FLAG_TEST_BOUNDS) launch_bounds_probe(lc, F64);
   CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int), c->stream));   // float-float outer defects first
   bool ff64 = false;                                           // ... until the loop moves to FP64
   if (use_graph) {

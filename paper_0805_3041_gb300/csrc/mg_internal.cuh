@@ -41,6 +41,8 @@ struct Lev {
   const T *ex, *ey, *ez;
   // Galerkin levels (K_NINE): diagonal, and the -x+y coupling (ez holds the +x+y one)
   const T *dg, *enw;
+  // the context's bounds word (device; used by the -DMG_DEBUG build's checks only)
+  unsigned *oob;
 
   __host__ __device__ int ylo() const { return per ? 0 : 1; }
   __host__ __device__ int yrows() const { return per ? n1 : n1 - 2; }
@@ -48,6 +50,29 @@ struct Lev {
   __host__ __device__ long long unk_rows() const { return (long long)yrows() * zrows(); }
   __host__ __device__ int xunk() const { return n0 - 2; }
 };
+
+// Device-side bounds checks of the debug build (-DMG_DEBUG).  MG_CK(L, p) is true when node
+// index p lies inside a node array of level L (plane * n2 elements); otherwise the first failing
+// check records its site, (file id << 16) | line, in the context's bounds word and the caller
+// skips the access; the host then returns MG_EBOUNDS (no trap, no fault).  MG_CKN(L, p, n) checks
+// an index into an array of n elements.  In the normal build both are the constant true.
+#ifndef MG_FILE_ID
+#define MG_FILE_ID 0
+#endif
+#ifdef MG_DEBUG
+template <typename T>
+__device__ __forceinline__ bool mg_ck_n(const Lev<T> &L, long long p, long long n, unsigned site) {
+  if (p >= 0 && p < n) return true;
+  if (L.oob) atomicCAS(L.oob, 0u, site);
+  return false;
+}
+#define MG_SITE (((unsigned)MG_FILE_ID << 16) | (unsigned)__LINE__)
+#define MG_CKN(L, p, n) mg::mg_ck_n((L), (long long)(p), (long long)(n), MG_SITE)
+#define MG_CK(L, p) MG_CKN((L), (p), (L).plane * ((L).dim == 3 ? (L).n2 : 1))
+#else
+#define MG_CKN(L, p, n) true
+#define MG_CK(L, p) true
+#endif
 
 // Offsets of the y neighbours of row j (periodic wrap).
 template <typename T, typename IT>
@@ -152,6 +177,17 @@ struct Weights {
 template <typename T, int DIM, int KIND, typename IT>
 __device__ __forceinline__ T residual_at(const Lev<T> &L, const Weights<T, DIM, KIND> &w, const T *__restrict__ u,
                                          IT p, IT dm, IT dp, T gp) {
+#ifdef MG_DEBUG
+  if (sizeof(IT) == 8) {   // global arrays (shared-memory copies are indexed by the coarse kernel)
+    const long long n = L.plane * (L.dim == 3 ? L.n2 : 1);
+    const unsigned site = (15u << 16) | (unsigned)__LINE__;   // 15: this header
+    bool ok = mg_ck_n(L, p - 1, n, site) && mg_ck_n(L, p + 1, n, site) && mg_ck_n(L, p + dm, n, site) &&
+              mg_ck_n(L, p + dp, n, site);
+    if (KIND == K_NINE) ok = ok && mg_ck_n(L, p + dm - 1, n, site) && mg_ck_n(L, p + dp + 1, n, site);
+    if (DIM == 3) ok = ok && mg_ck_n(L, p - (long long)L.plane, n, site) && mg_ck_n(L, p + (long long)L.plane, n, site);
+    if (!ok) return gp;
+  }
+#endif
   T up = u[p];
   T s;
   if (KIND == K_NINE) {
@@ -197,6 +233,13 @@ __device__ __forceinline__ void cyclic_yline(const Lev<T> &L, long long base, in
                                              T omega, T *cps, T *dps, T *zps) {
   const int m = L.n1;
   const long long stride = L.pitch;
+#ifdef MG_DEBUG
+  {   // the line's first and last nodes (every access of the three passes lies between them)
+    const long long n = L.plane * (L.dim == 3 ? L.n2 : 1);
+    const unsigned site = (15u << 16) | (unsigned)__LINE__;
+    if (!mg_ck_n(L, base, n, site) || !mg_ck_n(L, base + (m - 1) * stride, n, site)) return;
+  }
+#endif
   T beta = T(0), gamma = T(1), cprev = T(0), yprev = T(0), zprev = T(0);
   for (int s = 0; s < m; ++s) {
     long long p = base + s * stride;
@@ -432,6 +475,8 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out);
 // dst[0] = sqrt(src[0])
 void launch_sqrt(const Launch &lc, const double *src, double *dst);
+// test hook of the -DMG_DEBUG build: a bounds check one past the level's last node (no access)
+void launch_bounds_probe(const Launch &lc, const Lev<double> &L);
 // end of a cycle of a device-side solve loop: history, cycle count, status, WHILE condition.
 // After a float-float defect (tsq: its sum of squares of |b| + |A||x|; null otherwise) the loop
 // stops only when the residual is below tol by the estimated error E = ff_err * sqrt(tsq), and

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "../../include/mg.h"
+#define MG_FILE_ID 9   // bounds-check sites (-DMG_DEBUG)
 #include "mg_internal.cuh"
 
 using namespace mg;
