@@ -123,6 +123,10 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        past the finest grid's last node (nothing is accessed there), so
                                        that it returns MG_EBOUNDS with the context still usable; the
                                        normal build returns MG_EINVAL for this flag */
+#define MG_FLAG_TRACE           4096u /* per-kernel trace: solves run one graph launch per refinement
+                                       step / cycle from the host, with an event after every kernel;
+                                       mg_trace_report gives the time per kernel and level (slower than
+                                       the device-side loop: for profiling) */
 #define MG_FLAG_TEST_WAIT_TIMEOUT 128u /* test hook, never for production: in each solve one copy of the
                                        first single-precision TMA sweep is left out, so that the compute
                                        warps' bounded waits run out (about a second) and the solve returns
@@ -364,6 +368,14 @@ long long mg_launch_count(const mg_ctx *c);
 void mg_destroy(mg_ctx *c);
 const char *mg_status_str(mg_status s);
 const char *mg_last_error(const mg_ctx *c);
+
+/* Contexts made with MG_FLAG_TRACE: the trace gathered by the solves since the last report, as
+ * text, one line per kernel launcher and level ("name level launches total_ms", the most
+ * expensive first; a kernel's time is the time between the events after it and after the kernel
+ * before it, launch latency included).  Writes the full length + 1 to *len (may be NULL); with
+ * buf (host) non-NULL also writes at most cap bytes (NUL-terminated) there and clears the trace.
+ * MG_EINVAL for contexts without the flag. */
+mg_status mg_trace_report(mg_ctx *c, char *buf, size_t cap, size_t *len);
 
 /* 1 for the checking build of this library (compiled with -DMG_DEBUG: every kernel checks the
  * node indices of its global accesses against the level's arrays, skips an access out of range

@@ -26,6 +26,7 @@ FLAG_GALERKIN = 256
 FLAG_FP64_DEFECT = 512
 FLAG_NO_PDL = 1024
 FLAG_TEST_BOUNDS = 2048
+FLAG_TRACE = 4096
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EDIVERGED",
           6: "MG_ETIMEOUT", 7: "MG_EBOUNDS"}
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EDIVERGED, ETIMEOUT, EBOUNDS = 0, 1, 2, 3, 4, 5, 6, 7
@@ -34,7 +35,7 @@ EXPORTS = ["mg_workspace_bytes", "mg_setup", "mg_solve", "mg_solve_host", "mg_so
            "mg_residual_norm", "mg_residual_norm_noalloc", "mg_level_dims", "mg_step_smooth", "mg_step_defect", "mg_step_restrict", "mg_step_prolong",
            "mg_step_coarse", "mg_step_cycle", "mg_step_descend", "mg_step_ascend", "mg_step_outer_defect", "mg_kernel_timing", "mg_launch_count", "mg_destroy",
            "mg_status_str", "mg_last_error", "mg_batch_create", "mg_batch_create_ex", "mg_batch_info",
-           "mg_batch_solve", "mg_batch_destroy", "mg_solve_batched", "mg_debug_build"]
+           "mg_batch_solve", "mg_batch_destroy", "mg_solve_batched", "mg_debug_build", "mg_trace_report"]
 BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = True, debug: bool = False):
     L.mg_solve_batched.restype = I
     L.mg_debug_build.argtypes = []
     L.mg_debug_build.restype = I
+    L.mg_trace_report.argtypes = [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mg_trace_report.restype = I
     _libs[debug] = L
     return L
 
@@ -404,6 +407,20 @@ class Solver:
         ms, n, by = C.c_double(), C.c_int(), C.c_double()
         self._check(self.lib.mg_kernel_timing(self.ctx, C.byref(ms), C.byref(n), C.byref(by)))
         return ms.value, n.value, by.value
+
+    def trace_report(self):
+        """mg_trace_report (contexts made with FLAG_TRACE): list of (kernel, level, launches, ms) since
+        the last report, the most expensive first."""
+        n = C.c_size_t()
+        self._check(self.lib.mg_trace_report(self.ctx, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.mg_trace_report(self.ctx, buf, n.value, C.byref(n)))
+        rows = []
+        self.trace_header = buf.value.decode().splitlines()[0]
+        for line in buf.value.decode().splitlines()[1:]:
+            name, lev, cnt, ms = line.split()
+            rows.append((name, int(lev), int(cnt), float(ms)))
+        return rows
 
     def launch_count(self):
         return int(self.lib.mg_launch_count(self.ctx))

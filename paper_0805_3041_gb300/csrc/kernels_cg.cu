@@ -180,7 +180,7 @@ void launch_coarse_cg(const Launch &lc, const Lev<double> &L, int kind, const T 
     else if (kind == K_CELL) go(k_coarse_cg<T, 3, K_CELL>);
     else go(k_coarse_cg<T, 3, K_EDGE>);
   }
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template void launch_coarse_cg<double>(const Launch &, const Lev<double> &, int, const double *, double *, double *,

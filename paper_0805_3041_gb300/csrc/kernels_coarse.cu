@@ -582,7 +582,7 @@ void launch_coarse_cycle(const Launch &lc, int dim, int kind, const void *levs, 
     else CC_LAUNCH(3, K_EDGE);
   }
 #undef CC_LAUNCH
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>

@@ -77,6 +77,54 @@ __device__ __forceinline__ T relax_at(const Lev<T> &L, const T *s, int r, int c,
   sum = fma(w.wN, s[(r + 1) * S + c], sum);
   return fma(omega * w.dinv, sum, uc);
 }
+
+// Stage rows [j0 - H, j0 - H + RW) x columns [i0 - H, i0 - H + W) of u and g into shared memory
+// (row stride S): every thread first issues all of its loads, then its shared-memory stores, so
+// the tile costs one round trip to L2 instead of one per element.  Rows outside a Dirichlet grid
+// and columns outside [0, n0) read 0; periodic rows wrap.  MODE 1: u is zero (not read); MODE 2:
+// u + omega_corr P ec at the unknowns (the coarse-grid correction folded into the staging).
+template <typename T, int KIND, int MODE, int RW, int W, int S>
+__device__ __forceinline__ void stage_tile(const Lev<T> &L, const T *__restrict__ u, const T *__restrict__ g, int i0,
+                                           int j0, int H, T *su, T *sg, const Lev<T> &C, const T *__restrict__ ec,
+                                           T omega_corr) {
+  constexpr int N = RW * W, PER = (N + 255) / 256;
+  T vu[PER], vg[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = (int)threadIdx.x + 256 * q;
+    vu[q] = T(0);
+    vg[q] = T(0);
+    if (t < N) {
+      const int r = t / W, c = t - r * W;
+      const int j = j0 - H + r, i = i0 - H + c;
+      const bool inx = i >= 0 && i < L.n0;
+      const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
+      const T *gp = row_ptr(g, L, j);
+      if (rp && inx) vu[q] = rp[i];
+      if (gp && inx) vg[q] = gp[i];
+      if (MODE == 2 && unk_row(L, j) && i >= 1 && i <= L.n0 - 2) {
+        const int jw = wrap_row(L, j);
+        int J0 = jw >> 1, J1 = (jw + 1) >> 1;
+        if (J1 >= C.n1) J1 -= C.n1;
+        if (MG_CKN(C, J0, C.n1) && MG_CKN(C, J1, C.n1) && MG_CKN(C, (i + 1) >> 1, C.n0)) {
+          const T *e0 = ec + (long long)J0 * C.pitch, *e1 = ec + (long long)J1 * C.pitch;
+          const int I0 = i >> 1, I1 = (i + 1) >> 1;
+          const T sc = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
+          vu[q] = fma(omega_corr, sc, vu[q]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int t = (int)threadIdx.x + 256 * q;
+    if (t < N) {
+      const int r = t / W, c = t - r * W;
+      su[r * S + c] = vu[q];
+      sg[r * S + c] = vg[q];
+    }
+  }
+}
 }  // namespace
 
 // MODE 0: plain sweep; 1: from a zero iterate; 2: u := u + omega_corr P ec before the sweep
@@ -180,29 +228,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   // ---- stage u (with the optional fused correction) and g ----
-  for (int r = warp; r < RW; r += 8) {
-    int j = j0 - H + r;
-    const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
-    const T *gp = row_ptr(g, L, j);
-    bool corr = (MODE == 2) && unk_row(L, j);
-    int jw = wrap_row(L, j);
-    int J0 = jw >> 1, J1 = (jw + 1) >> 1;
-    if (J1 >= C.n1) J1 -= C.n1;
-    const T *e0 = ec + (long long)J0 * C.pitch, *e1 = ec + (long long)J1 * C.pitch;
-    for (int c = lane; c < TX + 2 * H; c += 32) {
-      int i = i0 - H + c;
-      bool inx = i >= 0 && i < L.n0;
-      T v = (rp && inx) ? rp[i] : T(0);
-      if (MODE == 2 && corr && i >= 1 && i <= L.n0 - 2 && MG_CKN(C, J0, C.n1) && MG_CKN(C, J1, C.n1) &&
-          MG_CKN(C, (i + 1) >> 1, C.n0)) {
-        int I0 = i >> 1, I1 = (i + 1) >> 1;
-        T s = ((e0[I0] + e0[I1]) + (e1[I0] + e1[I1])) * T(0.25);
-        v = fma(omega_corr, s, v);
-      }
-      su[r * SXN + c] = v;
-      sg[r * SXN + c] = (gp && inx) ? gp[i] : T(0);
-    }
-  }
+  stage_tile<T, KIND, MODE, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, C, ec, omega_corr);
   __syncthreads();
   // ---- 2 NS half-sweeps on shrinking regions ----
 #pragma unroll 1
@@ -258,17 +284,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
   __shared__ T sr[(TY + 2) * DS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  for (int r = warp; r < RW; r += 8) {
-    int j = j0 - H + r;
-    const T *rp = (MODE == 1) ? nullptr : row_ptr(u, L, j);
-    const T *gp = row_ptr(g, L, j);
-    for (int c = lane; c < TX + 2 * H; c += 32) {
-      int i = i0 - H + c;
-      bool inx = i >= 0 && i < L.n0;
-      su[r * SXN + c] = (rp && inx) ? rp[i] : T(0);
-      sg[r * SXN + c] = (gp && inx) ? gp[i] : T(0);
-    }
-  }
+  stage_tile<T, KIND, MODE == 1 ? 1 : 0, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, L, u, T(0));
   __syncthreads();
 #pragma unroll 1
   for (int h = 0; h < 2 * NS; ++h) {
@@ -432,7 +448,7 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
     }
   }
 #undef RB_L
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -454,7 +470,7 @@ void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
     }
   }
 #undef RB2_L
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -474,7 +490,7 @@ void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int ki
     }
   }
 #undef RB2D_L
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -485,7 +501,7 @@ void launch_defect_restrict2d(const Launch &lc, const Lev<T> &F, const Lev<T> &C
   else if (kind == K_SEP) k_defect_restrict2d<T, K_SEP><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   else if (kind == K_CELL) k_defect_restrict2d<T, K_CELL><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
   else k_defect_restrict2d<T, K_EDGE><<<gr, 256, 0, lc.s>>>(F, C, u, g, gc);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template void launch_rb2d<double>(const Launch &, const Lev<double> &, int, const double *, const double *, double *,

@@ -312,9 +312,9 @@ bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const do
   const dim3 gr((unsigned)gx, (unsigned)((rows + R - 1) / R)), bl(FX, FY);
   if (kind == K_CONST) k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
   else k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
-  ++*lc.counter;
+  lc.done(__func__);
   k_ff_finish<<<2, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), half, out_sq, out_t);
-  ++*lc.counter;
+  lc.done(__func__);
   return true;
 }
 

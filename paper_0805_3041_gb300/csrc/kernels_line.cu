@@ -429,7 +429,7 @@ void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra
       if (kind == K_CONST) YR(3, K_CONST); else if (kind == K_SEP) YR(3, K_SEP); else if (kind == K_CELL) YR(3, K_CELL); else YR(3, K_EDGE);
     }
 #undef YR
-    ++*lc.counter;
+    lc.done(__func__);
     return;
   }
   if (dir == 1 && s3 && mrows >= 32) {
@@ -443,7 +443,7 @@ void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra
       if (kind == K_CONST) YP(3, K_CONST); else if (kind == K_SEP) YP(3, K_SEP); else if (kind == K_CELL) YP(3, K_CELL); else YP(3, K_EDGE);
     }
 #undef YP
-    ++*lc.counter;
+    lc.done(__func__);
     return;
   }
   long long nlines = dir == 0 ? L.unk_rows() : (long long)(L.n0 - 2) * L.zrows();
@@ -460,7 +460,7 @@ void launch_line(const Launch &lc, const Lev<T> &L, int kind, int dir, int zebra
     else if (kind == K_CELL) k_line<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2, s3);
     else k_line<T, 3, K_EDGE><<<bl, th, 0, lc.s>>>(L, dir, zebra, colour, u, g, out, omega, s1, s2, s3);
   }
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template void launch_line<double>(const Launch &, const Lev<double> &, int, int, int, int, const double *,

@@ -292,7 +292,7 @@ bool launch_rb2d_march(const Launch &lc, const Lev<T> &L, int kind, const T *u, 
     if (mode == 0) MARCH(K_SEP, 0); else if (mode == 1) MARCH(K_SEP, 1); else MARCH(K_SEP, 2);
   }
 #undef MARCH
-  ++*lc.counter;
+  lc.done(__func__);
   return true;
 }
 

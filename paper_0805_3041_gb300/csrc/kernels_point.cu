@@ -486,7 +486,7 @@ void launch_jacobi(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   DISPATCH_DK9(L.dim, kind, k_jacobi, <<<gr, bl, 0, lc.s>>>(L, u, g, out, omega, R));
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -495,7 +495,7 @@ void launch_jacobi_zero(const Lev<T> &L, int kind, const Launch &lc, const T *g,
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   DISPATCH_DK9(L.dim, kind, k_jacobi_zero, <<<gr, bl, 0, lc.s>>>(L, g, out, omega, R));
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -504,7 +504,7 @@ void launch_rb_half(const Launch &lc, const Lev<T> &L, int kind, T *u, const T *
   int R = rows_per_thread(rows);
   dim3 gr = grid_for((L.xunk() + 1) / 2, rows, R), bl(BX, BY);
   DISPATCH_DK(L.dim, kind, k_rb_half, <<<gr, bl, 0, lc.s>>>(L, u, g, omega, colour, R));
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -516,7 +516,7 @@ void launch_gs9_colour(const Launch &lc, const Lev<T> &L, T *u, const T *g, T om
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(xs, rows, R), bl(BX, BY);
   k_gs9_colour<T><<<gr, bl, 0, lc.s>>>(L, u, g, omega, ci, cj, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -525,7 +525,7 @@ void launch_defect(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
   int R = rows_per_thread(rows);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   DISPATCH_DK9(L.dim, kind, k_defect, <<<gr, bl, 0, lc.s>>>(L, u, g, r, R));
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // Rows per thread of a reduction over `rows` unknown rows of `xthreads` unknowns each, such that
@@ -554,7 +554,7 @@ void launch_defect_norm(const Launch &lc, const Lev<T> &L, int kind, const T *u,
   int R = norm_R(rows, L.xunk(), nparts);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   DISPATCH_DK9(L.dim, kind, k_defect_norm, <<<gr, bl, 0, lc.s>>>(L, u, g, partials, R));
-  ++*lc.counter;
+  lc.done(__func__);
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
 
@@ -564,7 +564,7 @@ void launch_norm_parts(const Launch &lc, const Lev<T> &L, const T *v, double *pa
   int R = norm_R(rows, L.xunk(), nparts);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   k_norm_parts<T><<<gr, bl, 0, lc.s>>>(L, v, partials, R);
-  ++*lc.counter;
+  lc.done(__func__);
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
 
@@ -575,7 +575,7 @@ void launch_corr_weight(const Launch &lc, const Lev<T> &L, int kind, const T *u,
   int R = norm_R(rows, L.xunk(), nparts / 2 < 4096 ? nparts / 2 : 4096);
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   DISPATCH_DK(L.dim, kind, k_corr_dots, <<<gr, bl, 0, lc.s>>>(L, u, g, pe, partials, count, omega, R));
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -583,12 +583,12 @@ void launch_scale_by(const Launch &lc, T *e, long long n, const double *omega) {
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_scale_by<T><<<(unsigned)blocks, 256, 0, lc.s>>>(e, n, omega);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 void launch_norm_finish(const Launch &lc, const double *partials, int nparts, double *out_sq) {
   k_norm_finish<<<1, 1024, 0, lc.s>>>(partials, nparts, out_sq);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // End of a cycle inside a device-side solve loop (a CUDA-graph WHILE node): record the
@@ -638,7 +638,7 @@ void launch_step_end(const Launch &lc, cudaGraphConditionalHandle h, const doubl
                      double *hist, int *st, const double *tol, int maxit, int init, const double *tsq,
                      double ff_err, double ff_switch) {
   k_step_end<<<1, 1, 0, lc.s>>>(h, sq, bsq, hist, st, tol, maxit, init, tsq, ff_err, ff_switch);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // After a loop that stopped on the float-float defect: the FP64 relative residual replaces
@@ -654,7 +654,7 @@ __global__ void k_final_check(const double *sq, const double *bsq, double *hist,
 void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
                         const double *tol) {
   k_final_check<<<1, 1, 0, lc.s>>>(sq, bsq, hist, st, tol);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // Test hook of the -DMG_DEBUG build (MG_FLAG_TEST_BOUNDS): one bounds check of the index one past
@@ -665,7 +665,7 @@ __global__ void k_bounds_probe(Lev<double> L) {
 }
 void launch_bounds_probe(const Launch &lc, const Lev<double> &L) {
   k_bounds_probe<<<1, 1, 0, lc.s>>>(L);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 __global__ void k_sqrt(const double *src, double *dst) {
@@ -674,12 +674,12 @@ __global__ void k_sqrt(const double *src, double *dst) {
 }
 void launch_sqrt(const Launch &lc, const double *src, double *dst) {
   k_sqrt<<<1, 1, 0, lc.s>>>(src, dst);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 void launch_relres(const Launch &lc, const double *sq, const double *bsq, double *hist, int it, double *relres_out) {
   k_relres<<<1, 1, 0, lc.s>>>(sq, bsq, hist, it, relres_out);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b,
@@ -706,7 +706,7 @@ void launch_defect64_to32(const Launch &lc, const Lev<double> &L, int kind, cons
     else D64_R(3, K_EDGE);
   }
 #undef D64_R
-  ++*lc.counter;
+  lc.done(__func__);
   launch_norm_finish(lc, partials, (int)(gr.x * gr.y), out_sq);
 }
 
@@ -716,7 +716,7 @@ void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const f
   dim3 gr = grid_for(L.xunk(), rows, R), bl(BX, BY);
   if (R == 4) k_ir_update<4><<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
   else k_ir_update<0><<<gr, bl, 0, lc.s>>>(L, x, c, L.pitch, L.plane, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, const double *lam, double *dk) {
@@ -726,7 +726,7 @@ void launch_grad_k(const Launch &lc, const Lev<double> &L, const double *u, cons
   dim3 gr = grid_for(L.n0 - 1, rows, R), bl(BX, BY);
   if (L.dim == 2) k_grad_k<2><<<gr, bl, 0, lc.s>>>(L, u, lam, dk, R);
   else k_grad_k<3><<<gr, bl, 0, lc.s>>>(L, u, lam, dk, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 #define INST(T)                                                                                              \

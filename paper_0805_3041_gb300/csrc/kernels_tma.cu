@@ -741,7 +741,7 @@ bool launch_defect_restrict_tma(const Launch &lc, const Lev<float> &L, const Lev
     k_defect_restrict_tma<K_CONST><<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, C, u, g, gc, RCc, ngroups, err);
   else
     k_defect_restrict_tma<K_SEP><<<blocks, 32 * (NW + 1), smem, lc.s>>>(L, C, u, g, gc, RCc, ngroups, err);
-  ++*lc.counter;
+  lc.done(__func__);
   return true;
 }
 
@@ -815,7 +815,7 @@ bool launch_rb2d_tma(const Launch &lc, const Lev<float> &L, int kind, const floa
   }
 #undef TMA_L
 #undef TMA_K
-  ++*lc.counter;
+  lc.done(__func__);
   return true;
 }
 

@@ -146,7 +146,7 @@ void launch_interp(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T *
   dim3 gr = grid2(F.n0, rows, R), bl(BX, BY);
   if (F.dim == 2) k_interp<T, 2><<<gr, bl, 0, lc.s>>>(F, C, ec, out, R);
   else k_interp<T, 3><<<gr, bl, 0, lc.s>>>(F, C, ec, out, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -156,7 +156,7 @@ void launch_restrict(const Launch &lc, const Lev<T> &F, const Lev<T> &C, const T
   dim3 gr = grid2(C.xunk(), rows, R), bl(BX, BY);
   if (F.dim == 2) k_restrict<T, 2><<<gr, bl, 0, lc.s>>>(F, C, rf, gc, R);
   else k_restrict<T, 3><<<gr, bl, 0, lc.s>>>(F, C, rf, gc, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <typename T>
@@ -166,7 +166,7 @@ void launch_prolong_add(const Launch &lc, const Lev<T> &F, const Lev<T> &C, cons
   dim3 gr = grid2(F.xunk(), rows, R), bl(BX, BY);
   if (F.dim == 2) k_prolong_add<T, 2><<<gr, bl, 0, lc.s>>>(F, C, ec, uf, w, R);
   else k_prolong_add<T, 3><<<gr, bl, 0, lc.s>>>(F, C, ec, uf, w, R);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -191,7 +191,7 @@ template <typename T>
 void launch_coarse_apply(const Launch &lc, const double *Ainv, const long long *cidx, int nc, const T *g, T *u) {
   int threads = 256, blocks = (nc * 32 + threads - 1) / threads;
   k_coarse_apply<T><<<blocks, threads, 0, lc.s>>>(Ainv, cidx, nc, g, u);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // Dense matrix of the coarsest operator: row r of unknown p = cidx[r] holds D_p on the
@@ -249,7 +249,7 @@ void launch_assemble_dense(const Launch &lc, const Lev<T> &L, int kind, const lo
     else if (kind == K_CELL) k_assemble_dense<T, 3, K_CELL><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
     else k_assemble_dense<T, 3, K_EDGE><<<bl, th, 0, lc.s>>>(L, cidx, cmap, nc, A);
   }
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed), step k:
@@ -276,7 +276,8 @@ void launch_gj_step(const Launch &lc, double *A, double *col, int n, int kstep) 
   k_gj_a<<<1, 256, 0, lc.s>>>(A, col, n, kstep);
   long long tot = (long long)n * n;
   k_gj_b<<<(unsigned)((tot + 255) / 256), 256, 0, lc.s>>>(A, col, n, kstep);
-  *lc.counter += 2;
+  lc.done("k_gj_a");
+  lc.done("k_gj_b");
 }
 
 // ---------------------------------------------------------------------------------------
@@ -301,7 +302,7 @@ __global__ void k_coarsen_sep(const double *fsx, const double *fsy, const double
 void launch_coarsen_sep(const Launch &lc, const double *fsx, const double *fsy, const double *fsz, int nf0,
                         double *csx, double *csy, double *csz, int nc0) {
   k_coarsen_sep<<<(nc0 + 127) / 128, 128, 0, lc.s>>>(fsx, fsy, fsz, nf0, csx, csy, csz, nc0);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 __global__ void k_sep_dinv(const double *sx, const double *sy, const double *sz, int n0, int dim, double *dinv) {
@@ -316,7 +317,7 @@ __global__ void k_sep_dinv(const double *sx, const double *sy, const double *sz,
 void launch_sep_dinv(const Launch &lc, const double *sx, const double *sy, const double *sz, int n0, int dim,
                      double *dinv) {
   k_sep_dinv<<<(n0 + 127) / 128, 128, 0, lc.s>>>(sx, sy, sz, n0, dim, dinv);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // coarse cell coefficient = mean of the 2^d child cells
@@ -341,7 +342,7 @@ void launch_coarsen_cell(const Launch &lc, const Lev<double> &F, const Lev<doubl
   int ncx = C.n0 - 1, ncy = C.per ? C.n1 : C.n1 - 1, ncz = C.dim == 3 ? C.n2 - 1 : 1;
   dim3 gr((ncx + 127) / 128, ncy, ncz);
   k_coarsen_cell<<<gr, 128, 0, lc.s>>>(F, C, kf, kc);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 template <int DIM>
@@ -376,7 +377,7 @@ void launch_cell_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
   dim3 gr((L.xunk() + 127) / 128, gy, gz);
   if (L.dim == 2) k_cell_dinv<2><<<gr, 128, 0, lc.s>>>(L, dinv);
   else k_cell_dinv<3><<<gr, 128, 0, lc.s>>>(L, dinv);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -459,7 +460,7 @@ void launch_rap(const Launch &lc, const Lev<double> &F, int fkind, const Lev<dou
   else if (fkind == K_CELL) k_rap<K_CELL><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
   else if (fkind == K_EDGE) k_rap<K_EDGE><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
   else k_rap<K_NINE><<<gr, 128, 0, lc.s>>>(F, C, dg, ex, ey, ene, enw, dinv);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // edge coefficients: coarse weights edge by edge, and 1/D
@@ -486,7 +487,7 @@ void launch_coarsen_edge(const Launch &lc, const Lev<double> &F, const Lev<doubl
                          const double *fy, const double *fz, double *cx, double *cy, double *cz) {
   dim3 gr((C.n0 + 127) / 128, C.n1, C.dim == 3 ? C.n2 : 1);
   k_coarsen_edge<<<gr, 128, 0, lc.s>>>(F, C, fx, fy, fz, cx, cy, cz);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // 1/D at the unknowns, D = the sum of the weights of the edges at the node
@@ -513,7 +514,7 @@ void launch_edge_dinv(const Launch &lc, const Lev<double> &L, double *dinv) {
   dim3 gr((L.xunk() + 127) / 128, gy, gz);
   if (L.dim == 2) k_edge_dinv<2><<<gr, 128, 0, lc.s>>>(L, dinv);
   else k_edge_dinv<3><<<gr, 128, 0, lc.s>>>(L, dinv);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 __global__ void k_to_float(const double *__restrict__ s, float *__restrict__ d, long long n) {
@@ -527,7 +528,7 @@ void launch_to_float(const Launch &lc, const double *src, float *dst, long long 
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   k_to_float<<<(unsigned)blocks, 256, 0, lc.s>>>(src, dst, n);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -571,7 +572,7 @@ template <typename T>
 void launch_zero_boundary(const Launch &lc, const Lev<T> &L, T *dst) {
   dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
   k_zero_boundary<T><<<gr, 128, 0, lc.s>>>(L, dst);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 template <typename T>
 __global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
@@ -586,19 +587,19 @@ template <typename T>
 void launch_pack(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary) {
   dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
   k_pack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, zero_boundary);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 template <typename T>
 void launch_unpack(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale) {
   dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
   k_unpack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, scale);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 template <typename T>
 void launch_zero_level(const Launch &lc, const Lev<T> &L, T *dst) {
   dim3 gr((unsigned)((L.pitch + 127) / 128), L.n1, L.dim == 3 ? L.n2 : 1);
   k_zero_level<T><<<gr, 128, 0, lc.s>>>(L, dst);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 // Axis-swapped copies (y-line smoothers run as x-line smoothers on the transposed
@@ -642,26 +643,26 @@ template <typename T>
 void launch_pack_swapped(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary) {
   dim3 gr((L.n0 + 31) / 32, (L.n1 + 31) / 32, L.dim == 3 ? L.n2 : 1), bl(32, 8);
   k_transpose_copy<T, double><<<gr, bl, 0, lc.s>>>(src, dst, L.n1, L.n0, L.pitch, L.plane, 1, 1.0);
-  ++*lc.counter;
+  lc.done(__func__);
   if (zero_boundary) launch_zero_boundary<T>(lc, L, dst);
 }
 template <typename T>
 void launch_unpack_swapped(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale) {
   dim3 gr((L.n0 + 31) / 32, (L.n1 + 31) / 32, L.dim == 3 ? L.n2 : 1), bl(32, 8);
   k_transpose_copy<double, T><<<gr, bl, 0, lc.s>>>(src, dst, L.n1, L.n0, L.pitch, L.plane, 0, scale);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 void launch_cell_pack_swapped(const Launch &lc, const Lev<double> &L, const double *src_compact, double *dst) {
   int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
   dim3 gr((ncx + 31) / 32, (ncy + 31) / 32, ncz), bl(32, 8);
   k_transpose_copy<double, double><<<gr, bl, 0, lc.s>>>(src_compact, dst, ncy, ncx, L.pitch, L.plane, 1, 1.0);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 void launch_cell_unpack_swapped(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact) {
   int ncx = L.n0 - 1, ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
   dim3 gr((ncx + 31) / 32, (ncy + 31) / 32, ncz), bl(32, 8);
   k_transpose_copy<double, double><<<gr, bl, 0, lc.s>>>(src, dst_compact, ncy, ncx, L.pitch, L.plane, 0, 1.0);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 template void launch_pack_swapped<double>(const Launch &, const Lev<double> &, const double *, double *, int);
 template void launch_pack_swapped<float>(const Launch &, const Lev<float> &, const double *, float *, int);
@@ -684,13 +685,13 @@ void launch_cell_pack(const Launch &lc, const Lev<double> &L, const double *src_
   int ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
   dim3 gr((L.n0 - 1 + 127) / 128, ncy, ncz);
   k_cell_pack<<<gr, 128, 0, lc.s>>>(L, src_compact, dst, 0);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 void launch_cell_unpack(const Launch &lc, const Lev<double> &L, const double *src, double *dst_compact) {
   int ncy = L.per ? L.n1 : L.n1 - 1, ncz = L.dim == 3 ? L.n2 - 1 : 1;
   dim3 gr((L.n0 - 1 + 127) / 128, ncy, ncz);
   k_cell_pack<<<gr, 128, 0, lc.s>>>(L, src, dst_compact, 1);
-  ++*lc.counter;
+  lc.done(__func__);
 }
 
 #define INST(T)                                                                                              \

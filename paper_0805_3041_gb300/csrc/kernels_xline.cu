@@ -391,7 +391,7 @@ bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int co
       if (kind == K_CONST) XW(3, K_CONST); else if (kind == K_SEP) XW(3, K_SEP); else if (kind == K_CELL) XW(3, K_CELL); else XW(3, K_EDGE);
     }
 #undef XW
-    ++*lc.counter;
+    lc.done(__func__);
     return true;
   }
   size_t smem = sizeof(T) * ((kind == K_CONST ? 1 : 4) * (size_t)XL_SZ + 16 * NT);
@@ -406,7 +406,7 @@ bool launch_xline(const Launch &lc, const Lev<T> &L, int kind, int zebra, int co
     if (kind == K_CONST) XL(3, K_CONST); else if (kind == K_SEP) XL(3, K_SEP); else if (kind == K_CELL) XL(3, K_CELL); else XL(3, K_EDGE);
   }
 #undef XL
-  ++*lc.counter;
+  lc.done(__func__);
   return true;
 }
 

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <map>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -126,7 +127,18 @@ struct mg_ctx {
   long long t_count = 0;
   std::vector<double> ev_bytes;   // algorithmic bytes of the launch opened by each pool event
   std::string err;
+  // MG_FLAG_TRACE: event marks after every kernel of a refinement step / cycle (the forward
+  // schedule in marks [0, kTraceMarks), the transposed one after it), and the sums per kernel
+  // and level since the last report
+  Tracer tracer;
+  std::vector<cudaEvent_t> tr_ev;
+  std::vector<const char *> tr_label;
+  std::vector<int> tr_lev;
+  int tr_n[2] = {0, 0};
+  long long tr_steps = 0, tr_unread = 0;   // harvested schedules, marks whose time could not be read
+  std::map<std::pair<std::string, int>, std::pair<long long, double>> tr_sum;
 };
+static const int kTraceMarks = 2048;
 
 // Error estimate of the float-float outer defect relative to the norm of |b| + |A||x| (which
 // that kernel also returns).  Each operand carries 47 significant bits, so a node's error is a
@@ -465,6 +477,7 @@ template <> struct LevOf<float> {
     }                                                                    \
   } while (0)
 
+#ifdef MG_DEBUG
 // Source file of a bounds-check site id (the MG_FILE_ID of each translation unit).
 static const char *site_file(unsigned id) {
   static const char *names[] = {"?", "kernels_point.cu", "kernels_transfer.cu", "kernels_line.cu",
@@ -473,6 +486,7 @@ static const char *site_file(unsigned id) {
                                 "kernels_ff.cu", "mg_capi.cu", "?", "mg_internal.cuh"};
   return id < 16 ? names[id] : "?";
 }
+#endif
 
 // After the context's stream has been synchronised: a failed launch, and in the -DMG_DEBUG
 // build a device-side bounds check that failed since the last call (the word is cleared).
@@ -678,6 +692,7 @@ template <typename T>
 static void coarse_solve(Sched &S, const T *g) {
   NvtxRange nr("coarsest solve");
   mg_ctx *c = S.c;
+  c->tracer.level = 1;
   LevData<T> &D = LevOf<T>::data(c, 1);
   coarse_solve_into<T>(c, S.lc, g, D.u[c->cur[1]]);
 }
@@ -692,6 +707,7 @@ template <typename T>
 static void launch_csk(Sched &S, int pid, const T *g_in, const T *u_in, T *u_out) {
   NvtxRange nr("coarse grids in one CTA");
   mg_ctx *c = S.c;
+  c->tracer.level = c->lcut;
   launch_coarse_cycle<T>(S.lc, c->P.dim, c->kind, c->slev, c->prog + c->prog_off[pid], c->prog_len[pid], c->lcut,
                          g_in, u_in, u_out, c->Ainv, c->cidx_s, c->nc, (T)c->P.omega, (T)corr_weight(c),
                          c->csk_smem, c->P.smoother > MG_RBGS || adaptive_corr(c));
@@ -830,6 +846,7 @@ template <typename T>
 static void descend(Sched &S, int l, const T *g, int transposed, bool zero_start) {
   NvtxRange nr("pre-smoothing, defect, restriction", l);
   mg_ctx *c = S.c;
+  c->tracer.level = l;
   LevData<T> &D = LevOf<T>::data(c, l);
   LevData<T> &Dc = LevOf<T>::data(c, l - 1);
   Lev<T> L = LevOf<T>::get(c, l), Lc = LevOf<T>::get(c, l - 1);
@@ -862,6 +879,7 @@ template <typename T>
 static void ascend(Sched &S, int l, const T *g, int transposed) {
   NvtxRange nr("correction, post-smoothing", l);
   mg_ctx *c = S.c;
+  c->tracer.level = l;
   LevData<T> &Dc = LevOf<T>::data(c, l - 1);
   Lev<T> Lc = LevOf<T>::get(c, l - 1);
   int npost = transposed ? c->P.nu1 : c->P.nu2;
@@ -962,6 +980,7 @@ static void emit_fp64_cycle(Sched &S, int transposed) {
   if (c->lcut == L) launch_csk<double>(S, prog_id_fine(0, transposed), c->d64[L].g, c->d64[L].u[0], c->d64[L].u[0]);
   else cycle<double>(S, L, c->d64[L].g, 0, transposed, false);
   finest_to_zero<double>(S);
+  c->tracer.level = L;
   launch_defect_norm<double>(S.lc, lev64(c, L), c->kind, c->d64[L].u[0], c->d64[L].g, c->partials,
                              norm_parts_count(), c->scal + 1);
   if (S.loop) launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4,
@@ -982,6 +1001,7 @@ static void emit_mixed_step(Sched &S, int transposed) {
       cycle<float>(S, L, c->d32[L].g, 0, transposed, q == 0);
     finest_to_zero<float>(S);
   }
+  c->tracer.level = L;
   launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
   const bool ff = c->ff && launch_defect_ff(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials,
                                             norm_parts_count(), c->scal + 1, c->scal + 5, c->st + 6);
@@ -1138,6 +1158,45 @@ static mg_status build_loop_graph(mg_ctx *c, int transposed) {
   return MG_OK;
 }
 
+// MG_FLAG_TRACE: the marks of one step schedule (direction t) start with an unlabelled mark;
+// every launch through lc then adds one
+static void trace_begin(mg_ctx *c, Launch &lc, int t, bool capture) {
+  if (!(c->P.flags & MG_FLAG_TRACE)) return;
+  Tracer &tr = c->tracer;
+  tr.capture = capture;
+  tr.ev = c->tr_ev.data() + t * kTraceMarks;
+  tr.label = c->tr_label.data() + t * kTraceMarks;
+  tr.lev = c->tr_lev.data() + t * kTraceMarks;
+  tr.cap = kTraceMarks;
+  tr.n = 0;
+  tr.level = c->L;
+  tr.mark(lc.s, nullptr);
+  lc.tr = &tr;
+}
+static void trace_end(mg_ctx *c, int t) {
+  if (c->P.flags & MG_FLAG_TRACE) c->tr_n[t] = c->tracer.n;
+}
+// after the step ran (stream synchronised): the time between consecutive marks goes to the kernel
+// that ends at the later one
+static void trace_harvest(mg_ctx *c, int t) {
+  if (!(c->P.flags & MG_FLAG_TRACE)) return;
+  const int b = t * kTraceMarks;
+  ++c->tr_steps;
+  for (int i = 1; i < c->tr_n[t]; ++i) {
+    const char *lab = c->tr_label[b + i];
+    float ms = 0.f;
+    if (!lab) continue;
+    if (cudaEventElapsedTime(&ms, c->tr_ev[b + i - 1], c->tr_ev[b + i]) != cudaSuccess) {
+      ++c->tr_unread;
+      continue;
+    }
+    auto &e = c->tr_sum[{std::string(lab), c->tr_lev[b + i]}];
+    e.first += 1;
+    e.second += ms;
+  }
+  cudaGetLastError();
+}
+
 static mg_status build_graph(mg_ctx *c, int transposed) {
   if (c->gexec[transposed]) return MG_OK;
   bool timing = (c->P.flags & MG_FLAG_TIMING) != 0;
@@ -1145,8 +1204,10 @@ static mg_status build_graph(mg_ctx *c, int transposed) {
   Sched S{c, Launch{c->cap, &c->launches}, timing, 2048 * (1 + transposed), &c->ev_graph_n[transposed]};
   long long before = c->launches;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  trace_begin(c, S.lc, transposed, true);
   if (c->mixed) emit_mixed_step(S, transposed);
   else emit_fp64_cycle(S, transposed);
+  trace_end(c, transposed);
   cudaGraph_t graph;
   cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
   if (e != cudaSuccess) {
@@ -1567,6 +1628,12 @@ mg_status mg_setup(const mg_params *p, const mg_coeffs *k, void *workspace, size
     c->ev_bytes.assign(6144, 0.0);
     for (auto &e : c->ev) cudaEventCreate(&e);
   }
+  if (p->flags & MG_FLAG_TRACE) {
+    c->tr_ev.resize(2 * kTraceMarks);
+    c->tr_label.assign(2 * kTraceMarks, nullptr);
+    c->tr_lev.assign(2 * kTraceMarks, 0);
+    for (auto &e : c->tr_ev) cudaEventCreate(&e);
+  }
   st = setup_levels(c);
   if (st) {
     *out = c;   // keep the error text available through mg_last_error
@@ -1583,6 +1650,7 @@ void mg_destroy(mg_ctx *c) {
   for (int t = 0; t < 2; ++t)
     if (c->lexec[t]) cudaGraphExecDestroy(c->lexec[t]);
   for (auto &e : c->ev) cudaEventDestroy(e);
+  for (auto &e : c->tr_ev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
   if (c->h_relres) cudaFreeHost(c->h_relres);
@@ -1604,6 +1672,31 @@ const char *mg_status_str(mg_status s) {
 }
 
 const char *mg_last_error(const mg_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+mg_status mg_trace_report(mg_ctx *c, char *buf, size_t cap, size_t *len) {
+  if (!c || !(c->P.flags & MG_FLAG_TRACE)) return MG_EINVAL;
+  std::vector<std::pair<double, std::string>> rows;
+  for (const auto &kv : c->tr_sum) {
+    char line[160];
+    std::snprintf(line, sizeof(line), "%-32s %3d %9lld %12.4f\n", kv.first.first.c_str(), kv.first.second,
+                  kv.second.first, kv.second.second);
+    rows.push_back({kv.second.second, line});
+  }
+  std::sort(rows.begin(), rows.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+  std::string out = "kernel                           level  launches     total_ms   (" +
+                    std::to_string(c->tr_steps) + " schedules, " + std::to_string(c->tr_n[0]) + "/" +
+                    std::to_string(c->tr_n[1]) + " marks, " + std::to_string(c->tr_unread) + " unreadable)\n";
+  for (const auto &r : rows) out += r.second;
+  if (len) *len = out.size() + 1;
+  if (buf && cap) {   // a call with a buffer consumes the trace; one without only sizes it
+    const size_t n = std::min(cap - 1, out.size());
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+    c->tr_sum.clear();
+    c->tr_steps = c->tr_unread = 0;
+  }
+  return MG_OK;
+}
 
 int mg_debug_build(void) {
 #ifdef MG_DEBUG
@@ -1685,7 +1778,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   int L = c->L;
   Launch lc{c->stream, &c->launches};
   bool use_graph = !(c->P.flags & MG_FLAG_NO_GRAPH);
-  bool timing = (c->P.flags & MG_FLAG_TIMING) != 0;
+  bool timing = (c->P.flags & (MG_FLAG_TIMING | MG_FLAG_TRACE)) != 0;   // host loop, per-step graph
   bool launched = false;
   Lev<double> F64 = lev64(c, L);
   mg_status lst;
@@ -1785,6 +1878,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
       if (use_graph) harvest_events(c, 2048 * (1 + transposed), c->ev_graph_n[transposed]);
       else harvest_events(c, 0, c->ev_used);
       c->ev_used = 0;
+      trace_harvest(c, transposed);
     }
     mg_status st = last_launch(c);
     if (st) return st;
@@ -1831,8 +1925,10 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     } else {
       c->ev_used = 0;
       Sched S{c, lc, timing, 0, &c->ev_used};
+      trace_begin(c, S.lc, transposed, false);
       if (c->mixed) emit_mixed_step(S, transposed);
       else emit_fp64_cycle(S, transposed);
+      trace_end(c, transposed);
     }
     launched = true;
   }

@@ -298,9 +298,33 @@ __device__ __forceinline__ void cyclic_yline(const Lev<T> &L, long long base, in
 // launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------------------
 
+// Per-kernel trace of a solve (MG_FLAG_TRACE): an event recorded on the launch stream after every
+// kernel, with the launcher's name and the level being processed.  The time between two
+// consecutive marks is the later kernel's time on the GPU timeline (launch latency included).
+struct Tracer {
+  cudaEvent_t *ev = nullptr;
+  const char **label = nullptr;
+  int *lev = nullptr;
+  int cap = 0, n = 0;
+  int level = 0;   // level the schedule is working on (set by the host-side cycle)
+  bool capture = false;   // marks become event-record nodes of a graph being captured
+  void mark(cudaStream_t s, const char *what) {
+    if (n >= cap) return;
+    if (capture) cudaEventRecordWithFlags(ev[n], s, cudaEventRecordExternal);
+    else cudaEventRecord(ev[n], s);
+    label[n] = what;
+    lev[n++] = level;
+  }
+};
+
 struct Launch {
   cudaStream_t s;
   long long *counter;   // incremented once per kernel launch
+  Tracer *tr = nullptr; // MG_FLAG_TRACE: marks after every launch
+  void done(const char *what) const {
+    ++*counter;
+    if (tr) tr->mark(s, what);
+  }
 };
 
 template <typename T>
