@@ -117,13 +117,24 @@ __device__ __forceinline__ void block_sum2_ff(float &v, float &w) {
 // r32^2 per block, and one of (|b| + |A||x|)^2 per block (partials + half).  With *use64 set
 // the same marching evaluates the defect in FP64, in the FP64 defect kernel's order, and the
 // second sum is 0.
+// Fused refinement update (c32 != null): the iterate is double-buffered, *par selecting the
+// current buffer (xa or xb).  The kernel reads the current one only, forms x + (double) c at
+// every node it touches (the FP64 update of the refinement step, rounded as a separate update
+// would round it), takes the defect of that, and writes it into the other buffer at its own
+// nodes; the buffer it reads is never written during the launch, so neighbouring blocks need no
+// ordering.  The finish kernel then flips *par.  c32 == null: the defect of xa, nothing written.
 template <int KIND>
-__global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const double *__restrict__ x,
-                                                      const double *__restrict__ b, float *__restrict__ r32,
-                                                      double *__restrict__ partials, int half, int R,
-                                                      const int *__restrict__ use64) {
+__global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const double *__restrict__ xa,
+                                                      double *__restrict__ xb, const double *__restrict__ b,
+                                                      float *__restrict__ r32, double *__restrict__ partials,
+                                                      int half, int R, const int *__restrict__ use64,
+                                                      const float *__restrict__ c32, const int *__restrict__ par) {
   MG_PDL_WAIT();
   const bool f64 = use64 != nullptr && *use64 != 0;
+  const bool upd = c32 != nullptr;
+  const bool odd = upd && *par != 0;
+  const double *__restrict__ x = odd ? xb : xa;   // the current iterate (read only)
+  double *__restrict__ xout = odd ? const_cast<double *>(xa) : xb;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const int i = 1 + (blockIdx.x * FY + threadIdx.y) * FX + lane;   // this thread's column
@@ -153,10 +164,12 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
     if (L.per) j = j < 0 ? j + L.n1 : (j >= L.n1 ? j - L.n1 : j);
     return (long long)j * L.pitch;
   };
+  // x at node q, updated by the correction when the update is fused
+  auto xat = [&](long long q) -> double { return upd ? x[q] + (double)c32[q] : x[q]; };
   auto raw = [&](int r) -> double {   // x at (i, row r); rows outside the unknowns (Dirichlet) read 0
     if (!act || (!L.per && (r < 0 || r >= rows))) return 0.0;
     const long long q = row_of(r) + i;
-    return MG_CK(L, q) ? x[q] : 0.0;   // (the check: debug build only)
+    return MG_CK(L, q) ? xat(q) : 0.0;   // (the check: debug build only)
   };
   auto bval = [&](int r) -> double {   // b at (i, row r) of an unknown row
     const long long q = row_of(r) + i;
@@ -184,7 +197,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
       const long long p = row_of(r) + i;
       double xw = __shfl_up_sync(FULL, xc, 1), xe = __shfl_down_sync(FULL, xc, 1);
       if (edge) {
-        const double xo = (oin && MG_CK(L, p - i + io)) ? x[p - i + io] : 0.0;
+        const double xo = (oin && MG_CK(L, p - i + io)) ? xat(p - i + io) : 0.0;
         if (lane == 0) xw = xo;
         else xe = xo;
       }
@@ -195,7 +208,10 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         s = fma(wY, xm, s);
         s = fma(wY, xp, s);
         const float res = (float)s;
-        if (MG_CK(L, p)) r32[p] = res;
+        if (MG_CK(L, p)) {
+          r32[p] = res;
+          if (upd) xout[p] = xc;
+        }
         acc = fmaf(res, res, acc);
       }
       xm = xc;
@@ -205,7 +221,8 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
     }
   } else if (r0 < r1) {
     const float aW = fabsf(cW.h), aE = fabsf(cE.h), aY = fabsf(cY.h), aD = fabsf(cD.h);
-    FF xm = split(raw(r0 - 1)), xc = split(raw(r0)), xp;
+    double xcd = raw(r0);   // row r's x in FP64 (written to the other buffer when the update is fused)
+    FF xm = split(raw(r0 - 1)), xc = split(xcd), xp;
     // one row of lookahead: the loads of row r + 2 (x) and r + 1 (b) are in flight while row r
     // is computed
     double xnext = raw(r0 + 1);
@@ -225,7 +242,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
         FF xo;
         xo.h = 0.f;
         xo.l = 0.f;
-        if (oin && MG_CK(L, p - i + io)) xo = split(x[p - i + io]);
+        if (oin && MG_CK(L, p - i + io)) xo = split(xat(p - i + io));
         if (lane == 0) xw = xo;
         else xe = xo;
       }
@@ -255,7 +272,10 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
           lo = (((bb.l - e1) + (e2 + e3)) + e4) + ((t1 + t2) + (t3 + t4));
         }
         const float res = s + lo;
-        if (MG_CK(L, p)) r32[p] = res;
+        if (MG_CK(L, p)) {
+          r32[p] = res;
+          if (upd) xout[p] = xcd;
+        }
         acc = fmaf(res, res, acc);
         // |b| + |A||x| from the leading parts: the scale of this node's float-float error
         const float tt = fmaf(aD, fabsf(xc.h),
@@ -265,6 +285,7 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
       }
       xm = xc;
       xc = xp;
+      xcd = xnext;
       xnext = xafter;
       bcur = bnext;
     }
@@ -280,8 +301,9 @@ __global__ void __launch_bounds__(FX *FY) k_defect_ff(Lev<double> L, const doubl
 // block 0: out_sq = sum of partials[0, n); block 1: out_t = sum of partials[half, half + n)
 // (fixed order, as the norm finish)
 __global__ void __launch_bounds__(1024) k_ff_finish(const double *__restrict__ partials, int n, int half,
-                                                    double *out_sq, double *out_t) {
+                                                    double *out_sq, double *out_t, int *par) {
   MG_PDL_WAIT();
+  if (par && blockIdx.x == 0 && threadIdx.x == 0) par[0] ^= 1;   // the fused update's buffer swap
   const double *src = partials + (blockIdx.x ? half : 0);
   double acc = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) acc += src[t];
@@ -297,9 +319,11 @@ __global__ void __launch_bounds__(1024) k_ff_finish(const double *__restrict__ p
 }
 }  // namespace
 
-bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
-                      double *partials, int nparts, double *out_sq, double *out_t, const int *use64) {
+bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, double *xa, double *xb, const double *b,
+                      float *r32, double *partials, int nparts, double *out_sq, double *out_t, const int *use64,
+                      const float *c32, int *par) {
   if (L.dim != 2 || (kind != K_CONST && kind != K_SEP)) return false;
+  if (c32 && (!xb || !par)) return false;
   const int nx = L.n0 - 2, rows = L.per ? L.n1 : L.n1 - 2;
   if (nx < 1 || rows < 1) return false;
   const int half = nparts / 2;   // the two sums' partials side by side
@@ -310,12 +334,28 @@ bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const do
   const long long gy_max = std::min<long long>(65535, half / gx);
   if ((rows + R - 1) / R > gy_max) R = (rows + gy_max - 1) / gy_max;
   const dim3 gr((unsigned)gx, (unsigned)((rows + R - 1) / R)), bl(FX, FY);
-  if (kind == K_CONST) k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
-  else k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, x, b, r32, partials, half, (int)R, use64);
+  if (kind == K_CONST)
+    k_defect_ff<K_CONST><<<gr, bl, 0, lc.s>>>(L, xa, xb, b, r32, partials, half, (int)R, use64, c32, par);
+  else
+    k_defect_ff<K_SEP><<<gr, bl, 0, lc.s>>>(L, xa, xb, b, r32, partials, half, (int)R, use64, c32, par);
   lc.done(__func__);
-  k_ff_finish<<<2, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), half, out_sq, out_t);
+  k_ff_finish<<<2, 1024, 0, lc.s>>>(partials, (int)(gr.x * gr.y), half, out_sq, out_t, c32 ? par : nullptr);
   lc.done(__func__);
   return true;
+}
+
+// After a loop of fused updates: bring the iterate into xa (copy from xb when *par is set).
+__global__ void k_x_settle(double *__restrict__ xa, const double *__restrict__ xb, long long n,
+                           const int *__restrict__ par) {
+  MG_PDL_WAIT();
+  if (*par == 0) return;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    xa[t] = xb[t];
+}
+void launch_x_settle(const Launch &lc, double *xa, const double *xb, long long n, int *par) {
+  k_x_settle<<<1216, 256, 0, lc.s>>>(xa, xb, n, par);
+  lc.done(__func__);
+  cudaMemsetAsync(par, 0, sizeof(int), lc.s);
 }
 
 }  // namespace mg

@@ -76,6 +76,7 @@ struct mg_ctx {
   bool mixed;
   // finest FP64 vectors of the mixed form
   double *x64 = nullptr, *b64 = nullptr;
+  double *x64b = nullptr;       // float-float contexts: the second buffer of the fused update (st[7]: current)
   // scratch for reductions and scalars
   double *partials = nullptr;
   double *scal = nullptr;       // [0] bsq, [1] sq, [2] relres, [3] scratch, [4] tol, [5] float-float error scale, [8] omega
@@ -337,6 +338,7 @@ static size_t layout(mg_ctx *c, char *ws) {
   size_t fine = (size_t)c->geo[c->L].count;
   if (c->mixed) {
     c->x64 = b.take<double>(fine);
+    if (c->ff) c->x64b = b.take<double>(fine);
     c->b64 = b.take<double>(fine);
     // FP64 scratch of the finest level for mg_apply and the gradient
     c->d64[c->L].u[0] = b.take<double>(fine);
@@ -1002,12 +1004,16 @@ static void emit_mixed_step(Sched &S, int transposed) {
     finest_to_zero<float>(S);
   }
   c->tracer.level = L;
-  launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
-  const bool ff = c->ff && launch_defect_ff(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials,
-                                            norm_parts_count(), c->scal + 1, c->scal + 5, c->st + 6);
-  if (!ff)
+  // float-float contexts: the update x += c fused into the outer defect (double-buffered iterate);
+  // otherwise the update, then the FP64 defect
+  const bool ff = c->ff && launch_defect_ff(S.lc, lev64(c, L), c->kind, c->x64, c->x64b, c->b64, c->d32[L].g,
+                                            c->partials, norm_parts_count(), c->scal + 1, c->scal + 5, c->st + 6,
+                                            c->d32[L].u[0], c->st + 7);
+  if (!ff) {
+    launch_ir_update(S.lc, lev64(c, L), c->x64, c->d32[L].u[0]);
     launch_defect64_to32(S.lc, lev64(c, L), c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
                          c->scal + 1);
+  }
   if (S.loop) launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4,
                               c->P.max_cycles, 0, ff ? c->scal + 5 : nullptr, kFFErr, kFFSwitch);
   else launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
@@ -1123,9 +1129,11 @@ static cudaError_t capture_loop(mg_ctx *c, cudaStream_t s, int transposed, long 
     }
   }
   if (e == cudaSuccess && c->mixed && c->ff) {
-    // the loop stopped on the float-float defect: the FP64 residual of the result, reported
+    // the loop stopped on the float-float defect: the iterate back into x64, and the FP64
+    // residual of the result, reported
     long long f0 = c->launches;
     Launch lc{s, &c->launches};
+    launch_x_settle(lc, c->x64, c->x64b, (long long)c->geo[c->L].count, c->st + 7);
     launch_defect64_to32(lc, lev64(c, c->L), c->kind, c->x64, c->b64, c->d32[c->L].g, c->partials,
                          norm_parts_count(), c->scal + 1);
     launch_final_check(lc, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4);
@@ -1339,6 +1347,7 @@ static mg_status setup_levels(mg_ctx *c) {
     size_t fine = (size_t)c->geo[L].count;
     for (double *p : {c->x64, c->b64, c->d64[L].u[0], c->d64[L].g, c->d64[L].r})
       CK(cudaMemsetAsync(p, 0, sizeof(double) * fine, c->stream));
+    if (c->x64b) CK(cudaMemsetAsync(c->x64b, 0, sizeof(double) * fine, c->stream));   // Dirichlet nodes stay 0
   }
   // coarsest grid: unknown index maps (built on the host: O(nodes of the coarsest grid))
   {
@@ -1792,7 +1801,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     CK(cudaMemcpyAsync(c->scal + 4, c->h_relres + 3, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
     if (c->P.flags & MG_FLAG_TEST_BOUNDS) launch_bounds_probe(lc, F64);
-    CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int), c->stream));   // float-float outer defects first
+    CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, c->stream));   // float-float defects first; iterate in x64
     double *xin = c->mixed ? c->x64 : c->d64[L].u[0];
     std::vector<double> hbuf((size_t)c->P.max_cycles + 2), hall;
     int sth[3] = {0, 0, 0};
@@ -1861,7 +1870,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
   if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
   if (c->P.flags & MG_FLAG_TEST_BOUNDS) launch_bounds_probe(lc, F64);
-  CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int), c->stream));   // float-float outer defects first
+  CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, c->stream));   // float-float defects first; iterate in x64
   bool ff64 = false;                                           // ... until the loop moves to FP64
   if (use_graph) {
     mg_status st = build_graph(c, transposed);
@@ -1902,6 +1911,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
       bool to64 =
           !exact && (err >= 0.5 * tol || rr <= tol + kFFSwitch * err || (it >= 2 && rr > 0.5 * hist.back()));
       if (exact) {
+        launch_x_settle(lc, c->x64, c->x64b, (long long)c->geo[L].count, c->st + 7);
         launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
                              c->scal + 1);
         launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
@@ -1932,7 +1942,8 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     }
     launched = true;
   }
-  // write back the solution
+  // write back the solution (after fused updates, the iterate back into x64 first)
+  if (c->mixed && c->ff) launch_x_settle(lc, c->x64, c->x64b, (long long)c->geo[L].count, c->st + 7);
   if (bsq == 0.0) {
     if (c->mixed) CK(cudaMemsetAsync(c->x64, 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
     else CK(cudaMemsetAsync(c->d64[L].u[0], 0, sizeof(double) * (size_t)c->geo[L].count, c->stream));
@@ -2365,7 +2376,7 @@ static mg_status batch_create(mg_ctx *const *cs, int count, const double *const 
     long long k0 = c->launches;
     e = cudaStreamWaitEvent(s, evs[count], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->scal + 4, bt->host, sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->st + 6, 0, sizeof(int), s);   // float-float outer defects first
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, s);   // float-float defects first
     if (e == cudaSuccess) {
       load_vec(c, lc, F64, b[i], c->mixed ? c->b64 : c->d64[c->L].g, false);
       load_vec(c, lc, F64, x[i], c->mixed ? c->x64 : c->d64[c->L].u[0], false);
@@ -2635,8 +2646,8 @@ mg_status mg_step_outer_defect(mg_ctx *c, const double *x, const double *b, doub
   Lev<double> F64 = lev64(c, L);
   pack_in(c, lc, F64, x, c->x64, 1);
   pack_in(c, lc, F64, b, c->b64, 1);
-  if (!(c->ff && launch_defect_ff(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
-                                  c->scal + 1, c->scal + 5, nullptr)))
+  if (!(c->ff && launch_defect_ff(lc, F64, c->kind, c->x64, nullptr, c->b64, c->d32[L].g, c->partials,
+                                  norm_parts_count(), c->scal + 1, c->scal + 5, nullptr)))
     launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
   unpack_lvl<float>(c, lc, L, c->d32[L].g, r);
   if (sq) CK(cudaMemcpyAsync(sq, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

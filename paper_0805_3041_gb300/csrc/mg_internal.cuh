@@ -473,8 +473,14 @@ void launch_ir_update(const Launch &lc, const Lev<double> &L, double *x, const f
 // separable coefficients; false, and nothing launched, otherwise).  out_t: the sum of squares of
 // |b| + |A||x| over the unknowns, the scale of the float-float error (0 in FP64 mode); use64:
 // device flag (null: never set) that makes the kernel evaluate the defect in FP64 instead
-bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, const double *x, const double *b, float *r32,
-                      double *partials, int nparts, double *out_sq, double *out_t, const int *use64);
+// c32 != null: the refinement update is fused in -- the iterate is double-buffered (xa, xb; *par
+// selects the current one), the defect is that of x + c, which is written into the other buffer,
+// and *par flips; c32 == null: the defect of xa (xb and par unused)
+bool launch_defect_ff(const Launch &lc, const Lev<double> &L, int kind, double *xa, double *xb, const double *b,
+                      float *r32, double *partials, int nparts, double *out_sq, double *out_t, const int *use64,
+                      const float *c32 = nullptr, int *par = nullptr);
+// the iterate back into xa after fused updates (a copy when *par is set), then *par = 0
+void launch_x_settle(const Launch &lc, double *xa, const double *xb, long long n, int *par);
 // after a loop stopped on the float-float defect: its FP64 relative residual into hist[st[0]], status 8
 // when it stopped as converged but the FP64 residual is above tol
 void launch_final_check(const Launch &lc, const double *sq, const double *bsq, double *hist, int *st,
