@@ -103,6 +103,38 @@ def test_yline_sweeps_match_oracle(case):
         assert rel(s.smooth(u, g, sweeps, order), o.smooth(u, g, sweeps, order)) <= tol
 
 
+FP32_CASES = SWEEP_CASES + [
+    (2, (129, 1024), True, inputs.SEPARABLE, "zebra_y", 1.0),     # 64 lines of 128 segments
+    (2, (257, 513), False, EDGE, "line_y", 0.7),                  # 255 lines of 64 segments, ragged
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES,
+                         ids=lambda c: f"{c[0]}d-{'x'.join(map(str, c[1]))}-{'per' if c[2] else 'dir'}-k{c[3]}-{c[4]}")
+def test_yline_fp32_sweeps_match_oracle(case):
+    """The single-precision y-line kernels (mixed contexts) against the oracle's FP64 sweep on the
+    same FP64 inputs.  Inputs and coefficients are rounded to FP32 and the line
+    solves run in FP32, so the bar is the FP64 one with u = 2^-24: max(1e-6, 8 kappa_G u)."""
+    dim, n, per, kind, sm, om = case
+    sp = make_spec(dim, n, per, kind, seed=sum(n) + 7 * kind)
+    if kind == EDGE:
+        p = orc.Problem(dim=sp.dim, n=sp.n, periodic_y=sp.periodic_y, kind=orc.EDGE, h=sp.h, ex=sp.ex, ey=sp.ey,
+                        ez=sp.ez)
+        o = orc.Oracle(p, levels=2, smoother=sm, omega=om, dense_max=4096)
+    else:
+        o = oracle_of(sp, 2, sm, om)
+    s = Solver(sp, levels=2, smoother=sm, omega=om, max_cycles=10, precision="mixed")
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(o.shape()) * o.unknown_mask()
+    g = rng.standard_normal(o.shape())
+    kappa = line_condition_bound(o)
+    tol = max(1e-6, 8.0 * kappa * 2.0 ** -24)
+    for sweeps, order in ((1, 0), (2, 1)):
+        e = rel(s.smooth(u, g, sweeps, order), o.smooth(u, g, sweeps, order))
+        print(f"{case}: kappa_G {kappa:.2e}, error {e:.2e} = {e / (kappa * 2.0 ** -24):.3f} kappa_G u32")
+        assert e <= tol
+
+
 SOLVE_CASES = [
     # dim, n, periodic, kind, levels, smoother
     (2, (17, 2049), False, inputs.SEPARABLE, 4, "zebra_y"),
