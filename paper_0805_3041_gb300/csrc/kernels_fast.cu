@@ -215,18 +215,18 @@ __global__ void __launch_bounds__(256) k_rb2d(Lev<T> L, const T *__restrict__ u,
 // `first`) relaxes the tile plus a ring of width 2 NS - 1 - h, so every node of the tile
 // ends with exactly the values NS successive sweeps give.  MODE applies to the first sweep
 // (1: zero iterate, 2: coarse-grid correction folded in), as in k_rb2d.
-template <typename T, int KIND, int MODE, int NS>
+template <typename T, int KIND, int MODE, int NS, int THY>
 __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__ u, const T *__restrict__ g,
                                                  T *__restrict__ out, T omega, int first, Lev<T> C,
                                                  const T *__restrict__ ec, T omega_corr) {
   MG_PDL_WAIT();
   constexpr int H = 2 * NS;                 // halo of the u tile
-  constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
+  constexpr int RW = THY + 2 * H;            // staged rows j0-H .. j0+THY+H-1
   constexpr int SXN = TX + 2 * H + 1;       // smem row stride
   __shared__ T su[RW * SXN];
   __shared__ T sg[RW * SXN];                // same indexing as su (outer ring unused)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * THY;
   // ---- stage u (with the optional fused correction) and g ----
   stage_tile<T, KIND, MODE, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, C, ec, omega_corr);
   __syncthreads();
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
 #pragma unroll 1
   for (int h = 0; h < 2 * NS; ++h) {
     const int col = (h & 1) ? 1 - first : first, w = 2 * NS - 1 - h;
-    for (int rr = warp; rr < TY + 2 * w; rr += 8) {
+    for (int rr = warp; rr < THY + 2 * w; rr += 8) {
       int j = j0 - w + rr;
       if (!unk_row(L, j)) continue;
       int jw = wrap_row(L, j);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
     __syncthreads();
   }
   // ---- write the tile's unknowns ----
-  for (int rr = warp; rr < TY; rr += 8) {
+  for (int rr = warp; rr < THY; rr += 8) {
     int j = j0 + rr;
     if (!owned_row(L, j)) continue;
     T *op = out + (long long)j * L.pitch;
@@ -270,26 +270,26 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
 // on the tile plus a ring of 2; the defect is formed on the tile plus a ring of 1 and
 // restricted to the tile's 32 x 8 coarse nodes (coarse node I sits at fine 2I).  Writes
 // the tile of u and the coarse g; the fine defect is never stored.
-template <typename T, int KIND, int MODE, int NS>
+template <typename T, int KIND, int MODE, int NS, int THY>
 __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T *__restrict__ u,
                                                     const T *__restrict__ g, T *__restrict__ out, T omega, int first,
                                                     T *__restrict__ gc) {
   MG_PDL_WAIT();
   constexpr int H = 2 * NS + 2;             // halo of the u tile
-  constexpr int RW = TY + 2 * H;            // staged rows j0-H .. j0+TY+H-1
+  constexpr int RW = THY + 2 * H;            // staged rows j0-H .. j0+THY+H-1
   constexpr int SXN = TX + 2 * H + 1;       // smem row stride
-  constexpr int DS = TX + 3;                // stride of the defect tile (rows j0-1 .. j0+TY)
+  constexpr int DS = TX + 3;                // stride of the defect tile (rows j0-1 .. j0+THY)
   __shared__ T su[RW * SXN];
   __shared__ T sg[RW * SXN];
-  __shared__ T sr[(TY + 2) * DS];
+  __shared__ T sr[(THY + 2) * DS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * THY;
   stage_tile<T, KIND, MODE == 1 ? 1 : 0, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, L, u, T(0));
   __syncthreads();
 #pragma unroll 1
   for (int h = 0; h < 2 * NS; ++h) {
     const int col = (h & 1) ? 1 - first : first, w = 2 * NS + 1 - h;
-    for (int rr = warp; rr < TY + 2 * w; rr += 8) {
+    for (int rr = warp; rr < THY + 2 * w; rr += 8) {
       int j = j0 - w + rr;
       if (!unk_row(L, j)) continue;
       int jw = wrap_row(L, j);
@@ -307,8 +307,8 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     }
     __syncthreads();
   }
-  // ---- defect on rows j0-1 .. j0+TY, columns i0-1 .. i0+TX ----
-  for (int rr = warp; rr < TY + 2; rr += 8) {
+  // ---- defect on rows j0-1 .. j0+THY, columns i0-1 .. i0+TX ----
+  for (int rr = warp; rr < THY + 2; rr += 8) {
     int j = j0 - 1 + rr;
     bool rowok = unk_row(L, j);
     int jw = wrap_row(L, j);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
   }
   __syncthreads();
   // ---- the tile of u, and the coarse g ----
-  for (int rr = warp; rr < TY; rr += 8) {
+  for (int rr = warp; rr < THY; rr += 8) {
     int j = j0 + rr;
     if (!owned_row(L, j)) continue;
     T *op = out + (long long)j * L.pitch;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     }
   }
   int I = (i0 >> 1) + lane, J = (j0 >> 1) + warp;
-  if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
+  if (warp < THY / 2 && I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
       MG_CK(C, (long long)J * C.pitch + I)) {
     const T *sp = sr + (2 * warp + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
     auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
@@ -451,13 +451,28 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
   lc.done(__func__);
 }
 
+// Tile height of the two-sweep tile kernels: on small grids each CTA's chain of staging, four
+// half-sweeps and stores is the launch's time, and a shorter tile shortens it: 4 rows up to 257^2,
+// 8 up to 513^2, 16 above
+template <typename T>
+static inline int tile_rows(const Lev<T> &L) {
+  const long long nn = (long long)L.n0 * L.n1;
+  return nn <= 66049 ? 4 : nn <= 263169 ? 8 : TY;
+}
+
 template <typename T>
 void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
                    int mode, const Lev<T> *C, const T *ec, T omega_corr) {
-  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + TY - 1) / TY);
+  const int th = tile_rows(L);
+  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + th - 1) / th);
   Lev<T> Cv = C ? *C : L;
   const T *e = ec ? ec : u;
-#define RB2_L(K, M) k_rb2d_ns<T, K, M, 2><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr)
+#define RB2_L(K, M)                                                                                      \
+  do {                                                                                                   \
+    if (th == 4) k_rb2d_ns<T, K, M, 2, 4><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr);  \
+    else if (th == 8) k_rb2d_ns<T, K, M, 2, 8><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr); \
+    else k_rb2d_ns<T, K, M, 2, TY><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr);        \
+  } while (0)
   if (kind == K_CONST) {
     if (mode == 0) RB2_L(K_CONST, 0); else if (mode == 1) RB2_L(K_CONST, 1); else RB2_L(K_CONST, 2);
   } else if (kind == K_SEP) {
@@ -476,8 +491,14 @@ void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
 template <typename T>
 void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int kind, const T *u, const T *g, T *out,
                       T omega, int first, int mode, T *gc) {
-  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + TY - 1) / TY);
-#define RB2D_L(K, M) k_rb2d_ns_dr<T, K, M, 2><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc)
+  const int th = tile_rows(L);
+  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + th - 1) / th);
+#define RB2D_L(K, M)                                                                                   \
+  do {                                                                                                 \
+    if (th == 4) k_rb2d_ns_dr<T, K, M, 2, 4><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);     \
+    else if (th == 8) k_rb2d_ns_dr<T, K, M, 2, 8><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc); \
+    else k_rb2d_ns_dr<T, K, M, 2, TY><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);           \
+  } while (0)
   if (kind == K_CONST) {
     if (mode == 1) RB2D_L(K_CONST, 1); else RB2D_L(K_CONST, 0);
   } else if (kind == K_SEP) {
