@@ -351,12 +351,15 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
       if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + H) * SXN + c + H];
     }
   }
-  int I = (i0 >> 1) + lane, J = (j0 >> 1) + warp;
-  if (warp < THY / 2 && I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
-      MG_CK(C, (long long)J * C.pitch + I)) {
-    const T *sp = sr + (2 * warp + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
-    auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
-    gc[(long long)J * C.pitch + I] = ((row3(sp - DS) + row3(sp + DS)) + T(2) * row3(sp)) * T(0.0625);
+  // the tile's THY / 2 coarse rows, one a warp at a time
+  for (int cy = warp; cy < THY / 2; cy += 8) {
+    const int I = (i0 >> 1) + lane, J = (j0 >> 1) + cy;
+    if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
+        MG_CK(C, (long long)J * C.pitch + I)) {
+      const T *sp = sr + (2 * cy + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
+      auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
+      gc[(long long)J * C.pitch + I] = ((row3(sp - DS) + row3(sp + DS)) + T(2) * row3(sp)) * T(0.0625);
+    }
   }
 }
 
@@ -453,11 +456,14 @@ void launch_rb2d(const Launch &lc, const Lev<T> &L, int kind, const T *u, const 
 
 // Tile height of the two-sweep tile kernels: on small grids each CTA's chain of staging, four
 // half-sweeps and stores is the launch's time, and a shorter tile shortens it: 4 rows up to 257^2,
-// 8 up to 513^2, 16 above
+// 8 up to 513^2; above, where the launch is bound by instructions, a taller tile recomputes less
+// of its halo: 32 rows in FP32, 16 in FP64 (within 48 KB of static shared memory)
+template <typename T>
+constexpr int kTileRowsBig = sizeof(T) == 8 ? 16 : 32;
 template <typename T>
 static inline int tile_rows(const Lev<T> &L) {
   const long long nn = (long long)L.n0 * L.n1;
-  return nn <= 66049 ? 4 : nn <= 263169 ? 8 : TY;
+  return nn <= 66049 ? 4 : nn <= 263169 ? 8 : kTileRowsBig<T>;
 }
 
 template <typename T>
@@ -471,7 +477,7 @@ void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, cons
   do {                                                                                                   \
     if (th == 4) k_rb2d_ns<T, K, M, 2, 4><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr);  \
     else if (th == 8) k_rb2d_ns<T, K, M, 2, 8><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr); \
-    else k_rb2d_ns<T, K, M, 2, TY><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr);        \
+    else k_rb2d_ns<T, K, M, 2, kTileRowsBig<T>><<<gr, 256, 0, lc.s>>>(L, u, g, out, omega, first, Cv, e, omega_corr); \
   } while (0)
   if (kind == K_CONST) {
     if (mode == 0) RB2_L(K_CONST, 0); else if (mode == 1) RB2_L(K_CONST, 1); else RB2_L(K_CONST, 2);
@@ -497,7 +503,7 @@ void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int ki
   do {                                                                                                 \
     if (th == 4) k_rb2d_ns_dr<T, K, M, 2, 4><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);     \
     else if (th == 8) k_rb2d_ns_dr<T, K, M, 2, 8><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc); \
-    else k_rb2d_ns_dr<T, K, M, 2, TY><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);           \
+    else k_rb2d_ns_dr<T, K, M, 2, kTileRowsBig<T>><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);  \
   } while (0)
   if (kind == K_CONST) {
     if (mode == 1) RB2D_L(K_CONST, 1); else RB2D_L(K_CONST, 0);
