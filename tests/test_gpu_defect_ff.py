@@ -104,16 +104,23 @@ def test_fp64_flag_keeps_the_fp64_defect():
 def test_mixed_solve_reports_the_fp64_residual(flags):
     """The loop stops on the float-float residual (below the tolerance by its error estimate) and reports the FP64
     one: 1e-10 in the oracle's residual, the same report to 1e-3, graph and kernel by kernel."""
-    from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH
+    from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH, FLAG_NO_PDL
     sp = inputs.anisotropic(n=2049, eps=0.3, seed_f=4)
     o = oracle_for(sp, 11)
-    for extra in (0, FLAG_NO_GRAPH):
+    xs = []
+    for extra in (0, FLAG_NO_GRAPH, FLAG_NO_PDL):
         s = Solver(sp, levels=11, smoother="rbgs", precision="mixed", max_cycles=40, flags=flags | extra)
         x, info = s.solve(sp.b, tol=1e-10)
-        rr = o.norm(o.defect(x.cpu().numpy(), sp.b)) / o.norm(sp.b)
+        xn = x.cpu().numpy()
+        xs.append((extra, xn, info["cycles"]))
+        rr = o.norm(o.defect(xn, sp.b)) / o.norm(sp.b)
         print(f"flags {flags | extra}: {info['cycles']} steps, report {info['relres']:.4e}, oracle {rr:.4e}")
         assert info["status"] == "MG_OK" and rr <= 1e-10
         assert abs(rr - info["relres"]) <= 1e-3 * rr
+    # the device loop, the host loop and ordinary graph edges run the same kernels on the same data,
+    # the fused update's buffer swaps included: the same iterate, bit for bit
+    for extra, xn, cyc in xs[1:]:
+        assert cyc == xs[0][2] and np.array_equal(xn, xs[0][1]), extra
 
 
 def test_strongly_coupled_lines_move_the_loop_to_fp64_defects():
