@@ -306,12 +306,15 @@ __device__ __forceinline__ void band_sweep(const Lev<float> L, const float *__re
       for (int e = 0; e < 4; ++e)
         if (K.act[e]) R.u[e] += omega_corr * ((sq[e >> 1] + sq[(e + 1) >> 1]) * 0.25f);
       if (edge) {
-        auto corr_at = [&](int i) {
-          const int q0 = (i >> 1) - cbase, q1 = ((i + 1) >> 1) - cbase;
-          return omega_corr * (((e0[q0] + e0[q1]) + (e1[q0] + e1[q1])) * 0.25f);
-        };
-        if (oact) R.out += corr_at(io);
-        if (io2 >= 1 && io2 <= L.n0 - 2) R.out2 += corr_at(io2);
+        // the outside columns, in the same form the neighbouring strip gives its own columns: lane 0's
+        // sw - 1 and sw - 2 take coarse positions q - 1 and q, lane 31's sw + 128 and sw + 129 take
+        // q + 2 and q + 3 (s = e0 + e1 at each)
+        const int qx = lane == 0 ? q - 1 : q + 3;
+        const float sx = e0[qx] + e1[qx];
+        const float c_out = lane == 0 ? sx + sq[0] : sq[2] + sq[2];
+        const float c_out2 = lane == 0 ? sx + sx : sq[2] + sx;
+        if (oact) R.out += omega_corr * (c_out * 0.25f);
+        if (io2 >= 1 && io2 <= L.n0 - 2) R.out2 += omega_corr * (c_out2 * 0.25f);
       }
     }
   };
