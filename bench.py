@@ -77,8 +77,8 @@ FP64_TFLOPS_MEASURED = 1.197
 # file has changed since, the counters no longer describe the kernel and traffic is reported
 # as null.
 FINEST_SWEEP_TRAFFIC = {"source": "paper_0805_3041_gb300/csrc/kernels_tma.cu",
-                        "sha256": "38f466be16cd4d7e1b0a7b0956e4d2e96289d755475977766fd38165363a5589",
-                        "bytes": 167.2e6,
+                        "sha256": "2fdb2ea6bf718c3e68d5fd34865b1d796ef638a43e16641caf66cff68263f44a",
+                        "bytes": 167.0e6,
                         "capture": "profiles/fcycle_mixed_rbgs_aniso4097.md"}
 
 
