@@ -193,8 +193,11 @@ __device__ __forceinline__ void lines_pcr(const Lev<T> &L, int dir, int zebra, i
 // FULL = false leaves out the line-smoother and adaptive-weight steps (programs of the point
 // smoothers with a fixed weight never hold them): a smaller kernel spends less of each step
 // fetching instructions.
+// The kernel always runs as one block on one SM: the bound of one resident block lets the compiler
+// give each thread the registers it needs (at its default choice the FP64 forms spilled to local
+// memory).
 template <typename T, int DIM, int KIND, bool FULL>
-__global__ void __launch_bounds__(csk_threads<T>()) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
+__global__ void __launch_bounds__(csk_threads<T>(), 1) k_coarse_cycle(const SLev<T> *__restrict__ levs, const int4 *__restrict__ prog,
                                                        int nops, int lc, const T *__restrict__ g_in,
                                                        const T *__restrict__ u_in, T *__restrict__ u_out,
                                                        const double *__restrict__ Ainv,

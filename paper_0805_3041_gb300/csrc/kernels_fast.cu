@@ -23,6 +23,14 @@ namespace mg {
 
 namespace {
 constexpr int TX = 64, TY = 16;   // RB output tile
+// Tile widths of the multi-sweep kernels: the widest half-sweep region (tile + 2 (2 NS - 1)
+// columns; + 2 (2 NS + 1) with the fused defect) is 64 columns, 32 nodes of one colour a row,
+// so every row of every half-sweep is one pass of a full warp.  Even, so that a tile's first
+// column has the parity of its index and coarse node I sits at fine column 2I.
+template <int NS>
+constexpr int kTxNs = 64 - 2 * (2 * NS - 1);
+template <int NS>
+constexpr int kTxNsDr = 64 - 2 * (2 * NS + 1);
 constexpr int SX = TX + 5;        // smem row stride of the u tile (halo 2 + pad)
 constexpr int CX = 32;            // coarse tile of the defect/restriction: CX x CY_OF(T)
 template <typename T>
@@ -220,15 +228,16 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
                                                  T *__restrict__ out, T omega, int first, Lev<T> C,
                                                  const T *__restrict__ ec, T omega_corr) {
   MG_PDL_WAIT();
+  constexpr int TXN = kTxNs<NS>;            // tile width
   constexpr int H = 2 * NS;                 // halo of the u tile
   constexpr int RW = THY + 2 * H;            // staged rows j0-H .. j0+THY+H-1
-  constexpr int SXN = TX + 2 * H + 1;       // smem row stride
+  constexpr int SXN = TXN + 2 * H + 1;       // smem row stride
   __shared__ T su[RW * SXN];
   __shared__ T sg[RW * SXN];                // same indexing as su (outer ring unused)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * THY;
+  const int i0 = blockIdx.x * TXN, j0 = blockIdx.y * THY;
   // ---- stage u (with the optional fused correction) and g ----
-  stage_tile<T, KIND, MODE, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, C, ec, omega_corr);
+  stage_tile<T, KIND, MODE, RW, TXN + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, C, ec, omega_corr);
   __syncthreads();
   // ---- 2 NS half-sweeps on shrinking regions ----
 #pragma unroll 1
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
       int ib = i0 - w;                               // first column of the region
       int par = (col + ib + j) & 1;                  // i = ib + 2q + par has colour col
       int r = j - (j0 - H);
-      for (int q = lane; 2 * q + par < TX + 2 * w; q += 32) {
+      for (int q = lane; 2 * q + par < TXN + 2 * w; q += 32) {
         int i = ib + 2 * q + par;
         if (i < 1 || i > L.n0 - 2) continue;
         int c = i - (i0 - H);
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns(Lev<T> L, const T *__restrict__
     int j = j0 + rr;
     if (!owned_row(L, j)) continue;
     T *op = out + (long long)j * L.pitch;
-    for (int c = lane; c < TX; c += 32) {
+    for (int c = lane; c < TXN; c += 32) {
       int i = i0 + c;
       if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + H) * SXN + c + H];
     }
@@ -275,16 +284,17 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
                                                     const T *__restrict__ g, T *__restrict__ out, T omega, int first,
                                                     T *__restrict__ gc) {
   MG_PDL_WAIT();
+  constexpr int TXN = kTxNsDr<NS>;          // tile width
   constexpr int H = 2 * NS + 2;             // halo of the u tile
   constexpr int RW = THY + 2 * H;            // staged rows j0-H .. j0+THY+H-1
-  constexpr int SXN = TX + 2 * H + 1;       // smem row stride
-  constexpr int DS = TX + 3;                // stride of the defect tile (rows j0-1 .. j0+THY)
+  constexpr int SXN = TXN + 2 * H + 1;       // smem row stride
+  constexpr int DS = TXN + 3;                // stride of the defect tile (rows j0-1 .. j0+THY)
   __shared__ T su[RW * SXN];
   __shared__ T sg[RW * SXN];
   __shared__ T sr[(THY + 2) * DS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * THY;
-  stage_tile<T, KIND, MODE == 1 ? 1 : 0, RW, TX + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, L, u, T(0));
+  const int i0 = blockIdx.x * TXN, j0 = blockIdx.y * THY;
+  stage_tile<T, KIND, MODE == 1 ? 1 : 0, RW, TXN + 2 * H, SXN>(L, u, g, i0, j0, H, su, sg, L, u, T(0));
   __syncthreads();
 #pragma unroll 1
   for (int h = 0; h < 2 * NS; ++h) {
@@ -298,7 +308,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
       int ib = i0 - w;
       int par = (col + ib + j) & 1;
       int r = j - (j0 - H);
-      for (int q = lane; 2 * q + par < TX + 2 * w; q += 32) {
+      for (int q = lane; 2 * q + par < TXN + 2 * w; q += 32) {
         int i = ib + 2 * q + par;
         if (i < 1 || i > L.n0 - 2) continue;
         int c = i - (i0 - H);
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     }
     __syncthreads();
   }
-  // ---- defect on rows j0-1 .. j0+THY, columns i0-1 .. i0+TX ----
+  // ---- defect on rows j0-1 .. j0+THY, columns i0-1 .. i0+TXN ----
   for (int rr = warp; rr < THY + 2; rr += 8) {
     int j = j0 - 1 + rr;
     bool rowok = unk_row(L, j);
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     long long rowoff = (long long)jw * L.pitch;
     long long dm = (long long)wrap_row(L, jw - 1) * L.pitch - rowoff;
     int r = j - (j0 - H);
-    for (int cc = lane; cc < TX + 2; cc += 32) {
+    for (int cc = lane; cc < TXN + 2; cc += 32) {
       int i = i0 - 1 + cc;
       T d = T(0);
       if (rowok && i >= 1 && i <= L.n0 - 2 && MG_CK(L, rowoff + i) && MG_CK(L, rowoff + i + dm)) {
@@ -346,15 +356,15 @@ __global__ void __launch_bounds__(256) k_rb2d_ns_dr(Lev<T> L, Lev<T> C, const T 
     int j = j0 + rr;
     if (!owned_row(L, j)) continue;
     T *op = out + (long long)j * L.pitch;
-    for (int c = lane; c < TX; c += 32) {
+    for (int c = lane; c < TXN; c += 32) {
       int i = i0 + c;
       if (i >= 1 && i <= L.n0 - 2 && MG_CK(L, (long long)j * L.pitch + i)) op[i] = su[(rr + H) * SXN + c + H];
     }
   }
-  // the tile's THY / 2 coarse rows, one a warp at a time
+  // the tile's THY / 2 coarse rows (TXN / 2 coarse columns), one a warp at a time
   for (int cy = warp; cy < THY / 2; cy += 8) {
     const int I = (i0 >> 1) + lane, J = (j0 >> 1) + cy;
-    if (I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
+    if (lane < TXN / 2 && I >= 1 && I <= C.n0 - 2 && (C.per ? J < C.n1 : (J >= 1 && J <= C.n1 - 2)) &&
         MG_CK(C, (long long)J * C.pitch + I)) {
       const T *sp = sr + (2 * cy + 1) * DS + (2 * lane + 1);   // fine (2I, 2J) in sr
       auto row3 = [&](const T *q) -> T { return (q[-1] + q[1]) + T(2) * q[0]; };
@@ -470,7 +480,7 @@ template <typename T>
 void launch_rb2d_2(const Launch &lc, const Lev<T> &L, int kind, const T *u, const T *g, T *out, T omega, int first,
                    int mode, const Lev<T> *C, const T *ec, T omega_corr) {
   const int th = tile_rows(L);
-  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + th - 1) / th);
+  dim3 gr((L.n0 + kTxNs<2> - 1) / kTxNs<2>, (L.n1 + th - 1) / th);
   Lev<T> Cv = C ? *C : L;
   const T *e = ec ? ec : u;
 #define RB2_L(K, M)                                                                                      \
@@ -498,7 +508,7 @@ template <typename T>
 void launch_rb2d_2_dr(const Launch &lc, const Lev<T> &L, const Lev<T> &C, int kind, const T *u, const T *g, T *out,
                       T omega, int first, int mode, T *gc) {
   const int th = tile_rows(L);
-  dim3 gr((L.n0 + TX - 1) / TX, (L.n1 + th - 1) / th);
+  dim3 gr((L.n0 + kTxNsDr<2> - 1) / kTxNsDr<2>, (L.n1 + th - 1) / th);
 #define RB2D_L(K, M)                                                                                   \
   do {                                                                                                 \
     if (th == 4) k_rb2d_ns_dr<T, K, M, 2, 4><<<gr, 256, 0, lc.s>>>(L, C, u, g, out, omega, first, gc);     \
