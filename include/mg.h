@@ -147,8 +147,8 @@ typedef struct {
   void *stream;           /* cudaStream_t; NULL = legacy default stream */
   unsigned flags;         /* MG_FLAG_* */
   int coarse_cut_nodes;   /* grids with at most this many nodes run inside the single-CTA coarse
-                             cycle (0: 5000 in single precision, 1200 in FP64; it must also fit in
-                             shared memory) -- a tuning knob of the autotuner */
+                             cycle (0: 5000 for 3-D single precision, 1200 otherwise; it must also
+                             fit in shared memory) -- a tuning knob of the autotuner */
   int sweep_rows;         /* rows one CTA marches through in the fused 2-D red-black sweeps of
                              single precision (0: from the occupancy) -- a tuning knob; results do
                              not depend on it */

@@ -35,7 +35,7 @@ SCHEDULES = [
 ]
 KNOBS = [
     dict(),
-    dict(coarse_cut_nodes=1200),
+    dict(coarse_cut_nodes=5000),
     dict(tile_nodes=-1),
     dict(tile_nodes=1 << 30),
     dict(sweep_rows=16),

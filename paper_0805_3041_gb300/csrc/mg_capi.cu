@@ -372,7 +372,10 @@ static size_t layout(mg_ctx *c, char *ws) {
     size_t es = c->mixed ? 4 : 8, total = 0;
     size_t arrays = 4 + (c->kind == K_CELL ? 2 : c->kind == K_EDGE ? (P.dim == 3 ? 4 : 3) : 0) +
                     (line_smoother(P) ? 1 : 0);
-    long long cap = c->mixed ? 5000 : 1200;   // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small
+    // FP64 runs at 2 FMA/clk/SM: keep the one-SM part small.  In 2-D the 65^2 level is faster on the
+    // tile and line kernels too (4097^2 RB-GS solve 7.21 against 7.24 ms, annulus GSADI 19.9 against
+    // 20.9); a 3-D 17^3 level (4913 nodes) stays in the one-CTA program
+    long long cap = (c->mixed && P.dim == 3) ? 5000 : 1200;
     if (P.coarse_cut_nodes > 0) cap = P.coarse_cut_nodes;
     for (int l = 1; l <= c->L; ++l) {
       long long nodes = (long long)c->geo[l].n[0] * c->geo[l].n[1] * c->geo[l].n[2];
@@ -1019,6 +1022,20 @@ static void emit_mixed_step(Sched &S, int transposed) {
   else launch_relres(S.lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
 }
 
+// The start vector's defect of a mixed solve, into the FP32 right-hand side of the first
+// refinement step: in float-float arithmetic where the loop's defects are (with its error
+// estimate, which the stopping test uses as in the loop: a start that passes it is confirmed by
+// the FP64 defect after the loop), else in FP64.  Returns whether the float-float form ran.
+static bool start_defect(mg_ctx *c, const Launch &lc) {
+  const int L = c->L;
+  const Lev<double> F64 = lev64(c, L);
+  if (c->ff && launch_defect_ff(lc, F64, c->kind, c->x64, nullptr, c->b64, c->d32[L].g, c->partials,
+                                norm_parts_count(), c->scal + 1, c->scal + 5, c->st + 6, nullptr, nullptr))
+    return true;
+  launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
+  return false;
+}
+
 // Initial check of a device-side solve: ||b||^2, the defect of the start vector, and the
 // loop condition (the packed b and x already sit in the finest-level buffers).
 static void emit_solve_init(Sched &S) {
@@ -1028,13 +1045,14 @@ static void emit_solve_init(Sched &S) {
   if (c->P.flags & MG_FLAG_FMG_START) emit_fmg_start(S);
   if (c->mixed) {
     launch_norm_parts<double>(S.lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
-    launch_defect64_to32(S.lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(),
-                         c->scal + 1);
-  } else {
-    launch_norm_parts<double>(S.lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
-    launch_defect_norm<double>(S.lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
-                               c->scal + 1);
+    const bool ff = start_defect(c, S.lc);
+    launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4, c->P.max_cycles, 1,
+                    ff ? c->scal + 5 : nullptr, kFFErr, kFFSwitch);
+    return;
   }
+  launch_norm_parts<double>(S.lc, F64, c->d64[L].g, c->partials, norm_parts_count(), c->scal + 0);
+  launch_defect_norm<double>(S.lc, F64, c->kind, c->d64[L].u[0], c->d64[L].g, c->partials, norm_parts_count(),
+                             c->scal + 1);
   launch_step_end(S.lc, S.loop_h, c->scal + 1, c->scal + 0, c->hist, c->st, c->scal + 4, c->P.max_cycles, 1);
 }
 
@@ -1847,6 +1865,7 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     }
     return result;
   }
+  bool ff_start = false;   // the start vector's defect in float-float (mixed solves)
   if (c->mixed) {
     if ((lst = load_vec(c, lc, F64, b, c->b64, host))) return lst;
     if ((lst = load_vec(c, lc, F64, x, c->x64, host))) return lst;
@@ -1855,7 +1874,8 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
       emit_fmg_start(S);
     }
     launch_norm_parts<double>(lc, F64, c->b64, c->partials, norm_parts_count(), c->scal + 0);
-    launch_defect64_to32(lc, F64, c->kind, c->x64, c->b64, c->d32[L].g, c->partials, norm_parts_count(), c->scal + 1);
+    CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, c->stream));   // float-float defects first; iterate in x64
+    ff_start = start_defect(c, lc);
   } else {
     if ((lst = load_vec(c, lc, F64, b, c->d64[L].g, host))) return lst;
     if ((lst = load_vec(c, lc, F64, x, c->d64[L].u[0], host))) return lst;
@@ -1870,8 +1890,8 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
   launch_relres(lc, c->scal + 1, c->scal + 0, nullptr, 0, c->scal + 2);
   if (c->P.flags & MG_FLAG_TEST_WAIT_TIMEOUT) CK(cudaMemsetAsync(c->st + 5, 1, sizeof(int), c->stream));
   if (c->P.flags & MG_FLAG_TEST_BOUNDS) launch_bounds_probe(lc, F64);
-  CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, c->stream));   // float-float defects first; iterate in x64
-  bool ff64 = false;                                           // ... until the loop moves to FP64
+  if (!c->mixed) CK(cudaMemsetAsync(c->st + 6, 0, sizeof(int) * 2, c->stream));
+  bool ff64 = false;   // float-float defects until the loop moves to FP64
   if (use_graph) {
     mg_status st = build_graph(c, transposed);
     if (st) return st;
@@ -1899,13 +1919,14 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
       result = MG_OK;
       break;
     }
-    // after a refinement step the float-float defect's residual is a stopping signal only: below
-    // tol by the defect's error estimate the FP64 residual is computed, decides and is reported;
+    // the float-float defect's residual (of the start vector, or after a refinement step) is a
+    // stopping signal only: below tol by the defect's error estimate the FP64 residual is
+    // computed, decides and is reported;
     // with an estimate of half of tol or more, within kFFSwitch times the estimate of tol, or
     // after a step that cut the residual by less than half, the loop moves to FP64 outer defects
     // (as the device loop does)
     bool exact = true;
-    if (c->mixed && c->ff && !ff64 && it > 0 && std::isfinite(rr)) {
+    if (c->mixed && c->ff && !ff64 && (it > 0 || ff_start) && std::isfinite(rr)) {
       const double err = kFFErr * std::sqrt(c->h_relres[5] / bsq);
       exact = rr + err <= tol;
       bool to64 =
