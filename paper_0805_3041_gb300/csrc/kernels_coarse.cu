@@ -85,7 +85,8 @@ __device__ __forceinline__ T interp_at(const Lev<T> &C, const T *ec, int i, int 
 }
 
 // Equations a thread holds in one line pass by cyclic reduction: lines x rows <= K * threads.  FP32
-// levels of the coarse kernel reach 5000 nodes, FP64 ones 1200 (and twice the registers a value).
+// levels of the coarse kernel reach 5000 nodes (the 3-D cut, and the larger of the two cuts the
+// autotuner tries in 2-D), FP64 ones 1200 (and twice the registers a value).
 template <typename T>
 __host__ __device__ constexpr int line_pcr_k() { return sizeof(T) == 4 ? 8 : 4; }
 
