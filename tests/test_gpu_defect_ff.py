@@ -123,6 +123,28 @@ def test_mixed_solve_reports_the_fp64_residual(flags):
         assert cyc == xs[0][2] and np.array_equal(xn, xs[0][1]), extra
 
 
+def test_start_vector_meeting_the_tolerance_takes_no_step():
+    """The start vector's defect is a float-float one too: a start that already meets the
+    tolerance by the defect's error estimate stops the loop before any refinement step, the FP64
+    residual after the loop confirms it and is reported, and the iterate comes back unchanged, in
+    the device loop and the host loop alike."""
+    from paper_0805_3041_gb300.binding import FLAG_NO_GRAPH
+    sp = inputs.anisotropic(n=513, eps=1.0, seed_f=6)
+    o = oracle_for(sp, 9)
+    xs, info0 = Solver(sp, levels=9, smoother="rbgs", precision="mixed", max_cycles=40).solve(sp.b, tol=1e-12)
+    assert info0["status"] == "MG_OK" and info0["cycles"] > 0
+    b = torch.from_numpy(sp.b).to(xs.device)
+    for extra in (0, FLAG_NO_GRAPH):
+        s = Solver(sp, levels=9, smoother="rbgs", precision="mixed", max_cycles=40, flags=extra)
+        x = xs.clone()
+        info = s.solve_into(b, x, tol=1e-10)
+        rr = o.norm(o.defect(x.cpu().numpy(), sp.b)) / o.norm(sp.b)
+        print(f"flags {extra}: {info['cycles']} steps, report {info['relres']:.4e}, oracle {rr:.4e}")
+        assert info["status"] == "MG_OK" and info["cycles"] == 0, (extra, info)
+        assert torch.equal(x, xs), extra
+        assert rr <= 1e-10 and abs(rr - info["relres"]) <= 1e-2 * rr
+
+
 def test_strongly_coupled_lines_move_the_loop_to_fp64_defects():
     """x-lines with eps = 1e3 (n = 2049 x 17): the float-float defect's error (~7e-11 ||b|| near
     the solution) is close to the tolerance, so the loop has to finish on FP64 defects; it then
