@@ -1921,10 +1921,9 @@ static mg_status run_solve(mg_ctx *c, const double *b, double *x, double tol, mg
     }
     // the float-float defect's residual (of the start vector, or after a refinement step) is a
     // stopping signal only: below tol by the defect's error estimate the FP64 residual is
-    // computed, decides and is reported;
-    // with an estimate of half of tol or more, within kFFSwitch times the estimate of tol, or
-    // after a step that cut the residual by less than half, the loop moves to FP64 outer defects
-    // (as the device loop does)
+    // computed, decides and is reported; with an estimate of half of tol or more, within
+    // kFFSwitch times the estimate of tol, or after a step that cut the residual by less than
+    // half, the loop moves to FP64 outer defects (as the device loop does)
     bool exact = true;
     if (c->mixed && c->ff && !ff64 && (it > 0 || ff_start) && std::isfinite(rr)) {
       const double err = kFFErr * std::sqrt(c->h_relres[5] / bsq);
