@@ -534,28 +534,47 @@ void launch_to_float(const Launch &lc, const double *src, float *dst, long long 
 // ---------------------------------------------------------------------------------------
 // layout conversions (compact caller arrays <-> padded level arrays)
 // ---------------------------------------------------------------------------------------
+// A block of 128 threads copies PACK_ELEMS * 128 consecutive nodes of one row, each thread
+// PACK_ELEMS of them 128 apart: every load of a thread is issued before its stores.
+constexpr int PACK_ELEMS = 4;
 template <typename T>
 __global__ void k_pack(Lev<T> L, const double *__restrict__ src, T *__restrict__ dst, int zero_boundary) {
   MG_PDL_WAIT();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y, k = blockIdx.z;
-  if (i >= L.n0) return;
-  long long s = ((long long)k * L.n1 + j) * L.n0 + i;
-  long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
-  if (!MG_CK(L, d)) return;
-  bool bnd = (i == 0 || i == L.n0 - 1) || (!L.per && (j == 0 || j == L.n1 - 1)) ||
-             (L.dim == 3 && (k == 0 || k == L.n2 - 1));
-  dst[d] = (zero_boundary && bnd) ? T(0) : (T)src[s];
+  const int i0 = blockIdx.x * (PACK_ELEMS * 128) + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const long long s0 = ((long long)k * L.n1 + j) * L.n0, d0 = (long long)k * L.plane + (long long)j * L.pitch;
+  const bool brow = (!L.per && (j == 0 || j == L.n1 - 1)) || (L.dim == 3 && (k == 0 || k == L.n2 - 1));
+  double v[PACK_ELEMS];
+#pragma unroll
+  for (int q = 0; q < PACK_ELEMS; ++q) {
+    const int i = i0 + 128 * q;
+    v[q] = i < L.n0 ? src[s0 + i] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < PACK_ELEMS; ++q) {
+    const int i = i0 + 128 * q;
+    if (i >= L.n0 || !MG_CK(L, d0 + i)) continue;
+    const bool bnd = brow || i == 0 || i == L.n0 - 1;
+    dst[d0 + i] = (zero_boundary && bnd) ? T(0) : (T)v[q];
+  }
 }
 template <typename T>
 __global__ void k_unpack(Lev<T> L, const T *__restrict__ src, double *__restrict__ dst, double scale) {
   MG_PDL_WAIT();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y, k = blockIdx.z;
-  if (i >= L.n0) return;
-  const long long d = (long long)k * L.plane + (long long)j * L.pitch + i;
-  if (!MG_CK(L, d)) return;
-  dst[((long long)k * L.n1 + j) * L.n0 + i] = scale * (double)src[d];
+  const int i0 = blockIdx.x * (PACK_ELEMS * 128) + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const long long s0 = (long long)k * L.plane + (long long)j * L.pitch, d0 = ((long long)k * L.n1 + j) * L.n0;
+  T v[PACK_ELEMS];
+#pragma unroll
+  for (int q = 0; q < PACK_ELEMS; ++q) {
+    const int i = i0 + 128 * q;
+    v[q] = (i < L.n0 && MG_CK(L, s0 + i)) ? src[s0 + i] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < PACK_ELEMS; ++q) {
+    const int i = i0 + 128 * q;
+    if (i < L.n0 && MG_CK(L, s0 + i)) dst[d0 + i] = scale * (double)v[q];
+  }
 }
 template <typename T>
 __global__ void k_zero_boundary(Lev<T> L, T *__restrict__ dst) {
@@ -585,13 +604,13 @@ __global__ void k_zero_level(Lev<T> L, T *__restrict__ dst) {
 
 template <typename T>
 void launch_pack(const Launch &lc, const Lev<T> &L, const double *src, T *dst, int zero_boundary) {
-  dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
+  dim3 gr((L.n0 + PACK_ELEMS * 128 - 1) / (PACK_ELEMS * 128), L.n1, L.dim == 3 ? L.n2 : 1);
   k_pack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, zero_boundary);
   lc.done(__func__);
 }
 template <typename T>
 void launch_unpack(const Launch &lc, const Lev<T> &L, const T *src, double *dst, double scale) {
-  dim3 gr((L.n0 + 127) / 128, L.n1, L.dim == 3 ? L.n2 : 1);
+  dim3 gr((L.n0 + PACK_ELEMS * 128 - 1) / (PACK_ELEMS * 128), L.n1, L.dim == 3 ? L.n2 : 1);
   k_unpack<T><<<gr, 128, 0, lc.s>>>(L, src, dst, scale);
   lc.done(__func__);
 }
