@@ -105,9 +105,10 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
                                        MG_EINVAL.  The single-CTA coarse cycle is not used */
 #define MG_FLAG_FP64_DEFECT     512u /* MG_MIXED: keep the refinement loop's defect r = b - A x in FP64.
                                        By default, in 2-D with constant or separable coefficients, that
-                                       defect is evaluated in float-float arithmetic (each FP64 operand
-                                       split into two floats, error-free FP32 sums and products; about
-                                       2^-46 of |b| + |A||x| in error instead of 2^-53).  The kernel
+                                       defect (the start vector's included) is evaluated in float-float
+                                       arithmetic (each FP64 operand split into two floats, error-free
+                                       FP32 sums and products; about 2^-46 of |b| + |A||x| in error
+                                       instead of 2^-53).  The kernel
                                        also sums (|b| + |A||x|)^2; the loop stops on that residual only
                                        when it is below the tolerance by the error estimate E = 2^-46
                                        times the root of that sum, moves to FP64 defects when E is half
