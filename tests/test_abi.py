@@ -121,3 +121,26 @@ def test_binding_structs_match_the_header_layout(tmp_path):
             assert (f.offset, f.size) == (int(off), int(size)), (cname, fname)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_every_header_function_is_documented():
+    """Each entry point of include/mg.h follows a comment block (a group of declarations, or the
+    constants that belong to it, may share one)."""
+    lines = open(os.path.join(ROOT, "include", "mg.h")).read().split("\n")
+    decl = re.compile(r"^\s*(?:[A-Za-z_][A-Za-z0-9_]*\s+)+\*?\s*(mg_[a-z_0-9]+)\s*\(")
+    found = 0
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        found += 1
+        j = i - 1
+        while j >= 0:
+            t = lines[j].strip()
+            cont = lines[j].startswith(" ") and t.endswith((",", ");"))   # a declaration's later lines
+            if not t or decl.match(lines[j]) or cont or t.startswith(("#define", "typedef")):
+                j -= 1   # blank lines and the group's declarations, constants and types
+                continue
+            break
+        assert j >= 0 and lines[j].strip().endswith("*/"), m.group(1)
+    assert found == len(declared_functions())
